@@ -1,0 +1,360 @@
+/*
+ * moco oracle: a plain, slow, obviously correct CPU statement of the
+ * translation search of "moco: Fast Motion Correction for Calcium Imaging"
+ * (Dubbs, Guevara, Peterka, Yuste; arXiv 1506.06039).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product library links, loads or
+ * calls this file; only the tests, the package's smoke check and the
+ * benchmark's CPU-baseline leg do. It shares no code, header, table or helper
+ * with the CUDA path.
+ *
+ * Everything here follows the definitions of Section 2 literally:
+ *   - f_{s,t} = (1 / Area(D_{s,t})) * sum_{(i,j) in D_{s,t}} (a[i+s][j+t] - b[i][j])^2,
+ *     D_{s,t} = {(i,j) : 0 <= i < m, 0 <= j < n, 0 <= i+s < m, 0 <= j+t < n}
+ *     (the paper's 1-based set, written 0-based), for every max(|s|,|t|) < w.
+ *     The sum is formed in exact int64 by brute force over D: no summed-area
+ *     tables, no FFT (those are the paper's speed-ups; they compute the same f).
+ *   - Downsampling (Section 2, "downsampled if larger than 256x256"; Section 3,
+ *     "we downsample once"): one level when max(m, n) > 256, a 2x2 box. The
+ *     oracle carries the exact integer 4-sum; costs are reported in box-mean
+ *     units (4-sum cost / 16).
+ *   - Upsampling (Section 2): the coarse optimum (s,t) is doubled and f is
+ *     evaluated at full resolution for (2s+u, 2t+v), u, v in {-1, 0, 1}; the
+ *     minimum is kept.
+ *   - Ties (the paper is silent): among equal f the shift with the smallest
+ *     |s| + |t| wins, then the smallest s, then the smallest t. Costs are
+ *     compared as exact rationals S1 * A2 vs S2 * A1 in 128-bit integers.
+ *   - Soft-min and its gradient (not in the paper; the differentiable form):
+ *     L_f = -tau_f log sum_{s,t} exp(-f_{s,t} / tau_f), tau_f given, in FP64;
+ *     the gradient is the chain rule through Section 2's f.
+ *
+ * Build: gcc -O2 -fopenmp -shared -fPIC moco_oracle.c -o liboracle.so
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef __int128 i128;
+
+/* ---- Section 2: D_{s,t} and Area(D_{s,t}) --------------------------------- */
+
+/* Number of pairs in D_{s,t}: rows i with 0 <= i, i+s < m, times columns. */
+int64_t oracle_area(int m, int n, int s, int t) {
+    int64_t rows = 0, cols = 0;
+    for (int i = 0; i < m; ++i)
+        if (i + s >= 0 && i + s < m) ++rows;
+    for (int j = 0; j < n; ++j)
+        if (j + t >= 0 && j + t < n) ++cols;
+    return rows * cols;
+}
+
+/* Area(D_{s,t}) * f_{s,t} for one shift, exact, by brute force over D. */
+int64_t oracle_ssd_one(const int32_t *a, const int32_t *b, int m, int n, int s, int t) {
+    int64_t S = 0;
+    for (int i = 0; i < m; ++i) {
+        if (i + s < 0 || i + s >= m) continue;
+        for (int j = 0; j < n; ++j) {
+            if (j + t < 0 || j + t >= n) continue;
+            int64_t d = (int64_t)a[(int64_t)(i + s) * n + (j + t)] - (int64_t)b[(int64_t)i * n + j];
+            S += d * d;
+        }
+    }
+    return S;
+}
+
+/* All (2w-1)^2 shifts; S[(s+w-1)*(2w-1) + (t+w-1)]. */
+void oracle_ssd_all(const int32_t *a, const int32_t *b, int m, int n, int w, int64_t *S) {
+    int W = 2 * w - 1;
+    for (int s = -(w - 1); s <= w - 1; ++s)
+        for (int t = -(w - 1); t <= w - 1; ++t)
+            S[(s + w - 1) * W + (t + w - 1)] = oracle_ssd_one(a, b, m, n, s, t);
+}
+
+/* ---- Downsampling: one 2x2 box level (exact integer 4-sum) ---------------- */
+
+void oracle_downsample(const uint16_t *a, int m, int n, int32_t *out) {
+    int mc = m / 2, nc = n / 2;
+    for (int i = 0; i < mc; ++i)
+        for (int j = 0; j < nc; ++j)
+            out[(int64_t)i * nc + j] = (int32_t)a[(int64_t)(2 * i) * n + 2 * j] +
+                                       (int32_t)a[(int64_t)(2 * i + 1) * n + 2 * j] +
+                                       (int32_t)a[(int64_t)(2 * i) * n + 2 * j + 1] +
+                                       (int32_t)a[(int64_t)(2 * i + 1) * n + 2 * j + 1];
+}
+
+static void widen(const uint16_t *a, int64_t count, int32_t *out) {
+    for (int64_t k = 0; k < count; ++k) out[k] = (int32_t)a[k];
+}
+
+/* Paper rule for the number of levels: one iff the image is larger than 256x256. */
+int oracle_levels(int m, int n) { return (m > 256 || n > 256) ? 1 : 0; }
+
+/* ---- Comparison with the tie-break --------------------------------------- */
+
+/* Returns 1 when candidate 1 beats candidate 2: smaller S/A, then smaller
+ * |s|+|t|, then smaller s, then smaller t. */
+static int better(int64_t S1, int64_t A1, int s1, int t1, int64_t S2, int64_t A2, int s2, int t2) {
+    i128 l = (i128)S1 * (i128)A2, r = (i128)S2 * (i128)A1;
+    if (l != r) return l < r;
+    int k1 = abs(s1) + abs(t1), k2 = abs(s2) + abs(t2);
+    if (k1 != k2) return k1 < k2;
+    if (s1 != s2) return s1 < s2;
+    return t1 < t2;
+}
+
+/* ---- Align one frame ------------------------------------------------------ */
+
+typedef struct {
+    int32_t s, t;        /* final shift */
+    int32_t sc, tc;      /* optimum on the searched (coarse) grid */
+    double fbest;        /* coarse f at the optimum, box-mean units */
+    double margin;       /* (f2 - f1) / f1 on the searched grid */
+    double ffinal;       /* full-resolution f at the final shift (= fbest w/o levels) */
+} oracle_result;
+
+/* a, b are the full-resolution frame and template (uint16, m x n). */
+static void align_one(const uint16_t *a, const uint16_t *b, const int32_t *bc, int m, int n,
+                      int w, int levels, int32_t *ac, int32_t *afull, int32_t *bfull,
+                      int64_t *Sbuf, oracle_result *res) {
+    int mc = levels ? m / 2 : m, nc = levels ? n / 2 : n;
+    const int32_t *A, *B;
+    widen(a, (int64_t)m * n, afull);
+    widen(b, (int64_t)m * n, bfull);
+    if (levels) {
+        oracle_downsample(a, m, n, ac);
+        A = ac;
+        B = bc;
+    } else {
+        A = afull;
+        B = bfull;
+    }
+    double unit = levels ? 16.0 : 1.0;
+    int W = 2 * w - 1;
+    /* Coarse exhaustive search over max(|s|,|t|) < w. */
+    oracle_ssd_all(A, B, mc, nc, w, Sbuf);
+    int bs = 0, bt = 0;
+    int64_t bS = -1, bA = 1;
+    for (int s = -(w - 1); s <= w - 1; ++s)
+        for (int t = -(w - 1); t <= w - 1; ++t) {
+            int64_t S = Sbuf[(s + w - 1) * W + (t + w - 1)];
+            int64_t Ar = oracle_area(mc, nc, s, t);
+            if (bS < 0 || better(S, Ar, s, t, bS, bA, bs, bt)) {
+                bS = S; bA = Ar; bs = s; bt = t;
+            }
+        }
+    /* Second-best value over every other shift, for the margin. */
+    double f1 = (double)bS / (double)bA / unit, f2 = INFINITY;
+    for (int s = -(w - 1); s <= w - 1; ++s)
+        for (int t = -(w - 1); t <= w - 1; ++t) {
+            if (s == bs && t == bt) continue;
+            double f = (double)Sbuf[(s + w - 1) * W + (t + w - 1)] / (double)oracle_area(mc, nc, s, t) / unit;
+            if (f < f2) f2 = f;
+        }
+    res->sc = bs; res->tc = bt;
+    res->fbest = f1;
+    if (f1 > 0) res->margin = (f2 - f1) / f1;
+    else res->margin = (f2 > 0) ? INFINITY : 0.0;
+    if (!levels) {
+        res->s = bs; res->t = bt; res->ffinal = f1;
+        return;
+    }
+    /* Upsampling: double, then the 3x3 local search on the full grid. */
+    int fs = 0, ft = 0;
+    int64_t fS = -1, fA = 1;
+    for (int u = -1; u <= 1; ++u)
+        for (int v = -1; v <= 1; ++v) {
+            int s = 2 * bs + u, t = 2 * bt + v;
+            int64_t S = oracle_ssd_one(afull, bfull, m, n, s, t);
+            int64_t Ar = oracle_area(m, n, s, t);
+            if (fS < 0 || better(S, Ar, s, t, fS, fA, fs, ft)) {
+                fS = S; fA = Ar; fs = s; ft = t;
+            }
+        }
+    res->s = fs; res->t = ft;
+    res->ffinal = (double)fS / (double)fA;
+}
+
+/* Align T frames (uint16, T x m x n) against the template (uint16, m x n).
+ * levels: -1 = the paper's rule, else 0 or 1. Outputs (each nullable except
+ * shifts): shifts[T][2] final, coarse[T][2], fbest[T], margin[T], ffinal[T].
+ * nthreads <= 0 uses the OpenMP default. Returns 0, or -1 on bad arguments. */
+int oracle_align(const uint16_t *frames, int64_t T, const uint16_t *tmpl, int m, int n, int w,
+                 int levels, int32_t *shifts, int32_t *coarse, double *fbest, double *margin,
+                 double *ffinal, int nthreads) {
+    if (levels < 0) levels = oracle_levels(m, n);
+    int mc = levels ? m / 2 : m, nc = levels ? n / 2 : n;
+    if (w < 1 || 2 * w - 1 > mc || 2 * w - 1 > nc || levels > 1) return -1;
+    int32_t *bc = (int32_t *)malloc(sizeof(int32_t) * (size_t)mc * nc);
+    if (levels) oracle_downsample(tmpl, m, n, bc);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    int failed = 0;
+#pragma omp parallel
+    {
+        int32_t *ac = (int32_t *)malloc(sizeof(int32_t) * (size_t)mc * nc);
+        int32_t *af = (int32_t *)malloc(sizeof(int32_t) * (size_t)m * n);
+        int32_t *bf = (int32_t *)malloc(sizeof(int32_t) * (size_t)m * n);
+        int64_t *Sb = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * w - 1) * (2 * w - 1));
+        if (!ac || !af || !bf || !Sb) {
+#pragma omp atomic write
+            failed = 1;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t f = 0; f < T; ++f) {
+                oracle_result r;
+                align_one(frames + f * (int64_t)m * n, tmpl, bc, m, n, w, levels, ac, af, bf, Sb, &r);
+                shifts[2 * f] = r.s; shifts[2 * f + 1] = r.t;
+                if (coarse) { coarse[2 * f] = r.sc; coarse[2 * f + 1] = r.tc; }
+                if (fbest) fbest[f] = r.fbest;
+                if (margin) margin[f] = r.margin;
+                if (ffinal) ffinal[f] = r.ffinal;
+            }
+        }
+        free(ac); free(af); free(bf); free(Sb);
+    }
+    free(bc);
+    return failed ? -2 : 0;
+}
+
+/* The searched-grid cost surface of T frames in FP64, box-mean units:
+ * cost[f][(s+w-1)*(2w-1) + (t+w-1)] = f_{s,t}. Optional exact sums S (int64). */
+int oracle_cost_surface(const uint16_t *frames, int64_t T, const uint16_t *tmpl, int m, int n,
+                        int w, int levels, double *cost, int64_t *S_out, int nthreads) {
+    if (levels < 0) levels = oracle_levels(m, n);
+    int mc = levels ? m / 2 : m, nc = levels ? n / 2 : n;
+    if (w < 1 || 2 * w - 1 > mc || 2 * w - 1 > nc || levels > 1) return -1;
+    int W = 2 * w - 1;
+    double unit = levels ? 16.0 : 1.0;
+    int32_t *bc = (int32_t *)malloc(sizeof(int32_t) * (size_t)mc * nc);
+    if (levels) oracle_downsample(tmpl, m, n, bc);
+    else widen(tmpl, (int64_t)m * n, bc);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel
+    {
+        int32_t *ac = (int32_t *)malloc(sizeof(int32_t) * (size_t)mc * nc);
+        int64_t *S = (int64_t *)malloc(sizeof(int64_t) * (size_t)W * W);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t f = 0; f < T; ++f) {
+            const uint16_t *a = frames + f * (int64_t)m * n;
+            if (levels) oracle_downsample(a, m, n, ac);
+            else widen(a, (int64_t)m * n, ac);
+            oracle_ssd_all(ac, bc, mc, nc, w, S);
+            for (int s = -(w - 1); s <= w - 1; ++s)
+                for (int t = -(w - 1); t <= w - 1; ++t) {
+                    int k = (s + w - 1) * W + (t + w - 1);
+                    if (cost) cost[f * (int64_t)W * W + k] = (double)S[k] / (double)oracle_area(mc, nc, s, t) / unit;
+                    if (S_out) S_out[f * (int64_t)W * W + k] = S[k];
+                }
+        }
+        free(ac); free(S);
+    }
+    free(bc);
+    return 0;
+}
+
+/* ---- Real-valued form (FP64): cost, soft-min loss and its gradient -------- */
+
+/* f_{s,t} in FP64 for real images a, b (m x n), all (2w-1)^2 shifts. */
+void oracle_cost_f64(const double *a, const double *b, int m, int n, int w, double *cost) {
+    int W = 2 * w - 1;
+    for (int s = -(w - 1); s <= w - 1; ++s)
+        for (int t = -(w - 1); t <= w - 1; ++t) {
+            double S = 0.0;
+            for (int i = 0; i < m; ++i) {
+                if (i + s < 0 || i + s >= m) continue;
+                for (int j = 0; j < n; ++j) {
+                    if (j + t < 0 || j + t >= n) continue;
+                    double d = a[(int64_t)(i + s) * n + (j + t)] - b[(int64_t)i * n + j];
+                    S += d * d;
+                }
+            }
+            cost[(s + w - 1) * W + (t + w - 1)] = S / (double)oracle_area(m, n, s, t);
+        }
+}
+
+static int cmp_double(const void *x, const void *y) {
+    double a = *(const double *)x, b = *(const double *)y;
+    return (a > b) - (a < b);
+}
+
+/* Temperature of one frame: scale * the median of its (2w-1)^2 costs (an odd
+ * count, so the exact middle element). */
+double oracle_median(const double *cost, int count) {
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)count);
+    memcpy(tmp, cost, sizeof(double) * (size_t)count);
+    qsort(tmp, (size_t)count, sizeof(double), cmp_double);
+    double med = tmp[count / 2];
+    free(tmp);
+    return med;
+}
+
+/* Soft-min loss over frames: L = sum_f -tau_f log sum_{s,t} exp(-f_{s,t}/tau_f).
+ * frames: T x m x n (FP64), tmpl: m x n (FP64), tau[T] given (held constant).
+ * If grad_tmpl (m x n) / grad_frames (T x m x n) are non-null they receive
+ * dL/db and dL/da (overwritten). Per-frame losses go to loss_f if non-null. */
+double oracle_softmin_loss(const double *frames, int64_t T, const double *tmpl, int m, int n,
+                           int w, const double *tau, double *loss_f, double *grad_tmpl,
+                           double *grad_frames, int nthreads) {
+    int W = 2 * w - 1, K = W * W;
+    double total = 0.0;
+    if (grad_tmpl) memset(grad_tmpl, 0, sizeof(double) * (size_t)m * n);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel
+    {
+        double *cost = (double *)malloc(sizeof(double) * (size_t)K);
+        double *gb = grad_tmpl ? (double *)calloc((size_t)m * n, sizeof(double)) : NULL;
+        double local = 0.0;
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t f = 0; f < T; ++f) {
+            const double *a = frames + f * (int64_t)m * n;
+            oracle_cost_f64(a, tmpl, m, n, w, cost);
+            double tf = tau[f];
+            /* Stable log-sum-exp around the minimum cost. */
+            double fmin = cost[0];
+            for (int k = 1; k < K; ++k) if (cost[k] < fmin) fmin = cost[k];
+            double Z = 0.0;
+            for (int k = 0; k < K; ++k) Z += exp(-(cost[k] - fmin) / tf);
+            double L = fmin - tf * log(Z);
+            local += L;
+            if (loss_f) loss_f[f] = L;
+            if (!gb && !grad_frames) continue;
+            double *ga = grad_frames ? grad_frames + f * (int64_t)m * n : NULL;
+            if (ga) memset(ga, 0, sizeof(double) * (size_t)m * n);
+            /* dL/df_{s,t} = softmax weight; df/db and df/da from Section 2's f. */
+            for (int s = -(w - 1); s <= w - 1; ++s)
+                for (int t = -(w - 1); t <= w - 1; ++t) {
+                    int k = (s + w - 1) * W + (t + w - 1);
+                    double g = exp(-(cost[k] - fmin) / tf) / Z;
+                    double q = g / (double)oracle_area(m, n, s, t);
+                    for (int i = 0; i < m; ++i) {
+                        if (i + s < 0 || i + s >= m) continue;
+                        for (int j = 0; j < n; ++j) {
+                            if (j + t < 0 || j + t >= n) continue;
+                            int64_t ia = (int64_t)(i + s) * n + (j + t), ib = (int64_t)i * n + j;
+                            double d = a[ia] - tmpl[ib];
+                            if (gb) gb[ib] += -2.0 * q * d;
+                            if (ga) ga[ia] += 2.0 * q * d;
+                        }
+                    }
+                }
+        }
+#pragma omp critical
+        {
+            total += local;
+            if (gb)
+                for (int64_t p = 0; p < (int64_t)m * n; ++p) grad_tmpl[p] += gb[p];
+        }
+        free(cost);
+        free(gb);
+    }
+    return total;
+}
