@@ -1,0 +1,340 @@
+"""Benchmark: frames/s aligned on the standard workload (2000 frames of
+512x512 uint16, one 2x2 box level to 256x256, window w = 32, exhaustive
+search then the 3x3 jitter at full resolution), synthetic calcium-like data.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl moco|reference]
+
+One step = one full alignment of the whole stack (every kernel of the path)
+with the frames already resident in device memory; the stack (1 GiB) is
+larger than L2, so no flush is needed between steps. Prints one JSON line.
+Under torchrun each rank aligns its own stack (weak scaling, no collective on
+the data path); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "frames/s aligned (256², w=32, full search+upsample), plain vs chosen form"
+UNIT = "frames/s"
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="moco", choices=["moco", "reference"])
+    p.add_argument("--workload", default="std512")
+    p.add_argument("--form", default="auto", choices=["auto", "fft", "direct"])
+    p.add_argument("--group", type=int, default=0, help="frames per internal batch (0 = plan's choice)")
+    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_config(wl, form):
+    return {
+        "workload": "%s: %d frames of %dx%d uint16, 2x2 box to %dx%d, w=%d on the searched grid, "
+                    "3x3 jitter at full resolution" % (wl.name, wl.T, wl.m, wl.n, wl.m // 2, wl.n // 2, wl.w),
+        "frames": wl.T, "m": wl.m, "n": wl.n, "w": wl.w, "blobs": wl.nblobs,
+        "shift_range": wl.shift_max, "template": "rounded mean of the first 100 frames",
+        "form": form, "l2": "inputs (1 GiB of frames) larger than L2; no flush",
+    }
+
+
+# ---- clocks during the timed region ------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), hw=parts[5], hwt=parts[6],
+                                 swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        reasons = []
+        for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                          ("pcap", "sw_power_cap")):
+            if any(r[key].lower().startswith("active") for r in rows):
+                reasons.append(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- algorithmic work per kernel launch -------------------------
+
+def fft_flops(N):
+    return 5.0 * N * math.log2(N)
+
+
+def kernel_work(info, wl, frames):
+    """Per-kernel algorithmic work for `frames` frames: (bytes, flops)."""
+    m, n, w = wl.m, wl.n, wl.w
+    mc, nc, Nr, Nc = info["mc"], info["nc"], info["fft_rows"], info["fft_cols"]
+    W = 2 * w - 1
+    ncv = Nc // 2 + 1
+    per = {
+        "k_frame_rows": (2 * m * n + 8 * ncv * mc, (mc / 2) * fft_flops(Nc)),
+        "k_energy": (8 * (mc + nc) + 8 * W * W, 0.0),
+        "k_cols": (8 * ncv * mc + 8 * W * ncv, ncv * (2 * fft_flops(Nr) + 6 * Nr)),
+        "k_rows_inv": (8 * W * ncv + 8 * W * W, math.ceil(W / 2) * fft_flops(Nc)),
+        "k_jitter": (2 * m * n, 0.0),
+    }
+    return {k: (b * frames, f * frames) for k, (b, f) in per.items()}
+
+
+def roofline(profile, info, wl, frames_per_step, steps, peaks, clocks):
+    """Dominant kernel (largest share of device time) against its bound."""
+    total = sum(ms for _, ms in profile.values()) or 1.0
+    name = max(profile, key=lambda k: profile[k][1])
+    launches, ms = profile[name]
+    work = kernel_work(info, wl, frames_per_step * steps)
+    byts, flops = work.get(name, (0.0, 0.0))
+    dur_s = ms / 1e3
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s at max clock
+    frac_h = (byts / dur_s / 1e9) / hbm if byts else 0.0
+    frac_a = (flops / dur_s / 1e12) / fp32_peak if flops else 0.0
+    if frac_a >= frac_h:
+        rf = {"bound": "alu", "achieved": flops / launches / (dur_s / launches) / 1e12, "peak": fp32_peak,
+              "unit": "TFLOP/s", "frac": frac_a,
+              "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"}
+    else:
+        rf = {"bound": "hbm", "achieved": byts / dur_s / 1e9, "peak": hbm, "unit": "GB/s", "frac": frac_h,
+              "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    rf.update({"kernel": name, "launches": launches, "avg_launch_ms": ms / launches,
+               "share": ms / total, "traffic": None,
+               "algorithmic_per_launch": {"bytes": byts / launches, "flops": flops / launches}})
+    return rf
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+# ---- CPU baseline: the oracle as it stands --------------------------------------
+
+def cpu_baseline(frames_host, template_host, w, seconds):
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    done, t0 = 0, time.perf_counter()
+    chunk = cores
+    while True:
+        sel = frames_host[done % len(frames_host):done % len(frames_host) + chunk]
+        oracle.align(sel, template_host, w, nthreads=cores)
+        done += len(sel)
+        el = time.perf_counter() - t0
+        if el >= seconds or done >= len(frames_host):
+            break
+    return {"value": done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d frames of the same workload (%.1f s, OpenMP over frames)" % (done, el)}
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_1506_06039_gb300 import synth
+    oracle.build()
+    wl = synth.WORKLOADS[args.workload]
+    cores = os.cpu_count() or 1
+    sample = max(cores, 8)
+    st = synth.make_stack_np(wl.m, wl.n, sample, wl.nblobs, wl.shift_max, wl.seed, template="mean100")
+    for _ in range(args.warmup):
+        oracle.align(st.frames[:cores], st.template, wl.w, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.align(st.frames, st.template, wl.w, nthreads=cores)
+    el = time.perf_counter() - t0
+    value = sample * args.steps / el
+    cfg = workload_config(wl, "oracle (exact int64 brute force)")
+    cfg["sample_frames_per_step"] = sample
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+           "data": "synthetic", "config": cfg,
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": "%d frames of the workload per step (host-generated, same recipe), OpenMP over frames" % sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---- the CUDA path ------------------------------------------------------------
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+    from paper_1506_06039_gb300 import Plan, XCORR_AUTO, XCORR_DIRECT_BF16X3, XCORR_FFT_FP32, build, synth
+
+    build.build()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    wl = synth.WORKLOADS[args.workload]
+    st = synth.make_stack_torch(wl.m, wl.n, wl.T, wl.nblobs, wl.shift_max, wl.seed + 1000 * rank,
+                                template=wl.template)
+    form = {"auto": XCORR_AUTO, "fft": XCORR_FFT_FP32, "direct": XCORR_DIRECT_BF16X3}[args.form]
+    plan = Plan(dict(m=wl.m, n=wl.n, w=wl.w, xcorr=form, group_frames=args.group), st.template)
+    info = plan.info()
+    form_name = {XCORR_FFT_FP32: "fft_fp32", XCORR_DIRECT_BF16X3: "direct_bf16x3"}[info["xcorr"]]
+    shifts = torch.empty((wl.T, 2), dtype=torch.int32, device="cuda")
+
+    def step():
+        plan_align(plan, st.frames, shifts)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    groups = math.ceil(wl.T / info["group_frames"])
+    plan.profile(max_launches=args.steps * groups * 6 + 64)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    profile = plan.profile_read(reset=True)
+    plan.profile(0)
+    value = world * wl.T * args.steps / (ms / 1e3)
+    launches = sum(l for l, _ in profile.values())
+    peaks = load_peaks()
+    rf = roofline(profile, info, wl, wl.T, args.steps, peaks, clocks)
+
+    # correctness guard on what was timed: planted shifts recovered
+    agree = float((shifts.cpu().numpy() == st.shifts).all(axis=1).mean())
+
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(st.frames.shape, dtype=torch.uint16).pin_memory()
+        host.copy_(st.frames.cpu())
+        out_h = torch.empty((wl.T, 2), dtype=torch.int32).pin_memory()
+        plan.align_host(host, shifts_host=out_h)
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            plan.align_host(host, shifts_host=out_h)
+        el = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([el], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * wl.T * args.e2e_steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(wl.T * wl.m * wl.n * 2), "d2h_bytes_per_step": int(wl.T * 8),
+               "steps": args.e2e_steps, "api": "moco_align_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        idx = np.random.default_rng(0).choice(wl.T, 256, replace=False)
+        cpu = cpu_baseline(st.frames[torch.from_numpy(idx).cuda()].cpu().numpy(), st.template.cpu().numpy(),
+                           wl.w, args.cpu_seconds)
+    if rank == 0:
+        tot_ms = sum(t for _, t in profile.values()) or 1.0
+        cfg = workload_config(wl, form_name)
+        cfg["group_frames"] = info["group_frames"]
+        cfg["fft"] = [info["fft_rows"], info["fft_cols"]]
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic", "config": cfg,
+               "plain_form": {"form": "fft_fp32", "value": value if form_name == "fft_fp32" else None},
+               "roofline": rf, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clocks, "planted_shift_agreement": agree,
+               "kernels": {k: {"launches": l, "ms": t, "share": t / tot_ms} for k, (l, t) in profile.items()}}
+        print(json.dumps(out), flush=True)
+    plan.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+def plan_align(plan, frames, shifts):
+    from paper_1506_06039_gb300 import moco_align_stack
+    moco_align_stack(plan.handle, [dict(shape_idx=0, frames=frames, shifts=shifts)])
+
+
+if __name__ == "__main__":
+    main()

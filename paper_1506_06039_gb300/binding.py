@@ -1,0 +1,327 @@
+"""Python binding of include/moco.h (argument marshalling only).
+
+Every function here has the C entry point's name and calls it through
+ctypes with torch tensors' device pointers and the current CUDA stream;
+all arithmetic runs in the CUDA library. The library must have been built
+(paper_1506_06039_gb300.build.build()); if it is missing, lib() raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+MOCO_OK = 0
+MOCO_ERR_INVALID_ARG = 1
+MOCO_ERR_UNSUPPORTED = 2
+MOCO_ERR_OOM = 3
+MOCO_ERR_CUDA = 4
+MOCO_ERR_TIMEOUT = 5
+
+XCORR_AUTO = 0
+XCORR_FFT_FP32 = 1
+XCORR_DIRECT_BF16X3 = 2
+
+TEMPLATE_U16 = 0
+TEMPLATE_F32 = 1
+
+# Every entry point include/moco.h declares (checked by the CPU tests).
+EXPORTS = (
+    "moco_plan", "moco_set_template", "moco_align_stack", "moco_cost_surface", "moco_softmin",
+    "moco_cost_backward", "moco_align_host", "moco_plan_query", "moco_plan_destroy",
+    "moco_status_string", "moco_last_error", "moco_profile_enable", "moco_profile_read",
+)
+
+
+class MocoShape(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("n", ctypes.c_int32), ("w", ctypes.c_int32),
+                ("levels", ctypes.c_int32), ("template_dtype", ctypes.c_int32),
+                ("xcorr", ctypes.c_int32), ("group_frames", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class MocoShapeInfo(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("mc", ctypes.c_int32), ("nc", ctypes.c_int32),
+                ("fft_rows", ctypes.c_int32), ("fft_cols", ctypes.c_int32),
+                ("xcorr", ctypes.c_int32), ("group_frames", ctypes.c_int32),
+                ("offset", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64)]
+
+
+class MocoStack(ctypes.Structure):
+    _fields_ = [("shape_idx", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("frames_dev", ctypes.c_void_p), ("T", ctypes.c_int64),
+                ("shifts_dev", ctypes.c_void_p), ("best_cost_dev", ctypes.c_void_p),
+                ("margin_dev", ctypes.c_void_p)]
+
+
+class MocoKernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+class MocoError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (_status_name(status), message))
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded libmoco.so (raises if it was never built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError("libmoco.so is missing (%s): build it with "
+                                   "paper_1506_06039_gb300.build.build()" % path)
+            L = ctypes.CDLL(path)
+            P, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+            L.moco_plan.argtypes = [ctypes.POINTER(MocoShape), i32, ctypes.POINTER(P), P, ctypes.POINTER(P)]
+            L.moco_set_template.argtypes = [P, i32, P, P]
+            L.moco_align_stack.argtypes = [P, ctypes.POINTER(MocoStack), i32, P]
+            L.moco_cost_surface.argtypes = [P, i32, P, i64, P, P]
+            L.moco_softmin.argtypes = [P, i32, P, i64, dbl, P, P, P]
+            L.moco_cost_backward.argtypes = [P, i32, P, i64, P, P, P, P]
+            L.moco_align_host.argtypes = [P, i32, P, i64, P, P]
+            L.moco_plan_query.argtypes = [P, i32, ctypes.POINTER(MocoShapeInfo)]
+            L.moco_plan_destroy.argtypes = [P]
+            L.moco_status_string.argtypes = [i32]
+            L.moco_status_string.restype = ctypes.c_char_p
+            L.moco_last_error.argtypes = []
+            L.moco_last_error.restype = ctypes.c_char_p
+            L.moco_profile_enable.argtypes = [P, i32]
+            L.moco_profile_read.argtypes = [P, ctypes.POINTER(MocoKernelStat), i32, ctypes.POINTER(i32), i32]
+            for name in EXPORTS:
+                if name not in ("moco_status_string", "moco_last_error"):
+                    getattr(L, name).restype = i32
+            _lib = L
+    return _lib
+
+
+def _status_name(status: int) -> str:
+    try:
+        return lib().moco_status_string(status).decode()
+    except Exception:  # pragma: no cover
+        return "status %d" % status
+
+
+def _check(status: int):
+    if status != MOCO_OK:
+        raise MocoError(status, lib().moco_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need(t, dtype, name, device=True):
+    import torch
+    if t is None:
+        raise ValueError("%s is required" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if device and not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t
+
+
+# ---- the C entry points, one to one ---------------------------------------
+
+def moco_plan(shapes, templates, stream=None) -> ctypes.c_void_p:
+    """shapes: list of dicts with m, n, w and optional levels (-1),
+    template_dtype (0 = U16, 1 = F32), xcorr (0 = auto), group_frames (0).
+    templates: list of CUDA tensors (uint16 or float32, [m, n])."""
+    import torch
+    arr = (MocoShape * len(shapes))()
+    for k, s in enumerate(shapes):
+        arr[k] = MocoShape(int(s["m"]), int(s["n"]), int(s["w"]), int(s.get("levels", -1)),
+                           int(s.get("template_dtype", TEMPLATE_U16)), int(s.get("xcorr", XCORR_AUTO)),
+                           int(s.get("group_frames", 0)), 0)
+        dt = torch.float32 if arr[k].template_dtype == TEMPLATE_F32 else torch.uint16
+        _need(templates[k], dt, "template %d" % k)
+    tp = (ctypes.c_void_p * len(templates))(*[t.data_ptr() for t in templates])
+    out = ctypes.c_void_p()
+    _check(lib().moco_plan(arr, len(shapes), tp, _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def moco_set_template(plan, shape_idx, template, stream=None):
+    _check(lib().moco_set_template(plan, shape_idx, _ptr(template), _stream(stream)))
+
+
+def moco_align_stack(plan, stacks, stream=None):
+    """stacks: list of dicts {shape_idx, frames, shifts, best_cost=None, margin=None}."""
+    import torch
+    arr = (MocoStack * len(stacks))()
+    for k, s in enumerate(stacks):
+        fr = _need(s["frames"], torch.uint16, "frames")
+        sh = _need(s["shifts"], torch.int32, "shifts")
+        bc = s.get("best_cost")
+        mg = s.get("margin")
+        if bc is not None:
+            _need(bc, torch.float64, "best_cost")
+        if mg is not None:
+            _need(mg, torch.float32, "margin")
+        T = fr.shape[0] if fr.dim() == 3 else 1
+        arr[k] = MocoStack(int(s.get("shape_idx", 0)), 0, fr.data_ptr(), T, sh.data_ptr(),
+                           bc.data_ptr() if bc is not None else None,
+                           mg.data_ptr() if mg is not None else None)
+    _check(lib().moco_align_stack(plan, arr, len(stacks), _stream(stream)))
+
+
+def moco_cost_surface(plan, shape_idx, frames, cost, stream=None):
+    import torch
+    _need(frames, torch.uint16, "frames")
+    _need(cost, torch.float64, "cost")
+    T = frames.shape[0] if frames.dim() == 3 else 1
+    _check(lib().moco_cost_surface(plan, shape_idx, _ptr(frames), T, _ptr(cost), _stream(stream)))
+
+
+def moco_softmin(plan, shape_idx, cost, tau_scale, loss, weights, stream=None):
+    import torch
+    _need(cost, torch.float64, "cost")
+    _need(loss, torch.float64, "loss")
+    _need(weights, torch.float32, "weights")
+    _check(lib().moco_softmin(plan, shape_idx, _ptr(cost), cost.shape[0], float(tau_scale), _ptr(loss),
+                              _ptr(weights), _stream(stream)))
+
+
+def moco_cost_backward(plan, shape_idx, frames, grad_cost, grad_template, grad_frames=None, stream=None):
+    import torch
+    _need(frames, torch.uint16, "frames")
+    _need(grad_cost, torch.float32, "grad_cost")
+    _need(grad_template, torch.float32, "grad_template")
+    if grad_frames is not None:
+        _need(grad_frames, torch.float32, "grad_frames")
+    T = frames.shape[0] if frames.dim() == 3 else 1
+    _check(lib().moco_cost_backward(plan, shape_idx, _ptr(frames), T, _ptr(grad_cost), _ptr(grad_template),
+                                    _ptr(grad_frames), _stream(stream)))
+
+
+def moco_align_host(plan, shape_idx, frames_host, shifts_host, stream=None):
+    import torch
+    _need(frames_host, torch.uint16, "frames_host", device=False)
+    _need(shifts_host, torch.int32, "shifts_host", device=False)
+    if frames_host.is_cuda or shifts_host.is_cuda:
+        raise ValueError("moco_align_host takes host tensors")
+    T = frames_host.shape[0] if frames_host.dim() == 3 else 1
+    _check(lib().moco_align_host(plan, shape_idx, _ptr(frames_host), T, _ptr(shifts_host), _stream(stream)))
+
+
+def moco_plan_query(plan, shape_idx) -> dict:
+    info = MocoShapeInfo()
+    _check(lib().moco_plan_query(plan, shape_idx, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in MocoShapeInfo._fields_}
+
+
+def moco_plan_destroy(plan):
+    _check(lib().moco_plan_destroy(plan))
+
+
+def moco_profile_enable(plan, max_launches: int):
+    _check(lib().moco_profile_enable(plan, int(max_launches)))
+
+
+def moco_profile_read(plan, reset: bool = True) -> dict:
+    """{kernel name: (launches, total_ms)} since the last reset."""
+    cap = 16
+    arr = (MocoKernelStat * cap)()
+    cnt = ctypes.c_int32()
+    _check(lib().moco_profile_read(plan, arr, cap, ctypes.byref(cnt), int(reset)))
+    return {arr[k].name.decode(): (int(arr[k].launches), float(arr[k].total_ms))
+            for k in range(min(cnt.value, cap))}
+
+
+def moco_status_string(status: int) -> str:
+    return lib().moco_status_string(status).decode()
+
+
+# ---- a small object wrapper ---------------------------------------------
+
+class Plan:
+    """Owns a moco plan for one or more shapes.
+
+        plan = Plan([dict(m=512, n=512, w=32)], [template_u16_cuda])
+        shifts = plan.align(frames_u16_cuda)           # (T, 2) int32
+    """
+
+    def __init__(self, shapes, templates, stream=None):
+        if isinstance(shapes, dict):
+            shapes = [shapes]
+        if not isinstance(templates, (list, tuple)):
+            templates = [templates]
+        self.shapes = [dict(s) for s in shapes]
+        self.handle = moco_plan(self.shapes, list(templates), stream)
+
+    def info(self, shape_idx=0) -> dict:
+        return moco_plan_query(self.handle, shape_idx)
+
+    def W(self, shape_idx=0) -> int:
+        return 2 * int(self.shapes[shape_idx]["w"]) - 1
+
+    def align(self, frames, shape_idx=0, best_cost=False, margin=False, stream=None):
+        import torch
+        T = frames.shape[0]
+        dev = frames.device
+        shifts = torch.empty((T, 2), dtype=torch.int32, device=dev)
+        bc = torch.empty(T, dtype=torch.float64, device=dev) if best_cost else None
+        mg = torch.empty(T, dtype=torch.float32, device=dev) if margin else None
+        moco_align_stack(self.handle, [dict(shape_idx=shape_idx, frames=frames, shifts=shifts,
+                                            best_cost=bc, margin=mg)], stream)
+        if best_cost or margin:
+            return shifts, bc, mg
+        return shifts
+
+    def cost_surface(self, frames, shape_idx=0, stream=None):
+        import torch
+        W = self.W(shape_idx)
+        cost = torch.empty((frames.shape[0], W, W), dtype=torch.float64, device=frames.device)
+        moco_cost_surface(self.handle, shape_idx, frames, cost, stream)
+        return cost
+
+    def set_template(self, template, shape_idx=0, stream=None):
+        moco_set_template(self.handle, shape_idx, template, stream)
+
+    def align_host(self, frames_host, shape_idx=0, shifts_host=None, stream=None):
+        import torch
+        if shifts_host is None:
+            shifts_host = torch.empty((frames_host.shape[0], 2), dtype=torch.int32).pin_memory()
+        moco_align_host(self.handle, shape_idx, frames_host, shifts_host, stream)
+        return shifts_host
+
+    def profile(self, max_launches: int):
+        moco_profile_enable(self.handle, max_launches)
+
+    def profile_read(self, reset: bool = True) -> dict:
+        return moco_profile_read(self.handle, reset)
+
+    def close(self):
+        if self.handle:
+            moco_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,46 @@
+// Internal launchers shared by the translation units of the engine.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace moco {
+
+typedef unsigned long long u64;
+
+// FFT lengths this build instantiates (each a product N1 * N2 of register
+// codelet sizes); fft_size_for returns the smallest one >= needed, or 0.
+int fft_size_for(int needed);
+bool fft_size_supported(int N);
+int fft_split_max(int N);  // max(N1, N2): threads per row of a four-step stage
+
+cudaError_t launch_frame_rows(int N, bool f32, const void* src, int64_t src_fstride, int64_t nimg, int m,
+                              int n, int levels, int mc, int nc, const int32_t* coff_i, const float* coff_f,
+                              const float2* tw, float2* X, int64_t x_fstride, int ldx, u64* rowE, u64* colE,
+                              u64* tot, uint32_t* corners, int wm1, cudaStream_t st);
+
+cudaError_t launch_cols(int N, bool spectrum, const float2* X, int64_t x_fstride, int ldx, int mc, int ncv,
+                        int64_t nimg, const float2* tw, const float2* bspec, float2* Y, int64_t y_fstride,
+                        int wm1, float scale, cudaStream_t st);
+
+cudaError_t launch_rows_inv(int N, const float2* Y, int64_t y_fstride, int ncv, int wm1, int64_t nimg,
+                            const float2* tw, const u64* Sa, const double* Sb, const double* inv_area,
+                            double unit, double* cost, int32_t* coarse, double* fbest, float* margin,
+                            cudaStream_t st);
+
+cudaError_t launch_energy(bool f32, bool out_double, const u64* rowE, const u64* colE, const u64* tot,
+                          const uint32_t* corners, int64_t nimg, int mc, int nc, int wm1, void* out, int flip,
+                          cudaStream_t st);
+
+cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg, const uint16_t* tmpl, int m,
+                          int n, const int32_t* coarse, int32_t* shifts, double* ffinal, cudaStream_t st);
+
+cudaError_t launch_copy_shifts(const int32_t* coarse, int32_t* shifts, const double* fbest, double* ffinal,
+                               int64_t T, cudaStream_t st);
+
+cudaError_t launch_template_offset(bool f32, const void* tmpl, int m, int n, int levels, int32_t* coff_i,
+                                   float* coff_f, cudaStream_t st);
+
+// Sets the dynamic shared-memory limit of `func` on the current device once.
+cudaError_t ensure_smem(const void* func, size_t bytes);
+
+}  // namespace moco

@@ -1,0 +1,649 @@
+// Device kernels of the translation search (Section 2 of the paper).
+//
+// For one frame a and the template b (both on the searched grid, offset by
+// the plan's integer c) every shift max(|s|,|t|) < w gets
+//     Area(D_st) f_st = Sa_st + Sb_st - 2 h_st                  (Section 2)
+// with Sa, Sb the energies of a and b over D_st (exact int64 here, the
+// paper's dynamic-programming sums restricted to the window) and h the
+// cross-correlation, computed through zero-padded 2-D FFTs (Section 2):
+//   k_frame_rows : 2x2 box (exact integer 4-sum), subtract c, energies of the
+//                  edge strips and corners, real row FFTs (length Nc) -> X
+//   k_energy     : Sa for every shift from totals, edge strips and corners
+//   k_cols       : column FFT (length Nr), x conj(template spectrum), inverse
+//                  column FFT kept on the 2w-1 needed rows -> Y
+//   k_rows_inv   : inverse row FFTs kept on the 2w-1 needed columns -> h;
+//                  f = (Sa + Sb - 2h) / Area in FP64; argmin with tie-break
+//   k_jitter     : Section 2's upsampling step: the 3x3 candidates around the
+//                  doubled optimum, exact int64 sums at full resolution
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "fft.cuh"
+
+namespace moco {
+
+typedef unsigned long long u64;
+
+constexpr int kRowsThreads = 512;
+constexpr int kRC = 32;          // searched-grid rows per chunk of k_frame_rows
+constexpr int kColsVC = 16;      // spectral columns per CTA of k_cols
+constexpr int kInvPC = 16;       // row pairs per chunk of k_rows_inv
+constexpr int kEnergyThreads = 256;
+constexpr int kJitterThreads = 256;
+
+template <bool F32>
+struct AccT { typedef u64 type; };
+template <>
+struct AccT<true> { typedef double type; };
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint32_t lo16(uint32_t w) { return w & 0xffffu; }
+// d^2 exactly, |d| < 2^32: one 32x32 -> 64-bit unsigned multiply.
+__device__ __forceinline__ u64 sq64(int32_t d) {
+    const uint32_t a = (uint32_t)abs(d);
+    return (u64)a * (u64)a;
+}
+__device__ __forceinline__ uint32_t hi16(uint32_t w) { return w >> 16; }
+
+// ---------------------------------------------------------------------------
+// k_frame_rows: one CTA per image (frame or template).
+//
+// src        : images, element stride src_fstride between them; uint16
+//              (frames, U16 template) or float (F32 template, levels = 0)
+// levels     : 1 = one 2x2 box level (4-sum), 0 = none
+// coff       : the plan's integer offset c (int32 for U16, float for F32)
+// X          : X[f*x_fstride + v*ldx + r], v in [0, Nc/2], r in [0, mc): the
+//              row DFT of the offset searched-grid rows
+// rowE, colE : per-row / per-column energies (only the 2(w-1) edge rows and
+//              columns are written), tot: total energy, all as 64-bit words
+//              (u64 for integer images, double for F32)
+// corners    : the four (w-1)x(w-1) corner blocks of the offset image
+//              (int32 or float bits), [f][q][ri][ci], q = 2*bottom + right
+template <int N, bool F32IN>
+__global__ void __launch_bounds__(kRowsThreads)
+k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, int levels, int mc,
+             int nc, const int32_t* __restrict__ coff_i, const float* __restrict__ coff_f,
+             const float2* __restrict__ tw_g, float2* __restrict__ X, int64_t x_fstride, int ldx,
+             u64* __restrict__ rowE, u64* __restrict__ colE, u64* __restrict__ tot,
+             uint32_t* __restrict__ corners, int wm1) {
+    typedef typename AccT<F32IN>::type Acc;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);  // (kRC/2) x N
+    float2* tw = buf + (kRC / 2) * N;                    // N
+    Acc* rowacc = reinterpret_cast<Acc*>(tw + N);        // kRC
+    Acc* colacc = rowacc + kRC;                          // nc
+    __shared__ Acc red[32];
+
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int64_t f = blockIdx.x;
+    for (int i = tid; i < N; i += nthr) tw[i] = tw_g[i];
+    for (int i = tid; i < nc; i += nthr) colacc[i] = 0;
+    for (int i = tid; i < kRC; i += nthr) rowacc[i] = 0;
+
+    const int CW = (levels ? 4 : 8);  // searched-grid values per thread per row
+    const int G = nc / CW;             // column groups per row
+    const int RPI = nthr / G;          // rows per pass (host guarantees G <= nthr)
+    const bool active = tid < RPI * G;
+    const int g = tid % G, rl0 = tid / G;
+    Acc cacc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) cacc[k] = 0;
+    Acc tacc = 0;
+    const int32_t ci_off = F32IN ? 0 : *coff_i;
+    const float cf_off = F32IN ? *coff_f : 0.f;
+    const size_t wm1sq = (size_t)wm1 * wm1;
+
+    for (int r0 = 0; r0 < mc; r0 += kRC) {
+        const int rows = min(kRC, mc - r0), nfft = (rows + 1) >> 1;
+        for (int i = tid; i < nfft * N; i += nthr) buf[i] = make_float2(0.f, 0.f);
+        __syncthreads();
+        if (active) {
+            for (int rl = rl0; rl < rows; rl += RPI) {
+                const int r = r0 + rl;
+                float val[8];
+                Acc e[8];
+                if (!F32IN) {
+                    const uint16_t* base = static_cast<const uint16_t*>(src) + f * src_fstride;
+                    int32_t iv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    if (levels) {
+                        const uint4 p0 = __ldg(reinterpret_cast<const uint4*>(base + (int64_t)(2 * r) * n + 8 * g));
+                        const uint4 p1 = __ldg(reinterpret_cast<const uint4*>(base + (int64_t)(2 * r + 1) * n + 8 * g));
+                        const uint32_t w0[4] = {p0.x, p0.y, p0.z, p0.w}, w1[4] = {p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            iv[k] = (int32_t)(lo16(w0[k]) + hi16(w0[k]) + lo16(w1[k]) + hi16(w1[k]));
+                    } else {
+                        const uint4 p0 = __ldg(reinterpret_cast<const uint4*>(base + (int64_t)r * n + 8 * g));
+                        const uint32_t w0[4] = {p0.x, p0.y, p0.z, p0.w};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            iv[2 * k] = (int32_t)lo16(w0[k]);
+                            iv[2 * k + 1] = (int32_t)hi16(w0[k]);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int32_t d = iv[k] - ci_off;
+                        val[k] = (float)d;  // |d| < 2^19: exact
+                        e[k] = (Acc)sq64(d);
+                    }
+                } else {
+                    const float* base = static_cast<const float*>(src) + f * src_fstride;
+                    const float4 q0 = __ldg(reinterpret_cast<const float4*>(base + (int64_t)r * n + 8 * g));
+                    const float4 q1 = __ldg(reinterpret_cast<const float4*>(base + (int64_t)r * n + 8 * g + 4));
+                    const float qv[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        val[k] = qv[k] - cf_off;
+                        e[k] = (Acc)((double)val[k] * (double)val[k]);
+                    }
+                }
+                Acc rs = 0;
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (k < CW) {
+                        cacc[k] += e[k];
+                        rs += e[k];
+                    }
+                tacc += rs;
+                const bool top = r < wm1, bot = r >= mc - wm1;
+                if (top || bot) {
+                    atomicAdd(&rowacc[rl], rs);
+                    const int ri = top ? r : r - (mc - wm1);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int c = g * CW + k;
+                        if (k < CW && (c < wm1 || c >= nc - wm1)) {
+                            const bool right = c >= nc - wm1;
+                            const int cj = right ? c - (nc - wm1) : c;
+                            const int q = (bot ? 2 : 0) + (right ? 1 : 0);
+                            uint32_t bits;
+                            if (F32IN) bits = __float_as_uint(val[k]);
+                            else bits = (uint32_t)(int32_t)val[k];
+                            corners[(f * 4 + q) * wm1sq + (size_t)ri * wm1 + cj] = bits;
+                        }
+                    }
+                }
+                float* dst = reinterpret_cast<float*>(buf + (rl >> 1) * N) + (rl & 1);
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (k < CW) dst[2 * (g * CW + k)] = val[k];
+            }
+        }
+        __syncthreads();
+        fft4_fwd<N>(buf, N, nfft, tw, tid, nthr);
+        // Two real rows were packed as one complex row: split the spectra.
+        constexpr int NH = N / 2 + 1;
+        for (int task = tid; task < NH * nfft; task += nthr) {
+            const int v = task / nfft, fi = task - v * nfft;
+            const float2 zk = buf[fi * N + spec_pos<N>(v)];
+            const float2 zn = cconj(buf[fi * N + spec_pos<N>((N - v) % N)]);
+            const float2 x1 = cscale(cadd(zk, zn), 0.5f);
+            const float2 d = csub(zk, zn);
+            const float2 x2 = make_float2(0.5f * d.y, -0.5f * d.x);
+            float2* out = X + f * x_fstride + (int64_t)v * ldx + r0 + 2 * fi;
+            if (2 * fi + 1 < rows)
+                *reinterpret_cast<float4*>(out) = make_float4(x1.x, x1.y, x2.x, x2.y);
+            else
+                out[0] = x1;
+        }
+        for (int rl = tid; rl < rows; rl += nthr) {
+            const int r = r0 + rl;
+            if (r < wm1 || r >= mc - wm1) {
+                Acc v = rowacc[rl];
+                rowE[f * mc + r] = *reinterpret_cast<u64*>(&v);
+            }
+            rowacc[rl] = 0;
+        }
+        __syncthreads();
+    }
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (k < CW) atomicAdd(&colacc[g * CW + k], cacc[k]);
+    }
+    tacc = warp_sum(tacc);
+    if ((tid & 31) == 0) red[tid >> 5] = tacc;
+    __syncthreads();
+    if (tid == 0) {
+        Acc s = 0;
+        for (int i = 0; i < (nthr + 31) / 32; ++i) s += red[i];
+        tot[f] = *reinterpret_cast<u64*>(&s);
+    }
+    for (int c = tid; c < nc; c += nthr)
+        if (c < wm1 || c >= nc - wm1) {
+            Acc v = colacc[c];
+            colE[f * nc + c] = *reinterpret_cast<u64*>(&v);
+        }
+}
+
+// ---------------------------------------------------------------------------
+// k_energy: Sa[s][t] = sum over the a-side of D_st of a'^2 for every shift.
+// The a-side of D_st keeps rows [max(0,s), mc+min(0,s)) and columns
+// [max(0,t), nc+min(0,t)), i.e. everything but an edge strip of |s| rows and
+// one of |t| columns, so
+//     Sa = Tot - ExR(s) - ExC(t) + Corner(s,t)
+// where the corner term is a 2-D prefix sum over one (w-1)^2 corner block
+// (the recurrence of Section 2 restricted to the window). With flip set the
+// result is stored at (-s,-t): the template's energy over the b-side of D.
+// OUT_DOUBLE stores doubles, else u64 (both exact for integer images).
+template <bool F32, bool OUT_DOUBLE>
+__global__ void __launch_bounds__(kEnergyThreads)
+k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* __restrict__ tot,
+         const uint32_t* __restrict__ corners, int mc, int nc, int wm1, void* __restrict__ out,
+         int flip) {
+    typedef typename AccT<F32>::type Acc;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int W = 2 * wm1 + 1, w = wm1 + 1;
+    Acc* exR = reinterpret_cast<Acc*>(smem_raw);  // W
+    Acc* exC = exR + W;                            // W
+    Acc* P = exC + W;                              // w x w
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int64_t f = blockIdx.x;
+    const u64* rE = rowE + f * mc;
+    const u64* cE = colE + f * nc;
+    auto ld = [](const u64* p) { u64 v = *p; return *reinterpret_cast<Acc*>(&v); };
+    if (tid == 0) {
+        exR[wm1] = 0;
+        Acc s = 0;
+        for (int k = 1; k <= wm1; ++k) { s += ld(rE + k - 1); exR[wm1 + k] = s; }
+        s = 0;
+        for (int k = 1; k <= wm1; ++k) { s += ld(rE + mc - k); exR[wm1 - k] = s; }
+    }
+    if (tid == 32) {  // (launched with kEnergyThreads > 32)
+        exC[wm1] = 0;
+        Acc s = 0;
+        for (int k = 1; k <= wm1; ++k) { s += ld(cE + k - 1); exC[wm1 + k] = s; }
+        s = 0;
+        for (int k = 1; k <= wm1; ++k) { s += ld(cE + nc - k); exC[wm1 - k] = s; }
+    }
+    const Acc T = ld(tot + f);
+    const size_t wm1sq = (size_t)wm1 * wm1;
+    for (int q = 0; q < 4; ++q) {
+        const bool bottom = q >= 2, right = q & 1;
+        __syncthreads();
+        // P[a][b] = sum over the a rows nearest the corner's horizontal edge
+        // and the b columns nearest its vertical edge.
+        for (int i = tid; i < w * w; i += nthr) {
+            const int a = i / w, b = i - a * w;
+            Acc v = 0;
+            if (a > 0 && b > 0) {
+                const int di = a - 1, dj = b - 1;  // distances from the outer edges
+                const int ri = bottom ? wm1 - 1 - di : di;
+                const int cj = right ? wm1 - 1 - dj : dj;
+                const uint32_t bits = corners[(f * 4 + q) * wm1sq + (size_t)ri * wm1 + cj];
+                if (F32) {
+                    const double x = (double)__uint_as_float(bits);
+                    v = (Acc)(x * x);
+                } else {
+                    const long long x = (int32_t)bits;
+                    v = (Acc)(x * x);
+                }
+            }
+            P[i] = v;
+        }
+        __syncthreads();
+        for (int a = tid; a < w; a += nthr) {
+            Acc s = 0;
+            for (int b = 0; b < w; ++b) { s += P[a * w + b]; P[a * w + b] = s; }
+        }
+        __syncthreads();
+        for (int b = tid; b < w; b += nthr) {
+            Acc s = 0;
+            for (int a = 0; a < w; ++a) { s += P[a * w + b]; P[a * w + b] = s; }
+        }
+        __syncthreads();
+        // Shifts of this quadrant: s >= 0 (top) or s < 0 (bottom), same for t.
+        for (int i = tid; i < w * w; i += nthr) {
+            const int a = i / w, b = i - a * w;
+            if (bottom && a == 0) continue;
+            if (right && b == 0) continue;
+            const int s = bottom ? -a : a, t = right ? -b : b;
+            const Acc val = T - exR[s + wm1] - exC[t + wm1] + P[i];
+            const int so = flip ? -s : s, to = flip ? -t : t;
+            const int64_t k = f * (int64_t)W * W + (int64_t)(so + wm1) * W + (to + wm1);
+            if (OUT_DOUBLE) static_cast<double*>(out)[k] = (double)val;
+            else static_cast<u64*>(out)[k] = *reinterpret_cast<const u64*>(&val);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_cols: one CTA per (frame = blockIdx.x, kColsVC spectral columns v = blockIdx.y).
+// Forward DFT along the image rows (length Nr) of X[:, v], multiplied by the
+// plan's conj(template spectrum) / (Nr Nc) (stored in the forward output
+// layout), inverse DFT, and only the 2w-1 rows s in [-(w-1), w-1] kept:
+// Y[f*y_fstride + (s+w-1)*ncv + v]. With SPECTRUM set, the forward transform
+// is written out conjugated and scaled instead (template preparation).
+template <int N, bool SPECTRUM>
+__global__ void __launch_bounds__(576)
+k_cols(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv,
+       const float2* __restrict__ tw_g, const float2* __restrict__ bspec, float2* __restrict__ Y,
+       int64_t y_fstride, int wm1, float scale) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);  // kColsVC x N
+    float2* tw = buf + kColsVC * N;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int v0 = blockIdx.y * kColsVC, nv = min(kColsVC, ncv - v0);
+    const int64_t f = blockIdx.x;
+    for (int i = tid; i < N; i += nthr) tw[i] = tw_g[i];
+    const float2* xs = X + f * x_fstride + (int64_t)v0 * ldx;
+    for (int task = tid; task < nv * N; task += nthr) {
+        const int vi = task / N, i = task - vi * N;
+        buf[vi * N + i] = (i < mc) ? xs[(int64_t)vi * ldx + i] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fft4_fwd<N>(buf, N, nv, tw, tid, nthr);
+    if (SPECTRUM) {
+        for (int task = tid; task < nv * N; task += nthr) {
+            const int vi = task / N, p = task - vi * N;
+            Y[(int64_t)(v0 + vi) * N + p] = cscale(cconj(buf[vi * N + p]), scale);
+        }
+        return;
+    }
+    for (int task = tid; task < nv * N; task += nthr) {
+        const int vi = task / N, p = task - vi * N;
+        buf[vi * N + p] = cmul(buf[vi * N + p], bspec[(int64_t)(v0 + vi) * N + p]);
+    }
+    __syncthreads();
+    fft4_inv<N>(buf, N, nv, tw, tid, nthr);
+    const int W = 2 * wm1 + 1;
+    float2* ys = Y + f * y_fstride + v0;
+    for (int task = tid; task < W * nv; task += nthr) {
+        const int si = task / nv, vi = task - si * nv;
+        const int pos = (si - wm1 + N) % N;
+        ys[(int64_t)si * ncv + vi] = buf[vi * N + pos];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_rows_inv: one CTA per frame. Inverse real DFTs along the image columns
+// (length Nc) of Y's 2w-1 rows, two rows per complex transform, keeping the
+// 2w-1 columns t in [-(w-1), w-1] -> h[s][t]. Then, in FP64,
+//     f_st = (Sa_st + Sb_st - 2 h_st) / Area_st * unit
+// and the argmin over the window with the tie-break: smallest f, then
+// smallest |s|+|t|, then smallest s, then smallest t. Also the second-best
+// value for the margin (f2 - f1) / f1.
+struct Best {
+    double f1;
+    int r1;
+    double f2;
+};
+__device__ __forceinline__ void best_push(Best& b, double f, int r) {
+    if (f < b.f1 || (f == b.f1 && r < b.r1)) {
+        b.f2 = fmin(b.f2, b.f1);
+        b.f1 = f;
+        b.r1 = r;
+    } else {
+        b.f2 = fmin(b.f2, f);
+    }
+}
+__device__ __forceinline__ void best_merge(Best& a, const Best& o) {
+    if (o.f1 < a.f1 || (o.f1 == a.f1 && o.r1 < a.r1)) {
+        a.f2 = fmin(o.f2, a.f1);
+        a.f1 = o.f1;
+        a.r1 = o.r1;
+    } else {
+        a.f2 = fmin(a.f2, o.f1);
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(576)
+k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
+           const float2* __restrict__ tw_g, const u64* __restrict__ Sa, const double* __restrict__ Sb,
+           const double* __restrict__ inv_area, double unit, double* __restrict__ cost,
+           int32_t* __restrict__ coarse, double* __restrict__ fbest, float* __restrict__ margin) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);  // kInvPC x N
+    float2* tw = buf + kInvPC * N;
+    const int W = 2 * wm1 + 1, WW = W * W;
+    float* hbuf = reinterpret_cast<float*>(tw + N);     // W x W
+    __shared__ Best red[32];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int64_t f = blockIdx.x;
+    for (int i = tid; i < N; i += nthr) tw[i] = tw_g[i];
+    const float2* ys = Y + f * y_fstride;
+    const int npairs = (W + 1) / 2;
+    constexpr int NH = N / 2;
+    for (int p0 = 0; p0 < npairs; p0 += kInvPC) {
+        const int np = min(kInvPC, npairs - p0);
+        __syncthreads();
+        for (int task = tid; task < np * N; task += nthr) {
+            const int pi = task / N, k = task - pi * N;
+            const int ra = 2 * (p0 + pi), rb = ra + 1;
+            const int kk = (k <= NH) ? k : N - k;
+            float2 A = ys[(int64_t)ra * ncv + kk];
+            float2 B = (rb < W) ? ys[(int64_t)rb * ncv + kk] : make_float2(0.f, 0.f);
+            if (k == 0 || k == NH) { A.y = 0.f; B.y = 0.f; }
+            if (k > NH) { A.y = -A.y; B.y = -B.y; }
+            buf[pi * N + spec_pos<N>(k)] = make_float2(A.x - B.y, A.y + B.x);
+        }
+        __syncthreads();
+        fft4_inv<N>(buf, N, np, tw, tid, nthr);
+        for (int task = tid; task < np * W; task += nthr) {
+            const int pi = task / W, ti = task - pi * W;
+            const int pos = (ti - wm1 + N) % N;
+            const float2 z = buf[pi * N + pos];
+            const int ra = 2 * (p0 + pi);
+            hbuf[ra * W + ti] = z.x;
+            if (ra + 1 < W) hbuf[(ra + 1) * W + ti] = z.y;
+        }
+    }
+    __syncthreads();
+    Best b;
+    b.f1 = INFINITY;
+    b.r1 = 0x7fffffff;
+    b.f2 = INFINITY;
+    const u64* sa = Sa + f * WW;
+    for (int k = tid; k < WW; k += nthr) {
+        const int si = k / W, ti = k - si * W;
+        const int s = si - wm1, t = ti - wm1;
+        const double num = ((double)sa[k] + Sb[k]) - 2.0 * (double)hbuf[k];
+        const double fv = num * inv_area[k] * unit;
+        if (cost) cost[f * WW + k] = fv;
+        best_push(b, fv, (abs(s) + abs(t)) * WW + k);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Best o2;
+        o2.f1 = __shfl_xor_sync(0xffffffffu, b.f1, o);
+        o2.r1 = __shfl_xor_sync(0xffffffffu, b.r1, o);
+        o2.f2 = __shfl_xor_sync(0xffffffffu, b.f2, o);
+        best_merge(b, o2);
+    }
+    if ((tid & 31) == 0) red[tid >> 5] = b;
+    __syncthreads();
+    if (tid == 0) {
+        for (int i = 1; i < (nthr + 31) / 32; ++i) best_merge(b, red[i]);
+        const int k = b.r1 % WW;
+        const int s = k / W - wm1, t = k % W - wm1;
+        coarse[2 * f] = s;
+        coarse[2 * f + 1] = t;
+        if (fbest) fbest[f] = b.f1;
+        if (margin) {
+            float mg;
+            if (b.f1 > 0) mg = (float)((b.f2 - b.f1) / b.f1);
+            else mg = (b.f2 > 0) ? INFINITY : 0.f;
+            margin[f] = mg;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_jitter: the upsampling step of Section 2. One CTA per frame. For the
+// nine candidates (2 sc + u, 2 tc + v), u, v in {-1, 0, 1}, the exact int64
+// S = sum over D of (a[i+s][j+t] - b[i][j])^2 at full resolution, all nine
+// accumulated in one pass over the frame (each thread walks down a strip of
+// 8 columns keeping the three frame rows it needs in registers), then the
+// minimum of S / Area with the tie-break, compared as exact rationals.
+__device__ __forceinline__ void unpack8(const uint4 p, int32_t (&v)[8]) {
+    const uint32_t w[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = (int32_t)lo16(w[k]);
+        v[2 * k + 1] = (int32_t)hi16(w[k]);
+    }
+}
+
+// Returns 1 when S1/A1 < S2/A2 exactly (A > 0).
+__device__ __forceinline__ int ratio_lt(u64 S1, u64 A1, u64 S2, u64 A2, int* eq) {
+    const u64 l_lo = S1 * A2, l_hi = __umul64hi(S1, A2);
+    const u64 r_lo = S2 * A1, r_hi = __umul64hi(S2, A1);
+    *eq = (l_lo == r_lo) && (l_hi == r_hi);
+    return (l_hi < r_hi) || (l_hi == r_hi && l_lo < r_lo);
+}
+
+static __global__ void __launch_bounds__(kJitterThreads)
+k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* __restrict__ tmpl,
+         int m, int n, const int32_t* __restrict__ coarse, int32_t* __restrict__ shifts,
+         double* __restrict__ ffinal) {
+    __shared__ u64 red[kJitterThreads / 32][9];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int64_t f = blockIdx.x;
+    const int s0 = 2 * coarse[2 * f], t0 = 2 * coarse[2 * f + 1];
+    const uint16_t* a = frames + f * fstride;
+    u64 acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = 0;
+    const int G = n / 8;  // column groups
+    const int nseg = max(1, nthr / G);
+    const int segrows = (m + nseg - 1) / nseg;
+    // a-row cache: values at columns j + t0 + v, v in {-1,0,1}, k in [0,8):
+    // cols j + t0 - 1 .. j + t0 + 8 (10 values) for the rows i+s0-1..i+s0+1.
+    for (int task = tid; task < G * nseg; task += nthr) {
+        const int g = task % G, seg = task / G;
+        const int j0 = 8 * g;
+        const int i_begin = seg * segrows, i_end = min(m, i_begin + segrows);
+        const int cbase = j0 + t0 - 1;  // first frame column needed
+        const bool col_interior = (cbase >= 0) && (cbase + 10 <= n);
+        for (int i = i_begin; i < i_end; ++i) {
+            int32_t bv[8];
+            unpack8(__ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)i * n + j0)), bv);
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                const int ar = i + s0 + u - 1;
+                if (ar < 0 || ar >= m) continue;
+                const uint16_t* arow = a + (int64_t)ar * n;
+                int32_t av[10];
+                if (col_interior) {
+#pragma unroll
+                    for (int k = 0; k < 10; ++k) av[k] = (int32_t)__ldg(arow + cbase + k);
+#pragma unroll
+                    for (int v = 0; v < 3; ++v) {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) acc[u * 3 + v] += sq64(av[k + v] - bv[k]);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 10; ++k) {
+                        const int c = cbase + k;
+                        av[k] = (c >= 0 && c < n) ? (int32_t)__ldg(arow + c) : 0;
+                    }
+#pragma unroll
+                    for (int v = 0; v < 3; ++v) {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int c = cbase + k + v;
+                            if (c >= 0 && c < n) acc[u * 3 + v] += sq64(av[k + v] - bv[k]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        u64 v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) red[tid >> 5][k] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        u64 S[9];
+        for (int k = 0; k < 9; ++k) {
+            S[k] = 0;
+            for (int wi = 0; wi < (nthr + 31) / 32; ++wi) S[k] += red[wi][k];
+        }
+        int bk = -1;
+        u64 bS = 0, bA = 1;
+        int bs = 0, bt = 0;
+        for (int u = 0; u < 3; ++u)
+            for (int v = 0; v < 3; ++v) {
+                const int s = s0 + u - 1, t = t0 + v - 1;
+                const u64 A = (u64)(m - abs(s)) * (u64)(n - abs(t));
+                const u64 Sk = S[u * 3 + v];
+                bool take = (bk < 0);
+                if (!take) {
+                    int eq;
+                    const int lt = ratio_lt(Sk, A, bS, bA, &eq);
+                    if (lt) take = true;
+                    else if (eq) {
+                        const int k1 = abs(s) + abs(t), k2 = abs(bs) + abs(bt);
+                        take = (k1 < k2) || (k1 == k2 && (s < bs || (s == bs && t < bt)));
+                    }
+                }
+                if (take) { bk = u * 3 + v; bS = Sk; bA = A; bs = s; bt = t; }
+            }
+        shifts[2 * f] = bs;
+        shifts[2 * f + 1] = bt;
+        if (ffinal) ffinal[f] = (double)bS / (double)bA;
+    }
+}
+
+// For searches without a level: the searched optimum is the answer.
+static __global__ void k_copy_shifts(const int32_t* __restrict__ coarse, int32_t* __restrict__ shifts,
+                              const double* __restrict__ fbest, double* __restrict__ ffinal, int64_t T) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < 2 * T) shifts[i] = coarse[i];
+    if (ffinal && i < T) ffinal[i] = fbest[i];
+}
+
+// ---------------------------------------------------------------------------
+// Template offset c = round(mean of the searched-grid template), integer.
+// One CTA. U16: exact integer sum of the (box-summed) template; F32: FP64.
+template <bool F32>
+__global__ void __launch_bounds__(1024)
+k_template_offset(const void* __restrict__ tmpl, int m, int n, int levels, int32_t* __restrict__ coff_i,
+                  float* __restrict__ coff_f) {
+    __shared__ double redd[32];
+    __shared__ u64 redu[32];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int mc = levels ? m / 2 : m, nc = levels ? n / 2 : n;
+    const int rows = levels ? 2 * mc : mc, cols = levels ? 2 * nc : nc;
+    u64 su = 0;
+    double sd = 0.0;
+    for (int64_t k = tid; k < (int64_t)rows * cols; k += nthr) {
+        const int i = (int)(k / cols), j = (int)(k % cols);
+        if (F32) sd += (double)static_cast<const float*>(tmpl)[(int64_t)i * n + j];
+        else su += static_cast<const uint16_t*>(tmpl)[(int64_t)i * n + j];
+    }
+    su = warp_sum(su);
+    sd = warp_sum(sd);
+    if ((tid & 31) == 0) { redu[tid >> 5] = su; redd[tid >> 5] = sd; }
+    __syncthreads();
+    if (tid == 0) {
+        u64 tu = 0;
+        double td = 0.0;
+        for (int i = 0; i < (nthr + 31) / 32; ++i) { tu += redu[i]; td += redd[i]; }
+        const u64 cnt = (u64)mc * (u64)nc;
+        if (F32) {
+            const double c = rint(td / (double)cnt);
+            *coff_i = (int32_t)c;
+            *coff_f = (float)c;
+        } else {
+            const u64 c = (2 * tu + cnt) / (2 * cnt);  // round half up of the mean
+            *coff_i = (int32_t)c;
+            *coff_f = (float)c;
+        }
+    }
+}
+
+}  // namespace moco

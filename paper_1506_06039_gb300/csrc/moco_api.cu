@@ -1,0 +1,502 @@
+// The C ABI of include/moco.h: plans, workspace, validation and the launch
+// sequence of the translation search (Section 2 of the paper).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "moco.h"
+#include "plan.h"
+
+namespace moco {
+
+const char* const kKernelNames[K_COUNT] = {"k_frame_rows", "k_energy", "k_cols", "k_rows_inv", "k_jitter",
+                                           "k_copy_shifts", "k_softmin", "k_backward", "k_direct"};
+
+thread_local std::string g_last_error;
+
+moco_status fail(moco_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+moco_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(MOCO_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+DeviceGuard::DeviceGuard(int dev) {
+    cudaGetDevice(&prev_);
+    if (prev_ != dev) cudaSetDevice(dev);
+}
+DeviceGuard::~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != prev_) cudaSetDevice(prev_);
+}
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Carves one device allocation into 256-byte aligned pieces.
+struct Carver {
+    size_t off = 0;
+    std::vector<std::pair<void**, size_t>> items;
+    template <typename T>
+    void add(T** p, size_t bytes) {
+        items.push_back({reinterpret_cast<void**>(p), off});
+        off = align_up(off + std::max<size_t>(bytes, 1), 256);
+    }
+    void bind(void* base) {
+        for (auto& it : items) *it.first = static_cast<char*>(base) + it.second;
+    }
+};
+
+void host_roots(int N, std::vector<float2>& out) {
+    out.resize(N);
+    for (int j = 0; j < N; ++j) {
+        // exp(-2 pi i j / N) in FP64, rounded once to FP32.
+        const double a = 2.0 * M_PI * (double)j / (double)N;
+        out[j] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    }
+}
+
+}  // namespace
+
+int64_t per_frame_scratch_bytes(const ShapePlan& sp) {
+    const int64_t W = sp.W, wm1 = sp.wm1;
+    int64_t b = 0;
+    b += (int64_t)sp.ncv * sp.ldx * 8;        // X
+    b += W * sp.ncv * 8;                       // Y
+    b += ((int64_t)sp.mc + sp.nc + 1) * 8;     // rowE, colE, tot
+    b += 4 * wm1 * wm1 * 4;                    // corners
+    b += W * W * 8;                            // Sa
+    b += 8 + 8 + 4;                            // coarse, fbest, margin
+    b += (int64_t)sp.desc.m * sp.desc.n * 2 + 8;  // host staging (frames + shifts)
+    return b;
+}
+
+moco_status resolve_shape(const moco_shape& d, ShapePlan& sp) {
+    if (d.reserved != 0) return fail(MOCO_ERR_INVALID_ARG, "moco_shape.reserved must be 0");
+    if (d.m < 1 || d.n < 8 || d.n % 8 != 0 || d.m > 4096 || d.n > 4096)
+        return fail(MOCO_ERR_INVALID_ARG, "need 1 <= m <= 4096, 8 <= n <= 4096 and n % 8 == 0");
+    if (d.levels < -1 || d.levels > 1) return fail(MOCO_ERR_INVALID_ARG, "levels must be -1, 0 or 1");
+    if (d.template_dtype != MOCO_TEMPLATE_U16 && d.template_dtype != MOCO_TEMPLATE_F32)
+        return fail(MOCO_ERR_INVALID_ARG, "bad template_dtype");
+    if (d.xcorr < MOCO_XCORR_AUTO || d.xcorr > MOCO_XCORR_DIRECT_BF16X3)
+        return fail(MOCO_ERR_INVALID_ARG, "bad xcorr");
+    if (d.group_frames < 0) return fail(MOCO_ERR_INVALID_ARG, "group_frames must be >= 0");
+    sp.desc = d;
+    sp.levels = d.levels < 0 ? ((d.m > 256 || d.n > 256) ? 1 : 0) : d.levels;
+    sp.f32 = d.template_dtype == MOCO_TEMPLATE_F32;
+    if (sp.f32 && sp.levels != 0)
+        return fail(MOCO_ERR_UNSUPPORTED, "a float template needs levels == 0");
+    sp.mc = sp.levels ? d.m / 2 : d.m;
+    sp.nc = sp.levels ? d.n / 2 : d.n;
+    if (sp.mc < 1) return fail(MOCO_ERR_INVALID_ARG, "image too small for a 2x2 level");
+    sp.w = d.w;
+    if (d.w < 1 || 2 * d.w - 1 > sp.mc || 2 * d.w - 1 > sp.nc)
+        return fail(MOCO_ERR_INVALID_ARG, "need w >= 1 and 2w-1 <= min(mc, nc)");
+    sp.wm1 = d.w - 1;
+    sp.W = 2 * d.w - 1;
+    sp.Nr = fft_size_for(sp.mc + d.w - 1);
+    sp.Nc = fft_size_for(sp.nc + d.w - 1);
+    if (!sp.Nr || !sp.Nc)
+        return fail(MOCO_ERR_UNSUPPORTED, "searched grid + window exceeds the largest FFT length (576)");
+    sp.ncv = sp.Nc / 2 + 1;
+    sp.ldx = sp.mc + (sp.mc & 1);
+    sp.unit = sp.levels ? 1.0 / 16.0 : 1.0;
+    if (d.xcorr == MOCO_XCORR_DIRECT_BF16X3)
+        return fail(MOCO_ERR_UNSUPPORTED, "the direct BF16x3 form is not built into this library");
+    sp.form = MOCO_XCORR_FFT_FP32;
+    if (d.group_frames > 0) {
+        sp.group = d.group_frames;
+    } else {
+        const int64_t target = 96ll << 20;  // workspace target: about the L2 size
+        sp.group = (int)std::max<int64_t>(1, std::min<int64_t>(4096, target / per_frame_scratch_bytes(sp)));
+    }
+    return MOCO_OK;
+}
+
+moco_status allocate_shape(ShapePlan& sp) {
+    const int64_t G = sp.group, W = sp.W, m = sp.desc.m, n = sp.desc.n;
+    Carver c;
+    c.add(&sp.tmpl, (size_t)m * n * (sp.f32 ? 4 : 2));
+    c.add(&sp.coff_i, 4);
+    c.add(&sp.coff_f, 4);
+    c.add(&sp.twr, (size_t)sp.Nr * 8);
+    c.add(&sp.twc, (size_t)sp.Nc * 8);
+    c.add(&sp.bspec, (size_t)sp.ncv * sp.Nr * 8);
+    c.add(&sp.Sb, (size_t)W * W * 8);
+    c.add(&sp.inv_area, (size_t)W * W * 8);
+    sp.x_fstride = (int64_t)sp.ncv * sp.ldx;
+    sp.y_fstride = W * sp.ncv;
+    c.add(&sp.X, (size_t)(G * sp.x_fstride * 8));
+    c.add(&sp.Y, (size_t)(G * sp.y_fstride * 8));
+    c.add(&sp.rowE, (size_t)(G * sp.mc * 8));
+    c.add(&sp.colE, (size_t)(G * sp.nc * 8));
+    c.add(&sp.tot, (size_t)(G * 8));
+    c.add(&sp.corners, (size_t)(G * 4 * sp.wm1 * sp.wm1 * 4));
+    c.add(&sp.Sa, (size_t)(G * W * W * 8));
+    c.add(&sp.coarse, (size_t)(G * 2 * 4));
+    c.add(&sp.fbest, (size_t)(G * 8));
+    c.add(&sp.margin, (size_t)(G * 4));
+    for (int k = 0; k < 2; ++k) {
+        c.add(&sp.stage[k], (size_t)(G * m * n * 2));
+        c.add(&sp.stage_shifts[k], (size_t)(G * 2 * 4));
+    }
+    sp.bytes = c.off;
+    cudaError_t e = cudaMalloc(&sp.base, sp.bytes);
+    if (e != cudaSuccess) {
+        sp.base = nullptr;
+        cudaGetLastError();
+        return fail(MOCO_ERR_OOM, "cudaMalloc of " + std::to_string(sp.bytes) + " bytes failed");
+    }
+    c.bind(sp.base);
+    // Host-computed constant tables.
+    std::vector<float2> tw;
+    host_roots(sp.Nr, tw);
+    e = cudaMemcpy(sp.twr, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload of row roots");
+    host_roots(sp.Nc, tw);
+    e = cudaMemcpy(sp.twc, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload of column roots");
+    std::vector<double> ia((size_t)W * W);
+    for (int s = -sp.wm1; s <= sp.wm1; ++s)
+        for (int t = -sp.wm1; t <= sp.wm1; ++t)
+            ia[(size_t)(s + sp.wm1) * W + (t + sp.wm1)] =
+                1.0 / ((double)(sp.mc - std::abs(s)) * (double)(sp.nc - std::abs(t)));
+    e = cudaMemcpy(sp.inv_area, ia.data(), ia.size() * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload of 1/Area");
+    return MOCO_OK;
+}
+
+// Offset, energies and spectrum of the template (run whenever it changes).
+moco_status prepare_template(ShapePlan& sp, const void* tmpl_dev, cudaStream_t st) {
+    const size_t bytes = (size_t)sp.desc.m * sp.desc.n * (sp.f32 ? 4 : 2);
+    cudaError_t e = cudaMemcpyAsync(sp.tmpl, tmpl_dev, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "template copy");
+    e = launch_template_offset(sp.f32, sp.tmpl, sp.desc.m, sp.desc.n, sp.levels, sp.coff_i, sp.coff_f, st);
+    if (e != cudaSuccess) return cuda_fail(e, "template offset");
+    e = launch_frame_rows(sp.Nc, sp.f32, sp.tmpl, 0, 1, sp.desc.m, sp.desc.n, sp.levels, sp.mc, sp.nc,
+                          sp.coff_i, sp.coff_f, sp.twc, sp.X, sp.x_fstride, sp.ldx, sp.rowE, sp.colE, sp.tot,
+                          sp.corners, sp.wm1, st);
+    if (e != cudaSuccess) return cuda_fail(e, "template rows");
+    e = launch_energy(sp.f32, true, sp.rowE, sp.colE, sp.tot, sp.corners, 1, sp.mc, sp.nc, sp.wm1, sp.Sb, 1, st);
+    if (e != cudaSuccess) return cuda_fail(e, "template energies");
+    e = launch_cols(sp.Nr, true, sp.X, sp.x_fstride, sp.ldx, sp.mc, sp.ncv, 1, sp.twr, nullptr, sp.bspec, 0,
+                    sp.wm1, (float)(1.0 / ((double)sp.Nr * (double)sp.Nc)), st);
+    if (e != cudaSuccess) return cuda_fail(e, "template spectrum");
+    return MOCO_OK;
+}
+
+// The searched-grid pass over frames [f0, f0+g) staged at `frames`:
+// energies, cross term, combine, argmin -> sp.coarse (and optional outputs).
+moco_status search_group(ShapePlan& sp, const uint16_t* frames, int64_t g, double* cost, double* fbest,
+                         float* margin, cudaStream_t st) {
+    const int m = sp.desc.m, n = sp.desc.n;
+    Profiler& P = *sp.prof;
+    P.begin(K_FRAME_ROWS, st);
+    cudaError_t e = launch_frame_rows(sp.Nc, false, frames, (int64_t)m * n, g, m, n, sp.levels, sp.mc, sp.nc,
+                                      sp.coff_i, nullptr, sp.twc, sp.X, sp.x_fstride, sp.ldx, sp.rowE, sp.colE,
+                                      sp.tot, sp.corners, sp.wm1, st);
+    P.end(st);
+    if (e != cudaSuccess) return cuda_fail(e, "k_frame_rows");
+    P.begin(K_ENERGY, st);
+    e = launch_energy(false, false, sp.rowE, sp.colE, sp.tot, sp.corners, g, sp.mc, sp.nc, sp.wm1, sp.Sa, 0, st);
+    P.end(st);
+    if (e != cudaSuccess) return cuda_fail(e, "k_energy");
+    P.begin(K_COLS, st);
+    e = launch_cols(sp.Nr, false, sp.X, sp.x_fstride, sp.ldx, sp.mc, sp.ncv, g, sp.twr, sp.bspec, sp.Y,
+                    sp.y_fstride, sp.wm1, 0.f, st);
+    P.end(st);
+    if (e != cudaSuccess) return cuda_fail(e, "k_cols");
+    P.begin(K_ROWS_INV, st);
+    e = launch_rows_inv(sp.Nc, sp.Y, sp.y_fstride, sp.ncv, sp.wm1, g, sp.twc, sp.Sa, sp.Sb, sp.inv_area, sp.unit,
+                        cost, sp.coarse, fbest ? fbest : sp.fbest, margin ? margin : sp.margin, st);
+    P.end(st);
+    if (e != cudaSuccess) return cuda_fail(e, "k_rows_inv");
+    return MOCO_OK;
+}
+
+moco_status align_frames(ShapePlan& sp, const uint16_t* frames, int64_t T, int32_t* shifts, double* best_cost,
+                         float* margin, cudaStream_t st) {
+    const int64_t mn = (int64_t)sp.desc.m * sp.desc.n;
+    for (int64_t f0 = 0; f0 < T; f0 += sp.group) {
+        const int64_t g = std::min<int64_t>(sp.group, T - f0);
+        moco_status s = search_group(sp, frames + f0 * mn, g, nullptr, best_cost ? best_cost + f0 : nullptr,
+                                     margin ? margin + f0 : nullptr, st);
+        if (s != MOCO_OK) return s;
+        cudaError_t e;
+        sp.prof->begin(sp.levels ? K_JITTER : K_COPY_SHIFTS, st);
+        if (sp.levels)
+            e = launch_jitter(frames + f0 * mn, mn, g, static_cast<const uint16_t*>(sp.tmpl), sp.desc.m,
+                              sp.desc.n, sp.coarse, shifts + 2 * f0, nullptr, st);
+        else
+            e = launch_copy_shifts(sp.coarse, shifts + 2 * f0, nullptr, nullptr, g, st);
+        sp.prof->end(st);
+        if (e != cudaSuccess) return cuda_fail(e, sp.levels ? "k_jitter" : "k_copy_shifts");
+    }
+    return MOCO_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+}  // namespace moco
+
+using namespace moco;
+
+extern "C" {
+
+const char* moco_status_string(moco_status s) {
+    switch (s) {
+        case MOCO_OK: return "MOCO_OK";
+        case MOCO_ERR_INVALID_ARG: return "MOCO_ERR_INVALID_ARG";
+        case MOCO_ERR_UNSUPPORTED: return "MOCO_ERR_UNSUPPORTED";
+        case MOCO_ERR_OOM: return "MOCO_ERR_OOM";
+        case MOCO_ERR_CUDA: return "MOCO_ERR_CUDA";
+        case MOCO_ERR_TIMEOUT: return "MOCO_ERR_TIMEOUT";
+    }
+    return "MOCO_ERR_UNKNOWN";
+}
+
+const char* moco_last_error(void) { return g_last_error.c_str(); }
+
+moco_status moco_plan_destroy(moco_plan_t plan) {
+    if (!plan) return fail(MOCO_ERR_INVALID_ARG, "null plan");
+    DeviceGuard guard(plan->device);
+    cudaDeviceSynchronize();
+    for (auto& sp : plan->shapes)
+        if (sp.base) cudaFree(sp.base);
+    if (plan->aux) cudaStreamDestroy(plan->aux);
+    for (auto& ev : plan->prof.pool) cudaEventDestroy(ev);
+    for (auto& ev : plan->ev)
+        if (ev) cudaEventDestroy(ev);
+    delete plan;
+    return MOCO_OK;
+}
+
+moco_status moco_plan(const moco_shape* shapes, int32_t nshapes, const void* const* templates_dev, void* stream,
+                      moco_plan_t* out) {
+    g_last_error.clear();
+    if (!out) return fail(MOCO_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    if (!shapes || nshapes < 1 || !templates_dev) return fail(MOCO_ERR_INVALID_ARG, "need shapes and templates");
+    for (int k = 0; k < nshapes; ++k)
+        if (!templates_dev[k]) return fail(MOCO_ERR_INVALID_ARG, "null template pointer");
+    moco_plan_t plan = new moco_plan_s();
+    cudaGetDevice(&plan->device);
+    plan->shapes.resize(nshapes);
+    for (auto& sp : plan->shapes) sp.prof = &plan->prof;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    moco_status s = MOCO_OK;
+    for (int k = 0; k < nshapes && s == MOCO_OK; ++k) s = resolve_shape(shapes[k], plan->shapes[k]);
+    for (int k = 0; k < nshapes && s == MOCO_OK; ++k) s = allocate_shape(plan->shapes[k]);
+    for (int k = 0; k < nshapes && s == MOCO_OK; ++k) s = prepare_template(plan->shapes[k], templates_dev[k], st);
+    if (s == MOCO_OK) {
+        cudaError_t e = cudaStreamCreateWithFlags(&plan->aux, cudaStreamNonBlocking);
+        for (auto& ev : plan->ev)
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(e, "plan set-up");
+    }
+    if (s != MOCO_OK) {
+        std::string msg = g_last_error;
+        moco_plan_destroy(plan);
+        g_last_error = msg;
+        return s;
+    }
+    *out = plan;
+    return MOCO_OK;
+}
+
+moco_status moco_set_template(moco_plan_t plan, int32_t shape_idx, const void* template_dev, void* stream) {
+    if (!plan || !template_dev) return fail(MOCO_ERR_INVALID_ARG, "null plan or template");
+    if (shape_idx < 0 || shape_idx >= (int)plan->shapes.size()) return fail(MOCO_ERR_INVALID_ARG, "bad shape_idx");
+    DeviceGuard guard(plan->device);
+    return prepare_template(plan->shapes[shape_idx], template_dev, static_cast<cudaStream_t>(stream));
+}
+
+moco_status moco_plan_query(moco_plan_t plan, int32_t shape_idx, moco_shape_info* info) {
+    if (!plan || !info) return fail(MOCO_ERR_INVALID_ARG, "null plan or info");
+    if (shape_idx < 0 || shape_idx >= (int)plan->shapes.size()) return fail(MOCO_ERR_INVALID_ARG, "bad shape_idx");
+    const ShapePlan& sp = plan->shapes[shape_idx];
+    DeviceGuard guard(plan->device);
+    int32_t off = 0;
+    cudaError_t e = cudaMemcpy(&off, sp.coff_i, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "offset read-back");
+    info->levels = sp.levels;
+    info->mc = sp.mc;
+    info->nc = sp.nc;
+    info->fft_rows = sp.Nr;
+    info->fft_cols = sp.Nc;
+    info->xcorr = sp.form;
+    info->group_frames = sp.group;
+    info->offset = off;
+    info->workspace_bytes = (int64_t)sp.bytes;
+    return MOCO_OK;
+}
+
+moco_status moco_align_stack(moco_plan_t plan, const moco_stack* stacks, int32_t nstacks, void* stream) {
+    if (!plan || (nstacks > 0 && !stacks) || nstacks < 0) return fail(MOCO_ERR_INVALID_ARG, "null plan or stacks");
+    for (int k = 0; k < nstacks; ++k) {
+        const moco_stack& s = stacks[k];
+        if (s.shape_idx < 0 || s.shape_idx >= (int)plan->shapes.size()) return fail(MOCO_ERR_INVALID_ARG, "bad shape_idx");
+        if (s.reserved != 0 || s.T < 0) return fail(MOCO_ERR_INVALID_ARG, "bad stack");
+        if (s.T > 0 && (!s.frames_dev || !s.shifts_dev)) return fail(MOCO_ERR_INVALID_ARG, "null frames or shifts");
+        if (s.T > 0 && !aligned16(s.frames_dev)) return fail(MOCO_ERR_INVALID_ARG, "frames must be 16-byte aligned");
+        if (plan->shapes[s.shape_idx].f32 && s.T > 0 && plan->shapes[s.shape_idx].levels)
+            return fail(MOCO_ERR_UNSUPPORTED, "float template with levels");
+    }
+    DeviceGuard guard(plan->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int k = 0; k < nstacks; ++k) {
+        const moco_stack& s = stacks[k];
+        if (s.T == 0) continue;
+        moco_status r = align_frames(plan->shapes[s.shape_idx], s.frames_dev, s.T, s.shifts_dev, s.best_cost_dev,
+                                     s.margin_dev, st);
+        if (r != MOCO_OK) return r;
+    }
+    return MOCO_OK;
+}
+
+moco_status moco_cost_surface(moco_plan_t plan, int32_t shape_idx, const uint16_t* frames_dev, int64_t T,
+                              double* cost_dev, void* stream) {
+    if (!plan) return fail(MOCO_ERR_INVALID_ARG, "null plan");
+    if (shape_idx < 0 || shape_idx >= (int)plan->shapes.size()) return fail(MOCO_ERR_INVALID_ARG, "bad shape_idx");
+    if (T < 0) return fail(MOCO_ERR_INVALID_ARG, "T < 0");
+    if (T == 0) return MOCO_OK;
+    if (!frames_dev || !cost_dev) return fail(MOCO_ERR_INVALID_ARG, "null frames or cost");
+    if (!aligned16(frames_dev)) return fail(MOCO_ERR_INVALID_ARG, "frames must be 16-byte aligned");
+    DeviceGuard guard(plan->device);
+    ShapePlan& sp = plan->shapes[shape_idx];
+    const int64_t mn = (int64_t)sp.desc.m * sp.desc.n, WW = (int64_t)sp.W * sp.W;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int64_t f0 = 0; f0 < T; f0 += sp.group) {
+        const int64_t g = std::min<int64_t>(sp.group, T - f0);
+        moco_status s = search_group(sp, frames_dev + f0 * mn, g, cost_dev + f0 * WW, nullptr, nullptr, st);
+        if (s != MOCO_OK) return s;
+    }
+    return MOCO_OK;
+}
+
+moco_status moco_softmin(moco_plan_t plan, int32_t shape_idx, const double* cost_dev, int64_t T, double tau_scale,
+                         double* loss_dev, float* weights_dev, void* stream) {
+    (void)plan; (void)shape_idx; (void)cost_dev; (void)T; (void)tau_scale; (void)loss_dev; (void)weights_dev;
+    (void)stream;
+    return fail(MOCO_ERR_UNSUPPORTED, "moco_softmin is not built into this library yet");
+}
+
+moco_status moco_cost_backward(moco_plan_t plan, int32_t shape_idx, const uint16_t* frames_dev, int64_t T,
+                               const float* grad_cost_dev, float* grad_template_dev, float* grad_frames_dev,
+                               void* stream) {
+    (void)plan; (void)shape_idx; (void)frames_dev; (void)T; (void)grad_cost_dev; (void)grad_template_dev;
+    (void)grad_frames_dev; (void)stream;
+    return fail(MOCO_ERR_UNSUPPORTED, "moco_cost_backward is not built into this library yet");
+}
+
+moco_status moco_profile_enable(moco_plan_t plan, int32_t max_launches) {
+    if (!plan || max_launches < 0) return fail(MOCO_ERR_INVALID_ARG, "null plan or negative size");
+    DeviceGuard guard(plan->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "moco_profile_enable");
+    Profiler& P = plan->prof;
+    for (auto& ev : P.pool) cudaEventDestroy(ev);
+    P.pool.clear();
+    P.marks.clear();
+    P.used = 0;
+    P.truncated = false;
+    P.on = max_launches > 0;
+    for (int32_t k = 0; k < 2 * max_launches; ++k) {
+        cudaEvent_t ev;
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) {
+            P.on = false;
+            return cuda_fail(e, "event pool");
+        }
+        P.pool.push_back(ev);
+    }
+    return MOCO_OK;
+}
+
+moco_status moco_profile_read(moco_plan_t plan, moco_kernel_stat* stats, int32_t capacity, int32_t* count,
+                              int32_t reset) {
+    if (!plan || !count || capacity < 0 || (capacity > 0 && !stats)) return fail(MOCO_ERR_INVALID_ARG, "bad arguments");
+    Profiler& P = plan->prof;
+    if (!P.on) return fail(MOCO_ERR_INVALID_ARG, "profiling is not enabled");
+    DeviceGuard guard(plan->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "moco_profile_read");
+    int64_t launches[K_COUNT] = {0};
+    double ms[K_COUNT] = {0};
+    for (auto& mk : P.marks) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, P.pool[mk.second], P.pool[mk.second + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        launches[mk.first] += 1;
+        ms[mk.first] += t;
+    }
+    int32_t c = 0;
+    for (int k = 0; k < K_COUNT; ++k) {
+        if (!launches[k]) continue;
+        if (c < capacity) {
+            std::memset(stats[c].name, 0, sizeof(stats[c].name));
+            std::strncpy(stats[c].name, kKernelNames[k], sizeof(stats[c].name) - 1);
+            stats[c].launches = launches[k];
+            stats[c].total_ms = ms[k];
+        }
+        ++c;
+    }
+    *count = c;
+    if (reset) {
+        P.marks.clear();
+        P.used = 0;
+        P.truncated = false;
+    }
+    return MOCO_OK;
+}
+
+moco_status moco_align_host(moco_plan_t plan, int32_t shape_idx, const uint16_t* frames_host, int64_t T,
+                            int32_t* shifts_host, void* stream) {
+    if (!plan) return fail(MOCO_ERR_INVALID_ARG, "null plan");
+    if (shape_idx < 0 || shape_idx >= (int)plan->shapes.size()) return fail(MOCO_ERR_INVALID_ARG, "bad shape_idx");
+    if (T < 0) return fail(MOCO_ERR_INVALID_ARG, "T < 0");
+    if (T == 0) return MOCO_OK;
+    if (!frames_host || !shifts_host) return fail(MOCO_ERR_INVALID_ARG, "null frames or shifts");
+    DeviceGuard guard(plan->device);
+    ShapePlan& sp = plan->shapes[shape_idx];
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStream_t cp = plan->aux;
+    cudaEvent_t copied[2] = {plan->ev[0], plan->ev[1]}, done[2] = {plan->ev[2], plan->ev[3]};
+    const int64_t mn = (int64_t)sp.desc.m * sp.desc.n;
+    cudaError_t e = cudaEventRecord(done[0], st);
+    if (e == cudaSuccess) e = cudaEventRecord(done[1], st);
+    if (e != cudaSuccess) return cuda_fail(e, "event record");
+    int k = 0;
+    for (int64_t f0 = 0; f0 < T; f0 += sp.group, k ^= 1) {
+        const int64_t g = std::min<int64_t>(sp.group, T - f0);
+        // The copy into staging buffer k waits for the compute that last used it.
+        e = cudaStreamWaitEvent(cp, done[k], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sp.stage[k], frames_host + f0 * mn, (size_t)(g * mn * 2), cudaMemcpyHostToDevice, cp);
+        if (e == cudaSuccess) e = cudaEventRecord(copied[k], cp);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, copied[k], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "host-to-device staging");
+        moco_status s = align_frames(sp, sp.stage[k], g, sp.stage_shifts[k], nullptr, nullptr, st);
+        if (s != MOCO_OK) return s;
+        e = cudaMemcpyAsync(shifts_host + 2 * f0, sp.stage_shifts[k], (size_t)(g * 8), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaEventRecord(done[k], st);
+        if (e != cudaSuccess) return cuda_fail(e, "device-to-host shifts");
+    }
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "moco_align_host");
+    return MOCO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+// Plan state shared by the host-side translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "moco.h"
+
+namespace moco {
+
+// Optional per-kernel timing: CUDA events recorded on the launching stream
+// around every kernel launch (enabled by moco_profile_enable).
+enum KernelId { K_FRAME_ROWS = 0, K_ENERGY, K_COLS, K_ROWS_INV, K_JITTER, K_COPY_SHIFTS, K_SOFTMIN,
+                K_BACKWARD, K_DIRECT, K_COUNT };
+extern const char* const kKernelNames[K_COUNT];
+
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<std::pair<int, size_t>> marks;  // kernel id, index of its start event
+    bool truncated = false;
+    void begin(int kid, cudaStream_t st) {
+        if (!on) return;
+        if (used + 2 > pool.size()) { truncated = true; return; }
+        cudaEventRecord(pool[used], st);
+        marks.push_back({kid, used});
+    }
+    void end(cudaStream_t st) {
+        if (!on || marks.empty() || marks.back().second != used) return;
+        cudaEventRecord(pool[used + 1], st);
+        used += 2;
+    }
+};
+
+// Everything one shape of a plan owns. All device pointers are carved from
+// the single allocation `base` (bytes long).
+struct ShapePlan {
+    moco_shape desc{};
+    int levels = 0, mc = 0, nc = 0, w = 0, wm1 = 0, W = 0;
+    int Nr = 0, Nc = 0, ncv = 0, ldx = 0;
+    int form = MOCO_XCORR_FFT_FP32;
+    int group = 1;
+    bool f32 = false;
+    double unit = 1.0;
+    int64_t x_fstride = 0, y_fstride = 0;
+    void* base = nullptr;
+    size_t bytes = 0;
+    // template-derived data
+    void* tmpl = nullptr;
+    int32_t* coff_i = nullptr;
+    float* coff_f = nullptr;
+    float2* twr = nullptr;
+    float2* twc = nullptr;
+    float2* bspec = nullptr;
+    double* Sb = nullptr;
+    double* inv_area = nullptr;
+    // per-group scratch
+    float2* X = nullptr;
+    float2* Y = nullptr;
+    u64* rowE = nullptr;
+    u64* colE = nullptr;
+    u64* tot = nullptr;
+    uint32_t* corners = nullptr;
+    u64* Sa = nullptr;
+    int32_t* coarse = nullptr;
+    double* fbest = nullptr;
+    float* margin = nullptr;
+    // staging for moco_align_host (double-buffered)
+    uint16_t* stage[2] = {nullptr, nullptr};
+    int32_t* stage_shifts[2] = {nullptr, nullptr};
+    Profiler* prof = nullptr;  // the owning plan's profiler
+};
+
+struct DeviceGuard {
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+    int prev_ = 0;
+};
+
+moco_status fail(moco_status s, const std::string& msg);
+moco_status cuda_fail(cudaError_t e, const char* what);
+
+}  // namespace moco
+
+struct moco_plan_s {
+    int device = 0;
+    std::vector<moco::ShapePlan> shapes;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    moco::Profiler prof;
+};

@@ -1,0 +1,94 @@
+// Energies, jitter, template offset, and small host helpers.
+#include <mutex>
+#include <set>
+#include <tuple>
+
+#include "fft_sizes.h"
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace moco {
+
+bool fft_size_supported(int N) {
+#define MOCO_CASE(NN) if (N == NN) return true;
+    MOCO_FOR_EACH_FFT_SIZE(MOCO_CASE)
+#undef MOCO_CASE
+    return false;
+}
+
+int fft_size_for(int needed) {
+    int best = 0;
+#define MOCO_CASE(NN) if (NN >= needed && (best == 0 || NN < best)) best = NN;
+    MOCO_FOR_EACH_FFT_SIZE(MOCO_CASE)
+#undef MOCO_CASE
+    return best;
+}
+
+int fft_split_max(int N) {
+#define MOCO_CASE(NN) if (N == NN) return Four<NN>::N1 > Four<NN>::N2 ? Four<NN>::N1 : Four<NN>::N2;
+    MOCO_FOR_EACH_FFT_SIZE(MOCO_CASE)
+#undef MOCO_CASE
+    return 0;
+}
+
+cudaError_t ensure_smem(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::set<std::tuple<const void*, int, size_t>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_tuple(func, dev, bytes);
+    if (done.count(key)) return cudaSuccess;
+    if (bytes > 48 * 1024) {
+        e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+    }
+    done.insert(key);
+    return cudaSuccess;
+}
+
+cudaError_t launch_energy(bool f32, bool out_double, const u64* rowE, const u64* colE, const u64* tot,
+                          const uint32_t* corners, int64_t nimg, int mc, int nc, int wm1, void* out, int flip,
+                          cudaStream_t st) {
+    if (nimg <= 0) return cudaSuccess;
+    const int W = 2 * wm1 + 1, w = wm1 + 1;
+    const size_t smem = sizeof(u64) * (2 * W + w * w);
+    const void* fn = f32 ? (out_double ? (const void*)k_energy<true, true> : (const void*)k_energy<true, false>)
+                         : (out_double ? (const void*)k_energy<false, true> : (const void*)k_energy<false, false>);
+    cudaError_t e = ensure_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    if (f32) {
+        if (out_double) k_energy<true, true><<<(unsigned)nimg, kEnergyThreads, smem, st>>>(rowE, colE, tot, corners, mc, nc, wm1, out, flip);
+        else k_energy<true, false><<<(unsigned)nimg, kEnergyThreads, smem, st>>>(rowE, colE, tot, corners, mc, nc, wm1, out, flip);
+    } else {
+        if (out_double) k_energy<false, true><<<(unsigned)nimg, kEnergyThreads, smem, st>>>(rowE, colE, tot, corners, mc, nc, wm1, out, flip);
+        else k_energy<false, false><<<(unsigned)nimg, kEnergyThreads, smem, st>>>(rowE, colE, tot, corners, mc, nc, wm1, out, flip);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg, const uint16_t* tmpl, int m,
+                          int n, const int32_t* coarse, int32_t* shifts, double* ffinal, cudaStream_t st) {
+    if (nimg <= 0) return cudaSuccess;
+    k_jitter<<<(unsigned)nimg, kJitterThreads, 0, st>>>(frames, fstride, tmpl, m, n, coarse, shifts, ffinal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_shifts(const int32_t* coarse, int32_t* shifts, const double* fbest, double* ffinal,
+                               int64_t T, cudaStream_t st) {
+    if (T <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t blocks = (2 * T + threads - 1) / threads;
+    k_copy_shifts<<<(unsigned)blocks, threads, 0, st>>>(coarse, shifts, fbest, ffinal, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_template_offset(bool f32, const void* tmpl, int m, int n, int levels, int32_t* coff_i,
+                                   float* coff_f, cudaStream_t st) {
+    if (f32) k_template_offset<true><<<1, 1024, 0, st>>>(tmpl, m, n, levels, coff_i, coff_f);
+    else k_template_offset<false><<<1, 1024, 0, st>>>(tmpl, m, n, levels, coff_i, coff_f);
+    return cudaGetLastError();
+}
+
+}  // namespace moco

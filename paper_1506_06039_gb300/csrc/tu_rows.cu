@@ -1,0 +1,76 @@
+// Row passes: k_frame_rows (forward) and k_rows_inv (inverse + combine + argmin).
+#include "fft_sizes.h"
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace moco {
+
+template <int N, bool F32>
+static cudaError_t frame_rows_n(const void* src, int64_t src_fstride, int64_t nimg, int m, int n, int levels,
+                                int mc, int nc, const int32_t* coff_i, const float* coff_f, const float2* tw,
+                                float2* X, int64_t x_fstride, int ldx, u64* rowE, u64* colE, u64* tot,
+                                uint32_t* corners, int wm1, cudaStream_t st) {
+    const size_t smem = sizeof(float2) * ((kRC / 2) * N + N) + sizeof(u64) * (kRC + nc);
+    const void* fn = (const void*)k_frame_rows<N, F32>;
+    cudaError_t e = ensure_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    k_frame_rows<N, F32><<<(unsigned)nimg, kRowsThreads, smem, st>>>(src, src_fstride, m, n, levels, mc, nc,
+                                                                      coff_i, coff_f, tw, X, x_fstride, ldx,
+                                                                      rowE, colE, tot, corners, wm1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_frame_rows(int N, bool f32, const void* src, int64_t src_fstride, int64_t nimg, int m,
+                              int n, int levels, int mc, int nc, const int32_t* coff_i, const float* coff_f,
+                              const float2* tw, float2* X, int64_t x_fstride, int ldx, u64* rowE, u64* colE,
+                              u64* tot, uint32_t* corners, int wm1, cudaStream_t st) {
+    if (nimg <= 0) return cudaSuccess;
+#define MOCO_CASE(NN)                                                                                     \
+    case NN:                                                                                              \
+        return f32 ? frame_rows_n<NN, true>(src, src_fstride, nimg, m, n, levels, mc, nc, coff_i, coff_f, \
+                                            tw, X, x_fstride, ldx, rowE, colE, tot, corners, wm1, st)     \
+                   : frame_rows_n<NN, false>(src, src_fstride, nimg, m, n, levels, mc, nc, coff_i,        \
+                                             coff_f, tw, X, x_fstride, ldx, rowE, colE, tot, corners,     \
+                                             wm1, st);
+    switch (N) {
+        MOCO_FOR_EACH_FFT_SIZE(MOCO_CASE)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef MOCO_CASE
+}
+
+template <int N>
+static cudaError_t rows_inv_n(const float2* Y, int64_t y_fstride, int ncv, int wm1, int64_t nimg,
+                              const float2* tw, const u64* Sa, const double* Sb, const double* inv_area,
+                              double unit, double* cost, int32_t* coarse, double* fbest, float* margin,
+                              cudaStream_t st) {
+    const int W = 2 * wm1 + 1;
+    const size_t smem = sizeof(float2) * (kInvPC * N + N) + sizeof(float) * W * W;
+    const void* fn = (const void*)k_rows_inv<N>;
+    cudaError_t e = ensure_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    int threads = kInvPC * (Four<N>::N1 > Four<N>::N2 ? Four<N>::N1 : Four<N>::N2);
+    threads = (threads + 31) / 32 * 32;
+    k_rows_inv<N><<<(unsigned)nimg, threads, smem, st>>>(Y, y_fstride, ncv, wm1, tw, Sa, Sb, inv_area, unit,
+                                                         cost, coarse, fbest, margin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_inv(int N, const float2* Y, int64_t y_fstride, int ncv, int wm1, int64_t nimg,
+                            const float2* tw, const u64* Sa, const double* Sb, const double* inv_area,
+                            double unit, double* cost, int32_t* coarse, double* fbest, float* margin,
+                            cudaStream_t st) {
+    if (nimg <= 0) return cudaSuccess;
+#define MOCO_CASE(NN) \
+    case NN:          \
+        return rows_inv_n<NN>(Y, y_fstride, ncv, wm1, nimg, tw, Sa, Sb, inv_area, unit, cost, coarse, fbest, margin, st);
+    switch (N) {
+        MOCO_FOR_EACH_FFT_SIZE(MOCO_CASE)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef MOCO_CASE
+}
+
+}  // namespace moco

@@ -1,0 +1,45 @@
+"""Comparison rules between the CUDA path and the oracle (shared by GPU tests).
+
+Tolerances, derived from the arithmetic: the cross term is FP32 (FFT) or
+BF16 hi+lo with FP32 accumulation; energies are exact int64; the combine is
+FP64. The cost surface must agree with the oracle's FP64 value within 1e-4
+relative, pointwise, with a floor of 1e-6 * max f for values near zero. The
+argmin must equal the oracle's on every frame whose oracle margin
+(f2 - f1) / f1 exceeds 1e-5; below that margin (near-ties, which an FP32
+cross term cannot resolve) the CUDA optimum's cost must still be within the
+cost tolerance of the oracle's best. Full-resolution jitter sums are exact
+int64 on both sides, so when the searched-grid optimum agrees the final
+shift must be identical.
+"""
+import numpy as np
+
+import oracle
+
+COST_RTOL = 1e-4
+COST_FLOOR = 1e-6
+MARGIN = 1e-5
+
+
+def cost_rel_err(gpu, ref):
+    gpu = np.asarray(gpu, np.float64)
+    ref = np.asarray(ref, np.float64)
+    floor = COST_FLOOR * ref.reshape(ref.shape[0], -1).max(axis=1)
+    floor = floor.reshape((-1,) + (1,) * (ref.ndim - 1))
+    return float((np.abs(gpu - ref) / np.maximum(np.abs(ref), floor)).max())
+
+
+def check_align(frames, template, w, levels, shifts_gpu, best_gpu=None, ref=None, nthreads=0):
+    """Returns (oracle result, number of frames exempt by margin)."""
+    if ref is None:
+        ref = oracle.align(frames, template, w, levels=levels, nthreads=nthreads)
+    shifts_gpu = np.asarray(shifts_gpu)
+    decided = ref["margin"] > MARGIN
+    bad = np.nonzero(decided & np.any(shifts_gpu != ref["shifts"], axis=1))[0]
+    assert bad.size == 0, "frames %s: gpu %s vs oracle %s (margins %s)" % (
+        bad[:8], shifts_gpu[bad[:8]].tolist(), ref["shifts"][bad[:8]].tolist(), ref["margin"][bad[:8]])
+    if best_gpu is not None:
+        best_gpu = np.asarray(best_gpu, np.float64)
+        floor = COST_FLOOR * np.maximum(ref["fbest"].max(), 1.0)
+        err = np.abs(best_gpu - ref["fbest"]) / np.maximum(ref["fbest"], floor)
+        assert err.max() <= COST_RTOL, "best cost rel err %g" % err.max()
+    return ref, int((~decided).sum())

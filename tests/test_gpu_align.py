@@ -1,0 +1,164 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1506_06039_gb300 import Plan, build, synth
+
+from parity import COST_RTOL, check_align, cost_rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def run_align(frames, tmpl, w, levels=-1, **shape_kw):
+    m, n = tmpl.shape
+    with Plan(dict(m=m, n=n, w=w, levels=levels, **shape_kw), dev(tmpl)) as plan:
+        shifts, best, margin = plan.align(dev(frames), best_cost=True, margin=True)
+        torch.cuda.synchronize()
+        return shifts.cpu().numpy(), best.cpu().numpy(), margin.cpu().numpy(), plan.info()
+
+
+def test_tiny128_workload_matches_oracle():
+    wl = synth.WORKLOADS["tiny128"]
+    st = synth.make_stack_np(wl.m, wl.n, wl.T, wl.nblobs, wl.shift_max, wl.seed, template=wl.template)
+    shifts, best, margin, info = run_align(st.frames, st.template, wl.w)
+    assert info["levels"] == 0 and info["fft_rows"] >= 128 + wl.w - 1
+    ref, exempt = check_align(st.frames, st.template, wl.w, -1, shifts, best)
+    assert exempt == 0
+    # the planted shifts are recovered on this clean-template stack
+    assert np.array_equal(shifts, st.shifts)
+
+
+def test_tiny128_cost_surface_within_tolerance():
+    wl = synth.WORKLOADS["tiny128"]
+    st = synth.make_stack_np(wl.m, wl.n, 16, wl.nblobs, wl.shift_max, wl.seed, template=wl.template)
+    with Plan(dict(m=wl.m, n=wl.n, w=wl.w), dev(st.template)) as plan:
+        cost = plan.cost_surface(dev(st.frames)).cpu().numpy()
+    ref = oracle.cost_surface(st.frames, st.template, wl.w)
+    assert cost_rel_err(cost, ref) <= COST_RTOL
+
+
+@pytest.mark.parametrize("m,n,w,levels", [
+    (72, 56, 7, 0),      # ragged, non-square, no level
+    (40, 48, 1, 0),      # a single shift
+    (33, 64, 17, 0),     # widest window: 2w - 1 == m
+    (300, 264, 9, -1),   # one 2x2 level (max > 256), ragged searched grid 150 x 132
+    (301, 272, 6, 1),    # odd m with a level: the last row is dropped
+])
+def test_ragged_shapes_match_oracle(m, n, w, levels):
+    st = synth.make_stack_np(m, n, 7, max(4, m * n // 1500), min(w - 1, 5) * (2 if levels else 1),
+                             seed=m * 1000 + n, template="clean")
+    shifts, best, _, _ = run_align(st.frames, st.template, w, levels)
+    check_align(st.frames, st.template, w, levels, shifts, best)
+    with Plan(dict(m=m, n=n, w=w, levels=levels), dev(st.template)) as plan:
+        cost = plan.cost_surface(dev(st.frames[:3])).cpu().numpy()
+    assert cost_rel_err(cost, oracle.cost_surface(st.frames[:3], st.template, w, levels=levels)) <= COST_RTOL
+
+
+@pytest.mark.parametrize("s0,t0", [(7, -5), (-13, 3), (1, 1), (0, -9)])
+def test_planted_odd_shift_full_resolution_exact(s0, t0):
+    # Noiseless frame = template moved by (s0, t0): f is exactly 0 there and the
+    # jitter at full resolution must land on it.
+    m = n = 320
+    st = synth.make_stack_np(m, n, 1, 60, 0, seed=31 + s0, template="clean", noise=False)
+    b = st.template
+    a = np.full((m, n), 100, np.uint16)
+    a[max(0, s0):min(m, m + s0), max(0, t0):min(n, n + t0)] = \
+        b[max(0, -s0):min(m, m - s0), max(0, -t0):min(n, n - t0)]
+    shifts, best, _, _ = run_align(a[None], b, 12)
+    assert tuple(shifts[0]) == (s0, t0)
+    check_align(a[None], b, 12, -1, shifts, best)
+
+
+def test_identity_and_constant_frames():
+    rng = np.random.default_rng(3)
+    b = rng.integers(0, 3000, (64, 64)).astype(np.uint16)
+    frames = np.stack([b, np.full_like(b, 500), np.full_like(b, int(b.mean().round()))])
+    shifts, best, margin, _ = run_align(frames, b, 9)
+    assert tuple(shifts[0]) == (0, 0) and best[0] == 0.0
+    check_align(frames, b, 9, -1, shifts, best)
+    c = np.full((64, 64), 700, np.uint16)
+    shifts, best, margin, _ = run_align(np.stack([c, c]), c, 5)
+    assert np.all(shifts == 0) and np.all(best == 0.0)
+
+
+def test_empty_and_single_frame():
+    st = synth.make_stack_np(64, 64, 1, 10, 3, seed=5, template="clean")
+    with Plan(dict(m=64, n=64, w=6), dev(st.template)) as plan:
+        out = plan.align(dev(st.frames[:0]))
+        assert out.shape == (0, 2)
+        one = plan.align(dev(st.frames[:1])).cpu().numpy()
+    check_align(st.frames[:1], st.template, 6, -1, one)
+
+
+def test_group_boundaries_do_not_change_results():
+    st = synth.make_stack_np(96, 96, 23, 20, 6, seed=77, template="clean")
+    a, _, _, _ = run_align(st.frames, st.template, 8, group_frames=5)
+    b, _, _, _ = run_align(st.frames, st.template, 8, group_frames=0)
+    assert np.array_equal(a, b)
+    check_align(st.frames, st.template, 8, -1, a)
+
+
+def test_align_host_matches_device_path():
+    st = synth.make_stack_np(264, 264, 11, 40, 6, seed=8, template="clean")
+    with Plan(dict(m=264, n=264, w=8, group_frames=4), dev(st.template)) as plan:
+        d = plan.align(dev(st.frames)).cpu().numpy()
+        h = plan.align_host(torch.from_numpy(st.frames).pin_memory()).numpy()
+    assert np.array_equal(d, h)
+    check_align(st.frames, st.template, 8, -1, d)
+
+
+def test_set_template_equals_fresh_plan():
+    s1 = synth.make_stack_np(80, 80, 6, 15, 5, seed=1, template="clean")
+    s2 = synth.make_stack_np(80, 80, 6, 15, 5, seed=2, template="clean")
+    with Plan(dict(m=80, n=80, w=7), dev(s1.template)) as plan:
+        plan.set_template(dev(s2.template))
+        a = plan.cost_surface(dev(s2.frames)).cpu().numpy()
+    with Plan(dict(m=80, n=80, w=7), dev(s2.template)) as plan:
+        b = plan.cost_surface(dev(s2.frames)).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_several_shapes_and_stacks_in_one_call():
+    from paper_1506_06039_gb300 import moco_align_stack
+    sa = synth.make_stack_np(64, 64, 5, 10, 4, seed=11, template="clean")
+    sb = synth.make_stack_np(272, 264, 4, 40, 6, seed=12, template="clean")
+    plan = Plan([dict(m=64, n=64, w=6), dict(m=272, n=264, w=5)], [dev(sa.template), dev(sb.template)])
+    try:
+        outa = torch.empty((5, 2), dtype=torch.int32, device="cuda")
+        outb = torch.empty((4, 2), dtype=torch.int32, device="cuda")
+        moco_align_stack(plan.handle, [dict(shape_idx=0, frames=dev(sa.frames), shifts=outa),
+                                       dict(shape_idx=1, frames=dev(sb.frames), shifts=outb)])
+        torch.cuda.synchronize()
+    finally:
+        plan.close()
+    check_align(sa.frames, sa.template, 6, -1, outa.cpu().numpy())
+    check_align(sb.frames, sb.template, 5, -1, outb.cpu().numpy())
+
+
+def test_std512_full_workload_sampled():
+    # The standard workload at full size, in the launch configuration the
+    # benchmark times; the oracle checks a seeded sample of frames one by one.
+    wl = synth.WORKLOADS["std512"]
+    st = synth.make_stack_torch(wl.m, wl.n, wl.T, wl.nblobs, wl.shift_max, wl.seed, template=wl.template)
+    with Plan(dict(m=wl.m, n=wl.n, w=wl.w), st.template) as plan:
+        shifts, best, margin = plan.align(st.frames, best_cost=True, margin=True)
+        torch.cuda.synchronize()
+        info = plan.info()
+    assert info["levels"] == 1 and info["mc"] == 256
+    shifts = shifts.cpu().numpy()
+    # planted shifts are recovered on (almost) every frame
+    assert (shifts == st.shifts).all(axis=1).mean() > 0.99
+    sample = np.random.default_rng(0).choice(wl.T, 12, replace=False)
+    fr = st.frames[torch.from_numpy(sample).cuda()].cpu().numpy()
+    check_align(fr, st.template.cpu().numpy(), wl.w, -1, shifts[sample], best.cpu().numpy()[sample])
