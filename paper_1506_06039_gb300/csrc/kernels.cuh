@@ -477,13 +477,20 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 }
 
 // ---------------------------------------------------------------------------
-// k_jitter: the upsampling step of Section 2. One CTA per frame. For the
-// nine candidates (2 sc + u, 2 tc + v), u, v in {-1, 0, 1}, the exact int64
-// S = sum over D of (a[i+s][j+t] - b[i][j])^2 at full resolution, all nine
-// accumulated in one pass over the frame (each thread walks down a strip of
-// 8 columns keeping the three frame rows it needs in registers), then the
-// minimum of S / Area with the tie-break, compared as exact rationals.
-__device__ __forceinline__ void unpack8(const uint4 p, int32_t (&v)[8]) {
+// k_jitter: the upsampling step of Section 2. For the nine candidates
+// (2 sc + u, 2 tc + v), u, v in {-1, 0, 1}, the exact int64
+//     S = sum over D of (a[i+s][j+t] - b[i][j])^2
+// at full resolution, all nine accumulated in one pass over the frame.
+// Grid (kJitCtas per frame, frames). Each thread owns 8 template columns of
+// a band of kJitRows rows and walks down it keeping the three frame rows it
+// needs (i+s0-1 .. i+s0+1, 10 columns each) in registers, so every frame row
+// is loaded once per thread with two 16-byte loads. Per-CTA partial sums go
+// to acc[f][9] by 64-bit atomics; the last CTA of a frame (ticket counter)
+// takes the minimum of S / Area with the tie-break, compared as exact
+// rationals. acc and ticket must be zero on entry (the host clears them).
+constexpr int kJitRows = 32;
+
+__device__ __forceinline__ void unpack8(const uint4 p, int32_t* v) {
     const uint32_t w[4] = {p.x, p.y, p.z, p.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -492,7 +499,39 @@ __device__ __forceinline__ void unpack8(const uint4 p, int32_t (&v)[8]) {
     }
 }
 
-// Returns 1 when S1/A1 < S2/A2 exactly (A > 0).
+// out[k] = in[O + k], k < 10 (O a compile-time offset < 8).
+template <int O>
+__device__ __forceinline__ void take10(const int32_t (&in)[16], int32_t (&out)[10]) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) out[k] = in[O + k];
+}
+
+__device__ __forceinline__ void window_row(const uint16_t* __restrict__ arow, int c0, int o, int n, bool interior,
+                                           int32_t (&out)[10]) {
+    int32_t v16[16];
+    if (interior) {
+        unpack8(__ldg(reinterpret_cast<const uint4*>(arow + c0)), v16);
+        unpack8(__ldg(reinterpret_cast<const uint4*>(arow + c0 + 8)), v16 + 8);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int c = c0 + k;
+            v16[k] = (c >= 0 && c < n) ? (int32_t)__ldg(arow + c) : 0;
+        }
+    }
+    switch (o) {
+        case 0: take10<0>(v16, out); break;
+        case 1: take10<1>(v16, out); break;
+        case 2: take10<2>(v16, out); break;
+        case 3: take10<3>(v16, out); break;
+        case 4: take10<4>(v16, out); break;
+        case 5: take10<5>(v16, out); break;
+        case 6: take10<6>(v16, out); break;
+        default: take10<7>(v16, out); break;
+    }
+}
+
+// Returns 1 when S1/A1 < S2/A2 exactly (A > 0); *eq when equal.
 __device__ __forceinline__ int ratio_lt(u64 S1, u64 A1, u64 S2, u64 A2, int* eq) {
     const u64 l_lo = S1 * A2, l_hi = __umul64hi(S1, A2);
     const u64 r_lo = S2 * A1, r_hi = __umul64hi(S2, A1);
@@ -501,101 +540,118 @@ __device__ __forceinline__ int ratio_lt(u64 S1, u64 A1, u64 S2, u64 A2, int* eq)
 }
 
 static __global__ void __launch_bounds__(kJitterThreads)
-k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* __restrict__ tmpl,
-         int m, int n, const int32_t* __restrict__ coarse, int32_t* __restrict__ shifts,
-         double* __restrict__ ffinal) {
+k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* __restrict__ tmpl, int m, int n,
+         const int32_t* __restrict__ coarse, int32_t* __restrict__ shifts, double* __restrict__ ffinal,
+         u64* __restrict__ acc_g, unsigned int* __restrict__ ticket) {
     __shared__ u64 red[kJitterThreads / 32][9];
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int64_t f = blockIdx.x;
+    __shared__ bool last;
+    const int tid = threadIdx.x;
+    const int64_t f = blockIdx.y;
     const int s0 = 2 * coarse[2 * f], t0 = 2 * coarse[2 * f + 1];
     const uint16_t* a = frames + f * fstride;
     u64 acc[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = 0;
-    const int G = n / 8;  // column groups
-    const int nseg = max(1, nthr / G);
-    const int segrows = (m + nseg - 1) / nseg;
-    // a-row cache: values at columns j + t0 + v, v in {-1,0,1}, k in [0,8):
-    // cols j + t0 - 1 .. j + t0 + 8 (10 values) for the rows i+s0-1..i+s0+1.
-    for (int task = tid; task < G * nseg; task += nthr) {
-        const int g = task % G, seg = task / G;
+    const int G = n / 8;
+    const int nb = (m + kJitRows - 1) / kJitRows;
+    const int task = blockIdx.x * kJitterThreads + tid;
+    if (task < G * nb) {
+        const int g = task % G, band = task / G;
         const int j0 = 8 * g;
-        const int i_begin = seg * segrows, i_end = min(m, i_begin + segrows);
-        const int cbase = j0 + t0 - 1;  // first frame column needed
-        const bool col_interior = (cbase >= 0) && (cbase + 10 <= n);
+        // Frame columns j0 + t0 - 1 + k, k < 10, live in the aligned 16-column
+        // block starting at c0, at offset o.
+        const int lead = j0 + t0 - 1;
+        const int c0 = lead >= 0 ? (lead & ~7) : -((-lead + 7) & ~7);
+        const int o = lead - c0;
+        const bool interior = (lead >= 0) && (lead + 10 <= n) && (c0 + 16 <= n);
+        const int i_begin = band * kJitRows, i_end = min(m, i_begin + kJitRows);
+        int32_t win[3][10];
+        bool ok[3];
+        // rows i_begin + s0 - 1 and i_begin + s0 fill window slots 0 and 1
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int ar = i_begin + s0 - 1 + u;
+            ok[u] = ar >= 0 && ar < m;
+            if (ok[u]) window_row(a + (int64_t)ar * n, c0, o, n, interior, win[u]);
+        }
         for (int i = i_begin; i < i_end; ++i) {
+            {
+                const int ar = i + s0 + 1;
+                ok[2] = ar >= 0 && ar < m;
+                if (ok[2]) window_row(a + (int64_t)ar * n, c0, o, n, interior, win[2]);
+            }
             int32_t bv[8];
             unpack8(__ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)i * n + j0)), bv);
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
-                const int ar = i + s0 + u - 1;
-                if (ar < 0 || ar >= m) continue;
-                const uint16_t* arow = a + (int64_t)ar * n;
-                int32_t av[10];
-                if (col_interior) {
+                if (!ok[u]) continue;
+                if (interior) {
 #pragma unroll
-                    for (int k = 0; k < 10; ++k) av[k] = (int32_t)__ldg(arow + cbase + k);
+                    for (int v = 0; v < 3; ++v)
 #pragma unroll
-                    for (int v = 0; v < 3; ++v) {
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) acc[u * 3 + v] += sq64(av[k + v] - bv[k]);
-                    }
+                        for (int k = 0; k < 8; ++k) acc[u * 3 + v] += sq64(win[u][k + v] - bv[k]);
                 } else {
 #pragma unroll
-                    for (int k = 0; k < 10; ++k) {
-                        const int c = cbase + k;
-                        av[k] = (c >= 0 && c < n) ? (int32_t)__ldg(arow + c) : 0;
-                    }
-#pragma unroll
-                    for (int v = 0; v < 3; ++v) {
+                    for (int v = 0; v < 3; ++v)
 #pragma unroll
                         for (int k = 0; k < 8; ++k) {
-                            const int c = cbase + k + v;
-                            if (c >= 0 && c < n) acc[u * 3 + v] += sq64(av[k + v] - bv[k]);
+                            const int c = lead + k + v;
+                            if (c >= 0 && c < n) acc[u * 3 + v] += sq64(win[u][k + v] - bv[k]);
                         }
-                    }
                 }
             }
+            // slide the window down one row
+#pragma unroll
+            for (int k = 0; k < 10; ++k) {
+                win[0][k] = win[1][k];
+                win[1][k] = win[2][k];
+            }
+            ok[0] = ok[1];
+            ok[1] = ok[2];
         }
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         u64 v = acc[k];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         if ((tid & 31) == 0) red[tid >> 5][k] = v;
     }
     __syncthreads();
-    if (tid == 0) {
-        u64 S[9];
-        for (int k = 0; k < 9; ++k) {
-            S[k] = 0;
-            for (int wi = 0; wi < (nthr + 31) / 32; ++wi) S[k] += red[wi][k];
-        }
-        int bk = -1;
-        u64 bS = 0, bA = 1;
-        int bs = 0, bt = 0;
-        for (int u = 0; u < 3; ++u)
-            for (int v = 0; v < 3; ++v) {
-                const int s = s0 + u - 1, t = t0 + v - 1;
-                const u64 A = (u64)(m - abs(s)) * (u64)(n - abs(t));
-                const u64 Sk = S[u * 3 + v];
-                bool take = (bk < 0);
-                if (!take) {
-                    int eq;
-                    const int lt = ratio_lt(Sk, A, bS, bA, &eq);
-                    if (lt) take = true;
-                    else if (eq) {
-                        const int k1 = abs(s) + abs(t), k2 = abs(bs) + abs(bt);
-                        take = (k1 < k2) || (k1 == k2 && (s < bs || (s == bs && t < bt)));
-                    }
-                }
-                if (take) { bk = u * 3 + v; bS = Sk; bA = A; bs = s; bt = t; }
-            }
-        shifts[2 * f] = bs;
-        shifts[2 * f + 1] = bt;
-        if (ffinal) ffinal[f] = (double)bS / (double)bA;
+    if (tid < 9) {
+        u64 sum = 0;
+        for (int wi = 0; wi < kJitterThreads / 32; ++wi) sum += red[wi][tid];
+        atomicAdd(&acc_g[f * 9 + tid], sum);
     }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = (atomicAdd(&ticket[f], 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last || tid != 0) return;
+    __threadfence();
+    int bk = -1;
+    u64 bS = 0, bA = 1;
+    int bs = 0, bt = 0;
+    for (int u = 0; u < 3; ++u)
+        for (int v = 0; v < 3; ++v) {
+            const int s = s0 + u - 1, t = t0 + v - 1;
+            const u64 A = (u64)(m - abs(s)) * (u64)(n - abs(t));
+            const u64 Sk = atomicAdd(&acc_g[f * 9 + u * 3 + v], 0ull);
+            bool take = (bk < 0);
+            if (!take) {
+                int eq;
+                const int lt = ratio_lt(Sk, A, bS, bA, &eq);
+                if (lt) take = true;
+                else if (eq) {
+                    const int k1 = abs(s) + abs(t), k2 = abs(bs) + abs(bt);
+                    take = (k1 < k2) || (k1 == k2 && (s < bs || (s == bs && t < bt)));
+                }
+            }
+            if (take) { bk = u * 3 + v; bS = Sk; bA = A; bs = s; bt = t; }
+        }
+    shifts[2 * f] = bs;
+    shifts[2 * f + 1] = bt;
+    if (ffinal) ffinal[f] = (double)bS / (double)bA;
 }
 
 // For searches without a level: the searched optimum is the answer.

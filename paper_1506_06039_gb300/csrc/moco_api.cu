@@ -78,7 +78,7 @@ int64_t per_frame_scratch_bytes(const ShapePlan& sp) {
     b += 4 * wm1 * wm1 * 4;                    // corners
     b += W * W * 8;                            // Sa
     b += 8 + 8 + 4;                            // coarse, fbest, margin
-    b += (int64_t)sp.desc.m * sp.desc.n * 2 + 8;  // host staging (frames + shifts)
+    b += 9 * 8 + 4;                            // jitter sums and tickets
     return b;
 }
 
@@ -118,9 +118,12 @@ moco_status resolve_shape(const moco_shape& d, ShapePlan& sp) {
     if (d.group_frames > 0) {
         sp.group = d.group_frames;
     } else {
-        const int64_t target = 96ll << 20;  // workspace target: about the L2 size
-        sp.group = (int)std::max<int64_t>(1, std::min<int64_t>(4096, target / per_frame_scratch_bytes(sp)));
+        // Large batches keep every per-frame kernel several waves deep on the
+        // 152 SMs; about 1 GiB of workspace.
+        const int64_t target = 1ll << 30;
+        sp.group = (int)std::max<int64_t>(1, std::min<int64_t>(2048, target / per_frame_scratch_bytes(sp)));
     }
+    sp.stage_frames = std::min(sp.group, 512);
     return MOCO_OK;
 }
 
@@ -147,9 +150,11 @@ moco_status allocate_shape(ShapePlan& sp) {
     c.add(&sp.coarse, (size_t)(G * 2 * 4));
     c.add(&sp.fbest, (size_t)(G * 8));
     c.add(&sp.margin, (size_t)(G * 4));
+    c.add(&sp.jit_acc, (size_t)(G * 9 * 8));
+    c.add(&sp.jit_ticket, (size_t)(G * 4));
     for (int k = 0; k < 2; ++k) {
-        c.add(&sp.stage[k], (size_t)(G * m * n * 2));
-        c.add(&sp.stage_shifts[k], (size_t)(G * 2 * 4));
+        c.add(&sp.stage[k], (size_t)((int64_t)sp.stage_frames * m * n * 2));
+        c.add(&sp.stage_shifts[k], (size_t)(sp.stage_frames * 2 * 4));
     }
     sp.bytes = c.off;
     cudaError_t e = cudaMalloc(&sp.base, sp.bytes);
@@ -237,7 +242,7 @@ moco_status align_frames(ShapePlan& sp, const uint16_t* frames, int64_t T, int32
         sp.prof->begin(sp.levels ? K_JITTER : K_COPY_SHIFTS, st);
         if (sp.levels)
             e = launch_jitter(frames + f0 * mn, mn, g, static_cast<const uint16_t*>(sp.tmpl), sp.desc.m,
-                              sp.desc.n, sp.coarse, shifts + 2 * f0, nullptr, st);
+                              sp.desc.n, sp.coarse, shifts + 2 * f0, nullptr, sp.jit_acc, sp.jit_ticket, st);
         else
             e = launch_copy_shifts(sp.coarse, shifts + 2 * f0, nullptr, nullptr, g, st);
         sp.prof->end(st);
@@ -479,8 +484,8 @@ moco_status moco_align_host(moco_plan_t plan, int32_t shape_idx, const uint16_t*
     if (e == cudaSuccess) e = cudaEventRecord(done[1], st);
     if (e != cudaSuccess) return cuda_fail(e, "event record");
     int k = 0;
-    for (int64_t f0 = 0; f0 < T; f0 += sp.group, k ^= 1) {
-        const int64_t g = std::min<int64_t>(sp.group, T - f0);
+    for (int64_t f0 = 0; f0 < T; f0 += sp.stage_frames, k ^= 1) {
+        const int64_t g = std::min<int64_t>(sp.stage_frames, T - f0);
         // The copy into staging buffer k waits for the compute that last used it.
         e = cudaStreamWaitEvent(cp, done[k], 0);
         if (e == cudaSuccess)

@@ -44,6 +44,7 @@ struct ShapePlan {
     int Nr = 0, Nc = 0, ncv = 0, ldx = 0;
     int form = MOCO_XCORR_FFT_FP32;
     int group = 1;
+    int stage_frames = 1;  // frames per host staging buffer
     bool f32 = false;
     double unit = 1.0;
     int64_t x_fstride = 0, y_fstride = 0;
@@ -69,6 +70,8 @@ struct ShapePlan {
     int32_t* coarse = nullptr;
     double* fbest = nullptr;
     float* margin = nullptr;
+    u64* jit_acc = nullptr;            // group x 9
+    unsigned int* jit_ticket = nullptr;  // group
     // staging for moco_align_host (double-buffered)
     uint16_t* stage[2] = {nullptr, nullptr};
     int32_t* stage_shifts[2] = {nullptr, nullptr};

@@ -69,9 +69,16 @@ cudaError_t launch_energy(bool f32, bool out_double, const u64* rowE, const u64*
 }
 
 cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg, const uint16_t* tmpl, int m,
-                          int n, const int32_t* coarse, int32_t* shifts, double* ffinal, cudaStream_t st) {
+                          int n, const int32_t* coarse, int32_t* shifts, double* ffinal, u64* acc,
+                          unsigned int* ticket, cudaStream_t st) {
     if (nimg <= 0) return cudaSuccess;
-    k_jitter<<<(unsigned)nimg, kJitterThreads, 0, st>>>(frames, fstride, tmpl, m, n, coarse, shifts, ffinal);
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(u64) * 9 * nimg, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int) * nimg, st);
+    if (e != cudaSuccess) return e;
+    const int tasks = (n / 8) * ((m + kJitRows - 1) / kJitRows);
+    const int ctas = (tasks + kJitterThreads - 1) / kJitterThreads;
+    dim3 grid((unsigned)ctas, (unsigned)nimg);
+    k_jitter<<<grid, kJitterThreads, 0, st>>>(frames, fstride, tmpl, m, n, coarse, shifts, ffinal, acc, ticket);
     return cudaGetLastError();
 }
 

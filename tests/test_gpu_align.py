@@ -85,7 +85,9 @@ def test_identity_and_constant_frames():
     b = rng.integers(0, 3000, (64, 64)).astype(np.uint16)
     frames = np.stack([b, np.full_like(b, 500), np.full_like(b, int(b.mean().round()))])
     shifts, best, margin, _ = run_align(frames, b, 9)
-    assert tuple(shifts[0]) == (0, 0) and best[0] == 0.0
+    # f = 0 at (0, 0) up to the FP32 cross term: within the 1e-6 * max f floor
+    ref = oracle.cost_surface(frames[:1], b, 9)
+    assert tuple(shifts[0]) == (0, 0) and abs(best[0]) <= 1e-6 * ref.max()
     check_align(frames, b, 9, -1, shifts, best)
     c = np.full((64, 64), 700, np.uint16)
     shifts, best, margin, _ = run_align(np.stack([c, c]), c, 5)
@@ -147,18 +149,31 @@ def test_several_shapes_and_stacks_in_one_call():
 
 
 def test_std512_full_workload_sampled():
-    # The standard workload at full size, in the launch configuration the
-    # benchmark times; the oracle checks a seeded sample of frames one by one.
+    # The standard workload at full size (2000 frames, template = mean of the
+    # first 100 frames), in the launch configuration the benchmark times; the
+    # oracle checks a seeded sample of frames one by one. The mean of frames
+    # shifted by up to 40 px is a blurred template, so planted shifts are not
+    # expected here; parity with the oracle is.
     wl = synth.WORKLOADS["std512"]
     st = synth.make_stack_torch(wl.m, wl.n, wl.T, wl.nblobs, wl.shift_max, wl.seed, template=wl.template)
     with Plan(dict(m=wl.m, n=wl.n, w=wl.w), st.template) as plan:
         shifts, best, margin = plan.align(st.frames, best_cost=True, margin=True)
         torch.cuda.synchronize()
         info = plan.info()
-    assert info["levels"] == 1 and info["mc"] == 256
+    assert info["levels"] == 1 and info["mc"] == 256 and info["group_frames"] >= wl.T
     shifts = shifts.cpu().numpy()
-    # planted shifts are recovered on (almost) every frame
-    assert (shifts == st.shifts).all(axis=1).mean() > 0.99
     sample = np.random.default_rng(0).choice(wl.T, 12, replace=False)
-    fr = st.frames[torch.from_numpy(sample).cuda()].cpu().numpy()
+    fr = st.frames.cpu().numpy()[sample]
     check_align(fr, st.template.cpu().numpy(), wl.w, -1, shifts[sample], best.cpu().numpy()[sample])
+
+
+def test_std512_clean_template_recovers_planted_shifts():
+    # Same frame recipe with the clean (unshifted, noise-free) template: the
+    # planted shifts are the answer on (almost) every frame.
+    wl = synth.WORKLOADS["std512"]
+    st = synth.make_stack_torch(wl.m, wl.n, 300, wl.nblobs, wl.shift_max, wl.seed, template="clean")
+    with Plan(dict(m=wl.m, n=wl.n, w=wl.w), st.template) as plan:
+        shifts = plan.align(st.frames).cpu().numpy()
+    assert (shifts == st.shifts).all(axis=1).mean() > 0.99
+    sample = np.random.default_rng(1).choice(300, 8, replace=False)
+    check_align(st.frames.cpu().numpy()[sample], st.template.cpu().numpy(), wl.w, -1, shifts[sample])
