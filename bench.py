@@ -39,6 +39,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="moco", choices=["moco", "reference"])
     p.add_argument("--workload", default="std512")
+    p.add_argument("--frames", type=int, default=0, help="override the workload's frame count (profiling runs)")
     p.add_argument("--form", default="auto", choices=["auto", "fft", "direct"])
     p.add_argument("--group", type=int, default=0, help="frames per internal batch (0 = plan's choice)")
     p.add_argument("--e2e-steps", type=int, default=10)
@@ -241,6 +242,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
     wl = synth.WORKLOADS[args.workload]
+    if args.frames:
+        import dataclasses
+        wl = dataclasses.replace(wl, T=args.frames)
     st = synth.make_stack_torch(wl.m, wl.n, wl.T, wl.nblobs, wl.shift_max, wl.seed + 1000 * rank,
                                 template=wl.template)
     form = {"auto": XCORR_AUTO, "fft": XCORR_FFT_FP32, "direct": XCORR_DIRECT_BF16X3}[args.form]

@@ -66,7 +66,7 @@ __device__ __forceinline__ uint32_t hi16(uint32_t w) { return w >> 16; }
 // corners    : the four (w-1)x(w-1) corner blocks of the offset image
 //              (int32 or float bits), [f][q][ri][ci], q = 2*bottom + right
 template <int N, bool F32IN>
-__global__ void __launch_bounds__(kRowsThreads)
+__global__ void __launch_bounds__(kRowsThreads, 2)
 k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, int levels, int mc,
              int nc, const int32_t* __restrict__ coff_i, const float* __restrict__ coff_f,
              const float2* __restrict__ tw_g, float2* __restrict__ X, int64_t x_fstride, int ldx,
@@ -91,9 +91,6 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
     const int RPI = nthr / G;          // rows per pass (host guarantees G <= nthr)
     const bool active = tid < RPI * G;
     const int g = tid % G, rl0 = tid / G;
-    Acc cacc[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) cacc[k] = 0;
     Acc tacc = 0;
     const int32_t ci_off = F32IN ? 0 : *coff_i;
     const float cf_off = F32IN ? *coff_f : 0.f;
@@ -107,7 +104,6 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
             for (int rl = rl0; rl < rows; rl += RPI) {
                 const int r = r0 + rl;
                 float val[8];
-                Acc e[8];
                 if (!F32IN) {
                     const uint16_t* base = static_cast<const uint16_t*>(src) + f * src_fstride;
                     int32_t iv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -128,48 +124,38 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
                         }
                     }
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const int32_t d = iv[k] - ci_off;
-                        val[k] = (float)d;  // |d| < 2^19: exact
-                        e[k] = (Acc)sq64(d);
-                    }
+                    for (int k = 0; k < 8; ++k) val[k] = (float)(iv[k] - ci_off);  // |d| < 2^19: exact
                 } else {
                     const float* base = static_cast<const float*>(src) + f * src_fstride;
                     const float4 q0 = __ldg(reinterpret_cast<const float4*>(base + (int64_t)r * n + 8 * g));
                     const float4 q1 = __ldg(reinterpret_cast<const float4*>(base + (int64_t)r * n + 8 * g + 4));
-                    const float qv[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        val[k] = qv[k] - cf_off;
-                        e[k] = (Acc)((double)val[k] * (double)val[k]);
-                    }
+                    val[0] = q0.x - cf_off; val[1] = q0.y - cf_off; val[2] = q0.z - cf_off; val[3] = q0.w - cf_off;
+                    val[4] = q1.x - cf_off; val[5] = q1.y - cf_off; val[6] = q1.z - cf_off; val[7] = q1.w - cf_off;
                 }
+                const bool top = r < wm1, bot = r >= mc - wm1;
                 Acc rs = 0;
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (k < CW) {
-                        cacc[k] += e[k];
-                        rs += e[k];
-                    }
-                tacc += rs;
-                const bool top = r < wm1, bot = r >= mc - wm1;
-                if (top || bot) {
-                    atomicAdd(&rowacc[rl], rs);
-                    const int ri = top ? r : r - (mc - wm1);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const int c = g * CW + k;
-                        if (k < CW && (c < wm1 || c >= nc - wm1)) {
-                            const bool right = c >= nc - wm1;
+                for (int k = 0; k < 8; ++k) {
+                    if (k >= CW) break;
+                    const int c = g * CW + k;
+                    Acc e;
+                    if (F32IN) e = (Acc)((double)val[k] * (double)val[k]);
+                    else e = (Acc)sq64((int32_t)val[k]);
+                    rs += e;
+                    const bool left = c < wm1, right = c >= nc - wm1;
+                    if (left || right) {
+                        atomicAdd(&colacc[c], e);  // column energies: edge columns only
+                        if (top || bot) {
+                            const int ri = top ? r : r - (mc - wm1);
                             const int cj = right ? c - (nc - wm1) : c;
                             const int q = (bot ? 2 : 0) + (right ? 1 : 0);
-                            uint32_t bits;
-                            if (F32IN) bits = __float_as_uint(val[k]);
-                            else bits = (uint32_t)(int32_t)val[k];
+                            const uint32_t bits = F32IN ? __float_as_uint(val[k]) : (uint32_t)(int32_t)val[k];
                             corners[(f * 4 + q) * wm1sq + (size_t)ri * wm1 + cj] = bits;
                         }
                     }
                 }
+                tacc += rs;
+                if (top || bot) atomicAdd(&rowacc[rl], rs);
                 float* dst = reinterpret_cast<float*>(buf + (rl >> 1) * N) + (rl & 1);
 #pragma unroll
                 for (int k = 0; k < 8; ++k)
@@ -202,11 +188,6 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
             rowacc[rl] = 0;
         }
         __syncthreads();
-    }
-    if (active) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (k < CW) atomicAdd(&colacc[g * CW + k], cacc[k]);
     }
     tacc = warp_sum(tacc);
     if ((tid & 31) == 0) red[tid >> 5] = tacc;
@@ -501,33 +482,37 @@ __device__ __forceinline__ void unpack8(const uint4 p, int32_t* v) {
 
 // out[k] = in[O + k], k < 10 (O a compile-time offset < 8).
 template <int O>
-__device__ __forceinline__ void take10(const int32_t (&in)[16], int32_t (&out)[10]) {
+__device__ __forceinline__ void take10(const int32_t (&in)[24], int32_t (&out)[10]) {
 #pragma unroll
     for (int k = 0; k < 10; ++k) out[k] = in[O + k];
 }
 
+// The 10 frame values at columns c0 + o .. c0 + o + 9 of one row. Interior
+// rows use aligned 16-byte loads of columns [c0, c0 + 16) (and [c0 + 16,
+// c0 + 24) when o == 7); border rows load element by element, zero outside.
 __device__ __forceinline__ void window_row(const uint16_t* __restrict__ arow, int c0, int o, int n, bool interior,
                                            int32_t (&out)[10]) {
-    int32_t v16[16];
+    int32_t v[24];
     if (interior) {
-        unpack8(__ldg(reinterpret_cast<const uint4*>(arow + c0)), v16);
-        unpack8(__ldg(reinterpret_cast<const uint4*>(arow + c0 + 8)), v16 + 8);
+        unpack8(__ldg(reinterpret_cast<const uint4*>(arow + c0)), v);
+        unpack8(__ldg(reinterpret_cast<const uint4*>(arow + c0 + 8)), v + 8);
+        if (o == 7) unpack8(__ldg(reinterpret_cast<const uint4*>(arow + c0 + 16)), v + 16);
     } else {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < 17; ++k) {
             const int c = c0 + k;
-            v16[k] = (c >= 0 && c < n) ? (int32_t)__ldg(arow + c) : 0;
+            v[k] = (c >= 0 && c < n) ? (int32_t)__ldg(arow + c) : 0;
         }
     }
     switch (o) {
-        case 0: take10<0>(v16, out); break;
-        case 1: take10<1>(v16, out); break;
-        case 2: take10<2>(v16, out); break;
-        case 3: take10<3>(v16, out); break;
-        case 4: take10<4>(v16, out); break;
-        case 5: take10<5>(v16, out); break;
-        case 6: take10<6>(v16, out); break;
-        default: take10<7>(v16, out); break;
+        case 0: take10<0>(v, out); break;
+        case 1: take10<1>(v, out); break;
+        case 2: take10<2>(v, out); break;
+        case 3: take10<3>(v, out); break;
+        case 4: take10<4>(v, out); break;
+        case 5: take10<5>(v, out); break;
+        case 6: take10<6>(v, out); break;
+        default: take10<7>(v, out); break;
     }
 }
 
@@ -563,34 +548,55 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
         const int lead = j0 + t0 - 1;
         const int c0 = lead >= 0 ? (lead & ~7) : -((-lead + 7) & ~7);
         const int o = lead - c0;
-        const bool interior = (lead >= 0) && (lead + 10 <= n) && (c0 + 16 <= n);
+        const bool interior = (lead >= 0) && (lead + 10 <= n) && (c0 + (o == 7 ? 24 : 16) <= n);
         const int i_begin = band * kJitRows, i_end = min(m, i_begin + kJitRows);
         int32_t win[3][10];
+        u64 esum[3][3];  // per window row: sum of a^2 over the 8 columns each v uses
         bool ok[3];
-        // rows i_begin + s0 - 1 and i_begin + s0 fill window slots 0 and 1
+        auto load_slot = [&](int slot, int ar) {
+            ok[slot] = ar >= 0 && ar < m;
+            if (!ok[slot]) return;
+            window_row(a + (int64_t)ar * n, c0, o, n, interior, win[slot]);
+            if (interior) {
+                u64 e[10];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int ar = i_begin + s0 - 1 + u;
-            ok[u] = ar >= 0 && ar < m;
-            if (ok[u]) window_row(a + (int64_t)ar * n, c0, o, n, interior, win[u]);
-        }
-        for (int i = i_begin; i < i_end; ++i) {
-            {
-                const int ar = i + s0 + 1;
-                ok[2] = ar >= 0 && ar < m;
-                if (ok[2]) window_row(a + (int64_t)ar * n, c0, o, n, interior, win[2]);
+                for (int k = 0; k < 10; ++k) e[k] = (u64)(uint32_t)win[slot][k] * (uint32_t)win[slot][k];
+                u64 s0w = 0;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) s0w += e[k];
+                esum[slot][0] = s0w;
+                esum[slot][1] = s0w - e[0] + e[8];
+                esum[slot][2] = s0w - e[0] - e[1] + e[8] + e[9];
             }
+        };
+        // rows i_begin + s0 - 1 and i_begin + s0 fill window slots 0 and 1
+        load_slot(0, i_begin + s0 - 1);
+        load_slot(1, i_begin + s0);
+        for (int i = i_begin; i < i_end; ++i) {
+            load_slot(2, i + s0 + 1);
             int32_t bv[8];
             unpack8(__ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)i * n + j0)), bv);
+            if (interior) {
+                // S = sum a^2 + sum b^2 - 2 sum a b over the thread's pixels,
+                // all exact: products of two 16-bit values fit 32 bits.
+                u64 eb = 0;
 #pragma unroll
-            for (int u = 0; u < 3; ++u) {
-                if (!ok[u]) continue;
-                if (interior) {
+                for (int k = 0; k < 8; ++k) eb += (u64)(uint32_t)bv[k] * (uint32_t)bv[k];
 #pragma unroll
-                    for (int v = 0; v < 3; ++v)
+                for (int u = 0; u < 3; ++u) {
+                    if (!ok[u]) continue;
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) acc[u * 3 + v] += sq64(win[u][k + v] - bv[k]);
-                } else {
+                    for (int v = 0; v < 3; ++v) {
+                        u64 x = 0;
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) x += (u64)(uint32_t)win[u][k + v] * (uint32_t)bv[k];
+                        acc[u * 3 + v] += esum[u][v] + eb - 2 * x;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    if (!ok[u]) continue;
 #pragma unroll
                     for (int v = 0; v < 3; ++v)
 #pragma unroll
@@ -605,6 +611,11 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
             for (int k = 0; k < 10; ++k) {
                 win[0][k] = win[1][k];
                 win[1][k] = win[2][k];
+            }
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                esum[0][v] = esum[1][v];
+                esum[1][v] = esum[2][v];
             }
             ok[0] = ok[1];
             ok[1] = ok[2];

@@ -2,8 +2,12 @@
 
 Tolerances, derived from the arithmetic: the cross term is FP32 (FFT) or
 BF16 hi+lo with FP32 accumulation; energies are exact int64; the combine is
-FP64. The cost surface must agree with the oracle's FP64 value within 1e-4
-relative, pointwise, with a floor of 1e-6 * max f for values near zero. The
+FP64. An FP32 FFT correlation has an absolute error of order
+u * log2(N) * ||a|| * ||b|| (u = 2^-24), so the error of f is of order
+1e-6 * max f whatever f itself is. The cost surface must therefore agree
+with the oracle's FP64 value within 1e-4 relative wherever f >= 1e-2 * max f
+(max over that frame's window), and within the absolute 1e-6 * max f below
+that (a relative error with the denominator floored at 1e-2 * max f). The
 argmin must equal the oracle's on every frame whose oracle margin
 (f2 - f1) / f1 exceeds 1e-5; below that margin (near-ties, which an FP32
 cross term cannot resolve) the CUDA optimum's cost must still be within the
@@ -16,7 +20,7 @@ import numpy as np
 import oracle
 
 COST_RTOL = 1e-4
-COST_FLOOR = 1e-6
+COST_FLOOR = 1e-2
 MARGIN = 1e-5
 
 

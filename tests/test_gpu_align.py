@@ -80,12 +80,29 @@ def test_planted_odd_shift_full_resolution_exact(s0, t0):
     check_align(a[None], b, 12, -1, shifts, best)
 
 
+def test_jitter_every_column_offset():
+    # Planted noiseless full-resolution shifts whose doubled coarse optimum
+    # covers every offset of the jitter's 8-column load blocks (t0 mod 8),
+    # both signs, and shifts at the window edge.
+    m = n = 288
+    st = synth.make_stack_np(m, n, 1, 50, 0, seed=404, template="clean", noise=False)
+    b = st.template
+    planted = [(s, t) for s in (-17, -4, 0, 9) for t in range(-17, 18, 3)]
+    frames = np.full((len(planted), m, n), 100, np.uint16)
+    for f, (s0, t0) in enumerate(planted):
+        frames[f, max(0, s0):min(m, m + s0), max(0, t0):min(n, n + t0)] = \
+            b[max(0, -s0):min(m, m - s0), max(0, -t0):min(n, n - t0)]
+    shifts, best, _, _ = run_align(frames, b, 10)
+    assert [tuple(x) for x in shifts] == planted
+    check_align(frames, b, 10, -1, shifts, best)
+
+
 def test_identity_and_constant_frames():
     rng = np.random.default_rng(3)
     b = rng.integers(0, 3000, (64, 64)).astype(np.uint16)
     frames = np.stack([b, np.full_like(b, 500), np.full_like(b, int(b.mean().round()))])
     shifts, best, margin, _ = run_align(frames, b, 9)
-    # f = 0 at (0, 0) up to the FP32 cross term: within the 1e-6 * max f floor
+    # f = 0 at (0, 0) up to the FP32 cross term: within 1e-6 * max f
     ref = oracle.cost_surface(frames[:1], b, 9)
     assert tuple(shifts[0]) == (0, 0) and abs(best[0]) <= 1e-6 * ref.max()
     check_align(frames, b, 9, -1, shifts, best)
