@@ -132,14 +132,18 @@ moco_status moco_cost_surface(moco_plan_t plan, int32_t shape_idx, const uint16_
 moco_status moco_softmin(moco_plan_t plan, int32_t shape_idx, const double* cost_dev, int64_t T,
                          double tau_scale, double* loss_dev, float* weights_dev, void* stream);
 
-/* Adjoint of f (Section 2's f, searched grid, levels == 0 shapes): given
- * grad_cost_dev[T][2w-1][2w-1] = dL/df_{s,t}, accumulates
- *   grad_template_dev[m][n] += dL/db  (float, caller zeroes it first)
- * and, if grad_frames_dev is non-null, writes grad_frames_dev[T][m][n] = dL/da.
- * Uses the plan's current template. */
+/* Adjoint of Section 2's f (not in the paper; the differentiable form), for
+ * shapes with levels == 0: given G = grad_scale * grad_cost_dev
+ * ([T][2w-1][2w-1] floats, dL/df_{s,t}), accumulates
+ *   grad_template_dev[m][n] += dL/db  (float; the caller zeroes it first)
+ * and, if grad_frames_dev is non-null, overwrites grad_frames_dev[T][m][n]
+ * with dL/da. Uses the plan's current template. The correlation parts run
+ * as direct FP32 contractions with FP32 atomics across frame chunks, so the
+ * last bits vary from run to run. MOCO_ERR_UNSUPPORTED when levels != 0 or
+ * the window needs more shared memory than a CTA has (w > 48). */
 moco_status moco_cost_backward(moco_plan_t plan, int32_t shape_idx, const uint16_t* frames_dev, int64_t T,
-                               const float* grad_cost_dev, float* grad_template_dev, float* grad_frames_dev,
-                               void* stream);
+                               const float* grad_cost_dev, float grad_scale, float* grad_template_dev,
+                               float* grad_frames_dev, void* stream);
 
 /* End-to-end alignment from host memory: copies frames_host [T][m][n] to the
  * device in batches, aligns them and copies shifts [T][2] back to

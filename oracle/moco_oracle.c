@@ -318,12 +318,17 @@ double oracle_softmin_loss(const double *frames, int64_t T, const double *tmpl, 
             const double *a = frames + f * (int64_t)m * n;
             oracle_cost_f64(a, tmpl, m, n, w, cost);
             double tf = tau[f];
-            /* Stable log-sum-exp around the minimum cost. */
+            /* Stable log-sum-exp around the minimum cost. With tau = 0 (a
+             * median of zero) the soft-min is the min and the weight is shared
+             * equally by the minimisers. */
             double fmin = cost[0];
             for (int k = 1; k < K; ++k) if (cost[k] < fmin) fmin = cost[k];
+            int nmin = 0;
+            for (int k = 0; k < K; ++k) nmin += (cost[k] == fmin);
             double Z = 0.0;
-            for (int k = 0; k < K; ++k) Z += exp(-(cost[k] - fmin) / tf);
-            double L = fmin - tf * log(Z);
+            if (tf > 0)
+                for (int k = 0; k < K; ++k) Z += exp(-(cost[k] - fmin) / tf);
+            double L = tf > 0 ? fmin - tf * log(Z) : fmin;
             local += L;
             if (loss_f) loss_f[f] = L;
             if (!gb && !grad_frames) continue;
@@ -333,7 +338,7 @@ double oracle_softmin_loss(const double *frames, int64_t T, const double *tmpl, 
             for (int s = -(w - 1); s <= w - 1; ++s)
                 for (int t = -(w - 1); t <= w - 1; ++t) {
                     int k = (s + w - 1) * W + (t + w - 1);
-                    double g = exp(-(cost[k] - fmin) / tf) / Z;
+                    double g = tf > 0 ? exp(-(cost[k] - fmin) / tf) / Z : (cost[k] == fmin ? 1.0 / nmin : 0.0);
                     double q = g / (double)oracle_area(m, n, s, t);
                     for (int i = 0; i < m; ++i) {
                         if (i + s < 0 || i + s >= m) continue;

@@ -1,0 +1,59 @@
+"""torch.autograd wrapper of the differentiable form (not in the paper).
+
+MocoSoftMin computes, for a float template b and uint16 frames a_f,
+    L = sum_f -tau_f log sum_{s,t} exp(-f_st(a_f, b) / tau_f),
+    tau_f = tau_scale * median_{s,t} f_st (held constant),
+with f Section 2's cost. Forward: moco_set_template, moco_cost_surface and
+moco_softmin; backward: moco_cost_backward with the saved soft-min weights.
+Only the per-frame losses are summed here (a reduction of T numbers).
+"""
+from __future__ import annotations
+
+import torch
+
+from .binding import TEMPLATE_F32, Plan
+
+
+class MocoSoftMin(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, template, frames, plan, tau_scale=0.05, shape_idx=0):
+        plan.set_template(template.detach().contiguous(), shape_idx)
+        cost = plan.cost_surface(frames, shape_idx)
+        loss, weights = plan.softmin(cost, tau_scale, shape_idx)
+        ctx.save_for_backward(frames, weights)
+        ctx.plan, ctx.shape_idx = plan, shape_idx
+        return loss.sum()
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        frames, weights = ctx.saved_tensors
+        grad_t = ctx.plan.cost_backward(frames, weights, grad_scale=float(grad_out), shape_idx=ctx.shape_idx)
+        return grad_t, None, None, None, None
+
+
+def softmin_plan(frames, template, w, group_frames=0):
+    """A plan for the differentiable form: float template, no downsampling."""
+    m, n = template.shape
+    return Plan(dict(m=m, n=n, w=w, levels=0, template_dtype=TEMPLATE_F32, group_frames=group_frames),
+                template.detach().float().contiguous())
+
+
+def refine_template(frames, template0, w, steps=50, lr=1.0, tau_scale=0.05, plan=None):
+    """Gradient-based template refinement with Adam. Returns (template, losses)."""
+    tmpl = template0.detach().clone().float().requires_grad_(True)
+    own = plan is None
+    if own:
+        plan = softmin_plan(frames, tmpl, w)
+    opt = torch.optim.Adam([tmpl], lr=lr)
+    losses = []
+    try:
+        for _ in range(steps):
+            opt.zero_grad(set_to_none=True)
+            loss = MocoSoftMin.apply(tmpl, frames, plan, tau_scale, 0)
+            loss.backward()
+            opt.step()
+            losses.append(float(loss))
+    finally:
+        if own:
+            plan.close()
+    return tmpl.detach(), losses

@@ -86,7 +86,7 @@ def lib():
             L.moco_align_stack.argtypes = [P, ctypes.POINTER(MocoStack), i32, P]
             L.moco_cost_surface.argtypes = [P, i32, P, i64, P, P]
             L.moco_softmin.argtypes = [P, i32, P, i64, dbl, P, P, P]
-            L.moco_cost_backward.argtypes = [P, i32, P, i64, P, P, P, P]
+            L.moco_cost_backward.argtypes = [P, i32, P, i64, P, ctypes.c_float, P, P, P]
             L.moco_align_host.argtypes = [P, i32, P, i64, P, P]
             L.moco_plan_query.argtypes = [P, i32, ctypes.POINTER(MocoShapeInfo)]
             L.moco_plan_destroy.argtypes = [P]
@@ -200,7 +200,8 @@ def moco_softmin(plan, shape_idx, cost, tau_scale, loss, weights, stream=None):
                               _ptr(weights), _stream(stream)))
 
 
-def moco_cost_backward(plan, shape_idx, frames, grad_cost, grad_template, grad_frames=None, stream=None):
+def moco_cost_backward(plan, shape_idx, frames, grad_cost, grad_template, grad_frames=None, grad_scale=1.0,
+                       stream=None):
     import torch
     _need(frames, torch.uint16, "frames")
     _need(grad_cost, torch.float32, "grad_cost")
@@ -208,8 +209,8 @@ def moco_cost_backward(plan, shape_idx, frames, grad_cost, grad_template, grad_f
     if grad_frames is not None:
         _need(grad_frames, torch.float32, "grad_frames")
     T = frames.shape[0] if frames.dim() == 3 else 1
-    _check(lib().moco_cost_backward(plan, shape_idx, _ptr(frames), T, _ptr(grad_cost), _ptr(grad_template),
-                                    _ptr(grad_frames), _stream(stream)))
+    _check(lib().moco_cost_backward(plan, shape_idx, _ptr(frames), T, _ptr(grad_cost), float(grad_scale),
+                                    _ptr(grad_template), _ptr(grad_frames), _stream(stream)))
 
 
 def moco_align_host(plan, shape_idx, frames_host, shifts_host, stream=None):
@@ -292,6 +293,24 @@ class Plan:
         cost = torch.empty((frames.shape[0], W, W), dtype=torch.float64, device=frames.device)
         moco_cost_surface(self.handle, shape_idx, frames, cost, stream)
         return cost
+
+    def softmin(self, cost, tau_scale, shape_idx=0, stream=None):
+        """(loss[T] float64, weights[T, W, W] float32) of a cost surface."""
+        import torch
+        loss = torch.empty(cost.shape[0], dtype=torch.float64, device=cost.device)
+        weights = torch.empty(cost.shape, dtype=torch.float32, device=cost.device)
+        moco_softmin(self.handle, shape_idx, cost, tau_scale, loss, weights, stream)
+        return loss, weights
+
+    def cost_backward(self, frames, grad_cost, grad_template=None, grad_frames=False, grad_scale=1.0,
+                      shape_idx=0, stream=None):
+        import torch
+        m, n = int(self.shapes[shape_idx]["m"]), int(self.shapes[shape_idx]["n"])
+        if grad_template is None:
+            grad_template = torch.zeros((m, n), dtype=torch.float32, device=frames.device)
+        gf = torch.empty(frames.shape, dtype=torch.float32, device=frames.device) if grad_frames else None
+        moco_cost_backward(self.handle, shape_idx, frames, grad_cost, grad_template, gf, grad_scale, stream)
+        return (grad_template, gf) if grad_frames else grad_template
 
     def set_template(self, template, shape_idx=0, stream=None):
         moco_set_template(self.handle, shape_idx, template, stream)

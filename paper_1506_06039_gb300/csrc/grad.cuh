@@ -1,0 +1,310 @@
+// The differentiable form (not in the paper): a soft-min over shifts of
+// Section 2's cost f, and the adjoint of f with respect to the template and
+// the frames.
+//
+//   L_f = -tau_f log sum_{s,t} exp(-f_st / tau_f),  tau_f = scale * median_st f_st
+//   dL_f/df_st = softmax weight g_st (tau held constant)
+//
+// f_st = (1/A_st) sum_{(i,j) in D_st} (a[i+s][j+t] - b[i][j])^2, so with
+// q_st = G_st / A_st (G = dL/df):
+//   dL/db[i][j] = -2 sum_f sum_st q_f,st a'_f[i+s][j+t] + 2 b'[i][j] sum_st Q_st 1[0<=i+s<m] 1[0<=j+t<n]
+//   dL/da_f[k][l] = 2 a'_f[k][l] sum_st q_f,st 1[0<=k-s<m] 1[0<=l-t<n] - 2 sum_st q_f,st b'[k-s][l-t]
+// with Q = sum_f q_f, a' = a - c, b' = b - c (the plan's offset; f does not
+// depend on it), and a', b' taken as zero outside the image (that zero
+// carries the 1[(i,j) in D_st] of each sum). The correlation sums run as
+// tiled direct FP32 contractions; the indicator sums are rectangle sums of a
+// 2-D prefix table of q (or Q).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace moco {
+
+constexpr int kSoftminThreads = 256;
+constexpr int kGradTile = 32;          // output tile edge
+constexpr int kGradThreads = 256;      // 8 x 32: each thread 4 outputs of one row
+constexpr int kGradFramesPerCta = 16;  // frames per CTA of the template adjoint
+
+// Order-preserving map of doubles to unsigned keys (and back).
+__device__ __forceinline__ unsigned long long dkey(double x) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+    unsigned long long u = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)u);
+}
+
+// One CTA per frame: exact median by 8-bit radix select, then the stable
+// log-sum-exp and the softmax weights.
+static __global__ void __launch_bounds__(kSoftminThreads)
+k_softmin(const double* __restrict__ cost, int K, double tau_scale, double* __restrict__ loss,
+          float* __restrict__ weights) {
+    __shared__ unsigned int hist[256];
+    __shared__ unsigned long long s_prefix;
+    __shared__ int s_rank;
+    __shared__ double s_red[32];
+    __shared__ int s_cnt[32];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int64_t f = blockIdx.x;
+    const double* c = cost + f * K;
+    if (tid == 0) {
+        s_prefix = 0;
+        s_rank = K / 2;
+    }
+    unsigned long long mask = 0;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        for (int i = tid; i < 256; i += nthr) hist[i] = 0;
+        __syncthreads();
+        const unsigned long long prefix = s_prefix;
+        for (int k = tid; k < K; k += nthr) {
+            const unsigned long long key = dkey(c[k]);
+            if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int r = s_rank;
+            unsigned int b = 0;
+            for (; b < 256; ++b) {
+                if ((int)hist[b] > r) break;
+                r -= (int)hist[b];
+            }
+            s_rank = r;
+            s_prefix = prefix | ((unsigned long long)b << shift);
+        }
+        mask |= 255ull << shift;
+        __syncthreads();
+    }
+    const double med = dkey_inv(s_prefix);
+    const double tau = tau_scale * med;
+    double vmin = INFINITY;
+    for (int k = tid; k < K; k += nthr) vmin = vmin < c[k] ? vmin : c[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double other = __shfl_xor_sync(0xffffffffu, vmin, o);
+        vmin = vmin < other ? vmin : other;
+    }
+    if ((tid & 31) == 0) s_red[tid >> 5] = vmin;
+    __syncthreads();
+    if (tid == 0) {
+        double v = s_red[0];
+        for (int i = 1; i < (nthr + 31) / 32; ++i) v = v < s_red[i] ? v : s_red[i];
+        s_red[0] = v;
+    }
+    __syncthreads();
+    const double fmin_v = s_red[0];
+    __syncthreads();
+    float* wf = weights + f * K;
+    if (!(tau > 0.0)) {
+        // tau = 0 (a median of zero): the soft-min is the min; the weight is
+        // shared equally by the minimisers.
+        int cnt = 0;
+        for (int k = tid; k < K; k += nthr) cnt += (c[k] == fmin_v);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if ((tid & 31) == 0) s_cnt[tid >> 5] = cnt;
+        __syncthreads();
+        if (tid == 0) {
+            int t = 0;
+            for (int i = 0; i < (nthr + 31) / 32; ++i) t += s_cnt[i];
+            s_cnt[0] = t;
+            loss[f] = fmin_v;
+        }
+        __syncthreads();
+        const float wv = 1.0f / (float)s_cnt[0];
+        for (int k = tid; k < K; k += nthr) wf[k] = (c[k] == fmin_v) ? wv : 0.0f;
+        return;
+    }
+    double z = 0.0;
+    for (int k = tid; k < K; k += nthr) z += exp(-(c[k] - fmin_v) / tau);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+    if ((tid & 31) == 0) s_red[tid >> 5] = z;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (nthr + 31) / 32; ++i) t += s_red[i];
+        s_red[0] = t;
+        loss[f] = fmin_v - tau * log(t);
+    }
+    __syncthreads();
+    const double Z = s_red[0];
+    for (int k = tid; k < K; k += nthr) wf[k] = (float)(exp(-(c[k] - fmin_v) / tau) / Z);
+}
+
+// Q[k] = scale * inv_area[k] * sum_f G[f][k] (k < K), one thread per k.
+static __global__ void k_grad_qsum(const float* __restrict__ G, int64_t T, int K, const double* __restrict__ inv_area,
+                            float scale, float* __restrict__ Q) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    double s = 0.0;
+    for (int64_t f = 0; f < T; ++f) s += (double)G[f * K + k];
+    Q[k] = (float)(s * inv_area[k] * (double)scale);
+}
+
+// 2-D inclusive prefix of a W x W table into P ((W+1) x (W+1), P[0][*] =
+// P[*][0] = 0), by one block in shared memory.
+__device__ __forceinline__ void prefix2d(const float* src, float* P, int W, int tid, int nthr) {
+    const int L = W + 1;
+    for (int i = tid; i < L * L; i += nthr) {
+        const int a = i / L, b = i - a * L;
+        P[i] = (a > 0 && b > 0) ? src[(a - 1) * W + (b - 1)] : 0.f;
+    }
+    __syncthreads();
+    for (int a = tid; a < L; a += nthr) {
+        float s = 0.f;
+        for (int b = 0; b < L; ++b) { s += P[a * L + b]; P[a * L + b] = s; }
+    }
+    __syncthreads();
+    for (int b = tid; b < L; b += nthr) {
+        float s = 0.f;
+        for (int a = 0; a < L; ++a) { s += P[a * L + b]; P[a * L + b] = s; }
+    }
+    __syncthreads();
+}
+
+// Sum of q over s in [slo, shi], t in [tlo, thi] (shift indices, inclusive).
+__device__ __forceinline__ float rect(const float* P, int W, int wm1, int slo, int shi, int tlo, int thi) {
+    const int L = W + 1;
+    const int a0 = slo + wm1, a1 = shi + wm1 + 1, b0 = tlo + wm1, b1 = thi + wm1 + 1;
+    if (a1 <= a0 || b1 <= b0) return 0.f;
+    return P[a1 * L + b1] - P[a0 * L + b1] - P[a1 * L + b0] + P[a0 * L + b0];
+}
+
+// Correlation part of dL/db: acc[i][j] += sum_{f in chunk} sum_st q_f,st a'_f[i+s][j+t]
+// for one 32 x 32 tile; q_f = scale * G_f * inv_area. Grid (tiles_x, tiles_y, frame chunks).
+static __global__ void __launch_bounds__(kGradThreads)
+k_grad_tmpl(const uint16_t* __restrict__ frames, int64_t T, int m, int n, int wm1, const float* __restrict__ G,
+            const double* __restrict__ inv_area, float scale, const int32_t* __restrict__ coff,
+            float* __restrict__ acc_out) {
+    extern __shared__ __align__(16) float sm[];
+    const int W = 2 * wm1 + 1, K = W * W;
+    const int H = kGradTile + 2 * wm1;  // halo edge
+    float* halo = sm;                   // H x H
+    float* q = sm + H * H;              // K
+    const int tid = threadIdx.x;
+    const int i0 = blockIdx.y * kGradTile, j0 = blockIdx.x * kGradTile;
+    const int ty = tid >> 3, tx = (tid & 7) * 4;  // output row ty, columns tx..tx+3
+    const float c = (float)*coff;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int64_t f_begin = (int64_t)blockIdx.z * kGradFramesPerCta;
+    const int64_t f_end = (T < f_begin + kGradFramesPerCta) ? T : f_begin + kGradFramesPerCta;
+    for (int64_t f = f_begin; f < f_end; ++f) {
+        __syncthreads();
+        const uint16_t* a = frames + f * (int64_t)m * n;
+        for (int k = tid; k < H * H; k += kGradThreads) {
+            const int r = k / H, cc = k - r * H;
+            const int ai = i0 - wm1 + r, aj = j0 - wm1 + cc;
+            halo[k] = (ai >= 0 && ai < m && aj >= 0 && aj < n) ? (float)a[(int64_t)ai * n + aj] - c : 0.f;
+        }
+        for (int k = tid; k < K; k += kGradThreads) q[k] = scale * G[f * K + k] * (float)inv_area[k];
+        __syncthreads();
+        for (int s = 0; s < W; ++s) {
+            const float* hrow = halo + (ty + s) * H + tx;
+            const float* qrow = q + s * W;
+            float seg[4];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) seg[x] = hrow[x];
+            for (int t = 0; t < W; ++t) {
+                seg[3] = hrow[t + 3];
+                const float qv = qrow[t];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) acc[x] = fmaf(qv, seg[x], acc[x]);
+#pragma unroll
+                for (int x = 0; x < 3; ++x) seg[x] = seg[x + 1];
+            }
+        }
+    }
+    const int i = i0 + ty;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        const int j = j0 + tx + x;
+        if (i < m && j < n) atomicAdd(&acc_out[(int64_t)i * n + j], acc[x]);
+    }
+}
+
+// dL/db[i][j] += -2 acc[i][j] + 2 b'[i][j] * sum of Q over the shifts whose
+// overlap contains (i, j).
+static __global__ void __launch_bounds__(256)
+k_grad_tmpl_finish(const float* __restrict__ acc, const float* __restrict__ Q, int m, int n, int wm1,
+                   const void* __restrict__ tmpl, int tmpl_f32, const int32_t* __restrict__ coff,
+                   float* __restrict__ grad) {
+    extern __shared__ __align__(16) float P[];
+    const int W = 2 * wm1 + 1;
+    prefix2d(Q, P, W, threadIdx.x, blockDim.x);
+    const float c = (float)*coff;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < (int64_t)m * n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p / n), j = (int)(p % n);
+        const float bv = tmpl_f32 ? static_cast<const float*>(tmpl)[p] : (float)static_cast<const uint16_t*>(tmpl)[p];
+        const float cover = rect(P, W, wm1, max(-wm1, -i), min(wm1, m - 1 - i), max(-wm1, -j), min(wm1, n - 1 - j));
+        grad[p] += -2.f * acc[p] + 2.f * (bv - c) * cover;
+    }
+}
+
+// dL/da_f for one 32 x 32 tile of one frame. Grid (tiles_x, tiles_y, T).
+static __global__ void __launch_bounds__(kGradThreads)
+k_grad_frames(const uint16_t* __restrict__ frames, int m, int n, int wm1, const float* __restrict__ G,
+              const double* __restrict__ inv_area, float scale, const void* __restrict__ tmpl, int tmpl_f32,
+              const int32_t* __restrict__ coff, float* __restrict__ grad_frames) {
+    extern __shared__ __align__(16) float sm[];
+    const int W = 2 * wm1 + 1, K = W * W, L = W + 1;
+    const int H = kGradTile + 2 * wm1;
+    float* halo = sm;         // H x H: b' around the tile
+    float* q = sm + H * H;    // K, stored flipped: qf[(wm1-s)][(wm1-t)]
+    float* P = q + K;         // (W+1)^2 prefix of q (unflipped)
+    float* qraw = P + L * L;  // K
+    const int tid = threadIdx.x;
+    const int i0 = blockIdx.y * kGradTile, j0 = blockIdx.x * kGradTile;
+    const int64_t f = blockIdx.z;
+    const float c = (float)*coff;
+    for (int k = tid; k < H * H; k += kGradThreads) {
+        const int r = k / H, cc = k - r * H;
+        const int bi = i0 - wm1 + r, bj = j0 - wm1 + cc;
+        float v = 0.f;
+        if (bi >= 0 && bi < m && bj >= 0 && bj < n) {
+            const int64_t p = (int64_t)bi * n + bj;
+            v = (tmpl_f32 ? static_cast<const float*>(tmpl)[p] : (float)static_cast<const uint16_t*>(tmpl)[p]) - c;
+        }
+        halo[k] = v;
+    }
+    for (int k = tid; k < K; k += kGradThreads) {
+        const float qv = scale * G[f * K + k] * (float)inv_area[k];
+        qraw[k] = qv;
+        q[K - 1 - k] = qv;  // flip both shift axes
+    }
+    __syncthreads();
+    prefix2d(qraw, P, W, tid, kGradThreads);
+    // sum_st q_st b'[k-s][l-t] = sum_{s',t'} qflip[s'][t'] b'[k-wm1+s'][l-wm1+t']
+    const int ty = tid >> 3, tx = (tid & 7) * 4;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int s = 0; s < W; ++s) {
+        const float* hrow = halo + (ty + s) * H + tx;
+        const float* qrow = q + s * W;
+        float seg[4];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) seg[x] = hrow[x];
+        for (int t = 0; t < W; ++t) {
+            seg[3] = hrow[t + 3];
+            const float qv = qrow[t];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) acc[x] = fmaf(qv, seg[x], acc[x]);
+#pragma unroll
+            for (int x = 0; x < 3; ++x) seg[x] = seg[x + 1];
+        }
+    }
+    const int k = i0 + ty;
+    const uint16_t* a = frames + f * (int64_t)m * n;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        const int l = j0 + tx + x;
+        if (k < m && l < n) {
+            // shifts (s, t) with (k - s, l - t) inside the template
+            const float cover = rect(P, W, wm1, max(-wm1, k - m + 1), min(wm1, k), max(-wm1, l - n + 1), min(wm1, l));
+            const float av = (float)a[(int64_t)k * n + l] - c;
+            grad_frames[f * (int64_t)m * n + (int64_t)k * n + l] = 2.f * av * cover - 2.f * acc[x];
+        }
+    }
+}
+
+}  // namespace moco

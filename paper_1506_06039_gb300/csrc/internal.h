@@ -42,6 +42,18 @@ cudaError_t launch_copy_shifts(const int32_t* coarse, int32_t* shifts, const dou
 cudaError_t launch_template_offset(bool f32, const void* tmpl, int m, int n, int levels, int32_t* coff_i,
                                    float* coff_f, cudaStream_t st);
 
+cudaError_t launch_softmin(const double* cost, int64_t T, int K, double tau_scale, double* loss, float* weights,
+                           cudaStream_t st);
+
+// Shared memory the adjoint kernels need for half-window wm1.
+size_t grad_smem_bytes(int wm1);
+
+// Adjoint of f (levels = 0): grad_template += dL/db, grad_frames = dL/da
+// (if non-null). acc (m*n floats) and Q (W*W floats) are scratch.
+cudaError_t launch_grad(const uint16_t* frames, int64_t T, int m, int n, int wm1, const float* G, float scale,
+                        const double* inv_area, const int32_t* coff, const void* tmpl, int tmpl_f32,
+                        float* acc, float* Q, float* grad_template, float* grad_frames, cudaStream_t st);
+
 // Sets the dynamic shared-memory limit of `func` on the current device once.
 cudaError_t ensure_smem(const void* func, size_t bytes);
 

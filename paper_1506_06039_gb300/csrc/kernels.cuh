@@ -462,57 +462,103 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 // (2 sc + u, 2 tc + v), u, v in {-1, 0, 1}, the exact int64
 //     S = sum over D of (a[i+s][j+t] - b[i][j])^2
 // at full resolution, all nine accumulated in one pass over the frame.
-// Grid (kJitCtas per frame, frames). Each thread owns 8 template columns of
-// a band of kJitRows rows and walks down it keeping the three frame rows it
-// needs (i+s0-1 .. i+s0+1, 10 columns each) in registers, so every frame row
-// is loaded once per thread with two 16-byte loads. Per-CTA partial sums go
-// to acc[f][9] by 64-bit atomics; the last CTA of a frame (ticket counter)
-// takes the minimum of S / Area with the tie-break, compared as exact
-// rationals. acc and ticket must be zero on entry (the host clears them).
-constexpr int kJitRows = 32;
+// Grid (CTAs per frame, frames). Each thread owns 8 template columns of a
+// band of kJitRows rows and walks down it keeping the three frame rows it
+// needs (i+s0-1 .. i+s0+1, 10 columns each) in rotating register slots, so
+// every frame row is loaded once per thread with two or three 16-byte loads.
+// Since 2 tc is even, the 10-column window starts at an odd half-word of its
+// aligned 8-column block: five byte permutes realign it. Columns outside the
+// frame are masked per thread (a fixed bit mask), rows outside by a flag.
+// Per-CTA partial sums go to acc[f][9] by 64-bit atomics; the last CTA of a
+// frame (ticket counter) takes the minimum of S / Area with the tie-break,
+// compared as exact rationals. acc and ticket are zero on entry.
+constexpr int kJitRows = 33;
 
-__device__ __forceinline__ void unpack8(const uint4 p, int32_t* v) {
-    const uint32_t w[4] = {p.x, p.y, p.z, p.w};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        v[2 * k] = (int32_t)lo16(w[k]);
-        v[2 * k + 1] = (int32_t)hi16(w[k]);
-    }
-}
+struct JitRow {
+    int32_t v[10];
+    bool ok;
+};
 
-// out[k] = in[O + k], k < 10 (O a compile-time offset < 8).
-template <int O>
-__device__ __forceinline__ void take10(const int32_t (&in)[24], int32_t (&out)[10]) {
-#pragma unroll
-    for (int k = 0; k < 10; ++k) out[k] = in[O + k];
-}
-
-// The 10 frame values at columns c0 + o .. c0 + o + 9 of one row. Interior
-// rows use aligned 16-byte loads of columns [c0, c0 + 16) (and [c0 + 16,
-// c0 + 24) when o == 7); border rows load element by element, zero outside.
-__device__ __forceinline__ void window_row(const uint16_t* __restrict__ arow, int c0, int o, int n, bool interior,
-                                           int32_t (&out)[10]) {
-    int32_t v[24];
+// The 10 frame values at columns c0 + 2Q + 1 + k, k < 10, of row `arow`.
+template <int Q>
+__device__ __forceinline__ void jit_load(const uint16_t* __restrict__ arow, int c0, int n, bool interior,
+                                         JitRow& r) {
+    uint32_t w[12];
     if (interior) {
-        unpack8(__ldg(reinterpret_cast<const uint4*>(arow + c0)), v);
-        unpack8(__ldg(reinterpret_cast<const uint4*>(arow + c0 + 8)), v + 8);
-        if (o == 7) unpack8(__ldg(reinterpret_cast<const uint4*>(arow + c0 + 16)), v + 16);
+        const uint4 p0 = __ldg(reinterpret_cast<const uint4*>(arow + c0));
+        const uint4 p1 = __ldg(reinterpret_cast<const uint4*>(arow + c0 + 8));
+        w[0] = p0.x; w[1] = p0.y; w[2] = p0.z; w[3] = p0.w;
+        w[4] = p1.x; w[5] = p1.y; w[6] = p1.z; w[7] = p1.w;
+        if (Q == 3) w[8] = __ldg(reinterpret_cast<const uint32_t*>(arow + c0 + 16));
     } else {
 #pragma unroll
-        for (int k = 0; k < 17; ++k) {
-            const int c = c0 + k;
-            v[k] = (c >= 0 && c < n) ? (int32_t)__ldg(arow + c) : 0;
+        for (int k = 0; k < 9; ++k) {
+            const int c = c0 + 2 * k;
+            const uint32_t lo = (c >= 0 && c < n) ? (uint32_t)__ldg(arow + c) : 0u;
+            const uint32_t hi = (c + 1 >= 0 && c + 1 < n) ? (uint32_t)__ldg(arow + c + 1) : 0u;
+            w[k] = lo | (hi << 16);
         }
     }
-    switch (o) {
-        case 0: take10<0>(v, out); break;
-        case 1: take10<1>(v, out); break;
-        case 2: take10<2>(v, out); break;
-        case 3: take10<3>(v, out); break;
-        case 4: take10<4>(v, out); break;
-        case 5: take10<5>(v, out); break;
-        case 6: take10<6>(v, out); break;
-        default: take10<7>(v, out); break;
+#pragma unroll
+    for (int p = 0; p < 5; ++p) {
+        const uint32_t pr = __byte_perm(w[Q + p], w[Q + p + 1], 0x5432);
+        r.v[2 * p] = (int32_t)(pr & 0xffffu);
+        r.v[2 * p + 1] = (int32_t)(pr >> 16);
+    }
+}
+
+// Accumulate one template row against window rows r0 (u=0), r1, r2.
+template <bool MASKED>
+__device__ __forceinline__ void jit_row(const JitRow& r0, const JitRow& r1, const JitRow& r2,
+                                        const int32_t (&bv)[8], uint32_t mask, long long (&acc)[9]) {
+    const JitRow* rows[3] = {&r0, &r1, &r2};
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+        if (!rows[u]->ok) continue;
+#pragma unroll
+        for (int v = 0; v < 3; ++v)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                int d = rows[u]->v[k + v] - bv[k];
+                if (MASKED) d = ((mask >> (v * 8 + k)) & 1u) ? d : 0;
+                acc[u * 3 + v] += (long long)d * d;
+            }
+    }
+}
+
+template <int Q, bool MASKED>
+__device__ __forceinline__ void jit_band(const uint16_t* __restrict__ a, const uint16_t* __restrict__ tmpl, int m,
+                                         int n, int s0, int c0, int j0, bool interior, uint32_t mask, int i_begin,
+                                         int i_end, long long (&acc)[9]) {
+    JitRow A, B, C;
+    auto load = [&](JitRow& r, int ar) {
+        r.ok = ar >= 0 && ar < m;
+        if (r.ok) jit_load<Q>(a + (int64_t)ar * n, c0, n, interior, r);
+    };
+    auto brow = [&](int i, int32_t (&bv)[8]) {
+        const uint4 p = __ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)i * n + j0));
+        const uint32_t w[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            bv[2 * k] = (int32_t)lo16(w[k]);
+            bv[2 * k + 1] = (int32_t)hi16(w[k]);
+        }
+    };
+    load(A, i_begin + s0 - 1);
+    load(B, i_begin + s0);
+    int32_t bv[8];
+    for (int i = i_begin; i < i_end; i += 3) {
+        load(C, i + s0 + 1);
+        brow(i, bv);
+        jit_row<MASKED>(A, B, C, bv, mask, acc);
+        if (i + 1 >= i_end) break;
+        load(A, i + s0 + 2);
+        brow(i + 1, bv);
+        jit_row<MASKED>(B, C, A, bv, mask, acc);
+        if (i + 2 >= i_end) break;
+        load(B, i + s0 + 3);
+        brow(i + 2, bv);
+        jit_row<MASKED>(C, A, B, bv, mask, acc);
     }
 }
 
@@ -534,7 +580,7 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     const int64_t f = blockIdx.y;
     const int s0 = 2 * coarse[2 * f], t0 = 2 * coarse[2 * f + 1];
     const uint16_t* a = frames + f * fstride;
-    u64 acc[9];
+    long long acc[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = 0;
     const int G = n / 8;
@@ -543,87 +589,41 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     if (task < G * nb) {
         const int g = task % G, band = task / G;
         const int j0 = 8 * g;
-        // Frame columns j0 + t0 - 1 + k, k < 10, live in the aligned 16-column
-        // block starting at c0, at offset o.
+        // Frame columns j0 + t0 - 1 + k (k < 10) start at the odd half-word
+        // 2Q + 1 of the aligned block beginning at c0.
         const int lead = j0 + t0 - 1;
         const int c0 = lead >= 0 ? (lead & ~7) : -((-lead + 7) & ~7);
-        const int o = lead - c0;
-        const bool interior = (lead >= 0) && (lead + 10 <= n) && (c0 + (o == 7 ? 24 : 16) <= n);
+        const int Q = (lead - c0 - 1) >> 1;
+        const bool interior = (c0 >= 0) && (c0 + (Q == 3 ? 18 : 16) <= n);
+        uint32_t mask = 0;
+#pragma unroll
+        for (int v = 0; v < 3; ++v)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int c = lead + k + v;
+                if (c >= 0 && c < n) mask |= 1u << (v * 8 + k);
+            }
+        const bool full = mask == 0xffffffu;
         const int i_begin = band * kJitRows, i_end = min(m, i_begin + kJitRows);
-        int32_t win[3][10];
-        u64 esum[3][3];  // per window row: sum of a^2 over the 8 columns each v uses
-        bool ok[3];
-        auto load_slot = [&](int slot, int ar) {
-            ok[slot] = ar >= 0 && ar < m;
-            if (!ok[slot]) return;
-            window_row(a + (int64_t)ar * n, c0, o, n, interior, win[slot]);
-            if (interior) {
-                u64 e[10];
-#pragma unroll
-                for (int k = 0; k < 10; ++k) e[k] = (u64)(uint32_t)win[slot][k] * (uint32_t)win[slot][k];
-                u64 s0w = 0;
-#pragma unroll
-                for (int k = 0; k < 8; ++k) s0w += e[k];
-                esum[slot][0] = s0w;
-                esum[slot][1] = s0w - e[0] + e[8];
-                esum[slot][2] = s0w - e[0] - e[1] + e[8] + e[9];
-            }
-        };
-        // rows i_begin + s0 - 1 and i_begin + s0 fill window slots 0 and 1
-        load_slot(0, i_begin + s0 - 1);
-        load_slot(1, i_begin + s0);
-        for (int i = i_begin; i < i_end; ++i) {
-            load_slot(2, i + s0 + 1);
-            int32_t bv[8];
-            unpack8(__ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)i * n + j0)), bv);
-            if (interior) {
-                // S = sum a^2 + sum b^2 - 2 sum a b over the thread's pixels,
-                // all exact: products of two 16-bit values fit 32 bits.
-                u64 eb = 0;
-#pragma unroll
-                for (int k = 0; k < 8; ++k) eb += (u64)(uint32_t)bv[k] * (uint32_t)bv[k];
-#pragma unroll
-                for (int u = 0; u < 3; ++u) {
-                    if (!ok[u]) continue;
-#pragma unroll
-                    for (int v = 0; v < 3; ++v) {
-                        u64 x = 0;
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) x += (u64)(uint32_t)win[u][k + v] * (uint32_t)bv[k];
-                        acc[u * 3 + v] += esum[u][v] + eb - 2 * x;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int u = 0; u < 3; ++u) {
-                    if (!ok[u]) continue;
-#pragma unroll
-                    for (int v = 0; v < 3; ++v)
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const int c = lead + k + v;
-                            if (c >= 0 && c < n) acc[u * 3 + v] += sq64(win[u][k + v] - bv[k]);
-                        }
-                }
-            }
-            // slide the window down one row
-#pragma unroll
-            for (int k = 0; k < 10; ++k) {
-                win[0][k] = win[1][k];
-                win[1][k] = win[2][k];
-            }
-#pragma unroll
-            for (int v = 0; v < 3; ++v) {
-                esum[0][v] = esum[1][v];
-                esum[1][v] = esum[2][v];
-            }
-            ok[0] = ok[1];
-            ok[1] = ok[2];
+#define MOCO_JIT_CASE(QQ)                                                                                    \
+    case QQ:                                                                                                 \
+        if (full && interior)                                                                                \
+            jit_band<QQ, false>(a, tmpl, m, n, s0, c0, j0, true, mask, i_begin, i_end, acc);                 \
+        else                                                                                                 \
+            jit_band<QQ, true>(a, tmpl, m, n, s0, c0, j0, interior, mask, i_begin, i_end, acc);              \
+        break;
+        switch (Q) {
+            MOCO_JIT_CASE(0)
+            MOCO_JIT_CASE(1)
+            MOCO_JIT_CASE(2)
+            default:
+            MOCO_JIT_CASE(3)
         }
+#undef MOCO_JIT_CASE
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        u64 v = acc[k];
+        u64 v = (u64)acc[k];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         if ((tid & 31) == 0) red[tid >> 5][k] = v;

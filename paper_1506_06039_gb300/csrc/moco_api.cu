@@ -150,6 +150,8 @@ moco_status allocate_shape(ShapePlan& sp) {
     c.add(&sp.coarse, (size_t)(G * 2 * 4));
     c.add(&sp.fbest, (size_t)(G * 8));
     c.add(&sp.margin, (size_t)(G * 4));
+    c.add(&sp.grad_acc, (size_t)(m * n * 4));
+    c.add(&sp.grad_Q, (size_t)(W * W * 4));
     c.add(&sp.jit_acc, (size_t)(G * 9 * 8));
     c.add(&sp.jit_ticket, (size_t)(G * 4));
     for (int k = 0; k < 2; ++k) {
@@ -393,17 +395,42 @@ moco_status moco_cost_surface(moco_plan_t plan, int32_t shape_idx, const uint16_
 
 moco_status moco_softmin(moco_plan_t plan, int32_t shape_idx, const double* cost_dev, int64_t T, double tau_scale,
                          double* loss_dev, float* weights_dev, void* stream) {
-    (void)plan; (void)shape_idx; (void)cost_dev; (void)T; (void)tau_scale; (void)loss_dev; (void)weights_dev;
-    (void)stream;
-    return fail(MOCO_ERR_UNSUPPORTED, "moco_softmin is not built into this library yet");
+    if (!plan) return fail(MOCO_ERR_INVALID_ARG, "null plan");
+    if (shape_idx < 0 || shape_idx >= (int)plan->shapes.size()) return fail(MOCO_ERR_INVALID_ARG, "bad shape_idx");
+    if (T < 0 || !(tau_scale >= 0.0)) return fail(MOCO_ERR_INVALID_ARG, "T < 0 or bad tau_scale");
+    if (T == 0) return MOCO_OK;
+    if (!cost_dev || !loss_dev || !weights_dev) return fail(MOCO_ERR_INVALID_ARG, "null cost, loss or weights");
+    DeviceGuard guard(plan->device);
+    ShapePlan& sp = plan->shapes[shape_idx];
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    plan->prof.begin(K_SOFTMIN, st);
+    cudaError_t e = launch_softmin(cost_dev, T, sp.W * sp.W, tau_scale, loss_dev, weights_dev, st);
+    plan->prof.end(st);
+    if (e != cudaSuccess) return cuda_fail(e, "k_softmin");
+    return MOCO_OK;
 }
 
 moco_status moco_cost_backward(moco_plan_t plan, int32_t shape_idx, const uint16_t* frames_dev, int64_t T,
-                               const float* grad_cost_dev, float* grad_template_dev, float* grad_frames_dev,
-                               void* stream) {
-    (void)plan; (void)shape_idx; (void)frames_dev; (void)T; (void)grad_cost_dev; (void)grad_template_dev;
-    (void)grad_frames_dev; (void)stream;
-    return fail(MOCO_ERR_UNSUPPORTED, "moco_cost_backward is not built into this library yet");
+                               const float* grad_cost_dev, float grad_scale, float* grad_template_dev,
+                               float* grad_frames_dev, void* stream) {
+    if (!plan) return fail(MOCO_ERR_INVALID_ARG, "null plan");
+    if (shape_idx < 0 || shape_idx >= (int)plan->shapes.size()) return fail(MOCO_ERR_INVALID_ARG, "bad shape_idx");
+    if (T < 0) return fail(MOCO_ERR_INVALID_ARG, "T < 0");
+    ShapePlan& sp = plan->shapes[shape_idx];
+    if (sp.levels != 0) return fail(MOCO_ERR_UNSUPPORTED, "the adjoint needs levels == 0");
+    if (grad_smem_bytes(sp.wm1) > 227 * 1024) return fail(MOCO_ERR_UNSUPPORTED, "window too large for the adjoint");
+    if (T == 0) return MOCO_OK;
+    if (!frames_dev || !grad_cost_dev || !grad_template_dev)
+        return fail(MOCO_ERR_INVALID_ARG, "null frames, grad_cost or grad_template");
+    DeviceGuard guard(plan->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    plan->prof.begin(K_BACKWARD, st);
+    cudaError_t e = launch_grad(frames_dev, T, sp.desc.m, sp.desc.n, sp.wm1, grad_cost_dev, grad_scale, sp.inv_area,
+                                sp.coff_i, sp.tmpl, sp.f32 ? 1 : 0, sp.grad_acc, sp.grad_Q, grad_template_dev,
+                                grad_frames_dev, st);
+    plan->prof.end(st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint kernels");
+    return MOCO_OK;
 }
 
 moco_status moco_profile_enable(moco_plan_t plan, int32_t max_launches) {

@@ -70,6 +70,8 @@ struct ShapePlan {
     int32_t* coarse = nullptr;
     double* fbest = nullptr;
     float* margin = nullptr;
+    float* grad_acc = nullptr;         // m x n (adjoint scratch)
+    float* grad_Q = nullptr;           // W x W
     u64* jit_acc = nullptr;            // group x 9
     unsigned int* jit_ticket = nullptr;  // group
     // staging for moco_align_host (double-buffered)

@@ -287,3 +287,11 @@ def test_softmin_gradient_central_differences(which):
             ap[f, i, j] += eps; am[f, i, j] -= eps
             fd = (oracle.softmin_loss(ap, b, w, tau)[0] - oracle.softmin_loss(am, b, w, tau)[0]) / (2 * eps)
             assert ga[f, i, j] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_softmin_zero_tau_is_the_min():
+    # tau = 0: the soft-min is the min, its weight split over the minimisers.
+    a = np.full((6, 8), 4.0)
+    b = np.full((6, 8), 4.0)
+    L, lf, gb, _ = oracle.softmin_loss(a, b, 2, [0.0], grad_template=True)
+    assert L == 0.0 and np.all(gb == 0.0)
