@@ -464,101 +464,110 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 // at full resolution, all nine accumulated in one pass over the frame.
 // Grid (CTAs per frame, frames). Each thread owns 8 template columns of a
 // band of kJitRows rows and walks down it keeping the three frame rows it
-// needs (i+s0-1 .. i+s0+1, 10 columns each) in rotating register slots, so
-// every frame row is loaded once per thread with two or three 16-byte loads.
-// Since 2 tc is even, the 10-column window starts at an odd half-word of its
-// aligned 8-column block: five byte permutes realign it. Columns outside the
-// frame are masked per thread (a fixed bit mask), rows outside by a flag.
+// needs (i+s0-1 .. i+s0+1, 10 columns each) in registers, so
+// every frame row is loaded once per thread.
+// Since 2 tc is even, the 10-column window starts at an odd column: six
+// 32-bit loads from the even column before it and five byte permutes give
+// the 10 values. The next row is prefetched one template row ahead. Columns
+// outside the frame are masked per thread (a fixed bit mask), rows outside
+// by a flag.
 // Per-CTA partial sums go to acc[f][9] by 64-bit atomics; the last CTA of a
 // frame (ticket counter) takes the minimum of S / Area with the tie-break,
 // compared as exact rationals. acc and ticket are zero on entry.
-constexpr int kJitRows = 33;
+constexpr int kJitRows = 32;
 
-struct JitRow {
-    int32_t v[10];
-    bool ok;
+// Raw words of one frame row: 6 x 32 bits = half-words lead-1 .. lead+10,
+// loaded from lead - 1 (even, so 4-byte aligned). Border threads load
+// element by element with zeros outside the frame.
+struct JitRaw {
+    uint32_t w[6];
 };
 
-// The 10 frame values at columns c0 + 2Q + 1 + k, k < 10, of row `arow`.
-template <int Q>
-__device__ __forceinline__ void jit_load(const uint16_t* __restrict__ arow, int c0, int n, bool interior,
-                                         JitRow& r) {
-    uint32_t w[12];
+__device__ __forceinline__ void jit_fetch(const uint16_t* __restrict__ arow, int lead, int n, bool interior,
+                                          bool ok, JitRaw& r) {
+    if (!ok) return;
     if (interior) {
-        const uint4 p0 = __ldg(reinterpret_cast<const uint4*>(arow + c0));
-        const uint4 p1 = __ldg(reinterpret_cast<const uint4*>(arow + c0 + 8));
-        w[0] = p0.x; w[1] = p0.y; w[2] = p0.z; w[3] = p0.w;
-        w[4] = p1.x; w[5] = p1.y; w[6] = p1.z; w[7] = p1.w;
-        if (Q == 3) w[8] = __ldg(reinterpret_cast<const uint32_t*>(arow + c0 + 16));
+        const uint32_t* p = reinterpret_cast<const uint32_t*>(arow + lead - 1);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) r.w[k] = __ldg(p + k);
     } else {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int c = c0 + 2 * k;
+        for (int k = 0; k < 6; ++k) {
+            const int c = lead - 1 + 2 * k;
             const uint32_t lo = (c >= 0 && c < n) ? (uint32_t)__ldg(arow + c) : 0u;
             const uint32_t hi = (c + 1 >= 0 && c + 1 < n) ? (uint32_t)__ldg(arow + c + 1) : 0u;
-            w[k] = lo | (hi << 16);
+            r.w[k] = lo | (hi << 16);
         }
     }
+}
+
+// The 10 values at columns lead .. lead + 9: drop the first half-word.
+__device__ __forceinline__ void jit_unpack(const JitRaw& r, int32_t (&v)[10]) {
 #pragma unroll
     for (int p = 0; p < 5; ++p) {
-        const uint32_t pr = __byte_perm(w[Q + p], w[Q + p + 1], 0x5432);
-        r.v[2 * p] = (int32_t)(pr & 0xffffu);
-        r.v[2 * p + 1] = (int32_t)(pr >> 16);
+        const uint32_t pr = __byte_perm(r.w[p], r.w[p + 1], 0x5432);
+        v[2 * p] = (int32_t)(pr & 0xffffu);
+        v[2 * p + 1] = (int32_t)(pr >> 16);
     }
 }
 
-// Accumulate one template row against window rows r0 (u=0), r1, r2.
 template <bool MASKED>
-__device__ __forceinline__ void jit_row(const JitRow& r0, const JitRow& r1, const JitRow& r2,
-                                        const int32_t (&bv)[8], uint32_t mask, long long (&acc)[9]) {
-    const JitRow* rows[3] = {&r0, &r1, &r2};
-#pragma unroll
-    for (int u = 0; u < 3; ++u) {
-        if (!rows[u]->ok) continue;
-#pragma unroll
-        for (int v = 0; v < 3; ++v)
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                int d = rows[u]->v[k + v] - bv[k];
-                if (MASKED) d = ((mask >> (v * 8 + k)) & 1u) ? d : 0;
-                acc[u * 3 + v] += (long long)d * d;
-            }
-    }
-}
-
-template <int Q, bool MASKED>
 __device__ __forceinline__ void jit_band(const uint16_t* __restrict__ a, const uint16_t* __restrict__ tmpl, int m,
-                                         int n, int s0, int c0, int j0, bool interior, uint32_t mask, int i_begin,
-                                         int i_end, long long (&acc)[9]) {
-    JitRow A, B, C;
-    auto load = [&](JitRow& r, int ar) {
-        r.ok = ar >= 0 && ar < m;
-        if (r.ok) jit_load<Q>(a + (int64_t)ar * n, c0, n, interior, r);
-    };
-    auto brow = [&](int i, int32_t (&bv)[8]) {
-        const uint4 p = __ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)i * n + j0));
-        const uint32_t w[4] = {p.x, p.y, p.z, p.w};
+                                         int n, int s0, int lead, int j0, bool interior, uint32_t mask,
+                                         int i_begin, int i_end, long long (&acc)[9]) {
+    int32_t win[3][10];
+    bool ok[3];
+    JitRaw raw;
+    // window rows i_begin + s0 - 1, i_begin + s0
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            bv[2 * k] = (int32_t)lo16(w[k]);
-            bv[2 * k + 1] = (int32_t)hi16(w[k]);
+    for (int u = 0; u < 2; ++u) {
+        const int ar = i_begin + s0 - 1 + u;
+        ok[u] = ar >= 0 && ar < m;
+        jit_fetch(a + (int64_t)ar * n, lead, n, interior, ok[u], raw);
+        if (ok[u]) jit_unpack(raw, win[u]);
+    }
+    // prefetch the first new row and template row
+    int ar = i_begin + s0 + 1;
+    bool okn = ar >= 0 && ar < m;
+    jit_fetch(a + (int64_t)ar * n, lead, n, interior, okn, raw);
+    uint4 braw = __ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)i_begin * n + j0));
+    for (int i = i_begin; i < i_end; ++i) {
+        ok[2] = okn;
+        if (okn) jit_unpack(raw, win[2]);
+        int32_t bv[8];
+        {
+            const uint32_t w[4] = {braw.x, braw.y, braw.z, braw.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                bv[2 * k] = (int32_t)lo16(w[k]);
+                bv[2 * k + 1] = (int32_t)hi16(w[k]);
+            }
         }
-    };
-    load(A, i_begin + s0 - 1);
-    load(B, i_begin + s0);
-    int32_t bv[8];
-    for (int i = i_begin; i < i_end; i += 3) {
-        load(C, i + s0 + 1);
-        brow(i, bv);
-        jit_row<MASKED>(A, B, C, bv, mask, acc);
-        if (i + 1 >= i_end) break;
-        load(A, i + s0 + 2);
-        brow(i + 1, bv);
-        jit_row<MASKED>(B, C, A, bv, mask, acc);
-        if (i + 2 >= i_end) break;
-        load(B, i + s0 + 3);
-        brow(i + 2, bv);
-        jit_row<MASKED>(C, A, B, bv, mask, acc);
+        if (i + 1 < i_end) {  // prefetch for the next template row
+            ar = i + s0 + 2;
+            okn = ar >= 0 && ar < m;
+            jit_fetch(a + (int64_t)ar * n, lead, n, interior, okn, raw);
+            braw = __ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)(i + 1) * n + j0));
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            if (!ok[u]) continue;
+#pragma unroll
+            for (int v = 0; v < 3; ++v)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    int d = win[u][k + v] - bv[k];
+                    if (MASKED) d = ((mask >> (v * 8 + k)) & 1u) ? d : 0;
+                    acc[u * 3 + v] += (long long)d * d;
+                }
+        }
+#pragma unroll
+        for (int k = 0; k < 10; ++k) {
+            win[0][k] = win[1][k];
+            win[1][k] = win[2][k];
+        }
+        ok[0] = ok[1];
+        ok[1] = ok[2];
     }
 }
 
@@ -589,12 +598,10 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     if (task < G * nb) {
         const int g = task % G, band = task / G;
         const int j0 = 8 * g;
-        // Frame columns j0 + t0 - 1 + k (k < 10) start at the odd half-word
-        // 2Q + 1 of the aligned block beginning at c0.
+        // Frame columns lead .. lead + 9 (lead = j0 + t0 - 1 is odd, so
+        // lead - 1 is 4-byte aligned).
         const int lead = j0 + t0 - 1;
-        const int c0 = lead >= 0 ? (lead & ~7) : -((-lead + 7) & ~7);
-        const int Q = (lead - c0 - 1) >> 1;
-        const bool interior = (c0 >= 0) && (c0 + (Q == 3 ? 18 : 16) <= n);
+        const bool interior = (lead - 1 >= 0) && (lead + 11 <= n);
         uint32_t mask = 0;
 #pragma unroll
         for (int v = 0; v < 3; ++v)
@@ -603,23 +610,11 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
                 const int c = lead + k + v;
                 if (c >= 0 && c < n) mask |= 1u << (v * 8 + k);
             }
-        const bool full = mask == 0xffffffu;
         const int i_begin = band * kJitRows, i_end = min(m, i_begin + kJitRows);
-#define MOCO_JIT_CASE(QQ)                                                                                    \
-    case QQ:                                                                                                 \
-        if (full && interior)                                                                                \
-            jit_band<QQ, false>(a, tmpl, m, n, s0, c0, j0, true, mask, i_begin, i_end, acc);                 \
-        else                                                                                                 \
-            jit_band<QQ, true>(a, tmpl, m, n, s0, c0, j0, interior, mask, i_begin, i_end, acc);              \
-        break;
-        switch (Q) {
-            MOCO_JIT_CASE(0)
-            MOCO_JIT_CASE(1)
-            MOCO_JIT_CASE(2)
-            default:
-            MOCO_JIT_CASE(3)
-        }
-#undef MOCO_JIT_CASE
+        if (interior && mask == 0xffffffu)
+            jit_band<false>(a, tmpl, m, n, s0, lead, j0, true, mask, i_begin, i_end, acc);
+        else
+            jit_band<true>(a, tmpl, m, n, s0, lead, j0, interior, mask, i_begin, i_end, acc);
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
