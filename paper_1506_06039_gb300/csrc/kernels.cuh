@@ -462,112 +462,80 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 // (2 sc + u, 2 tc + v), u, v in {-1, 0, 1}, the exact int64
 //     S = sum over D of (a[i+s][j+t] - b[i][j])^2
 // at full resolution, all nine accumulated in one pass over the frame.
-// Grid (CTAs per frame, frames). Each thread owns 8 template columns of a
-// band of kJitRows rows and walks down it keeping the three frame rows it
-// needs (i+s0-1 .. i+s0+1, 10 columns each) in registers, so
-// every frame row is loaded once per thread.
-// Since 2 tc is even, the 10-column window starts at an odd column: six
-// 32-bit loads from the even column before it and five byte permutes give
-// the 10 values. The next row is prefetched one template row ahead. Columns
-// outside the frame are masked per thread (a fixed bit mask), rows outside
-// by a flag.
-// Per-CTA partial sums go to acc[f][9] by 64-bit atomics; the last CTA of a
-// frame (ticket counter) takes the minimum of S / Area with the tie-break,
-// compared as exact rationals. acc and ticket are zero on entry.
+// Grid (row tiles, frames): a CTA takes kJitRows template rows. It stages
+// the kJitRows + 2 frame rows those rows meet (i0+s0-1 .. i0+s0+kJitRows),
+// shifted left by t0 - 1 columns so that every thread's 10-column window
+// starts on a 16-byte boundary (zeros outside the frame), and the template
+// rows, in shared memory. Each thread then owns 8 columns of
+// kJitRows / kJitRowSlices rows and walks down them with its three window
+// rows in registers. Columns outside the frame are masked per thread (a
+// fixed bit mask), rows outside by a per-row flag. Per-CTA partial sums go
+// to acc[f][9] by 64-bit atomics; the last CTA of a frame (ticket counter)
+// takes the minimum of S / Area with the tie-break, compared as exact
+// rationals. acc and ticket are zero on entry.
 constexpr int kJitRows = 32;
+constexpr int kJitRowSlices = kJitterThreads / 64;  // threads per column group
 
-// Raw words of one frame row: 6 x 32 bits = half-words lead-1 .. lead+10,
-// loaded from lead - 1 (even, so 4-byte aligned). Border threads load
-// element by element with zeros outside the frame.
-struct JitRaw {
-    uint32_t w[6];
-};
-
-__device__ __forceinline__ void jit_fetch(const uint16_t* __restrict__ arow, int lead, int n, bool interior,
-                                          bool ok, JitRaw& r) {
-    if (!ok) return;
-    if (interior) {
-        const uint32_t* p = reinterpret_cast<const uint32_t*>(arow + lead - 1);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) r.w[k] = __ldg(p + k);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const int c = lead - 1 + 2 * k;
-            const uint32_t lo = (c >= 0 && c < n) ? (uint32_t)__ldg(arow + c) : 0u;
-            const uint32_t hi = (c + 1 >= 0 && c + 1 < n) ? (uint32_t)__ldg(arow + c + 1) : 0u;
-            r.w[k] = lo | (hi << 16);
-        }
-    }
-}
-
-// The 10 values at columns lead .. lead + 9: drop the first half-word.
-__device__ __forceinline__ void jit_unpack(const JitRaw& r, int32_t (&v)[10]) {
-#pragma unroll
-    for (int p = 0; p < 5; ++p) {
-        const uint32_t pr = __byte_perm(r.w[p], r.w[p + 1], 0x5432);
-        v[2 * p] = (int32_t)(pr & 0xffffu);
-        v[2 * p + 1] = (int32_t)(pr >> 16);
-    }
+// smem bytes of k_jitter for width n.
+__host__ __device__ inline size_t jitter_smem_bytes(int n) {
+    const size_t ld = (size_t)n + 16;  // staged row length (halves)
+    return ld * 2 * (kJitRows + 2) + (size_t)n * 2 * kJitRows + 64;
 }
 
 template <bool MASKED>
-__device__ __forceinline__ void jit_band(const uint16_t* __restrict__ a, const uint16_t* __restrict__ tmpl, int m,
-                                         int n, int s0, int lead, int j0, bool interior, uint32_t mask,
-                                         int i_begin, int i_end, long long (&acc)[9]) {
-    int32_t win[3][10];
-    bool ok[3];
-    JitRaw raw;
-    // window rows i_begin + s0 - 1, i_begin + s0
+__device__ __forceinline__ void jit_rows(const uint16_t* __restrict__ as, const uint16_t* __restrict__ bs,
+                                         const unsigned char* __restrict__ rok, int ld, int n, int x0, int r0,
+                                         int nrows, uint32_t mask, long long (&acc)[9]) {
+    auto win = [&](int rr, int32_t (&v)[10]) {
+        const uint16_t* p = as + (size_t)rr * ld + x0;
+        const uint4 q = *reinterpret_cast<const uint4*>(p);
+        const uint32_t e = *reinterpret_cast<const uint32_t*>(p + 8);
+        const uint32_t w[5] = {q.x, q.y, q.z, q.w, e};
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const int ar = i_begin + s0 - 1 + u;
-        ok[u] = ar >= 0 && ar < m;
-        jit_fetch(a + (int64_t)ar * n, lead, n, interior, ok[u], raw);
-        if (ok[u]) jit_unpack(raw, win[u]);
-    }
-    // prefetch the first new row and template row
-    int ar = i_begin + s0 + 1;
-    bool okn = ar >= 0 && ar < m;
-    jit_fetch(a + (int64_t)ar * n, lead, n, interior, okn, raw);
-    uint4 braw = __ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)i_begin * n + j0));
-    for (int i = i_begin; i < i_end; ++i) {
-        ok[2] = okn;
-        if (okn) jit_unpack(raw, win[2]);
+        for (int k = 0; k < 5; ++k) {
+            v[2 * k] = (int32_t)lo16(w[k]);
+            v[2 * k + 1] = (int32_t)hi16(w[k]);
+        }
+    };
+    int32_t w0[10], w1[10], w2[10];
+    bool ok0 = rok[r0], ok1 = rok[r0 + 1];
+    win(r0, w0);
+    win(r0 + 1, w1);
+    for (int k = 0; k < nrows; ++k) {
+        const int rr = r0 + k;  // template row index within the tile
+        const bool ok2 = rok[rr + 2];
+        win(rr + 2, w2);
         int32_t bv[8];
         {
-            const uint32_t w[4] = {braw.x, braw.y, braw.z, braw.w};
+            const uint4 q = *reinterpret_cast<const uint4*>(bs + (size_t)rr * n + x0);
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                bv[2 * k] = (int32_t)lo16(w[k]);
-                bv[2 * k + 1] = (int32_t)hi16(w[k]);
+            for (int c = 0; c < 4; ++c) {
+                bv[2 * c] = (int32_t)lo16(w[c]);
+                bv[2 * c + 1] = (int32_t)hi16(w[c]);
             }
         }
-        if (i + 1 < i_end) {  // prefetch for the next template row
-            ar = i + s0 + 2;
-            okn = ar >= 0 && ar < m;
-            jit_fetch(a + (int64_t)ar * n, lead, n, interior, okn, raw);
-            braw = __ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)(i + 1) * n + j0));
-        }
+        const int32_t* rows[3] = {w0, w1, w2};
+        const bool oks[3] = {ok0, ok1, ok2};
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
-            if (!ok[u]) continue;
+            if (!oks[u]) continue;
 #pragma unroll
             for (int v = 0; v < 3; ++v)
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    int d = win[u][k + v] - bv[k];
-                    if (MASKED) d = ((mask >> (v * 8 + k)) & 1u) ? d : 0;
+                for (int c = 0; c < 8; ++c) {
+                    int d = rows[u][c + v] - bv[c];
+                    if (MASKED) d = ((mask >> (v * 8 + c)) & 1u) ? d : 0;
                     acc[u * 3 + v] += (long long)d * d;
                 }
         }
 #pragma unroll
-        for (int k = 0; k < 10; ++k) {
-            win[0][k] = win[1][k];
-            win[1][k] = win[2][k];
+        for (int c = 0; c < 10; ++c) {
+            w0[c] = w1[c];
+            w1[c] = w2[c];
         }
-        ok[0] = ok[1];
-        ok[1] = ok[2];
+        ok0 = ok1;
+        ok1 = ok2;
     }
 }
 
@@ -583,38 +551,59 @@ static __global__ void __launch_bounds__(kJitterThreads)
 k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* __restrict__ tmpl, int m, int n,
          const int32_t* __restrict__ coarse, int32_t* __restrict__ shifts, double* __restrict__ ffinal,
          u64* __restrict__ acc_g, unsigned int* __restrict__ ticket) {
+    extern __shared__ __align__(16) unsigned char jsm[];
     __shared__ u64 red[kJitterThreads / 32][9];
     __shared__ bool last;
+    const int ld = n + 16;
+    uint16_t* a_s = reinterpret_cast<uint16_t*>(jsm);        // (kJitRows + 2) x ld
+    uint16_t* b_s = a_s + (size_t)ld * (kJitRows + 2);        // kJitRows x n
+    unsigned char* rok = reinterpret_cast<unsigned char*>(b_s + (size_t)n * kJitRows);  // kJitRows + 2
     const int tid = threadIdx.x;
     const int64_t f = blockIdx.y;
     const int s0 = 2 * coarse[2 * f], t0 = 2 * coarse[2 * f + 1];
     const uint16_t* a = frames + f * fstride;
+    const int i0 = blockIdx.x * kJitRows;
+    const int rows = min(kJitRows, m - i0);
+    // Stage: as[rr][x] = a[i0 + s0 - 1 + rr][x + t0 - 1] (0 outside), bs = template rows.
+    for (int rr = 0; rr < rows + 2; ++rr) {
+        const int ar = i0 + s0 - 1 + rr;
+        const bool okr = ar >= 0 && ar < m;
+        if (tid == 0) rok[rr] = okr;
+        const uint16_t* arow = a + (int64_t)ar * n;
+        for (int x = tid; x < n + 2; x += kJitterThreads) {
+            const int c = x + t0 - 1;
+            a_s[(size_t)rr * ld + x] = (okr && c >= 0 && c < n) ? __ldg(arow + c) : (uint16_t)0;
+        }
+    }
+    for (int k = tid; k < rows * (n / 8); k += kJitterThreads) {
+        const int rr = k / (n / 8), q = k - rr * (n / 8);
+        *reinterpret_cast<uint4*>(b_s + (size_t)rr * n + 8 * q) =
+            __ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)(i0 + rr) * n + 8 * q));
+    }
+    __syncthreads();
     long long acc[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = 0;
     const int G = n / 8;
-    const int nb = (m + kJitRows - 1) / kJitRows;
-    const int task = blockIdx.x * kJitterThreads + tid;
-    if (task < G * nb) {
-        const int g = task % G, band = task / G;
-        const int j0 = 8 * g;
-        // Frame columns lead .. lead + 9 (lead = j0 + t0 - 1 is odd, so
-        // lead - 1 is 4-byte aligned).
-        const int lead = j0 + t0 - 1;
-        const bool interior = (lead - 1 >= 0) && (lead + 11 <= n);
+    const int per = kJitRows / kJitRowSlices;
+    for (int task = tid; task < G * kJitRowSlices; task += kJitterThreads) {
+        const int g = task % G, slice = task / G;
+        const int r0 = slice * per;
+        const int nrows = min(per, rows - r0);
+        if (nrows <= 0) continue;
+        const int x0 = 8 * g;  // window = frame columns x0 + t0 - 1 .. x0 + t0 + 8
         uint32_t mask = 0;
 #pragma unroll
         for (int v = 0; v < 3; ++v)
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                const int c = lead + k + v;
+                const int c = x0 + t0 - 1 + k + v;
                 if (c >= 0 && c < n) mask |= 1u << (v * 8 + k);
             }
-        const int i_begin = band * kJitRows, i_end = min(m, i_begin + kJitRows);
-        if (interior && mask == 0xffffffu)
-            jit_band<false>(a, tmpl, m, n, s0, lead, j0, true, mask, i_begin, i_end, acc);
+        if (mask == 0xffffffu)
+            jit_rows<false>(a_s, b_s, rok, ld, n, x0, r0, nrows, mask, acc);
         else
-            jit_band<true>(a, tmpl, m, n, s0, lead, j0, interior, mask, i_begin, i_end, acc);
+            jit_rows<true>(a_s, b_s, rok, ld, n, x0, r0, nrows, mask, acc);
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {

@@ -75,10 +75,10 @@ cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg,
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(u64) * 9 * nimg, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int) * nimg, st);
     if (e != cudaSuccess) return e;
-    const int tasks = (n / 8) * ((m + kJitRows - 1) / kJitRows);
-    const int ctas = (tasks + kJitterThreads - 1) / kJitterThreads;
-    dim3 grid((unsigned)ctas, (unsigned)nimg);
-    k_jitter<<<grid, kJitterThreads, 0, st>>>(frames, fstride, tmpl, m, n, coarse, shifts, ffinal, acc, ticket);
+    const size_t smem = jitter_smem_bytes(n);
+    if ((e = ensure_smem((const void*)k_jitter, smem)) != cudaSuccess) return e;
+    dim3 grid((unsigned)((m + kJitRows - 1) / kJitRows), (unsigned)nimg);
+    k_jitter<<<grid, kJitterThreads, smem, st>>>(frames, fstride, tmpl, m, n, coarse, shifts, ffinal, acc, ticket);
     return cudaGetLastError();
 }
 
