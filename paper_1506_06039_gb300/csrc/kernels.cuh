@@ -462,11 +462,12 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 // (2 sc + u, 2 tc + v), u, v in {-1, 0, 1}, the exact int64
 //     S = sum over D of (a[i+s][j+t] - b[i][j])^2
 // at full resolution, all nine accumulated in one pass over the frame.
-// Grid (row tiles, frames): a CTA takes kJitRows template rows. It stages
-// the kJitRows + 2 frame rows those rows meet (i0+s0-1 .. i0+s0+kJitRows),
-// shifted left by t0 - 1 columns so that every thread's 10-column window
-// starts on a 16-byte boundary (zeros outside the frame), and the template
-// rows, in shared memory. Each thread then owns 8 columns of
+// Grid (row tiles, frames): a CTA takes kJitRows template rows. It copies
+// the kJitRows + 2 frame rows those rows meet (i0+s0-1 .. i0+s0+kJitRows)
+// and the template rows into shared memory with asynchronous 16-byte copies,
+// then rewrites the frame rows shifted left by t0 - 1 columns (zeros outside
+// the frame) so that every thread's 10-column window starts on a 16-byte
+// boundary. Each thread then owns 8 columns of
 // kJitRows / kJitRowSlices rows and walks down them with its three window
 // rows in registers. Columns outside the frame are masked per thread (a
 // fixed bit mask), rows outside by a per-row flag. Per-CTA partial sums go
@@ -476,10 +477,19 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 constexpr int kJitRows = 32;
 constexpr int kJitRowSlices = kJitterThreads / 64;  // threads per column group
 
-// smem bytes of k_jitter for width n.
+// smem bytes of k_jitter for width n: shifted frame rows, raw frame rows,
+// template rows, row flags.
 __host__ __device__ inline size_t jitter_smem_bytes(int n) {
     const size_t ld = (size_t)n + 16;  // staged row length (halves)
-    return ld * 2 * (kJitRows + 2) + (size_t)n * 2 * kJitRows + 64;
+    return ld * 2 * (kJitRows + 2) * 2 + (size_t)n * 2 * kJitRows + 64;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 template <bool MASKED>
@@ -555,8 +565,9 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     __shared__ u64 red[kJitterThreads / 32][9];
     __shared__ bool last;
     const int ld = n + 16;
-    uint16_t* a_s = reinterpret_cast<uint16_t*>(jsm);        // (kJitRows + 2) x ld
-    uint16_t* b_s = a_s + (size_t)ld * (kJitRows + 2);        // kJitRows x n
+    uint16_t* a_s = reinterpret_cast<uint16_t*>(jsm);        // (kJitRows + 2) x ld, shifted
+    uint16_t* a_raw = a_s + (size_t)ld * (kJitRows + 2);      // (kJitRows + 2) x ld, as in the frame
+    uint16_t* b_s = a_raw + (size_t)ld * (kJitRows + 2);      // kJitRows x n
     unsigned char* rok = reinterpret_cast<unsigned char*>(b_s + (size_t)n * kJitRows);  // kJitRows + 2
     const int tid = threadIdx.x;
     const int64_t f = blockIdx.y;
@@ -564,27 +575,38 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     const uint16_t* a = frames + f * fstride;
     const int i0 = blockIdx.x * kJitRows;
     const int rows = min(kJitRows, m - i0);
-    // Stage: as[rr][x] = a[i0 + s0 - 1 + rr][x + t0 - 1] (0 outside), bs = template rows.
-    for (int rr = 0; rr < rows + 2; ++rr) {
+    const int G = n / 8;
+    // 1) asynchronous copies of the frame rows and template rows (all in flight)
+    for (int k = tid; k < (rows + 2) * G; k += kJitterThreads) {
+        const int rr = k / G, q = k - rr * G;
         const int ar = i0 + s0 - 1 + rr;
-        const bool okr = ar >= 0 && ar < m;
-        if (tid == 0) rok[rr] = okr;
-        const uint16_t* arow = a + (int64_t)ar * n;
-        for (int x = tid; x < n + 2; x += kJitterThreads) {
-            const int c = x + t0 - 1;
-            a_s[(size_t)rr * ld + x] = (okr && c >= 0 && c < n) ? __ldg(arow + c) : (uint16_t)0;
-        }
+        if (ar >= 0 && ar < m) cp_async16(a_raw + (size_t)rr * ld + 8 * q, a + (int64_t)ar * n + 8 * q);
     }
-    for (int k = tid; k < rows * (n / 8); k += kJitterThreads) {
-        const int rr = k / (n / 8), q = k - rr * (n / 8);
-        *reinterpret_cast<uint4*>(b_s + (size_t)rr * n + 8 * q) =
-            __ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)(i0 + rr) * n + 8 * q));
+    for (int k = tid; k < rows * G; k += kJitterThreads) {
+        const int rr = k / G, q = k - rr * G;
+        cp_async16(b_s + (size_t)rr * n + 8 * q, tmpl + (int64_t)(i0 + rr) * n + 8 * q);
+    }
+    for (int rr = tid; rr < rows + 2; rr += kJitterThreads) {
+        const int ar = i0 + s0 - 1 + rr;
+        rok[rr] = ar >= 0 && ar < m;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // 2) a_s[rr][x] = frame column x + t0 - 1 (odd shift: one byte permute per
+    //    word), zero outside the frame; x < n + 2.
+    const int W2 = n / 2 + 1;  // words per shifted row
+    for (int k = tid; k < (rows + 2) * W2; k += kJitterThreads) {
+        const int rr = k / W2, xw = k - rr * W2;
+        const int c = 2 * xw + t0 - 1;  // frame column of the word's low half (odd)
+        const uint32_t* raw = reinterpret_cast<const uint32_t*>(a_raw + (size_t)rr * ld);
+        uint32_t lo = (c >= 0 && c < n) ? raw[(c - 1) >> 1] : 0u;        // holds column c in its high half
+        uint32_t hi = (c + 1 >= 0 && c + 1 < n) ? raw[(c + 1) >> 1] : 0u;  // column c + 1 in its low half
+        reinterpret_cast<uint32_t*>(a_s + (size_t)rr * ld)[xw] = __byte_perm(lo, hi, 0x5432);
     }
     __syncthreads();
     long long acc[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = 0;
-    const int G = n / 8;
     const int per = kJitRows / kJitRowSlices;
     for (int task = tid; task < G * kJitRowSlices; task += kJitterThreads) {
         const int g = task % G, slice = task / G;
