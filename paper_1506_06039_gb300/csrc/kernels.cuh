@@ -492,22 +492,34 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// |a - b| (one instruction) and acc + x * y in 64 bits (one multiply-add).
+__device__ __forceinline__ uint32_t absdiff_u32(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("sad.u32 %0, %1, %2, 0;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ u64 madw_u32(uint32_t x, uint32_t y, u64 acc) {
+    u64 d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(x), "r"(y), "l"(acc));
+    return d;
+}
+
 template <bool MASKED>
 __device__ __forceinline__ void jit_rows(const uint16_t* __restrict__ as, const uint16_t* __restrict__ bs,
                                          const unsigned char* __restrict__ rok, int ld, int n, int x0, int r0,
-                                         int nrows, uint32_t mask, long long (&acc)[9]) {
-    auto win = [&](int rr, int32_t (&v)[10]) {
+                                         int nrows, uint32_t mask, u64 (&acc)[9]) {
+    auto win = [&](int rr, uint32_t (&v)[10]) {
         const uint16_t* p = as + (size_t)rr * ld + x0;
         const uint4 q = *reinterpret_cast<const uint4*>(p);
         const uint32_t e = *reinterpret_cast<const uint32_t*>(p + 8);
         const uint32_t w[5] = {q.x, q.y, q.z, q.w, e};
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            v[2 * k] = (int32_t)lo16(w[k]);
-            v[2 * k + 1] = (int32_t)hi16(w[k]);
+            v[2 * k] = lo16(w[k]);
+            v[2 * k + 1] = hi16(w[k]);
         }
     };
-    int32_t w0[10], w1[10], w2[10];
+    uint32_t w0[10], w1[10], w2[10];
     bool ok0 = rok[r0], ok1 = rok[r0 + 1];
     win(r0, w0);
     win(r0 + 1, w1);
@@ -515,29 +527,32 @@ __device__ __forceinline__ void jit_rows(const uint16_t* __restrict__ as, const 
         const int rr = r0 + k;  // template row index within the tile
         const bool ok2 = rok[rr + 2];
         win(rr + 2, w2);
-        int32_t bv[8];
+        uint32_t bv[8];
         {
             const uint4 q = *reinterpret_cast<const uint4*>(bs + (size_t)rr * n + x0);
             const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                bv[2 * c] = (int32_t)lo16(w[c]);
-                bv[2 * c + 1] = (int32_t)hi16(w[c]);
+                bv[2 * c] = lo16(w[c]);
+                bv[2 * c + 1] = hi16(w[c]);
             }
         }
-        const int32_t* rows[3] = {w0, w1, w2};
+        const uint32_t* rows[3] = {w0, w1, w2};
         const bool oks[3] = {ok0, ok1, ok2};
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
             if (!oks[u]) continue;
 #pragma unroll
-            for (int v = 0; v < 3; ++v)
+            for (int v = 0; v < 3; ++v) {
+                u64 s = acc[u * 3 + v];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    int d = rows[u][c + v] - bv[c];
-                    if (MASKED) d = ((mask >> (v * 8 + c)) & 1u) ? d : 0;
-                    acc[u * 3 + v] += (long long)d * d;
+                    uint32_t d = absdiff_u32(rows[u][c + v], bv[c]);
+                    if (MASKED) d = ((mask >> (v * 8 + c)) & 1u) ? d : 0u;
+                    s = madw_u32(d, d, s);
                 }
+                acc[u * 3 + v] = s;
+            }
         }
 #pragma unroll
         for (int c = 0; c < 10; ++c) {
@@ -604,7 +619,7 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
         reinterpret_cast<uint32_t*>(a_s + (size_t)rr * ld)[xw] = __byte_perm(lo, hi, 0x5432);
     }
     __syncthreads();
-    long long acc[9];
+    u64 acc[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = 0;
     const int per = kJitRows / kJitRowSlices;
@@ -629,7 +644,7 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        u64 v = (u64)acc[k];
+        u64 v = acc[k];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         if ((tid & 31) == 0) red[tid >> 5][k] = v;
