@@ -462,26 +462,32 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 // (2 sc + u, 2 tc + v), u, v in {-1, 0, 1}, the exact int64
 //     S = sum over D of (a[i+s][j+t] - b[i][j])^2
 // at full resolution, all nine accumulated in one pass over the frame.
-// Grid (row tiles, frames): a CTA takes kJitRows template rows. It copies
-// the kJitRows + 2 frame rows those rows meet (i0+s0-1 .. i0+s0+kJitRows)
-// and the template rows into shared memory with asynchronous 16-byte copies,
-// then rewrites the frame rows shifted left by t0 - 1 columns (zeros outside
-// the frame) so that every thread's 10-column window starts on a 16-byte
-// boundary. Each thread then owns 8 columns of
-// kJitRows / kJitRowSlices rows and walks down them with its three window
-// rows in registers. Columns outside the frame are masked per thread (a
-// fixed bit mask), rows outside by a per-row flag. Per-CTA partial sums go
-// to acc[f][9] by 64-bit atomics; the last CTA of a frame (ticket counter)
-// takes the minimum of S / Area with the tie-break, compared as exact
-// rationals. acc and ticket are zero on entry.
+//
+// Grid (row tiles, frames); a CTA takes kJitRows template rows. Thread g
+// owns template columns j = 8g - rho + c (c < 8), rho = (1 - t0) mod 8, so
+// that the frame columns it meets, j + t0 - 1 + v + c, start on a multiple
+// of 8; the plan keeps shifted template copies tsh[rho][i][x] = b[i][x - rho]
+// so the template side is 8-aligned too. The CTA copies its kJitRows + 2
+// frame rows and kJitRows template rows into shared memory with
+// asynchronous 16-byte copies, then every thread walks down its rows with
+// the three frame rows it needs (10 columns each) in registers, reading
+// 16-byte aligned vectors only. Pixels outside the template or the frame
+// are masked per thread (a fixed bit mask), frame rows outside by a flag.
+// Per-CTA partial sums go to acc[f][9] by 64-bit atomics; the last CTA of
+// a frame (ticket counter) takes the minimum of S / Area with the
+// tie-break, compared as exact rationals. acc and ticket are zero on entry.
 constexpr int kJitRows = 32;
-constexpr int kJitRowSlices = kJitterThreads / 64;  // threads per column group
+constexpr int kJitRowSlices = 4;  // threads per column group
+constexpr int kJitMargin = 16;    // spare columns on each side of a staged frame row
 
-// smem bytes of k_jitter for width n: shifted frame rows, raw frame rows,
-// template rows, row flags.
+// 9 warps: 65 column groups x 4 row slices of a 512-wide frame in one pass.
+constexpr int kJitThreads = 288;
+__host__ __device__ inline int jitter_threads(int) { return kJitThreads; }
+__host__ __device__ inline int jitter_ld(int n) { return n + 2 * kJitMargin; }
+__host__ __device__ inline int jitter_tld(int n) { return n + 8; }  // shifted-template row length
+// smem bytes: staged frame rows, template rows, row flags.
 __host__ __device__ inline size_t jitter_smem_bytes(int n) {
-    const size_t ld = (size_t)n + 16;  // staged row length (halves)
-    return ld * 2 * (kJitRows + 2) * 2 + (size_t)n * 2 * kJitRows + 64;
+    return (size_t)jitter_ld(n) * 2 * (kJitRows + 2) + (size_t)jitter_tld(n) * 2 * kJitRows + 64;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -504,37 +510,39 @@ __device__ __forceinline__ u64 madw_u32(uint32_t x, uint32_t y, u64 acc) {
     return d;
 }
 
+// 10 frame values from an 8-aligned staged position (one 16-byte and one
+// 4-byte shared load).
+__device__ __forceinline__ void jit_win(const uint16_t* p, uint32_t (&v)[10]) {
+    const uint4 q = *reinterpret_cast<const uint4*>(p);
+    const uint32_t e = *reinterpret_cast<const uint32_t*>(p + 8);
+    const uint32_t w[5] = {q.x, q.y, q.z, q.w, e};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        v[2 * k] = w[k] & 0xffffu;
+        v[2 * k + 1] = w[k] >> 16;
+    }
+}
+
 template <bool MASKED>
 __device__ __forceinline__ void jit_rows(const uint16_t* __restrict__ as, const uint16_t* __restrict__ bs,
-                                         const unsigned char* __restrict__ rok, int ld, int n, int x0, int r0,
-                                         int nrows, uint32_t mask, u64 (&acc)[9]) {
-    auto win = [&](int rr, uint32_t (&v)[10]) {
-        const uint16_t* p = as + (size_t)rr * ld + x0;
-        const uint4 q = *reinterpret_cast<const uint4*>(p);
-        const uint32_t e = *reinterpret_cast<const uint32_t*>(p + 8);
-        const uint32_t w[5] = {q.x, q.y, q.z, q.w, e};
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            v[2 * k] = lo16(w[k]);
-            v[2 * k + 1] = hi16(w[k]);
-        }
-    };
+                                         const unsigned char* __restrict__ rok, int ld, int tld, int xa, int xb,
+                                         int r0, int nrows, uint32_t mask, u64 (&acc)[9]) {
     uint32_t w0[10], w1[10], w2[10];
     bool ok0 = rok[r0], ok1 = rok[r0 + 1];
-    win(r0, w0);
-    win(r0 + 1, w1);
+    jit_win(as + (size_t)r0 * ld + xa, w0);
+    jit_win(as + (size_t)(r0 + 1) * ld + xa, w1);
     for (int k = 0; k < nrows; ++k) {
-        const int rr = r0 + k;  // template row index within the tile
+        const int rr = r0 + k;
         const bool ok2 = rok[rr + 2];
-        win(rr + 2, w2);
+        jit_win(as + (size_t)(rr + 2) * ld + xa, w2);
         uint32_t bv[8];
         {
-            const uint4 q = *reinterpret_cast<const uint4*>(bs + (size_t)rr * n + x0);
+            const uint4 q = *reinterpret_cast<const uint4*>(bs + (size_t)rr * tld + xb);
             const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                bv[2 * c] = lo16(w[c]);
-                bv[2 * c + 1] = hi16(w[c]);
+                bv[2 * c] = w[c] & 0xffffu;
+                bv[2 * c + 1] = w[c] >> 16;
             }
         }
         const uint32_t* rows[3] = {w0, w1, w2};
@@ -572,75 +580,79 @@ __device__ __forceinline__ int ratio_lt(u64 S1, u64 A1, u64 S2, u64 A2, int* eq)
     return (l_hi < r_hi) || (l_hi == r_hi && l_lo < r_lo);
 }
 
-static __global__ void __launch_bounds__(kJitterThreads)
-k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* __restrict__ tmpl, int m, int n,
+static __global__ void __launch_bounds__(kJitThreads, 2)
+k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* __restrict__ tsh, int m, int n,
          const int32_t* __restrict__ coarse, int32_t* __restrict__ shifts, double* __restrict__ ffinal,
          u64* __restrict__ acc_g, unsigned int* __restrict__ ticket) {
     extern __shared__ __align__(16) unsigned char jsm[];
-    __shared__ u64 red[kJitterThreads / 32][9];
+    __shared__ u64 red[kJitThreads / 32][9];
     __shared__ bool last;
-    const int ld = n + 16;
-    uint16_t* a_s = reinterpret_cast<uint16_t*>(jsm);        // (kJitRows + 2) x ld, shifted
-    uint16_t* a_raw = a_s + (size_t)ld * (kJitRows + 2);      // (kJitRows + 2) x ld, as in the frame
-    uint16_t* b_s = a_raw + (size_t)ld * (kJitRows + 2);      // kJitRows x n
-    unsigned char* rok = reinterpret_cast<unsigned char*>(b_s + (size_t)n * kJitRows);  // kJitRows + 2
-    const int tid = threadIdx.x;
+    const int ld = jitter_ld(n), tld = jitter_tld(n);
+    uint16_t* a_s = reinterpret_cast<uint16_t*>(jsm);        // (kJitRows + 2) x ld; column x at x + kJitMargin
+    uint16_t* b_s = a_s + (size_t)ld * (kJitRows + 2);        // kJitRows x tld
+    unsigned char* rok = reinterpret_cast<unsigned char*>(b_s + (size_t)tld * kJitRows);
+    const int tid = threadIdx.x, nthr = blockDim.x;
     const int64_t f = blockIdx.y;
     const int s0 = 2 * coarse[2 * f], t0 = 2 * coarse[2 * f + 1];
+    const int rho = (1 - t0) & 7;
+    const int kappa = (t0 - 1 + rho) >> 3;  // frame column of a thread-0 window = 8 * kappa
     const uint16_t* a = frames + f * fstride;
+    const uint16_t* tb = tsh + (size_t)rho * m * tld;
     const int i0 = blockIdx.x * kJitRows;
     const int rows = min(kJitRows, m - i0);
-    const int G = n / 8;
-    // 1) asynchronous copies of the frame rows and template rows (all in flight)
-    for (int k = tid; k < (rows + 2) * G; k += kJitterThreads) {
-        const int rr = k / G, q = k - rr * G;
-        const int ar = i0 + s0 - 1 + rr;
-        if (ar >= 0 && ar < m) cp_async16(a_raw + (size_t)rr * ld + 8 * q, a + (int64_t)ar * n + 8 * q);
-    }
-    for (int k = tid; k < rows * G; k += kJitterThreads) {
-        const int rr = k / G, q = k - rr * G;
-        cp_async16(b_s + (size_t)rr * n + 8 * q, tmpl + (int64_t)(i0 + rr) * n + 8 * q);
-    }
-    for (int rr = tid; rr < rows + 2; rr += kJitterThreads) {
-        const int ar = i0 + s0 - 1 + rr;
-        rok[rr] = ar >= 0 && ar < m;
+    // 1) asynchronous copies, all in flight: frame rows (16-byte chunks) and
+    //    shifted template rows.
+    {
+        const int G = n / 8, Gt = tld / 8;
+        for (int rr = 0; rr < rows + 2; ++rr) {
+            const int ar = i0 + s0 - 1 + rr;
+            if (ar >= 0 && ar < m)
+                for (int q = tid; q < G; q += nthr)
+                    cp_async16(a_s + (size_t)rr * ld + kJitMargin + 8 * q, a + (int64_t)ar * n + 8 * q);
+        }
+        for (int rr = 0; rr < rows; ++rr)
+            for (int q = tid; q < Gt; q += nthr)
+                cp_async16(b_s + (size_t)rr * tld + 8 * q, tb + (int64_t)(i0 + rr) * tld + 8 * q);
+        for (int rr = tid; rr < rows + 2; rr += nthr) {
+            const int ar = i0 + s0 - 1 + rr;
+            rok[rr] = ar >= 0 && ar < m;
+        }
     }
     cp_async_wait_all();
-    __syncthreads();
-    // 2) a_s[rr][x] = frame column x + t0 - 1 (odd shift: one byte permute per
-    //    word), zero outside the frame; x < n + 2.
-    const int W2 = n / 2 + 1;  // words per shifted row
-    for (int k = tid; k < (rows + 2) * W2; k += kJitterThreads) {
-        const int rr = k / W2, xw = k - rr * W2;
-        const int c = 2 * xw + t0 - 1;  // frame column of the word's low half (odd)
-        const uint32_t* raw = reinterpret_cast<const uint32_t*>(a_raw + (size_t)rr * ld);
-        uint32_t lo = (c >= 0 && c < n) ? raw[(c - 1) >> 1] : 0u;        // holds column c in its high half
-        uint32_t hi = (c + 1 >= 0 && c + 1 < n) ? raw[(c + 1) >> 1] : 0u;  // column c + 1 in its low half
-        reinterpret_cast<uint32_t*>(a_s + (size_t)rr * ld)[xw] = __byte_perm(lo, hi, 0x5432);
-    }
     __syncthreads();
     u64 acc[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = 0;
+    const int Gp = n / 8 + 1;  // column groups (one extra to cover the right edge)
     const int per = kJitRows / kJitRowSlices;
-    for (int task = tid; task < G * kJitRowSlices; task += kJitterThreads) {
-        const int g = task % G, slice = task / G;
+    for (int task = tid; task < Gp * kJitRowSlices; task += nthr) {
+        const int g = task % Gp, slice = task / Gp;
         const int r0 = slice * per;
         const int nrows = min(per, rows - r0);
-        if (nrows <= 0) continue;
-        const int x0 = 8 * g;  // window = frame columns x0 + t0 - 1 .. x0 + t0 + 8
-        uint32_t mask = 0;
+        if (nrows > 0) {
+            const int jbase = 8 * g - rho;       // first template column
+            const int abase = 8 * (g + kappa);   // first frame column (= jbase + t0 - 1)
+            uint32_t mask = 0;
 #pragma unroll
-        for (int v = 0; v < 3; ++v)
+            for (int v = 0; v < 3; ++v)
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int c = x0 + t0 - 1 + k + v;
-                if (c >= 0 && c < n) mask |= 1u << (v * 8 + k);
+                for (int c = 0; c < 8; ++c) {
+                    const int j = jbase + c, col = abase + c + v;
+                    if (j >= 0 && j < n && col >= 0 && col < n) mask |= 1u << (v * 8 + c);
+                }
+            if (mask != 0) {
+                if (mask == 0xffffffu) {
+                    jit_rows<false>(a_s, b_s, rok, ld, tld, abase + kJitMargin, 8 * g, r0, nrows, mask, acc);
+                } else {
+                    // keep shared reads inside the staged row; masked values are unused
+                    const int xa = min(max(abase, -kJitMargin), n + kJitMargin - 16) + kJitMargin;
+                    const int xb = min(8 * g, tld - 8);
+                    uint32_t msk = mask;
+                    if (xa - kJitMargin != abase || xb != 8 * g) msk = 0;  // clamped: nothing valid moved
+                    jit_rows<true>(a_s, b_s, rok, ld, tld, xa, xb, r0, nrows, msk, acc);
+                }
             }
-        if (mask == 0xffffffu)
-            jit_rows<false>(a_s, b_s, rok, ld, n, x0, r0, nrows, mask, acc);
-        else
-            jit_rows<true>(a_s, b_s, rok, ld, n, x0, r0, nrows, mask, acc);
+        }
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -652,7 +664,7 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     __syncthreads();
     if (tid < 9) {
         u64 sum = 0;
-        for (int wi = 0; wi < kJitterThreads / 32; ++wi) sum += red[wi][tid];
+        for (int wi = 0; wi < nthr / 32; ++wi) sum += red[wi][tid];
         atomicAdd(&acc_g[f * 9 + tid], sum);
     }
     __threadfence();
@@ -684,6 +696,20 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     shifts[2 * f] = bs;
     shifts[2 * f + 1] = bt;
     if (ffinal) ffinal[f] = (double)bS / (double)bA;
+}
+
+// tsh[rho][i][x] = b[i][x - rho] (zero outside), rho < 8, x < n + 8: the
+// template copies k_jitter reads 16-byte aligned.
+static __global__ void k_template_shifts(const uint16_t* __restrict__ tmpl, int m, int n, uint16_t* __restrict__ tsh) {
+    const int tld = n + 8;
+    const int64_t total = (int64_t)8 * m * tld;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int rho = (int)(k / ((int64_t)m * tld));
+        const int64_t r = k - (int64_t)rho * m * tld;
+        const int i = (int)(r / tld), x = (int)(r - (int64_t)i * tld);
+        const int c = x - rho;
+        tsh[k] = (c >= 0 && c < n) ? tmpl[(int64_t)i * n + c] : (uint16_t)0;
+    }
 }
 
 // For searches without a level: the searched optimum is the answer.

@@ -68,7 +68,14 @@ cudaError_t launch_energy(bool f32, bool out_double, const u64* rowE, const u64*
     return cudaGetLastError();
 }
 
-cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg, const uint16_t* tmpl, int m,
+size_t template_shifts_elems(int m, int n) { return (size_t)8 * m * (n + 8); }
+
+cudaError_t launch_template_shifts(const uint16_t* tmpl, int m, int n, uint16_t* tsh, cudaStream_t st) {
+    k_template_shifts<<<256, 256, 0, st>>>(tmpl, m, n, tsh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg, const uint16_t* tsh, int m,
                           int n, const int32_t* coarse, int32_t* shifts, double* ffinal, u64* acc,
                           unsigned int* ticket, cudaStream_t st) {
     if (nimg <= 0) return cudaSuccess;
@@ -78,7 +85,7 @@ cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg,
     const size_t smem = jitter_smem_bytes(n);
     if ((e = ensure_smem((const void*)k_jitter, smem)) != cudaSuccess) return e;
     dim3 grid((unsigned)((m + kJitRows - 1) / kJitRows), (unsigned)nimg);
-    k_jitter<<<grid, kJitterThreads, smem, st>>>(frames, fstride, tmpl, m, n, coarse, shifts, ffinal, acc, ticket);
+    k_jitter<<<grid, jitter_threads(n), smem, st>>>(frames, fstride, tsh, m, n, coarse, shifts, ffinal, acc, ticket);
     return cudaGetLastError();
 }
 
