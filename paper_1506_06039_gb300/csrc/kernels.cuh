@@ -464,7 +464,7 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 // at full resolution, all nine accumulated in one pass over the frame.
 //
 // Grid (row tiles, frames); a CTA takes kJitRows template rows. Thread g
-// owns template columns j = 8g - rho + c (c < 8), rho = (1 - t0) mod 8, so
+// owns template columns j = 8g - rho + c (c < 8), rho = (t0 - 1) mod 8, so
 // that the frame columns it meets, j + t0 - 1 + v + c, start on a multiple
 // of 8; the plan keeps shifted template copies tsh[rho][i][x] = b[i][x - rho]
 // so the template side is 8-aligned too. The CTA copies its kJitRows + 2
@@ -498,15 +498,10 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// |a - b| (one instruction) and acc + x * y in 64 bits (one multiply-add).
-__device__ __forceinline__ uint32_t absdiff_u32(uint32_t a, uint32_t b) {
-    uint32_t d;
-    asm("sad.u32 %0, %1, %2, 0;" : "=r"(d) : "r"(a), "r"(b));
-    return d;
-}
-__device__ __forceinline__ u64 madw_u32(uint32_t x, uint32_t y, u64 acc) {
-    u64 d;
-    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(x), "r"(y), "l"(acc));
+// acc + x * y with a 32 x 32 -> 64-bit signed multiply-add (one instruction).
+__device__ __forceinline__ long long madw_s32(int x, int y, long long acc) {
+    long long d;
+    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(x), "r"(y), "l"(acc));
     return d;
 }
 
@@ -526,7 +521,7 @@ __device__ __forceinline__ void jit_win(const uint16_t* p, uint32_t (&v)[10]) {
 template <bool MASKED>
 __device__ __forceinline__ void jit_rows(const uint16_t* __restrict__ as, const uint16_t* __restrict__ bs,
                                          const unsigned char* __restrict__ rok, int ld, int tld, int xa, int xb,
-                                         int r0, int nrows, uint32_t mask, u64 (&acc)[9]) {
+                                         int r0, int nrows, uint32_t mask, long long (&acc)[9]) {
     uint32_t w0[10], w1[10], w2[10];
     bool ok0 = rok[r0], ok1 = rok[r0 + 1];
     jit_win(as + (size_t)r0 * ld + xa, w0);
@@ -552,12 +547,12 @@ __device__ __forceinline__ void jit_rows(const uint16_t* __restrict__ as, const 
             if (!oks[u]) continue;
 #pragma unroll
             for (int v = 0; v < 3; ++v) {
-                u64 s = acc[u * 3 + v];
+                long long s = acc[u * 3 + v];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    uint32_t d = absdiff_u32(rows[u][c + v], bv[c]);
-                    if (MASKED) d = ((mask >> (v * 8 + c)) & 1u) ? d : 0u;
-                    s = madw_u32(d, d, s);
+                    int d = (int)rows[u][c + v] - (int)bv[c];
+                    if (MASKED) d = ((mask >> (v * 8 + c)) & 1u) ? d : 0;
+                    s = madw_s32(d, d, s);
                 }
                 acc[u * 3 + v] = s;
             }
@@ -594,8 +589,8 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int64_t f = blockIdx.y;
     const int s0 = 2 * coarse[2 * f], t0 = 2 * coarse[2 * f + 1];
-    const int rho = (1 - t0) & 7;
-    const int kappa = (t0 - 1 + rho) >> 3;  // frame column of a thread-0 window = 8 * kappa
+    const int rho = (t0 - 1) & 7;
+    const int kappa = (t0 - 1 - rho) >> 3;  // frame column of thread 0's window = 8 * kappa
     const uint16_t* a = frames + f * fstride;
     const uint16_t* tb = tsh + (size_t)rho * m * tld;
     const int i0 = blockIdx.x * kJitRows;
@@ -620,7 +615,7 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     }
     cp_async_wait_all();
     __syncthreads();
-    u64 acc[9];
+    long long acc[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = 0;
     const int Gp = n / 8 + 1;  // column groups (one extra to cover the right edge)
@@ -656,7 +651,7 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        u64 v = acc[k];
+        u64 v = (u64)acc[k];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         if ((tid & 31) == 0) red[tid >> 5][k] = v;
