@@ -31,13 +31,8 @@ cudaError_t launch_energy(bool f32, bool out_double, const u64* rowE, const u64*
                           const uint32_t* corners, int64_t nimg, int mc, int nc, int wm1, void* out, int flip,
                           cudaStream_t st);
 
-// Column-shifted template copies for the jitter (8 x m x (n + 8) halves).
-size_t template_shifts_elems(int m, int n);
-cudaError_t launch_template_shifts(const uint16_t* tmpl, int m, int n, uint16_t* tsh, cudaStream_t st);
-
-// tsh: the shifted template copies; acc: nimg x 9 u64 and ticket: nimg u32
-// of scratch (cleared here).
-cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg, const uint16_t* tsh, int m,
+// acc: nimg x 9 u64 and ticket: nimg u32 of scratch (cleared here).
+cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg, const uint16_t* tmpl, int m,
                           int n, const int32_t* coarse, int32_t* shifts, double* ffinal, u64* acc,
                           unsigned int* ticket, cudaStream_t st);
 

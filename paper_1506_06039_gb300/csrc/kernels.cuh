@@ -462,108 +462,112 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 // (2 sc + u, 2 tc + v), u, v in {-1, 0, 1}, the exact int64
 //     S = sum over D of (a[i+s][j+t] - b[i][j])^2
 // at full resolution, all nine accumulated in one pass over the frame.
-//
-// Grid (row tiles, frames); a CTA takes kJitRows template rows. Thread g
-// owns template columns j = 8g - rho + c (c < 8), rho = (t0 - 1) mod 8, so
-// that the frame columns it meets, j + t0 - 1 + v + c, start on a multiple
-// of 8; the plan keeps shifted template copies tsh[rho][i][x] = b[i][x - rho]
-// so the template side is 8-aligned too. The CTA copies its kJitRows + 2
-// frame rows and kJitRows template rows into shared memory with
-// asynchronous 16-byte copies, then every thread walks down its rows with
-// the three frame rows it needs (10 columns each) in registers, reading
-// 16-byte aligned vectors only. Pixels outside the template or the frame
-// are masked per thread (a fixed bit mask), frame rows outside by a flag.
-// Per-CTA partial sums go to acc[f][9] by 64-bit atomics; the last CTA of
-// a frame (ticket counter) takes the minimum of S / Area with the
-// tie-break, compared as exact rationals. acc and ticket are zero on entry.
+// Grid (CTAs per frame, frames). Each thread owns 8 template columns of a
+// band of kJitRows rows and walks down it keeping the three frame rows it
+// needs (i+s0-1 .. i+s0+1, 10 columns each) in registers, so
+// every frame row is loaded once per thread.
+// Since 2 tc is even, the 10-column window starts at an odd column: six
+// 32-bit loads from the even column before it and five byte permutes give
+// the 10 values. The next row is prefetched one template row ahead. Columns
+// outside the frame are masked per thread (a fixed bit mask), rows outside
+// by a flag.
+// Per-CTA partial sums go to acc[f][9] by 64-bit atomics; the last CTA of a
+// frame (ticket counter) takes the minimum of S / Area with the tie-break,
+// compared as exact rationals. acc and ticket are zero on entry.
 constexpr int kJitRows = 32;
-constexpr int kJitRowSlices = 4;  // threads per column group
-constexpr int kJitMargin = 16;    // spare columns on each side of a staged frame row
 
-// 9 warps: 65 column groups x 4 row slices of a 512-wide frame in one pass.
-constexpr int kJitThreads = 288;
-__host__ __device__ inline int jitter_threads(int) { return kJitThreads; }
-__host__ __device__ inline int jitter_ld(int n) { return n + 2 * kJitMargin; }
-__host__ __device__ inline int jitter_tld(int n) { return n + 8; }  // shifted-template row length
-// smem bytes: staged frame rows, template rows, row flags.
-__host__ __device__ inline size_t jitter_smem_bytes(int n) {
-    return (size_t)jitter_ld(n) * 2 * (kJitRows + 2) + (size_t)jitter_tld(n) * 2 * kJitRows + 64;
-}
+// Raw words of one frame row: 6 x 32 bits = half-words lead-1 .. lead+10,
+// loaded from lead - 1 (even, so 4-byte aligned). Border threads load
+// element by element with zeros outside the frame.
+struct JitRaw {
+    uint32_t w[6];
+};
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-// acc + x * y with a 32 x 32 -> 64-bit signed multiply-add (one instruction).
-__device__ __forceinline__ long long madw_s32(int x, int y, long long acc) {
-    long long d;
-    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(x), "r"(y), "l"(acc));
-    return d;
-}
-
-// 10 frame values from an 8-aligned staged position (one 16-byte and one
-// 4-byte shared load).
-__device__ __forceinline__ void jit_win(const uint16_t* p, uint32_t (&v)[10]) {
-    const uint4 q = *reinterpret_cast<const uint4*>(p);
-    const uint32_t e = *reinterpret_cast<const uint32_t*>(p + 8);
-    const uint32_t w[5] = {q.x, q.y, q.z, q.w, e};
+__device__ __forceinline__ void jit_fetch(const uint16_t* __restrict__ arow, int lead, int n, bool interior,
+                                          bool ok, JitRaw& r) {
+    if (!ok) return;
+    if (interior) {
+        const uint32_t* p = reinterpret_cast<const uint32_t*>(arow + lead - 1);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        v[2 * k] = w[k] & 0xffffu;
-        v[2 * k + 1] = w[k] >> 16;
+        for (int k = 0; k < 6; ++k) r.w[k] = __ldg(p + k);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int c = lead - 1 + 2 * k;
+            const uint32_t lo = (c >= 0 && c < n) ? (uint32_t)__ldg(arow + c) : 0u;
+            const uint32_t hi = (c + 1 >= 0 && c + 1 < n) ? (uint32_t)__ldg(arow + c + 1) : 0u;
+            r.w[k] = lo | (hi << 16);
+        }
+    }
+}
+
+// The 10 values at columns lead .. lead + 9: drop the first half-word.
+__device__ __forceinline__ void jit_unpack(const JitRaw& r, int32_t (&v)[10]) {
+#pragma unroll
+    for (int p = 0; p < 5; ++p) {
+        const uint32_t pr = __byte_perm(r.w[p], r.w[p + 1], 0x5432);
+        v[2 * p] = (int32_t)(pr & 0xffffu);
+        v[2 * p + 1] = (int32_t)(pr >> 16);
     }
 }
 
 template <bool MASKED>
-__device__ __forceinline__ void jit_rows(const uint16_t* __restrict__ as, const uint16_t* __restrict__ bs,
-                                         const unsigned char* __restrict__ rok, int ld, int tld, int xa, int xb,
-                                         int r0, int nrows, uint32_t mask, long long (&acc)[9]) {
-    uint32_t w0[10], w1[10], w2[10];
-    bool ok0 = rok[r0], ok1 = rok[r0 + 1];
-    jit_win(as + (size_t)r0 * ld + xa, w0);
-    jit_win(as + (size_t)(r0 + 1) * ld + xa, w1);
-    for (int k = 0; k < nrows; ++k) {
-        const int rr = r0 + k;
-        const bool ok2 = rok[rr + 2];
-        jit_win(as + (size_t)(rr + 2) * ld + xa, w2);
-        uint32_t bv[8];
-        {
-            const uint4 q = *reinterpret_cast<const uint4*>(bs + (size_t)rr * tld + xb);
-            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+__device__ __forceinline__ void jit_band(const uint16_t* __restrict__ a, const uint16_t* __restrict__ tmpl, int m,
+                                         int n, int s0, int lead, int j0, bool interior, uint32_t mask,
+                                         int i_begin, int i_end, long long (&acc)[9]) {
+    int32_t win[3][10];
+    bool ok[3];
+    JitRaw raw;
+    // window rows i_begin + s0 - 1, i_begin + s0
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                bv[2 * c] = w[c] & 0xffffu;
-                bv[2 * c + 1] = w[c] >> 16;
+    for (int u = 0; u < 2; ++u) {
+        const int ar = i_begin + s0 - 1 + u;
+        ok[u] = ar >= 0 && ar < m;
+        jit_fetch(a + (int64_t)ar * n, lead, n, interior, ok[u], raw);
+        if (ok[u]) jit_unpack(raw, win[u]);
+    }
+    // prefetch the first new row and template row
+    int ar = i_begin + s0 + 1;
+    bool okn = ar >= 0 && ar < m;
+    jit_fetch(a + (int64_t)ar * n, lead, n, interior, okn, raw);
+    uint4 braw = __ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)i_begin * n + j0));
+    for (int i = i_begin; i < i_end; ++i) {
+        ok[2] = okn;
+        if (okn) jit_unpack(raw, win[2]);
+        int32_t bv[8];
+        {
+            const uint32_t w[4] = {braw.x, braw.y, braw.z, braw.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                bv[2 * k] = (int32_t)lo16(w[k]);
+                bv[2 * k + 1] = (int32_t)hi16(w[k]);
             }
         }
-        const uint32_t* rows[3] = {w0, w1, w2};
-        const bool oks[3] = {ok0, ok1, ok2};
+        if (i + 1 < i_end) {  // prefetch for the next template row
+            ar = i + s0 + 2;
+            okn = ar >= 0 && ar < m;
+            jit_fetch(a + (int64_t)ar * n, lead, n, interior, okn, raw);
+            braw = __ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)(i + 1) * n + j0));
+        }
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
-            if (!oks[u]) continue;
+            if (!ok[u]) continue;
 #pragma unroll
-            for (int v = 0; v < 3; ++v) {
-                long long s = acc[u * 3 + v];
+            for (int v = 0; v < 3; ++v)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    int d = (int)rows[u][c + v] - (int)bv[c];
-                    if (MASKED) d = ((mask >> (v * 8 + c)) & 1u) ? d : 0;
-                    s = madw_s32(d, d, s);
+                for (int k = 0; k < 8; ++k) {
+                    int d = win[u][k + v] - bv[k];
+                    if (MASKED) d = ((mask >> (v * 8 + k)) & 1u) ? d : 0;
+                    acc[u * 3 + v] += (long long)d * d;
                 }
-                acc[u * 3 + v] = s;
-            }
         }
 #pragma unroll
-        for (int c = 0; c < 10; ++c) {
-            w0[c] = w1[c];
-            w1[c] = w2[c];
+        for (int k = 0; k < 10; ++k) {
+            win[0][k] = win[1][k];
+            win[1][k] = win[2][k];
         }
-        ok0 = ok1;
-        ok1 = ok2;
+        ok[0] = ok[1];
+        ok[1] = ok[2];
     }
 }
 
@@ -575,79 +579,42 @@ __device__ __forceinline__ int ratio_lt(u64 S1, u64 A1, u64 S2, u64 A2, int* eq)
     return (l_hi < r_hi) || (l_hi == r_hi && l_lo < r_lo);
 }
 
-static __global__ void __launch_bounds__(kJitThreads, 2)
-k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* __restrict__ tsh, int m, int n,
+static __global__ void __launch_bounds__(kJitterThreads, 2)
+k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* __restrict__ tmpl, int m, int n,
          const int32_t* __restrict__ coarse, int32_t* __restrict__ shifts, double* __restrict__ ffinal,
          u64* __restrict__ acc_g, unsigned int* __restrict__ ticket) {
-    extern __shared__ __align__(16) unsigned char jsm[];
-    __shared__ u64 red[kJitThreads / 32][9];
+    __shared__ u64 red[kJitterThreads / 32][9];
     __shared__ bool last;
-    const int ld = jitter_ld(n), tld = jitter_tld(n);
-    uint16_t* a_s = reinterpret_cast<uint16_t*>(jsm);        // (kJitRows + 2) x ld; column x at x + kJitMargin
-    uint16_t* b_s = a_s + (size_t)ld * (kJitRows + 2);        // kJitRows x tld
-    unsigned char* rok = reinterpret_cast<unsigned char*>(b_s + (size_t)tld * kJitRows);
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = threadIdx.x;
     const int64_t f = blockIdx.y;
     const int s0 = 2 * coarse[2 * f], t0 = 2 * coarse[2 * f + 1];
-    const int rho = (t0 - 1) & 7;
-    const int kappa = (t0 - 1 - rho) >> 3;  // frame column of thread 0's window = 8 * kappa
     const uint16_t* a = frames + f * fstride;
-    const uint16_t* tb = tsh + (size_t)rho * m * tld;
-    const int i0 = blockIdx.x * kJitRows;
-    const int rows = min(kJitRows, m - i0);
-    // 1) asynchronous copies, all in flight: frame rows (16-byte chunks) and
-    //    shifted template rows.
-    {
-        const int G = n / 8, Gt = tld / 8;
-        for (int rr = 0; rr < rows + 2; ++rr) {
-            const int ar = i0 + s0 - 1 + rr;
-            if (ar >= 0 && ar < m)
-                for (int q = tid; q < G; q += nthr)
-                    cp_async16(a_s + (size_t)rr * ld + kJitMargin + 8 * q, a + (int64_t)ar * n + 8 * q);
-        }
-        for (int rr = 0; rr < rows; ++rr)
-            for (int q = tid; q < Gt; q += nthr)
-                cp_async16(b_s + (size_t)rr * tld + 8 * q, tb + (int64_t)(i0 + rr) * tld + 8 * q);
-        for (int rr = tid; rr < rows + 2; rr += nthr) {
-            const int ar = i0 + s0 - 1 + rr;
-            rok[rr] = ar >= 0 && ar < m;
-        }
-    }
-    cp_async_wait_all();
-    __syncthreads();
     long long acc[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = 0;
-    const int Gp = n / 8 + 1;  // column groups (one extra to cover the right edge)
-    const int per = kJitRows / kJitRowSlices;
-    for (int task = tid; task < Gp * kJitRowSlices; task += nthr) {
-        const int g = task % Gp, slice = task / Gp;
-        const int r0 = slice * per;
-        const int nrows = min(per, rows - r0);
-        if (nrows > 0) {
-            const int jbase = 8 * g - rho;       // first template column
-            const int abase = 8 * (g + kappa);   // first frame column (= jbase + t0 - 1)
-            uint32_t mask = 0;
+    const int G = n / 8;
+    const int nb = (m + kJitRows - 1) / kJitRows;
+    const int task = blockIdx.x * kJitterThreads + tid;
+    if (task < G * nb) {
+        const int g = task % G, band = task / G;
+        const int j0 = 8 * g;
+        // Frame columns lead .. lead + 9 (lead = j0 + t0 - 1 is odd, so
+        // lead - 1 is 4-byte aligned).
+        const int lead = j0 + t0 - 1;
+        const bool interior = (lead - 1 >= 0) && (lead + 11 <= n);
+        uint32_t mask = 0;
 #pragma unroll
-            for (int v = 0; v < 3; ++v)
+        for (int v = 0; v < 3; ++v)
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int j = jbase + c, col = abase + c + v;
-                    if (j >= 0 && j < n && col >= 0 && col < n) mask |= 1u << (v * 8 + c);
-                }
-            if (mask != 0) {
-                if (mask == 0xffffffu) {
-                    jit_rows<false>(a_s, b_s, rok, ld, tld, abase + kJitMargin, 8 * g, r0, nrows, mask, acc);
-                } else {
-                    // keep shared reads inside the staged row; masked values are unused
-                    const int xa = min(max(abase, -kJitMargin), n + kJitMargin - 16) + kJitMargin;
-                    const int xb = min(8 * g, tld - 8);
-                    uint32_t msk = mask;
-                    if (xa - kJitMargin != abase || xb != 8 * g) msk = 0;  // clamped: nothing valid moved
-                    jit_rows<true>(a_s, b_s, rok, ld, tld, xa, xb, r0, nrows, msk, acc);
-                }
+            for (int k = 0; k < 8; ++k) {
+                const int c = lead + k + v;
+                if (c >= 0 && c < n) mask |= 1u << (v * 8 + k);
             }
-        }
+        const int i_begin = band * kJitRows, i_end = min(m, i_begin + kJitRows);
+        if (interior && mask == 0xffffffu)
+            jit_band<false>(a, tmpl, m, n, s0, lead, j0, true, mask, i_begin, i_end, acc);
+        else
+            jit_band<true>(a, tmpl, m, n, s0, lead, j0, interior, mask, i_begin, i_end, acc);
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -659,7 +626,7 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     __syncthreads();
     if (tid < 9) {
         u64 sum = 0;
-        for (int wi = 0; wi < nthr / 32; ++wi) sum += red[wi][tid];
+        for (int wi = 0; wi < kJitterThreads / 32; ++wi) sum += red[wi][tid];
         atomicAdd(&acc_g[f * 9 + tid], sum);
     }
     __threadfence();
@@ -691,20 +658,6 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     shifts[2 * f] = bs;
     shifts[2 * f + 1] = bt;
     if (ffinal) ffinal[f] = (double)bS / (double)bA;
-}
-
-// tsh[rho][i][x] = b[i][x - rho] (zero outside), rho < 8, x < n + 8: the
-// template copies k_jitter reads 16-byte aligned.
-static __global__ void k_template_shifts(const uint16_t* __restrict__ tmpl, int m, int n, uint16_t* __restrict__ tsh) {
-    const int tld = n + 8;
-    const int64_t total = (int64_t)8 * m * tld;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
-        const int rho = (int)(k / ((int64_t)m * tld));
-        const int64_t r = k - (int64_t)rho * m * tld;
-        const int i = (int)(r / tld), x = (int)(r - (int64_t)i * tld);
-        const int c = x - rho;
-        tsh[k] = (c >= 0 && c < n) ? tmpl[(int64_t)i * n + c] : (uint16_t)0;
-    }
 }
 
 // For searches without a level: the searched optimum is the answer.

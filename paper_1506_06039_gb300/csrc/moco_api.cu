@@ -131,7 +131,6 @@ moco_status allocate_shape(ShapePlan& sp) {
     const int64_t G = sp.group, W = sp.W, m = sp.desc.m, n = sp.desc.n;
     Carver c;
     c.add(&sp.tmpl, (size_t)m * n * (sp.f32 ? 4 : 2));
-    c.add(&sp.tsh, sp.levels ? template_shifts_elems((int)m, (int)n) * 2 : 0);
     c.add(&sp.coff_i, 4);
     c.add(&sp.coff_f, 4);
     c.add(&sp.twr, (size_t)sp.Nr * 8);
@@ -190,10 +189,6 @@ moco_status prepare_template(ShapePlan& sp, const void* tmpl_dev, cudaStream_t s
     const size_t bytes = (size_t)sp.desc.m * sp.desc.n * (sp.f32 ? 4 : 2);
     cudaError_t e = cudaMemcpyAsync(sp.tmpl, tmpl_dev, bytes, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "template copy");
-    if (sp.levels) {
-        e = launch_template_shifts(static_cast<const uint16_t*>(sp.tmpl), sp.desc.m, sp.desc.n, sp.tsh, st);
-        if (e != cudaSuccess) return cuda_fail(e, "template shifts");
-    }
     e = launch_template_offset(sp.f32, sp.tmpl, sp.desc.m, sp.desc.n, sp.levels, sp.coff_i, sp.coff_f, st);
     if (e != cudaSuccess) return cuda_fail(e, "template offset");
     e = launch_frame_rows(sp.Nc, sp.f32, sp.tmpl, 0, 1, sp.desc.m, sp.desc.n, sp.levels, sp.mc, sp.nc,
@@ -248,8 +243,8 @@ moco_status align_frames(ShapePlan& sp, const uint16_t* frames, int64_t T, int32
         cudaError_t e;
         sp.prof->begin(sp.levels ? K_JITTER : K_COPY_SHIFTS, st);
         if (sp.levels)
-            e = launch_jitter(frames + f0 * mn, mn, g, sp.tsh, sp.desc.m, sp.desc.n, sp.coarse, shifts + 2 * f0,
-                              nullptr, sp.jit_acc, sp.jit_ticket, st);
+            e = launch_jitter(frames + f0 * mn, mn, g, static_cast<const uint16_t*>(sp.tmpl), sp.desc.m,
+                              sp.desc.n, sp.coarse, shifts + 2 * f0, nullptr, sp.jit_acc, sp.jit_ticket, st);
         else
             e = launch_copy_shifts(sp.coarse, shifts + 2 * f0, nullptr, nullptr, g, st);
         sp.prof->end(st);

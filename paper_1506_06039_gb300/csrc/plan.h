@@ -52,7 +52,6 @@ struct ShapePlan {
     size_t bytes = 0;
     // template-derived data
     void* tmpl = nullptr;
-    uint16_t* tsh = nullptr;  // column-shifted template copies (jitter)
     int32_t* coff_i = nullptr;
     float* coff_f = nullptr;
     float2* twr = nullptr;

@@ -68,24 +68,17 @@ cudaError_t launch_energy(bool f32, bool out_double, const u64* rowE, const u64*
     return cudaGetLastError();
 }
 
-size_t template_shifts_elems(int m, int n) { return (size_t)8 * m * (n + 8); }
-
-cudaError_t launch_template_shifts(const uint16_t* tmpl, int m, int n, uint16_t* tsh, cudaStream_t st) {
-    k_template_shifts<<<256, 256, 0, st>>>(tmpl, m, n, tsh);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg, const uint16_t* tsh, int m,
+cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg, const uint16_t* tmpl, int m,
                           int n, const int32_t* coarse, int32_t* shifts, double* ffinal, u64* acc,
                           unsigned int* ticket, cudaStream_t st) {
     if (nimg <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(u64) * 9 * nimg, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int) * nimg, st);
     if (e != cudaSuccess) return e;
-    const size_t smem = jitter_smem_bytes(n);
-    if ((e = ensure_smem((const void*)k_jitter, smem)) != cudaSuccess) return e;
-    dim3 grid((unsigned)((m + kJitRows - 1) / kJitRows), (unsigned)nimg);
-    k_jitter<<<grid, jitter_threads(n), smem, st>>>(frames, fstride, tsh, m, n, coarse, shifts, ffinal, acc, ticket);
+    const int tasks = (n / 8) * ((m + kJitRows - 1) / kJitRows);
+    const int ctas = (tasks + kJitterThreads - 1) / kJitterThreads;
+    dim3 grid((unsigned)ctas, (unsigned)nimg);
+    k_jitter<<<grid, kJitterThreads, 0, st>>>(frames, fstride, tmpl, m, n, coarse, shifts, ffinal, acc, ticket);
     return cudaGetLastError();
 }
 
