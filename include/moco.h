@@ -152,6 +152,11 @@ moco_status moco_cost_backward(moco_plan_t plan, int32_t shape_idx, const uint16
 moco_status moco_align_host(moco_plan_t plan, int32_t shape_idx, const uint16_t* frames_host, int64_t T,
                             int32_t* shifts_host, void* stream);
 
+/* Synchronises the plan's device and reports whether any bounded device-side
+ * wait of the plan's kernels gave up since the last check (MOCO_ERR_TIMEOUT,
+ * flag then cleared); MOCO_OK otherwise. */
+moco_status moco_plan_status(moco_plan_t plan);
+
 /* Fills *info for shape `shape_idx`. */
 moco_status moco_plan_query(moco_plan_t plan, int32_t shape_idx, moco_shape_info* info);
 

@@ -31,7 +31,7 @@ TEMPLATE_F32 = 1
 EXPORTS = (
     "moco_plan", "moco_set_template", "moco_align_stack", "moco_cost_surface", "moco_softmin",
     "moco_cost_backward", "moco_align_host", "moco_plan_query", "moco_plan_destroy",
-    "moco_status_string", "moco_last_error", "moco_profile_enable", "moco_profile_read",
+    "moco_status_string", "moco_last_error", "moco_profile_enable", "moco_profile_read", "moco_plan_status",
 )
 
 
@@ -95,6 +95,7 @@ def lib():
             L.moco_last_error.argtypes = []
             L.moco_last_error.restype = ctypes.c_char_p
             L.moco_profile_enable.argtypes = [P, i32]
+            L.moco_plan_status.argtypes = [P]
             L.moco_profile_read.argtypes = [P, ctypes.POINTER(MocoKernelStat), i32, ctypes.POINTER(i32), i32]
             for name in EXPORTS:
                 if name not in ("moco_status_string", "moco_last_error"):
@@ -233,6 +234,10 @@ def moco_plan_destroy(plan):
     _check(lib().moco_plan_destroy(plan))
 
 
+def moco_plan_status(plan):
+    _check(lib().moco_plan_status(plan))
+
+
 def moco_profile_enable(plan, max_launches: int):
     _check(lib().moco_profile_enable(plan, int(max_launches)))
 
@@ -321,6 +326,10 @@ class Plan:
             shifts_host = torch.empty((frames_host.shape[0], 2), dtype=torch.int32).pin_memory()
         moco_align_host(self.handle, shape_idx, frames_host, shifts_host, stream)
         return shifts_host
+
+    def status(self):
+        """Raises MocoError (MOCO_ERR_TIMEOUT) if a device-side wait gave up."""
+        moco_plan_status(self.handle)
 
     def profile(self, max_launches: int):
         moco_profile_enable(self.handle, max_launches)

@@ -1,0 +1,389 @@
+// The direct form of the cross term h_st (Section 2's third sum) on the 5th
+// generation tensor cores:
+//
+//   h[f][(s,t)] = sum_{(p,q)} A[f][(p,q)] * B[(p,q)][(s,t)],
+//   A[f][(p,q)] = a'_f[p][q],   B[(p,q)][(s,t)] = b'[p-s][q-t] (0 outside),
+//
+// a GEMM with M = frames, N = shifts and K = searched-grid pixels. a' and b'
+// are integers (offset by the plan's c) up to 2^19 in magnitude; each is
+// split into BF16 hi + lo (16 significant bits) and the product is formed as
+// hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory.
+//
+// For one K step (image row p, 64 columns from q0) and one shift row s, the
+// B block is the 64 x Wp Toeplitz matrix of template row r = p - s; those
+// blocks are precomputed per template (k_toeplitz) directly in the MMA's
+// canonical K-major layout without swizzle (8 x 8 core matrices of 128
+// bytes, core matrices 128 bytes apart along K and 1024 bytes apart along
+// M/N), so a K step copies them with one bulk copy each. A tiles (128
+// frames x 64 pixels, BF16 hi and lo planes written by the frame pass) come
+// in with 16-byte asynchronous copies. Two stages: the copies for step k+1
+// run while the MMAs of step k do. One thread issues the MMAs; every
+// mbarrier wait is bounded (about a second) and sets an error flag instead
+// of hanging.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace moco {
+
+constexpr int kDirThreads = 128;
+constexpr int kDirM = 128;      // frames per tile (MMA M)
+constexpr int kDirK = 64;       // pixels per K step
+constexpr int kDirQ = kDirK;    // columns per K step
+constexpr int kDirNmax = 256;   // MMA N (shifts per tile)
+
+__host__ __device__ inline int direct_wp(int W) { return (W + 15) / 16 * 16; }
+__host__ __device__ inline int direct_ns(int W) { return kDirNmax / direct_wp(W); }
+__host__ __device__ inline size_t direct_tile_bytes(int W) { return (size_t)direct_wp(W) * kDirK * 2; }
+__host__ __device__ inline size_t direct_stage_bytes(int W) {
+    return 2 * (size_t)kDirM * kDirK * 2 + 2 * (size_t)direct_ns(W) * direct_tile_bytes(W);
+}
+__host__ __device__ inline size_t direct_smem_bytes(int W) { return 1024 + 2 * direct_stage_bytes(W) + 64; }
+
+// Byte offset of element (row, k) in a K-major core-matrix tile with 64 K.
+__device__ __forceinline__ uint32_t core_off(int row, int k) {
+    return (uint32_t)((row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// Toeplitz tiles of the template: tiles[plane][r][qc] is the Wp x 64 block
+// B[(r row), q = qc*64 + k][t] = b'[r][qc*64 + k - t], t = ti - (w-1),
+// zero for ti >= W or a column outside [0, nc). plane 0 = hi, 1 = lo.
+static __global__ void k_toeplitz(const float* __restrict__ bprime, int mc, int nc, int nqc, int wm1,
+                                  uint8_t* __restrict__ tiles) {
+    const int W = 2 * wm1 + 1, Wp = direct_wp(W);
+    const size_t tb = direct_tile_bytes(W);
+    const int64_t per_plane = (int64_t)mc * nqc * Wp * kDirK;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per_plane;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e % kDirK);
+        int64_t rest = e / kDirK;
+        const int ti = (int)(rest % Wp);
+        rest /= Wp;
+        const int qc = (int)(rest % nqc);
+        const int r = (int)(rest / nqc);
+        const int col = qc * kDirQ + k - (ti - wm1);
+        float v = 0.f;
+        if (ti < W && col >= 0 && col < nc) v = bprime[(int64_t)r * nc + col];
+        __nv_bfloat16 hi, lo;
+        split_bf16(v, hi, lo);
+        const size_t base = ((size_t)r * nqc + qc) * tb + core_off(ti, k);
+        *reinterpret_cast<__nv_bfloat16*>(tiles + base) = hi;
+        *reinterpret_cast<__nv_bfloat16*>(tiles + (size_t)mc * nqc * tb + base) = lo;
+    }
+}
+
+// ---- PTX wrappers ------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bounded wait on an mbarrier phase: false after ~1 s (error flag set).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned int* err) {
+    const uint32_t a = smem_u32(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > (2ll << 30)) {
+            atomicExch(err, 1u);
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void cp16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// K-major, no swizzle: core matrices 128 B apart along K, 1024 B along M/N.
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+    const uint64_t a = smem_u32(p);
+    return ((a >> 4) & 0x3FFFull) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46);
+}
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major.
+__host__ __device__ constexpr uint32_t direct_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// ---- the GEMM ----------------------------------------------------------------
+//
+// Grid (N tiles, M tiles). N tile j covers shift rows s = -(w-1) + j*NS ..
+// (NS = 256 / Wp of them, Wp = W rounded up to 16); M tile covers frames
+// f0 .. f0 + 127. Output h[f][(s+w-1)*W + (t+w-1)] (FP32).
+static __global__ void __launch_bounds__(kDirThreads, 1)
+k_direct(const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict__ a_lo, int64_t T, int mc,
+         int ncp, int nqc, int wm1, const uint8_t* __restrict__ tiles, float* __restrict__ h,
+         unsigned int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char dsm_raw[];
+    unsigned char* dsm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t load_bar[2];
+    __shared__ __align__(8) uint64_t mma_bar[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_abort;
+    const int W = 2 * wm1 + 1, Wp = direct_wp(W), NS = direct_ns(W), N = NS * Wp;
+    const size_t tb = direct_tile_bytes(W), stage = direct_stage_bytes(W);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int s_first = -wm1 + (int)blockIdx.x * NS;
+    const int64_t f0 = (int64_t)blockIdx.y * kDirM;
+    const int ksteps = mc * nqc;
+    const uint32_t idesc = direct_idesc(kDirM, N);
+    const size_t plane_tiles = (size_t)mc * nqc * tb;
+
+    if (tid == 0) {
+        mbar_init(&load_bar[0], 1);
+        mbar_init(&load_bar[1], 1);
+        mbar_init(&mma_bar[0], 1);
+        mbar_init(&mma_bar[1], 1);
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        const uint32_t ncols = 256;
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    auto sA = [&](int st, int plane) { return dsm + st * stage + (size_t)plane * kDirM * kDirK * 2; };
+    auto sB = [&](int st, int plane) {
+        return dsm + st * stage + 2 * (size_t)kDirM * kDirK * 2 + (size_t)plane * NS * tb;
+    };
+
+    // Copies of K step k into stage st: A rows by cp.async, B tiles by bulk copies.
+    auto issue = [&](int k, int st) {
+        const int p = k / nqc, qc = k - p * nqc;
+        {
+            const int m = tid;  // one frame row per thread
+            const int64_t f = f0 + m;
+            for (int plane = 0; plane < 2; ++plane) {
+                unsigned char* dst = sA(st, plane);
+                if (f < T) {
+                    const __nv_bfloat16* src = (plane ? a_lo : a_hi) + ((f * mc + p) * (int64_t)ncp + (int64_t)qc * kDirQ);
+#pragma unroll
+                    for (int kg = 0; kg < 8; ++kg) cp16(dst + core_off(m, kg * 8), src + kg * 8);
+                } else {
+#pragma unroll
+                    for (int kg = 0; kg < 8; ++kg) *reinterpret_cast<uint4*>(dst + core_off(m, kg * 8)) = make_uint4(0, 0, 0, 0);
+                }
+            }
+        }
+        cp_commit();
+        // Tiles of shift rows that fall outside the window or the template: zeros.
+        for (int sl = 0; sl < NS; ++sl) {
+            const int s = s_first + sl, r = p - s;
+            if (s <= wm1 && r >= 0 && r < mc) continue;
+            for (int plane = 0; plane < 2; ++plane) {
+                uint4* z = reinterpret_cast<uint4*>(sB(st, plane) + sl * tb);
+                for (size_t i = tid; i < tb / 16; i += kDirThreads) z[i] = make_uint4(0, 0, 0, 0);
+            }
+        }
+        if (tid == 0) {
+            uint32_t bytes = 0;
+            for (int sl = 0; sl < NS; ++sl) {
+                const int s = s_first + sl, r = p - s;
+                if (s <= wm1 && r >= 0 && r < mc) bytes += 2 * (uint32_t)tb;
+            }
+            mbar_expect_tx(&load_bar[st], bytes);
+            for (int sl = 0; sl < NS; ++sl) {
+                const int s = s_first + sl, r = p - s;
+                if (!(s <= wm1 && r >= 0 && r < mc)) continue;
+                const uint8_t* src = tiles + ((size_t)r * nqc + qc) * tb;
+                bulk_g2s(sB(st, 0) + sl * tb, src, (uint32_t)tb, &load_bar[st]);
+                bulk_g2s(sB(st, 1) + sl * tb, src + plane_tiles, (uint32_t)tb, &load_bar[st]);
+            }
+        }
+    };
+
+    issue(0, 0);
+    for (int k = 0; k < ksteps; ++k) {
+        const int st = k & 1;
+        if (k + 1 < ksteps) {
+            if (k >= 1) {  // stage st^1 was last read by the MMAs of step k-1
+                if (!mbar_wait(&mma_bar[st ^ 1], ((k - 1) >> 1) & 1, err)) s_abort = 1;
+            }
+            __syncthreads();
+            if (s_abort) break;
+            issue(k + 1, st ^ 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        if (!mbar_wait(&load_bar[st], (k >> 1) & 1, err)) s_abort = 1;
+        fence_async_smem();
+        __syncthreads();
+        if (s_abort) break;
+        if (tid == 0) {
+            tc_fence_after();
+            const unsigned char* A0 = sA(st, 0);
+            const unsigned char* A1 = sA(st, 1);
+            const unsigned char* B0 = sB(st, 0);
+            const unsigned char* B1 = sB(st, 1);
+#pragma unroll
+            for (int kk = 0; kk < kDirK / 16; ++kk) {
+                const uint32_t off = kk * 256;  // two core matrices along K per K16
+                const uint32_t acc0 = (k > 0 || kk > 0) ? 1u : 0u;
+                mma_bf16(tmem, smem_desc(A0 + off), smem_desc(B0 + off), idesc, acc0);
+                mma_bf16(tmem, smem_desc(A0 + off), smem_desc(B1 + off), idesc, 1u);
+                mma_bf16(tmem, smem_desc(A1 + off), smem_desc(B0 + off), idesc, 1u);
+            }
+            mma_commit(&mma_bar[st]);
+        }
+    }
+    // Drain: the last commit covers every MMA issued before it.
+    if (!s_abort && ksteps > 0) {
+        if (!mbar_wait(&mma_bar[(ksteps - 1) & 1], ((ksteps - 1) >> 1) & 1, err)) s_abort = 1;
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (!s_abort) {
+        // Each warp reads its 32 TMEM lanes (frames), 32 columns at a time.
+        const int64_t f = f0 + warp * 32 + (tid & 31);
+        for (int c0 = 0; c0 < N; c0 += 32) {
+            uint32_t r[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (f < T) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const int n = c0 + c, sl = n / Wp, ti = n - sl * Wp;
+                    const int s = s_first + sl;
+                    if (ti < W && s <= wm1) h[f * (int64_t)W * W + (int64_t)(s + wm1) * W + ti] = __uint_as_float(r[c]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t ncols = 256;
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+// Offset searched-grid template b' = b_c - c as floats (exact for uint16).
+template <bool F32>
+__global__ void k_coarse_image(const void* __restrict__ src, int m, int n, int levels, int mc, int nc,
+                               const int32_t* __restrict__ coff_i, const float* __restrict__ coff_f,
+                               float* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)mc * nc;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / nc), j = (int)(e % nc);
+        float v;
+        if (F32) {
+            v = static_cast<const float*>(src)[(int64_t)i * n + j] - *coff_f;
+        } else {
+            const uint16_t* s = static_cast<const uint16_t*>(src);
+            int32_t x;
+            if (levels)
+                x = (int32_t)s[(int64_t)(2 * i) * n + 2 * j] + s[(int64_t)(2 * i + 1) * n + 2 * j] +
+                    s[(int64_t)(2 * i) * n + 2 * j + 1] + s[(int64_t)(2 * i + 1) * n + 2 * j + 1];
+            else
+                x = s[(int64_t)i * n + j];
+            v = (float)(x - *coff_i);
+        }
+        out[e] = v;
+    }
+}
+
+// f = (Sa + Sb - 2 h) / Area * unit with the argmin and margin, from an h
+// computed by the direct form. One CTA per frame.
+static __global__ void __launch_bounds__(256)
+k_combine_h(const float* __restrict__ hh, int wm1, const u64* __restrict__ Sa, const double* __restrict__ Sb,
+            const double* __restrict__ inv_area, double unit, double* __restrict__ cost, int32_t* __restrict__ coarse,
+            double* __restrict__ fbest, float* __restrict__ margin) {
+    __shared__ Best red[8];
+    const int W = 2 * wm1 + 1, WW = W * W;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int64_t f = blockIdx.x;
+    Best b;
+    b.f1 = INFINITY;
+    b.r1 = 0x7fffffff;
+    b.f2 = INFINITY;
+    for (int k = tid; k < WW; k += nthr) {
+        const int s = k / W - wm1, t = k % W - wm1;
+        const double num = ((double)Sa[f * WW + k] + Sb[k]) - 2.0 * (double)hh[f * WW + k];
+        const double fv = num * inv_area[k] * unit;
+        if (cost) cost[f * WW + k] = fv;
+        best_push(b, fv, (abs(s) + abs(t)) * WW + k);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Best o2;
+        o2.f1 = __shfl_xor_sync(0xffffffffu, b.f1, o);
+        o2.r1 = __shfl_xor_sync(0xffffffffu, b.r1, o);
+        o2.f2 = __shfl_xor_sync(0xffffffffu, b.f2, o);
+        best_merge(b, o2);
+    }
+    if ((tid & 31) == 0) red[tid >> 5] = b;
+    __syncthreads();
+    if (tid == 0) {
+        for (int i = 1; i < nthr / 32; ++i) best_merge(b, red[i]);
+        const int k = b.r1 % WW;
+        coarse[2 * f] = k / W - wm1;
+        coarse[2 * f + 1] = k % W - wm1;
+        if (fbest) fbest[f] = b.f1;
+        if (margin) {
+            float mg;
+            if (b.f1 > 0) mg = (float)((b.f2 - b.f1) / b.f1);
+            else mg = (b.f2 > 0) ? INFINITY : 0.f;
+            margin[f] = mg;
+        }
+    }
+}
+
+}  // namespace moco

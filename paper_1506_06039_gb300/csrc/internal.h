@@ -54,6 +54,21 @@ cudaError_t launch_grad(const uint16_t* frames, int64_t T, int m, int n, int wm1
                         const double* inv_area, const int32_t* coff, const void* tmpl, int tmpl_f32,
                         float* acc, float* Q, float* grad_template, float* grad_frames, cudaStream_t st);
 
+// ---- the direct (tensor-core) form -----------------------------------------
+size_t direct_tiles_bytes(int mc, int nqc, int W);  // hi + lo Toeplitz tiles
+size_t direct_smem(int W);
+cudaError_t launch_frame_planes(bool f32, const void* src, int64_t src_fstride, int64_t nimg, int m, int n, int levels,
+                                int mc, int nc, const int32_t* coff_i, const float* coff_f, const float2* tw,
+                                u64* rowE, u64* colE, u64* tot, uint32_t* corners, int wm1, void* p_hi, void* p_lo,
+                                int ldp, cudaStream_t st);
+cudaError_t launch_toeplitz(bool f32, const void* tmpl, int m, int n, int levels, int mc, int nc, int nqc, int wm1,
+                            const int32_t* coff_i, const float* coff_f, float* bprime, void* tiles, cudaStream_t st);
+cudaError_t launch_direct(const void* a_hi, const void* a_lo, int64_t T, int mc, int ncp, int nqc, int wm1,
+                          const void* tiles, float* h, unsigned int* err, cudaStream_t st);
+cudaError_t launch_combine_h(const float* h, int64_t nimg, int wm1, const u64* Sa, const double* Sb,
+                             const double* inv_area, double unit, double* cost, int32_t* coarse, double* fbest,
+                             float* margin, cudaStream_t st);
+
 // Sets the dynamic shared-memory limit of `func` on the current device once.
 cudaError_t ensure_smem(const void* func, size_t bytes);
 

@@ -16,6 +16,7 @@
 //   k_jitter     : Section 2's upsampling step: the 3x3 candidates around the
 //                  doubled optimum, exact int64 sums at full resolution
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "fft.cuh"
@@ -65,13 +66,18 @@ __device__ __forceinline__ uint32_t hi16(uint32_t w) { return w >> 16; }
 //              (u64 for integer images, double for F32)
 // corners    : the four (w-1)x(w-1) corner blocks of the offset image
 //              (int32 or float bits), [f][q][ri][ci], q = 2*bottom + right
-template <int N, bool F32IN>
+//
+// PLANES (the direct form): no FFT; the offset searched-grid image is written
+// as BF16 hi and lo planes instead, planes[f][r][c] with row length ldp
+// (columns nc .. ldp-1 are left as they are: zero from allocation).
+template <int N, bool F32IN, bool PLANES = false>
 __global__ void __launch_bounds__(kRowsThreads, 2)
 k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, int levels, int mc,
              int nc, const int32_t* __restrict__ coff_i, const float* __restrict__ coff_f,
              const float2* __restrict__ tw_g, float2* __restrict__ X, int64_t x_fstride, int ldx,
              u64* __restrict__ rowE, u64* __restrict__ colE, u64* __restrict__ tot,
-             uint32_t* __restrict__ corners, int wm1) {
+             uint32_t* __restrict__ corners, int wm1, __nv_bfloat16* __restrict__ p_hi = nullptr,
+             __nv_bfloat16* __restrict__ p_lo = nullptr, int ldp = 0) {
     typedef typename AccT<F32IN>::type Acc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* buf = reinterpret_cast<float2*>(smem_raw);  // (kRC/2) x N
@@ -98,7 +104,8 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
 
     for (int r0 = 0; r0 < mc; r0 += kRC) {
         const int rows = min(kRC, mc - r0), nfft = (rows + 1) >> 1;
-        for (int i = tid; i < nfft * N; i += nthr) buf[i] = make_float2(0.f, 0.f);
+        if constexpr (!PLANES)
+            for (int i = tid; i < nfft * N; i += nthr) buf[i] = make_float2(0.f, 0.f);
         __syncthreads();
         if (active) {
             for (int rl = rl0; rl < rows; rl += RPI) {
@@ -156,13 +163,26 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
                 }
                 tacc += rs;
                 if (top || bot) atomicAdd(&rowacc[rl], rs);
-                float* dst = reinterpret_cast<float*>(buf + (rl >> 1) * N) + (rl & 1);
+                if constexpr (PLANES) {
+                    __nv_bfloat16* ph = p_hi + (f * mc + r) * (int64_t)ldp + g * CW;
+                    __nv_bfloat16* pl = p_lo + (f * mc + r) * (int64_t)ldp + g * CW;
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (k < CW) dst[2 * (g * CW + k)] = val[k];
+                    for (int k = 0; k < 8; ++k)
+                        if (k < CW) {
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(val[k]);
+                            ph[k] = hi;
+                            pl[k] = __float2bfloat16_rn(val[k] - __bfloat162float(hi));
+                        }
+                } else {
+                    float* dst = reinterpret_cast<float*>(buf + (rl >> 1) * N) + (rl & 1);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (k < CW) dst[2 * (g * CW + k)] = val[k];
+                }
             }
         }
         __syncthreads();
+        if constexpr (!PLANES) {
         fft4_fwd<N>(buf, N, nfft, tw, tid, nthr);
         // Two real rows were packed as one complex row: split the spectra.
         constexpr int NH = N / 2 + 1;
@@ -178,6 +198,7 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
                 *reinterpret_cast<float4*>(out) = make_float4(x1.x, x1.y, x2.x, x2.y);
             else
                 out[0] = x1;
+        }
         }
         for (int rl = tid; rl < rows; rl += nthr) {
             const int r = r0 + rl;

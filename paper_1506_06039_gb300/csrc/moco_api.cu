@@ -72,8 +72,14 @@ void host_roots(int N, std::vector<float2>& out) {
 int64_t per_frame_scratch_bytes(const ShapePlan& sp) {
     const int64_t W = sp.W, wm1 = sp.wm1;
     int64_t b = 0;
-    b += (int64_t)sp.ncv * sp.ldx * 8;        // X
-    b += W * sp.ncv * 8;                       // Y
+    if (sp.has_fft) {
+        b += (int64_t)sp.ncv * sp.ldx * 8;    // X
+        b += W * sp.ncv * 8;                   // Y
+    }
+    if (sp.has_direct) {
+        b += (int64_t)sp.mc * sp.ncp * 4;      // BF16 hi + lo planes
+        b += W * W * 4;                        // h
+    }
     b += ((int64_t)sp.mc + sp.nc + 1) * 8;     // rowE, colE, tot
     b += 4 * wm1 * wm1 * 4;                    // corners
     b += W * W * 8;                            // Sa
@@ -107,14 +113,23 @@ moco_status resolve_shape(const moco_shape& d, ShapePlan& sp) {
     sp.W = 2 * d.w - 1;
     sp.Nr = fft_size_for(sp.mc + d.w - 1);
     sp.Nc = fft_size_for(sp.nc + d.w - 1);
-    if (!sp.Nr || !sp.Nc)
+    const bool fft_ok = sp.Nr && sp.Nc;
+    const bool direct_ok = direct_smem(sp.W) <= 227 * 1024 && sp.W <= 256;
+    sp.nqc = (sp.nc + 63) / 64;
+    sp.ncp = sp.nqc * 64;
+    if (d.xcorr == MOCO_XCORR_FFT_FP32 && !fft_ok)
         return fail(MOCO_ERR_UNSUPPORTED, "searched grid + window exceeds the largest FFT length (576)");
+    if (d.xcorr == MOCO_XCORR_DIRECT_BF16X3 && !direct_ok)
+        return fail(MOCO_ERR_UNSUPPORTED, "window too large for the direct form");
+    if (!fft_ok && !direct_ok) return fail(MOCO_ERR_UNSUPPORTED, "no cross-term form supports this shape");
+    sp.has_fft = fft_ok && d.xcorr != MOCO_XCORR_DIRECT_BF16X3;
+    sp.has_direct = direct_ok && d.xcorr != MOCO_XCORR_FFT_FP32;
+    sp.form = sp.has_fft ? MOCO_XCORR_FFT_FP32 : MOCO_XCORR_DIRECT_BF16X3;
+    if (!sp.Nr) sp.Nr = 48;  // placeholders: no FFT buffers are used
+    if (!sp.Nc) sp.Nc = 48;
     sp.ncv = sp.Nc / 2 + 1;
     sp.ldx = sp.mc + (sp.mc & 1);
     sp.unit = sp.levels ? 1.0 / 16.0 : 1.0;
-    if (d.xcorr == MOCO_XCORR_DIRECT_BF16X3)
-        return fail(MOCO_ERR_UNSUPPORTED, "the direct BF16x3 form is not built into this library");
-    sp.form = MOCO_XCORR_FFT_FP32;
     if (d.group_frames > 0) {
         sp.group = d.group_frames;
     } else {
@@ -135,13 +150,21 @@ moco_status allocate_shape(ShapePlan& sp) {
     c.add(&sp.coff_f, 4);
     c.add(&sp.twr, (size_t)sp.Nr * 8);
     c.add(&sp.twc, (size_t)sp.Nc * 8);
-    c.add(&sp.bspec, (size_t)sp.ncv * sp.Nr * 8);
+    c.add(&sp.bspec, sp.has_fft ? (size_t)sp.ncv * sp.Nr * 8 : 0);
+    c.add(&sp.dev_err, 4);
+    if (sp.has_direct) {
+        c.add(&sp.bprime, (size_t)sp.mc * sp.nc * 4);
+        c.add(&sp.dtiles, direct_tiles_bytes(sp.mc, sp.nqc, sp.W));
+        c.add(&sp.planes_hi, (size_t)(G * sp.mc * sp.ncp * 2));
+        c.add(&sp.planes_lo, (size_t)(G * sp.mc * sp.ncp * 2));
+        c.add(&sp.hbuf, (size_t)(G * W * W * 4));
+    }
     c.add(&sp.Sb, (size_t)W * W * 8);
     c.add(&sp.inv_area, (size_t)W * W * 8);
     sp.x_fstride = (int64_t)sp.ncv * sp.ldx;
     sp.y_fstride = W * sp.ncv;
-    c.add(&sp.X, (size_t)(G * sp.x_fstride * 8));
-    c.add(&sp.Y, (size_t)(G * sp.y_fstride * 8));
+    c.add(&sp.X, sp.has_fft ? (size_t)(G * sp.x_fstride * 8) : 0);
+    c.add(&sp.Y, sp.has_fft ? (size_t)(G * sp.y_fstride * 8) : 0);
     c.add(&sp.rowE, (size_t)(G * sp.mc * 8));
     c.add(&sp.colE, (size_t)(G * sp.nc * 8));
     c.add(&sp.tot, (size_t)(G * 8));
@@ -166,6 +189,10 @@ moco_status allocate_shape(ShapePlan& sp) {
         return fail(MOCO_ERR_OOM, "cudaMalloc of " + std::to_string(sp.bytes) + " bytes failed");
     }
     c.bind(sp.base);
+    e = cudaMemset(sp.dev_err, 0, 4);
+    if (e == cudaSuccess && sp.has_direct) e = cudaMemset(sp.planes_hi, 0, (size_t)(G * sp.mc * sp.ncp * 2));
+    if (e == cudaSuccess && sp.has_direct) e = cudaMemset(sp.planes_lo, 0, (size_t)(G * sp.mc * sp.ncp * 2));
+    if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
     // Host-computed constant tables.
     std::vector<float2> tw;
     host_roots(sp.Nr, tw);
@@ -191,15 +218,27 @@ moco_status prepare_template(ShapePlan& sp, const void* tmpl_dev, cudaStream_t s
     if (e != cudaSuccess) return cuda_fail(e, "template copy");
     e = launch_template_offset(sp.f32, sp.tmpl, sp.desc.m, sp.desc.n, sp.levels, sp.coff_i, sp.coff_f, st);
     if (e != cudaSuccess) return cuda_fail(e, "template offset");
-    e = launch_frame_rows(sp.Nc, sp.f32, sp.tmpl, 0, 1, sp.desc.m, sp.desc.n, sp.levels, sp.mc, sp.nc,
-                          sp.coff_i, sp.coff_f, sp.twc, sp.X, sp.x_fstride, sp.ldx, sp.rowE, sp.colE, sp.tot,
-                          sp.corners, sp.wm1, st);
+    if (sp.has_fft)
+        e = launch_frame_rows(sp.Nc, sp.f32, sp.tmpl, 0, 1, sp.desc.m, sp.desc.n, sp.levels, sp.mc, sp.nc,
+                              sp.coff_i, sp.coff_f, sp.twc, sp.X, sp.x_fstride, sp.ldx, sp.rowE, sp.colE, sp.tot,
+                              sp.corners, sp.wm1, st);
+    else
+        e = launch_frame_planes(sp.f32, sp.tmpl, 0, 1, sp.desc.m, sp.desc.n, sp.levels, sp.mc, sp.nc, sp.coff_i,
+                                sp.coff_f, sp.twc, sp.rowE, sp.colE, sp.tot, sp.corners, sp.wm1, sp.planes_hi,
+                                sp.planes_lo, sp.ncp, st);
     if (e != cudaSuccess) return cuda_fail(e, "template rows");
     e = launch_energy(sp.f32, true, sp.rowE, sp.colE, sp.tot, sp.corners, 1, sp.mc, sp.nc, sp.wm1, sp.Sb, 1, st);
     if (e != cudaSuccess) return cuda_fail(e, "template energies");
-    e = launch_cols(sp.Nr, true, sp.X, sp.x_fstride, sp.ldx, sp.mc, sp.ncv, 1, sp.twr, nullptr, sp.bspec, 0,
-                    sp.wm1, (float)(1.0 / ((double)sp.Nr * (double)sp.Nc)), st);
-    if (e != cudaSuccess) return cuda_fail(e, "template spectrum");
+    if (sp.has_fft) {
+        e = launch_cols(sp.Nr, true, sp.X, sp.x_fstride, sp.ldx, sp.mc, sp.ncv, 1, sp.twr, nullptr, sp.bspec, 0,
+                        sp.wm1, (float)(1.0 / ((double)sp.Nr * (double)sp.Nc)), st);
+        if (e != cudaSuccess) return cuda_fail(e, "template spectrum");
+    }
+    if (sp.has_direct) {
+        e = launch_toeplitz(sp.f32, sp.tmpl, sp.desc.m, sp.desc.n, sp.levels, sp.mc, sp.nc, sp.nqc, sp.wm1, sp.coff_i,
+                            sp.coff_f, sp.bprime, sp.dtiles, st);
+        if (e != cudaSuccess) return cuda_fail(e, "template Toeplitz tiles");
+    }
     return MOCO_OK;
 }
 
@@ -209,6 +248,29 @@ moco_status search_group(ShapePlan& sp, const uint16_t* frames, int64_t g, doubl
                          float* margin, cudaStream_t st) {
     const int m = sp.desc.m, n = sp.desc.n;
     Profiler& P = *sp.prof;
+    if (sp.form == MOCO_XCORR_DIRECT_BF16X3) {
+        P.begin(K_FRAME_ROWS, st);
+        cudaError_t e = launch_frame_planes(false, frames, (int64_t)m * n, g, m, n, sp.levels, sp.mc, sp.nc, sp.coff_i,
+                                            nullptr, sp.twc, sp.rowE, sp.colE, sp.tot, sp.corners, sp.wm1,
+                                            sp.planes_hi, sp.planes_lo, sp.ncp, st);
+        P.end(st);
+        if (e != cudaSuccess) return cuda_fail(e, "k_frame_rows (planes)");
+        P.begin(K_ENERGY, st);
+        e = launch_energy(false, false, sp.rowE, sp.colE, sp.tot, sp.corners, g, sp.mc, sp.nc, sp.wm1, sp.Sa, 0, st);
+        P.end(st);
+        if (e != cudaSuccess) return cuda_fail(e, "k_energy");
+        P.begin(K_DIRECT, st);
+        e = launch_direct(sp.planes_hi, sp.planes_lo, g, sp.mc, sp.ncp, sp.nqc, sp.wm1, sp.dtiles, sp.hbuf, sp.dev_err,
+                          st);
+        P.end(st);
+        if (e != cudaSuccess) return cuda_fail(e, "k_direct");
+        P.begin(K_ROWS_INV, st);
+        e = launch_combine_h(sp.hbuf, g, sp.wm1, sp.Sa, sp.Sb, sp.inv_area, sp.unit, cost, sp.coarse,
+                             fbest ? fbest : sp.fbest, margin ? margin : sp.margin, st);
+        P.end(st);
+        if (e != cudaSuccess) return cuda_fail(e, "k_combine_h");
+        return MOCO_OK;
+    }
     P.begin(K_FRAME_ROWS, st);
     cudaError_t e = launch_frame_rows(sp.Nc, false, frames, (int64_t)m * n, g, m, n, sp.levels, sp.mc, sp.nc,
                                       sp.coff_i, nullptr, sp.twc, sp.X, sp.x_fstride, sp.ldx, sp.rowE, sp.colE,
@@ -232,6 +294,8 @@ moco_status search_group(ShapePlan& sp, const uint16_t* frames, int64_t g, doubl
     return MOCO_OK;
 }
 
+moco_status autotune(ShapePlan& sp, cudaStream_t st);
+
 moco_status align_frames(ShapePlan& sp, const uint16_t* frames, int64_t T, int32_t* shifts, double* best_cost,
                          float* margin, cudaStream_t st) {
     const int64_t mn = (int64_t)sp.desc.m * sp.desc.n;
@@ -254,6 +318,43 @@ moco_status align_frames(ShapePlan& sp, const uint16_t* frames, int64_t T, int32
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// MOCO_XCORR_AUTO: time both forms on one batch (zero frames in the staging
+// buffer: the work does not depend on the values) and keep the faster.
+moco_status autotune(ShapePlan& sp, cudaStream_t st) {
+    if (!(sp.has_fft && sp.has_direct)) return MOCO_OK;
+    const int64_t g = std::min<int64_t>(sp.stage_frames, sp.group);
+    cudaError_t e = cudaMemsetAsync(sp.stage[0], 0, (size_t)(g * sp.desc.m * sp.desc.n * 2), st);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune clear");
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    Profiler off;
+    Profiler* keep = sp.prof;
+    sp.prof = &off;
+    moco_status r = MOCO_OK;
+    float best = 0.f;
+    int best_form = MOCO_XCORR_FFT_FP32;
+    for (int form : {MOCO_XCORR_FFT_FP32, MOCO_XCORR_DIRECT_BF16X3}) {
+        sp.form = form;
+        r = search_group(sp, sp.stage[0], g, nullptr, nullptr, nullptr, st);  // warm-up
+        if (r != MOCO_OK) break;
+        cudaEventRecord(a, st);
+        for (int it = 0; it < 3 && r == MOCO_OK; ++it) r = search_group(sp, sp.stage[0], g, nullptr, nullptr, nullptr, st);
+        cudaEventRecord(b, st);
+        e = cudaEventSynchronize(b);
+        if (e != cudaSuccess) { r = cuda_fail(e, "autotune"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        sp.tuned_ms[form] = ms / 3.f;
+        if (form == MOCO_XCORR_FFT_FP32 || ms < best) { best = ms; best_form = form; }
+    }
+    sp.prof = keep;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    sp.form = best_form;
+    return r;
+}
 
 }  // namespace moco
 
@@ -306,6 +407,7 @@ moco_status moco_plan(const moco_shape* shapes, int32_t nshapes, const void* con
     for (int k = 0; k < nshapes && s == MOCO_OK; ++k) s = resolve_shape(shapes[k], plan->shapes[k]);
     for (int k = 0; k < nshapes && s == MOCO_OK; ++k) s = allocate_shape(plan->shapes[k]);
     for (int k = 0; k < nshapes && s == MOCO_OK; ++k) s = prepare_template(plan->shapes[k], templates_dev[k], st);
+    for (int k = 0; k < nshapes && s == MOCO_OK; ++k) s = autotune(plan->shapes[k], st);
     if (s == MOCO_OK) {
         cudaError_t e = cudaStreamCreateWithFlags(&plan->aux, cudaStreamNonBlocking);
         for (auto& ev : plan->ev)
@@ -431,6 +533,24 @@ moco_status moco_cost_backward(moco_plan_t plan, int32_t shape_idx, const uint16
     plan->prof.end(st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint kernels");
     return MOCO_OK;
+}
+
+moco_status moco_plan_status(moco_plan_t plan) {
+    if (!plan) return fail(MOCO_ERR_INVALID_ARG, "null plan");
+    DeviceGuard guard(plan->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "moco_plan_status");
+    moco_status r = MOCO_OK;
+    for (auto& sp : plan->shapes) {
+        unsigned int flag = 0;
+        e = cudaMemcpy(&flag, sp.dev_err, 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "status read-back");
+        if (flag) {
+            cudaMemset(sp.dev_err, 0, 4);
+            r = fail(MOCO_ERR_TIMEOUT, "a device-side wait gave up (tensor-core pipeline)");
+        }
+    }
+    return r;
 }
 
 moco_status moco_profile_enable(moco_plan_t plan, int32_t max_launches) {

@@ -43,6 +43,9 @@ struct ShapePlan {
     int levels = 0, mc = 0, nc = 0, w = 0, wm1 = 0, W = 0;
     int Nr = 0, Nc = 0, ncv = 0, ldx = 0;
     int form = MOCO_XCORR_FFT_FP32;
+    bool has_fft = true, has_direct = false;  // which forms' buffers exist
+    int ncp = 0, nqc = 0;                     // direct form: padded row length, 64-column chunks
+    float tuned_ms[3] = {0, 0, 0};            // autotuner timings per form (ms per frame batch)
     int group = 1;
     int stage_frames = 1;  // frames per host staging buffer
     bool f32 = false;
@@ -59,6 +62,13 @@ struct ShapePlan {
     float2* bspec = nullptr;
     double* Sb = nullptr;
     double* inv_area = nullptr;
+    // direct form
+    float* bprime = nullptr;        // mc x nc offset template
+    void* dtiles = nullptr;         // Toeplitz tiles (hi, lo)
+    void* planes_hi = nullptr;      // group x mc x ncp BF16
+    void* planes_lo = nullptr;
+    float* hbuf = nullptr;          // group x W x W cross term
+    unsigned int* dev_err = nullptr;  // set by a device-side wait that gave up
     // per-group scratch
     float2* X = nullptr;
     float2* Y = nullptr;

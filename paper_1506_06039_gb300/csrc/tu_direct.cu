@@ -1,0 +1,71 @@
+// Launchers of the direct (tensor-core) form of the cross term.
+#include "internal.h"
+#include "kernels.cuh"
+#include "direct.cuh"
+
+namespace moco {
+
+size_t direct_tiles_bytes(int mc, int nqc, int W) { return 2 * (size_t)mc * nqc * direct_tile_bytes(W); }
+size_t direct_smem(int W) { return direct_smem_bytes(W); }
+
+cudaError_t launch_frame_planes(bool f32, const void* src, int64_t src_fstride, int64_t nimg, int m, int n, int levels,
+                                int mc, int nc, const int32_t* coff_i, const float* coff_f, const float2* tw,
+                                u64* rowE, u64* colE, u64* tot, uint32_t* corners, int wm1, void* p_hi, void* p_lo,
+                                int ldp, cudaStream_t st) {
+    if (nimg <= 0) return cudaSuccess;
+    constexpr int N = 48;  // the FFT buffer is unused in this mode
+    const size_t smem = sizeof(float2) * ((kRC / 2) * N + N) + sizeof(u64) * (kRC + nc);
+    const void* fn = f32 ? (const void*)k_frame_rows<N, true, true> : (const void*)k_frame_rows<N, false, true>;
+    cudaError_t e = ensure_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(p_hi);
+    __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(p_lo);
+    if (f32)
+        k_frame_rows<N, true, true><<<(unsigned)nimg, kRowsThreads, smem, st>>>(
+            src, src_fstride, m, n, levels, mc, nc, coff_i, coff_f, tw, nullptr, 0, 0, rowE, colE, tot, corners, wm1,
+            hi, lo, ldp);
+    else
+        k_frame_rows<N, false, true><<<(unsigned)nimg, kRowsThreads, smem, st>>>(
+            src, src_fstride, m, n, levels, mc, nc, coff_i, coff_f, tw, nullptr, 0, 0, rowE, colE, tot, corners, wm1,
+            hi, lo, ldp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_toeplitz(bool f32, const void* tmpl, int m, int n, int levels, int mc, int nc, int nqc, int wm1,
+                            const int32_t* coff_i, const float* coff_f, float* bprime, void* tiles,
+                            cudaStream_t st) {
+    if (f32)
+        k_coarse_image<true><<<256, 256, 0, st>>>(tmpl, m, n, levels, mc, nc, coff_i, coff_f, bprime);
+    else
+        k_coarse_image<false><<<256, 256, 0, st>>>(tmpl, m, n, levels, mc, nc, coff_i, coff_f, bprime);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_toeplitz<<<1024, 256, 0, st>>>(bprime, mc, nc, nqc, wm1, static_cast<uint8_t*>(tiles));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_direct(const void* a_hi, const void* a_lo, int64_t T, int mc, int ncp, int nqc, int wm1,
+                          const void* tiles, float* h, unsigned int* err, cudaStream_t st) {
+    if (T <= 0) return cudaSuccess;
+    const int W = 2 * wm1 + 1;
+    const size_t smem = direct_smem_bytes(W);
+    cudaError_t e = ensure_smem((const void*)k_direct, smem);
+    if (e != cudaSuccess) return e;
+    const int ntiles = (W + direct_ns(W) - 1) / direct_ns(W);
+    const int64_t mtiles = (T + kDirM - 1) / kDirM;
+    dim3 grid((unsigned)ntiles, (unsigned)mtiles);
+    k_direct<<<grid, kDirThreads, smem, st>>>(static_cast<const __nv_bfloat16*>(a_hi),
+                                              static_cast<const __nv_bfloat16*>(a_lo), T, mc, ncp, nqc, wm1,
+                                              static_cast<const uint8_t*>(tiles), h, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine_h(const float* h, int64_t nimg, int wm1, const u64* Sa, const double* Sb,
+                             const double* inv_area, double unit, double* cost, int32_t* coarse, double* fbest,
+                             float* margin, cudaStream_t st) {
+    if (nimg <= 0) return cudaSuccess;
+    k_combine_h<<<(unsigned)nimg, 256, 0, st>>>(h, wm1, Sa, Sb, inv_area, unit, cost, coarse, fbest, margin);
+    return cudaGetLastError();
+}
+
+}  // namespace moco

@@ -73,7 +73,7 @@ def test_plan_rejects_invalid_shapes(lib, shape, msg):
 def test_plan_rejects_unsupported(lib):
     st, handle, err = _plan_status(lib, binding.MocoShape(512, 512, 10, -1, 1, 0, 0, 0))
     assert st == binding.MOCO_ERR_UNSUPPORTED and "levels" in err
-    st, handle, err = _plan_status(lib, binding.MocoShape(4096, 4096, 64, 0, 0, 0, 0, 0))
+    st, handle, err = _plan_status(lib, binding.MocoShape(4096, 4096, 64, 0, 0, binding.XCORR_FFT_FP32, 0, 0))
     assert st == binding.MOCO_ERR_UNSUPPORTED and "FFT" in err
 
 
