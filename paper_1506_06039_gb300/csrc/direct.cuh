@@ -20,6 +20,13 @@
 // run while the MMAs of step k do. One thread issues the MMAs; every
 // mbarrier wait is bounded (about a second) and sets an error flag instead
 // of hanging.
+//
+// Accumulation: the tensor core's FP32 accumulator loses low bits on each
+// accumulation, which over the 12 MMAs x (mc * nc / 64) K steps of a frame
+// would bias h. So each K step accumulates into a fresh TMEM accumulator
+// (two of them, alternating), issuing the small hi*lo and lo*hi products
+// before the hi*hi ones, and every thread adds the finished accumulator of
+// its frame into round-to-nearest FP32 registers.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -31,7 +38,7 @@ constexpr int kDirThreads = 128;
 constexpr int kDirM = 128;      // frames per tile (MMA M)
 constexpr int kDirK = 64;       // pixels per K step
 constexpr int kDirQ = kDirK;    // columns per K step
-constexpr int kDirNmax = 256;   // MMA N (shifts per tile)
+constexpr int kDirNmax = 128;   // MMA N (shifts per tile)
 
 __host__ __device__ inline int direct_wp(int W) { return (W + 15) / 16 * 16; }
 __host__ __device__ inline int direct_ns(int W) { return kDirNmax / direct_wp(W); }
@@ -147,6 +154,31 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
+// Adds the accumulator at TMEM address `addr` (this warp's 32 lanes, N
+// columns) into hsum (column c of this thread's lane).
+__device__ __forceinline__ void drain_acc(uint32_t addr, int N, float (&hsum)[kDirNmax]) {
+    tc_fence_after();
+#pragma unroll
+    for (int c0 = 0; c0 < kDirNmax; c0 += 32) {
+        if (c0 < N) {
+            uint32_t r[32];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(addr + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int c = 0; c < 32; ++c) hsum[c0 + c] += __uint_as_float(r[c]);
+        }
+    }
+    tc_fence_before();
+}
+
 // ---- the GEMM ----------------------------------------------------------------
 //
 // Grid (N tiles, M tiles). N tile j covers shift rows s = -(w-1) + j*NS ..
@@ -170,6 +202,7 @@ k_direct(const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict
     const int ksteps = mc * nqc;
     const uint32_t idesc = direct_idesc(kDirM, N);
     const size_t plane_tiles = (size_t)mc * nqc * tb;
+    constexpr uint32_t kTmemCols = 2 * kDirNmax;  // two accumulators
 
     if (tid == 0) {
         mbar_init(&load_bar[0], 1);
@@ -179,9 +212,8 @@ k_direct(const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict
         s_abort = 0;
     }
     if (warp == 0) {
-        const uint32_t ncols = 256;
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(ncols)
+                     "r"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -240,15 +272,24 @@ k_direct(const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict
         }
     };
 
+    // FP32 sum of this thread's frame row over the K steps (columns < N).
+    float hsum[kDirNmax];
+#pragma unroll
+    for (int c = 0; c < kDirNmax; ++c) hsum[c] = 0.f;
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+
     issue(0, 0);
     for (int k = 0; k < ksteps; ++k) {
         const int st = k & 1;
-        if (k + 1 < ksteps) {
-            if (k >= 1) {  // stage st^1 was last read by the MMAs of step k-1
-                if (!mbar_wait(&mma_bar[st ^ 1], ((k - 1) >> 1) & 1, err)) s_abort = 1;
-            }
+        if (k >= 1) {
+            // Step k-1's MMAs (stage and accumulator st^1) are done: drain them,
+            // then reuse the stage for step k+1.
+            if (!mbar_wait(&mma_bar[st ^ 1], ((k - 1) >> 1) & 1, err)) s_abort = 1;
             __syncthreads();
             if (s_abort) break;
+            drain_acc(lane_addr + (uint32_t)((st ^ 1) * kDirNmax), N, hsum);
+        }
+        if (k + 1 < ksteps) {
             issue(k + 1, st ^ 1);
             cp_wait<1>();
         } else {
@@ -264,54 +305,47 @@ k_direct(const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict
             const unsigned char* A1 = sA(st, 1);
             const unsigned char* B0 = sB(st, 0);
             const unsigned char* B1 = sB(st, 1);
+            const uint32_t d = tmem + (uint32_t)(st * kDirNmax);
+            // small terms first, then hi*hi: a fresh accumulator every K step
 #pragma unroll
             for (int kk = 0; kk < kDirK / 16; ++kk) {
                 const uint32_t off = kk * 256;  // two core matrices along K per K16
-                const uint32_t acc0 = (k > 0 || kk > 0) ? 1u : 0u;
-                mma_bf16(tmem, smem_desc(A0 + off), smem_desc(B0 + off), idesc, acc0);
-                mma_bf16(tmem, smem_desc(A0 + off), smem_desc(B1 + off), idesc, 1u);
-                mma_bf16(tmem, smem_desc(A1 + off), smem_desc(B0 + off), idesc, 1u);
+                mma_bf16(d, smem_desc(A0 + off), smem_desc(B1 + off), idesc, kk > 0 ? 1u : 0u);
+                mma_bf16(d, smem_desc(A1 + off), smem_desc(B0 + off), idesc, 1u);
+            }
+#pragma unroll
+            for (int kk = 0; kk < kDirK / 16; ++kk) {
+                const uint32_t off = kk * 256;
+                mma_bf16(d, smem_desc(A0 + off), smem_desc(B0 + off), idesc, 1u);
             }
             mma_commit(&mma_bar[st]);
         }
     }
-    // Drain: the last commit covers every MMA issued before it.
+    // Drain the last step (its commit covers every earlier MMA).
     if (!s_abort && ksteps > 0) {
         if (!mbar_wait(&mma_bar[(ksteps - 1) & 1], ((ksteps - 1) >> 1) & 1, err)) s_abort = 1;
     }
     __syncthreads();
-    tc_fence_after();
+    if (!s_abort && ksteps > 0) drain_acc(lane_addr + (uint32_t)(((ksteps - 1) & 1) * kDirNmax), N, hsum);
+    if (s_abort) {
+        // Leave no copy in flight into this CTA's shared memory.
+        cp_wait<0>();
+    }
     if (!s_abort) {
-        // Each warp reads its 32 TMEM lanes (frames), 32 columns at a time.
         const int64_t f = f0 + warp * 32 + (tid & 31);
-        for (int c0 = 0; c0 < N; c0 += 32) {
-            uint32_t r[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (f < T) {
+        if (f < T) {
 #pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const int n = c0 + c, sl = n / Wp, ti = n - sl * Wp;
-                    const int s = s_first + sl;
-                    if (ti < W && s <= wm1) h[f * (int64_t)W * W + (int64_t)(s + wm1) * W + ti] = __uint_as_float(r[c]);
-                }
+            for (int c = 0; c < kDirNmax; ++c) {
+                const int sl = c / Wp, ti = c - sl * Wp;
+                const int s = s_first + sl;
+                if (c < N && ti < W && s <= wm1) h[f * (int64_t)W * W + (int64_t)(s + wm1) * W + ti] = hsum[c];
             }
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
-        const uint32_t ncols = 256;
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     }
 }
 
