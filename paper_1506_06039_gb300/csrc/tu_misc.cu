@@ -1,7 +1,7 @@
 // Energies, jitter, template offset, and small host helpers.
+#include <map>
 #include <mutex>
-#include <set>
-#include <tuple>
+#include <utility>
 
 #include "fft_sizes.h"
 #include "internal.h"
@@ -32,19 +32,19 @@ int fft_split_max(int N) {
 }
 
 cudaError_t ensure_smem(const void* func, size_t bytes) {
+    // The limit only ever grows: a launch with less shared memory must not
+    // lower it under a launch that needs more.
     static std::mutex mu;
-    static std::set<std::tuple<const void*, int, size_t>> done;
+    static std::map<std::pair<const void*, int>, size_t> limit;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(mu);
-    auto key = std::make_tuple(func, dev, bytes);
-    if (done.count(key)) return cudaSuccess;
-    if (bytes > 48 * 1024) {
-        e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
-    }
-    done.insert(key);
+    size_t& cur = limit[std::make_pair(func, dev)];
+    if (bytes <= cur || bytes <= 48 * 1024) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    cur = bytes;
     return cudaSuccess;
 }
 
