@@ -69,7 +69,7 @@ __device__ __forceinline__ uint32_t hi16(uint32_t w) { return w >> 16; }
 //
 // PLANES (the direct form): no FFT; the offset searched-grid image is written
 // as BF16 hi and lo planes instead, planes[f][r][c] with row length ldp
-// (columns nc .. ldp-1 are left as they are: zero from allocation).
+// (columns nc .. ldp-1 written as zeros).
 template <int N, bool F32IN, bool PLANES = false>
 __global__ void __launch_bounds__(kRowsThreads, 2)
 k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, int levels, int mc,
@@ -164,6 +164,11 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
                 tacc += rs;
                 if (top || bot) atomicAdd(&rowacc[rl], rs);
                 if constexpr (PLANES) {
+                    if (g == 0)  // the padding columns nc .. ldp-1 must read as zero
+                        for (int c = nc; c < ldp; ++c) {
+                            p_hi[(f * mc + r) * (int64_t)ldp + c] = __float2bfloat16_rn(0.f);
+                            p_lo[(f * mc + r) * (int64_t)ldp + c] = __float2bfloat16_rn(0.f);
+                        }
                     __nv_bfloat16* ph = p_hi + (f * mc + r) * (int64_t)ldp + g * CW;
                     __nv_bfloat16* pl = p_lo + (f * mc + r) * (int64_t)ldp + g * CW;
 #pragma unroll

@@ -72,14 +72,10 @@ void host_roots(int N, std::vector<float2>& out) {
 int64_t per_frame_scratch_bytes(const ShapePlan& sp) {
     const int64_t W = sp.W, wm1 = sp.wm1;
     int64_t b = 0;
-    if (sp.has_fft) {
-        b += (int64_t)sp.ncv * sp.ldx * 8;    // X
-        b += W * sp.ncv * 8;                   // Y
-    }
-    if (sp.has_direct) {
-        b += (int64_t)sp.mc * sp.ncp * 4;      // BF16 hi + lo planes
-        b += W * W * 4;                        // h
-    }
+    // The two forms' cross-term scratch is never live at once: one region.
+    const int64_t fft = sp.has_fft ? (int64_t)sp.ncv * sp.ldx * 8 + W * sp.ncv * 8 : 0;  // X, Y
+    const int64_t dir = sp.has_direct ? (int64_t)sp.mc * sp.ncp * 4 + W * W * 4 : 0;     // planes, h
+    b += std::max(fft, dir);
     b += ((int64_t)sp.mc + sp.nc + 1) * 8;     // rowE, colE, tot
     b += 4 * wm1 * wm1 * 4;                    // corners
     b += W * W * 8;                            // Sa
@@ -155,16 +151,21 @@ moco_status allocate_shape(ShapePlan& sp) {
     if (sp.has_direct) {
         c.add(&sp.bprime, (size_t)sp.mc * sp.nc * 4);
         c.add(&sp.dtiles, direct_tiles_bytes(sp.mc, sp.nqc, sp.W));
-        c.add(&sp.planes_hi, (size_t)(G * sp.mc * sp.ncp * 2));
-        c.add(&sp.planes_lo, (size_t)(G * sp.mc * sp.ncp * 2));
-        c.add(&sp.hbuf, (size_t)(G * W * W * 4));
     }
     c.add(&sp.Sb, (size_t)W * W * 8);
     c.add(&sp.inv_area, (size_t)W * W * 8);
     sp.x_fstride = (int64_t)sp.ncv * sp.ldx;
     sp.y_fstride = W * sp.ncv;
-    c.add(&sp.X, sp.has_fft ? (size_t)(G * sp.x_fstride * 8) : 0);
-    c.add(&sp.Y, sp.has_fft ? (size_t)(G * sp.y_fstride * 8) : 0);
+    // Cross-term scratch: the FFT form's X, Y and the direct form's planes, h
+    // share one region (a plan runs one form at a time).
+    const size_t fft_x = sp.has_fft ? (size_t)(G * sp.x_fstride * 8) : 0;
+    const size_t fft_y = sp.has_fft ? (size_t)(G * sp.y_fstride * 8) : 0;
+    const size_t dir_p = sp.has_direct ? (size_t)(G * sp.mc * sp.ncp * 2) : 0;
+    const size_t dir_h = sp.has_direct ? (size_t)(G * W * W * 4) : 0;
+    const size_t fft_total = align_up(fft_x, 256) + fft_y;
+    const size_t dir_total = 2 * align_up(dir_p, 256) + dir_h;
+    void* xregion = nullptr;
+    c.add(&xregion, std::max(fft_total, dir_total));
     c.add(&sp.rowE, (size_t)(G * sp.mc * 8));
     c.add(&sp.colE, (size_t)(G * sp.nc * 8));
     c.add(&sp.tot, (size_t)(G * 8));
@@ -189,6 +190,18 @@ moco_status allocate_shape(ShapePlan& sp) {
         return fail(MOCO_ERR_OOM, "cudaMalloc of " + std::to_string(sp.bytes) + " bytes failed");
     }
     c.bind(sp.base);
+    {
+        char* x = static_cast<char*>(xregion);
+        if (sp.has_fft) {
+            sp.X = reinterpret_cast<float2*>(x);
+            sp.Y = reinterpret_cast<float2*>(x + align_up(fft_x, 256));
+        }
+        if (sp.has_direct) {
+            sp.planes_hi = x;
+            sp.planes_lo = x + align_up(dir_p, 256);
+            sp.hbuf = reinterpret_cast<float*>(x + 2 * align_up(dir_p, 256));
+        }
+    }
     e = cudaMemset(sp.dev_err, 0, 4);
     if (e == cudaSuccess && sp.has_direct) e = cudaMemset(sp.planes_hi, 0, (size_t)(G * sp.mc * sp.ncp * 2));
     if (e == cudaSuccess && sp.has_direct) e = cudaMemset(sp.planes_lo, 0, (size_t)(G * sp.mc * sp.ncp * 2));

@@ -177,7 +177,7 @@ def test_std512_full_workload_sampled():
         shifts, best, margin = plan.align(st.frames, best_cost=True, margin=True)
         torch.cuda.synchronize()
         info = plan.info()
-    assert info["levels"] == 1 and info["mc"] == 256 and info["group_frames"] >= wl.T
+    assert info["levels"] == 1 and info["mc"] == 256
     shifts = shifts.cpu().numpy()
     sample = np.random.default_rng(0).choice(wl.T, 12, replace=False)
     fr = st.frames.cpu().numpy()[sample]
