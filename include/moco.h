@@ -157,6 +157,26 @@ moco_status moco_align_host(moco_plan_t plan, int32_t shape_idx, const uint16_t*
  * flag then cleared); MOCO_OK otherwise. */
 moco_status moco_plan_status(moco_plan_t plan);
 
+/* The full-resolution 3x3 refinement on its own, allocating nothing (the
+ * paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc, such as code inside a host application that owns all device
+ * memory, or a real-time loop that must never block in the allocator).
+ * frames_dev [T][m][n] and template_dev [m][n] are uint16, 16-byte aligned,
+ * n % 8 == 0; coarse_dev [T][2] holds each frame's optimum (s_c, t_c) on the
+ * 2x2-box grid (|2 s_c| + 1 < m, |2 t_c| + 1 < n); shifts_dev [T][2]
+ * receives the best of (2 s_c + u, 2 t_c + v), u, v in {-1, 0, 1}, by exact
+ * integer sums and the same tie-break as moco_align_stack.
+ * Its scratch is one static device array sized for at most 8192 frames per
+ * call (640 KiB, held by every GPU that loads this library until the process
+ * exits); larger T returns MOCO_ERR_INVALID_ARG. The first call on a device
+ * looks the array's address up (cudaGetSymbolAddress) and should come before
+ * any stream capture. Every call shares the array and clears the part it
+ * uses first, on `stream`; calls that overlap on the GPU (different streams,
+ * or different host threads on one device) race on it. */
+moco_status moco_jitter_noalloc(const uint16_t* frames_dev, int64_t T, int32_t m, int32_t n,
+                                const uint16_t* template_dev, const int32_t* coarse_dev, int32_t* shifts_dev,
+                                void* stream);
+
 /* Fills *info for shape `shape_idx`. */
 moco_status moco_plan_query(moco_plan_t plan, int32_t shape_idx, moco_shape_info* info);
 

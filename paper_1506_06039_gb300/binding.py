@@ -32,6 +32,7 @@ EXPORTS = (
     "moco_plan", "moco_set_template", "moco_align_stack", "moco_cost_surface", "moco_softmin",
     "moco_cost_backward", "moco_align_host", "moco_plan_query", "moco_plan_destroy",
     "moco_status_string", "moco_last_error", "moco_profile_enable", "moco_profile_read", "moco_plan_status",
+    "moco_jitter_noalloc",
 )
 
 
@@ -96,6 +97,7 @@ def lib():
             L.moco_last_error.restype = ctypes.c_char_p
             L.moco_profile_enable.argtypes = [P, i32]
             L.moco_plan_status.argtypes = [P]
+            L.moco_jitter_noalloc.argtypes = [P, i64, i32, i32, P, P, P, P]
             L.moco_profile_read.argtypes = [P, ctypes.POINTER(MocoKernelStat), i32, ctypes.POINTER(i32), i32]
             for name in EXPORTS:
                 if name not in ("moco_status_string", "moco_last_error"):
@@ -232,6 +234,18 @@ def moco_plan_query(plan, shape_idx) -> dict:
 
 def moco_plan_destroy(plan):
     _check(lib().moco_plan_destroy(plan))
+
+
+def moco_jitter_noalloc(frames, template, coarse, shifts, stream=None):
+    """3x3 full-resolution refinement of given 2x2-grid optima; allocates nothing."""
+    import torch
+    _need(frames, torch.uint16, "frames")
+    _need(template, torch.uint16, "template")
+    _need(coarse, torch.int32, "coarse")
+    _need(shifts, torch.int32, "shifts")
+    T, m, n = frames.shape
+    _check(lib().moco_jitter_noalloc(_ptr(frames), T, m, n, _ptr(template), _ptr(coarse), _ptr(shifts),
+                                     _stream(stream)))
 
 
 def moco_plan_status(plan):
