@@ -84,7 +84,7 @@ typedef struct {
     int32_t xcorr;           /* the form in use (never AUTO) */
     int32_t group_frames;    /* frames per internal batch */
     int32_t offset;          /* integer offset c subtracted from frame and template */
-    int64_t workspace_bytes; /* device bytes owned by this shape */
+    int64_t workspace_bytes; /* device bytes of this shape's tables plus the plan's shared batch scratch */
 } moco_shape_info;
 
 typedef struct moco_plan_s* moco_plan_t;

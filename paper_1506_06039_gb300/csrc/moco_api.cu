@@ -138,8 +138,9 @@ moco_status resolve_shape(const moco_shape& d, ShapePlan& sp) {
     return MOCO_OK;
 }
 
+// Per-shape data that lives as long as the plan (template-derived tables).
 moco_status allocate_shape(ShapePlan& sp) {
-    const int64_t G = sp.group, W = sp.W, m = sp.desc.m, n = sp.desc.n;
+    const int64_t W = sp.W, m = sp.desc.m, n = sp.desc.n;
     Carver c;
     c.add(&sp.tmpl, (size_t)m * n * (sp.f32 ? 4 : 2));
     c.add(&sp.coff_i, 4);
@@ -154,34 +155,10 @@ moco_status allocate_shape(ShapePlan& sp) {
     }
     c.add(&sp.Sb, (size_t)W * W * 8);
     c.add(&sp.inv_area, (size_t)W * W * 8);
-    sp.x_fstride = (int64_t)sp.ncv * sp.ldx;
-    sp.y_fstride = W * sp.ncv;
-    // Cross-term scratch: the FFT form's X, Y and the direct form's planes, h
-    // share one region (a plan runs one form at a time).
-    const size_t fft_x = sp.has_fft ? (size_t)(G * sp.x_fstride * 8) : 0;
-    const size_t fft_y = sp.has_fft ? (size_t)(G * sp.y_fstride * 8) : 0;
-    const size_t dir_p = sp.has_direct ? (size_t)(G * sp.mc * sp.ncp * 2) : 0;
-    const size_t dir_h = sp.has_direct ? (size_t)(G * W * W * 4) : 0;
-    const size_t fft_total = align_up(fft_x, 256) + fft_y;
-    const size_t dir_total = 2 * align_up(dir_p, 256) + dir_h;
-    void* xregion = nullptr;
-    c.add(&xregion, std::max(fft_total, dir_total));
-    c.add(&sp.rowE, (size_t)(G * sp.mc * 8));
-    c.add(&sp.colE, (size_t)(G * sp.nc * 8));
-    c.add(&sp.tot, (size_t)(G * 8));
-    c.add(&sp.corners, (size_t)(G * 4 * sp.wm1 * sp.wm1 * 4));
-    c.add(&sp.Sa, (size_t)(G * W * W * 8));
-    c.add(&sp.coarse, (size_t)(G * 2 * 4));
-    c.add(&sp.fbest, (size_t)(G * 8));
-    c.add(&sp.margin, (size_t)(G * 4));
     c.add(&sp.grad_acc, (size_t)(m * n * 4));
     c.add(&sp.grad_Q, (size_t)(W * W * 4));
-    c.add(&sp.jit_acc, (size_t)(G * 9 * 8));
-    c.add(&sp.jit_ticket, (size_t)(G * 4));
-    for (int k = 0; k < 2; ++k) {
-        c.add(&sp.stage[k], (size_t)((int64_t)sp.stage_frames * m * n * 2));
-        c.add(&sp.stage_shifts[k], (size_t)(sp.stage_frames * 2 * 4));
-    }
+    sp.x_fstride = (int64_t)sp.ncv * sp.ldx;
+    sp.y_fstride = W * sp.ncv;
     sp.bytes = c.off;
     cudaError_t e = cudaMalloc(&sp.base, sp.bytes);
     if (e != cudaSuccess) {
@@ -190,21 +167,7 @@ moco_status allocate_shape(ShapePlan& sp) {
         return fail(MOCO_ERR_OOM, "cudaMalloc of " + std::to_string(sp.bytes) + " bytes failed");
     }
     c.bind(sp.base);
-    {
-        char* x = static_cast<char*>(xregion);
-        if (sp.has_fft) {
-            sp.X = reinterpret_cast<float2*>(x);
-            sp.Y = reinterpret_cast<float2*>(x + align_up(fft_x, 256));
-        }
-        if (sp.has_direct) {
-            sp.planes_hi = x;
-            sp.planes_lo = x + align_up(dir_p, 256);
-            sp.hbuf = reinterpret_cast<float*>(x + 2 * align_up(dir_p, 256));
-        }
-    }
     e = cudaMemset(sp.dev_err, 0, 4);
-    if (e == cudaSuccess && sp.has_direct) e = cudaMemset(sp.planes_hi, 0, (size_t)(G * sp.mc * sp.ncp * 2));
-    if (e == cudaSuccess && sp.has_direct) e = cudaMemset(sp.planes_lo, 0, (size_t)(G * sp.mc * sp.ncp * 2));
     if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
     // Host-computed constant tables.
     std::vector<float2> tw;
@@ -222,6 +185,51 @@ moco_status allocate_shape(ShapePlan& sp) {
     e = cudaMemcpy(sp.inv_area, ia.data(), ia.size() * 8, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "upload of 1/Area");
     return MOCO_OK;
+}
+
+// Per-batch scratch of one shape, carved from `base` (or only sized when
+// base is null). Shapes run one after another on the plan's stream, so all
+// shapes of a plan share one scratch region sized for the largest.
+size_t bind_scratch(ShapePlan& sp, void* base) {
+    const int64_t G = sp.group, W = sp.W, m = sp.desc.m, n = sp.desc.n;
+    Carver c;
+    // Cross-term scratch: the FFT form's X, Y and the direct form's planes, h
+    // share one region (a shape runs one form at a time).
+    const size_t fft_x = sp.has_fft ? (size_t)(G * sp.x_fstride * 8) : 0;
+    const size_t fft_y = sp.has_fft ? (size_t)(G * sp.y_fstride * 8) : 0;
+    const size_t dir_p = sp.has_direct ? (size_t)(G * sp.mc * sp.ncp * 2) : 0;
+    const size_t dir_h = sp.has_direct ? (size_t)(G * W * W * 4) : 0;
+    const size_t fft_total = align_up(fft_x, 256) + fft_y;
+    const size_t dir_total = 2 * align_up(dir_p, 256) + dir_h;
+    void* xregion = nullptr;
+    c.add(&xregion, std::max(fft_total, dir_total));
+    c.add(&sp.rowE, (size_t)(G * sp.mc * 8));
+    c.add(&sp.colE, (size_t)(G * sp.nc * 8));
+    c.add(&sp.tot, (size_t)(G * 8));
+    c.add(&sp.corners, (size_t)(G * 4 * sp.wm1 * sp.wm1 * 4));
+    c.add(&sp.Sa, (size_t)(G * W * W * 8));
+    c.add(&sp.coarse, (size_t)(G * 2 * 4));
+    c.add(&sp.fbest, (size_t)(G * 8));
+    c.add(&sp.margin, (size_t)(G * 4));
+    c.add(&sp.jit_acc, (size_t)(G * 9 * 8));
+    c.add(&sp.jit_ticket, (size_t)(G * 4));
+    for (int k = 0; k < 2; ++k) {
+        c.add(&sp.stage[k], (size_t)((int64_t)sp.stage_frames * m * n * 2));
+        c.add(&sp.stage_shifts[k], (size_t)(sp.stage_frames * 2 * 4));
+    }
+    if (!base) return c.off;
+    c.bind(base);
+    char* x = static_cast<char*>(xregion);
+    if (sp.has_fft) {
+        sp.X = reinterpret_cast<float2*>(x);
+        sp.Y = reinterpret_cast<float2*>(x + align_up(fft_x, 256));
+    }
+    if (sp.has_direct) {
+        sp.planes_hi = x;
+        sp.planes_lo = x + align_up(dir_p, 256);
+        sp.hbuf = reinterpret_cast<float*>(x + 2 * align_up(dir_p, 256));
+    }
+    return c.off;
 }
 
 // Offset, energies and spectrum of the template (run whenever it changes).
@@ -395,6 +403,7 @@ moco_status moco_plan_destroy(moco_plan_t plan) {
     cudaDeviceSynchronize();
     for (auto& sp : plan->shapes)
         if (sp.base) cudaFree(sp.base);
+    if (plan->scratch) cudaFree(plan->scratch);
     if (plan->aux) cudaStreamDestroy(plan->aux);
     for (auto& ev : plan->prof.pool) cudaEventDestroy(ev);
     for (auto& ev : plan->ev)
@@ -419,6 +428,19 @@ moco_status moco_plan(const moco_shape* shapes, int32_t nshapes, const void* con
     moco_status s = MOCO_OK;
     for (int k = 0; k < nshapes && s == MOCO_OK; ++k) s = resolve_shape(shapes[k], plan->shapes[k]);
     for (int k = 0; k < nshapes && s == MOCO_OK; ++k) s = allocate_shape(plan->shapes[k]);
+    if (s == MOCO_OK) {
+        size_t need = 0;
+        for (auto& sp : plan->shapes) need = std::max(need, bind_scratch(sp, nullptr));
+        cudaError_t e = cudaMalloc(&plan->scratch, need);
+        if (e != cudaSuccess) {
+            plan->scratch = nullptr;
+            cudaGetLastError();
+            s = fail(MOCO_ERR_OOM, "cudaMalloc of " + std::to_string(need) + " bytes of batch scratch failed");
+        } else {
+            plan->scratch_bytes = need;
+            for (auto& sp : plan->shapes) bind_scratch(sp, plan->scratch);
+        }
+    }
     for (int k = 0; k < nshapes && s == MOCO_OK; ++k) s = prepare_template(plan->shapes[k], templates_dev[k], st);
     for (int k = 0; k < nshapes && s == MOCO_OK; ++k) s = autotune(plan->shapes[k], st);
     if (s == MOCO_OK) {
@@ -461,7 +483,7 @@ moco_status moco_plan_query(moco_plan_t plan, int32_t shape_idx, moco_shape_info
     info->xcorr = sp.form;
     info->group_frames = sp.group;
     info->offset = off;
-    info->workspace_bytes = (int64_t)sp.bytes;
+    info->workspace_bytes = (int64_t)(sp.bytes + plan->scratch_bytes);
     return MOCO_OK;
 }
 

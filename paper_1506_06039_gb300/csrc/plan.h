@@ -107,4 +107,6 @@ struct moco_plan_s {
     cudaStream_t aux = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     moco::Profiler prof;
+    void* scratch = nullptr;  // per-batch scratch shared by all shapes
+    size_t scratch_bytes = 0;
 };
