@@ -56,6 +56,26 @@ def dist_env():
     return world, rank, local
 
 
+def rank_seed(seed, rank):
+    """Weak scaling: every rank aligns its own stack, drawn from its own seed."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The slowest rank's number (the job's time); x itself with one rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, frames_per_rank, steps, seconds):
+    """Whole-job frames/s: the frames all ranks aligned over the slowest rank's time."""
+    return world * frames_per_rank * steps / seconds
+
+
 def workload_config(wl, form):
     return {
         "workload": "%s: %d frames of %dx%d uint16, 2x2 box to %dx%d, w=%d on the searched grid, "
@@ -247,7 +267,7 @@ def main():
     if args.frames:
         import dataclasses
         wl = dataclasses.replace(wl, T=args.frames)
-    st = synth.make_stack_torch(wl.m, wl.n, wl.T, wl.nblobs, wl.shift_max, wl.seed + 1000 * rank,
+    st = synth.make_stack_torch(wl.m, wl.n, wl.T, wl.nblobs, wl.shift_max, rank_seed(wl.seed, rank),
                                 template=wl.template)
     form = {"auto": XCORR_AUTO, "fft": XCORR_FFT_FP32, "direct": XCORR_DIRECT_BF16X3}[args.form]
     plan = Plan(dict(m=wl.m, n=wl.n, w=wl.w, xcorr=form, group_frames=args.group), st.template)
@@ -279,14 +299,10 @@ def main():
     if pg:
         pg.barrier()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), pg, "cuda")
     profile = plan.profile_read(reset=True)
     plan.profile(0)
-    value = world * wl.T * args.steps / (ms / 1e3)
+    value = job_value(world, wl.T, args.steps, ms / 1e3)
     launches = sum(l for l, _ in profile.values())
     peaks = load_peaks()
     rf = roofline(profile, info, wl, wl.T, args.steps, peaks, clocks)
@@ -303,12 +319,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             plan.align_host(host, shifts_host=out_h)
-        el = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([el], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": world * wl.T * args.e2e_steps / el, "unit": UNIT,
+        el = max_over_ranks(time.perf_counter() - t0, pg, "cuda")
+        e2e = {"value": job_value(world, wl.T, args.e2e_steps, el), "unit": UNIT,
                "h2d_bytes_per_step": int(wl.T * wl.m * wl.n * 2), "d2h_bytes_per_step": int(wl.T * 8),
                "steps": args.e2e_steps, "api": "moco_align_host (pinned host buffers)"}
 
@@ -349,8 +361,8 @@ def run_mixed(args, world, rank, local):
             s_["T"] = min(s_["T"], args.frames)
     stacks = []
     for s_ in specs:
-        st = synth.make_stack_torch(s_["m"], s_["n"], s_["T"], s_["nblobs"], s_["shift_max"], s_["seed"] + rank,
-                                    template="clean", chunk=64)
+        st = synth.make_stack_torch(s_["m"], s_["n"], s_["T"], s_["nblobs"], s_["shift_max"],
+                                    rank_seed(s_["seed"], rank), template="clean", chunk=64)
         stacks.append((st, s_["w"]))
     plan = Plan([dict(m=s_["m"], n=s_["n"], w=s_["w"]) for s_ in specs], [st.template for st, _ in stacks])
     outs = [torch.empty((st.frames.shape[0], 2), dtype=torch.int32, device="cuda") for st, _ in stacks]
