@@ -13,7 +13,8 @@
 //    then N1 tasks per row each run an N2-point codelet on a contiguous block.
 //    The forward transform leaves X[k] at position N2*(k mod N1) + k/N1; the
 //    inverse takes exactly that layout and returns natural order, so the
-//    frequency-domain product in between never needs a reorder.
+//    frequency-domain product in between never needs a reorder. Positions
+//    map to shared-memory slots through sk() (a bank-conflict skew).
 #pragma once
 #include <cuda_runtime.h>
 #include "twiddles.cuh"
@@ -186,6 +187,21 @@ MOCO_FOUR(512, 16, 32)
 MOCO_FOUR(576, 16, 36)
 #undef MOCO_FOUR
 
+// Shared-memory slot of logical position p in a row: with an even N2 one
+// spare slot follows every N2 positions, so that the second stage's
+// contiguous N2-blocks (one per thread) start on different banks.
+template <int N>
+struct Skew {
+    enum { S = (Four<N>::N2 % 2 == 0) ? 1 : 0, ROW = N + S * Four<N>::N1 + 1 };
+};
+template <int N>
+__device__ __forceinline__ int sk(int p) {
+    return Skew<N>::S ? p + p / Four<N>::N2 : p;
+}
+// Row stride (in complex elements) of a transform buffer: skewed length + 1.
+template <int N>
+constexpr int fft_ld() { return Skew<N>::ROW; }
+
 // Position of spectral index k in the forward output layout.
 template <int N>
 __device__ __forceinline__ int spec_pos(int k) {
@@ -198,23 +214,23 @@ __device__ __forceinline__ int spec_pos(int k) {
 // Every thread of the block must call this (it synchronises).
 template <int N>
 __device__ void fft4_fwd(float2* buf, int ld, int rows, const float2* tw, int tid, int nthr) {
-    constexpr int N1 = Four<N>::N1, N2 = Four<N>::N2;
+    constexpr int N1 = Four<N>::N1, N2 = Four<N>::N2, B = N2 + Skew<N>::S;  // B: skewed block stride
     for (int task = tid; task < rows * N2; task += nthr) {
         int r = task / N2, n2 = task - r * N2;
         float2* p = buf + r * ld + n2;
         float2 x[N1];
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) x[n1] = p[N2 * n1];
+        for (int n1 = 0; n1 < N1; ++n1) x[n1] = p[B * n1];
         Dft<N1, false>::run(x);
 #pragma unroll
         for (int k1 = 1; k1 < N1; ++k1) x[k1] = cmul(x[k1], tw[n2 * k1]);
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) p[N2 * k1] = x[k1];
+        for (int k1 = 0; k1 < N1; ++k1) p[B * k1] = x[k1];
     }
     __syncthreads();
     for (int task = tid; task < rows * N1; task += nthr) {
         int r = task / N1, k1 = task - r * N1;
-        float2* p = buf + r * ld + N2 * k1;
+        float2* p = buf + r * ld + B * k1;
         float2 x[N2];
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) x[n2] = p[n2];
@@ -229,10 +245,10 @@ __device__ void fft4_fwd(float2* buf, int ld, int rows, const float2* tw, int ti
 // layout, output in natural order.
 template <int N>
 __device__ void fft4_inv(float2* buf, int ld, int rows, const float2* tw, int tid, int nthr) {
-    constexpr int N1 = Four<N>::N1, N2 = Four<N>::N2;
+    constexpr int N1 = Four<N>::N1, N2 = Four<N>::N2, B = N2 + Skew<N>::S;  // B: skewed block stride
     for (int task = tid; task < rows * N1; task += nthr) {
         int r = task / N1, k1 = task - r * N1;
-        float2* p = buf + r * ld + N2 * k1;
+        float2* p = buf + r * ld + B * k1;
         float2 x[N2];
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) x[k2] = p[k2];
@@ -248,10 +264,10 @@ __device__ void fft4_inv(float2* buf, int ld, int rows, const float2* tw, int ti
         float2* p = buf + r * ld + n2;
         float2 x[N1];
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) x[k1] = p[N2 * k1];
+        for (int k1 = 0; k1 < N1; ++k1) x[k1] = p[B * k1];
         Dft<N1, true>::run(x);
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) p[N2 * n1] = x[n1];
+        for (int n1 = 0; n1 < N1; ++n1) p[B * n1] = x[n1];
     }
     __syncthreads();
 }

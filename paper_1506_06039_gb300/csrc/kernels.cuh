@@ -80,8 +80,9 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
              __nv_bfloat16* __restrict__ p_lo = nullptr, int ldp = 0) {
     typedef typename AccT<F32IN>::type Acc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* buf = reinterpret_cast<float2*>(smem_raw);  // (kRC/2) x N
-    float2* tw = buf + (kRC / 2) * N;                    // N
+    constexpr int LD = fft_ld<N>();                      // skewed, padded row
+    float2* buf = reinterpret_cast<float2*>(smem_raw);  // (kRC/2) x LD
+    float2* tw = buf + (kRC / 2) * LD;                   // N
     Acc* rowacc = reinterpret_cast<Acc*>(tw + N);        // kRC
     Acc* colacc = rowacc + kRC;                          // nc
     __shared__ Acc red[32];
@@ -102,10 +103,94 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
     const float cf_off = F32IN ? *coff_f : 0.f;
     const size_t wm1sq = (size_t)wm1 * wm1;
 
+    // FFT-mode loader: a thread owns one column c of a row pair (rows 2p and
+    // 2p+1 of the chunk, packed as one complex value), so consecutive threads
+    // write consecutive 8-byte words of the transform buffer. Its column set
+    // is the same in every chunk: edge-column energies stay in registers.
+    const int CS = (nc + nthr - 1) / nthr;  // column slots per thread (nc > nthr)
+    const int PPI = nc <= nthr ? nthr / nc : 1;
+    const bool warp_rows = (nc % 32 == 0);  // every warp then shares one row pair
+    Acc colreg[4] = {0, 0, 0, 0};
+
     for (int r0 = 0; r0 < mc; r0 += kRC) {
         const int rows = min(kRC, mc - r0), nfft = (rows + 1) >> 1;
-        if constexpr (!PLANES)
-            for (int i = tid; i < nfft * N; i += nthr) buf[i] = make_float2(0.f, 0.f);
+        if constexpr (!PLANES) {
+            for (int i = tid; i < nfft * (N - nc); i += nthr) {
+                const int pr = i / (N - nc), cc = nc + (i - pr * (N - nc));
+                buf[pr * LD + sk<N>(cc)] = make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int slot = 0; slot < 4; ++slot) {
+                if (slot >= CS) break;
+                int c, p0;
+                if (nc <= nthr) {
+                    c = tid % nc;
+                    p0 = tid / nc;
+                    if (p0 >= PPI) break;
+                } else {
+                    c = tid + slot * nthr;
+                    p0 = 0;
+                    if (c >= nc) break;
+                }
+                const bool left = c < wm1, right = c >= nc - wm1;
+                for (int pr = p0; pr < nfft; pr += PPI) {
+                    const int rl = 2 * pr, r = r0 + rl;
+                    const bool has1 = rl + 1 < rows;
+                    float v[2];
+                    if (!F32IN) {
+                        const uint16_t* base = static_cast<const uint16_t*>(src) + f * src_fstride;
+                        int32_t iv[2] = {0, 0};
+                        if (levels) {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                if (h == 1 && !has1) break;
+                                const uint32_t w0 = __ldg(reinterpret_cast<const uint32_t*>(base + (int64_t)(2 * (r + h)) * n + 2 * c));
+                                const uint32_t w1 = __ldg(reinterpret_cast<const uint32_t*>(base + (int64_t)(2 * (r + h) + 1) * n + 2 * c));
+                                iv[h] = (int32_t)(lo16(w0) + hi16(w0) + lo16(w1) + hi16(w1));
+                            }
+                        } else {
+                            iv[0] = (int32_t)__ldg(base + (int64_t)r * n + c);
+                            if (has1) iv[1] = (int32_t)__ldg(base + (int64_t)(r + 1) * n + c);
+                        }
+                        v[0] = (float)(iv[0] - ci_off);
+                        v[1] = has1 ? (float)(iv[1] - ci_off) : 0.f;
+                    } else {
+                        const float* base = static_cast<const float*>(src) + f * src_fstride;
+                        v[0] = __ldg(base + (int64_t)r * n + c) - cf_off;
+                        v[1] = has1 ? __ldg(base + (int64_t)(r + 1) * n + c) - cf_off : 0.f;
+                    }
+                    buf[pr * LD + sk<N>(c)] = make_float2(v[0], v[1]);
+                    Acc e[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (F32IN) e[h] = (Acc)((double)v[h] * (double)v[h]);
+                        else e[h] = (Acc)sq64((int32_t)v[h]);
+                    }
+                    tacc += e[0] + e[1];
+                    if (left || right) colreg[slot] += e[0] + e[1];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int rr = r + h;
+                        if (h == 1 && !has1) break;
+                        const bool top = rr < wm1, bot = rr >= mc - wm1;
+                        if (!(top || bot)) continue;
+                        if (warp_rows) {
+                            const Acc sum = warp_sum(e[h]);
+                            if ((tid & 31) == 0) atomicAdd(&rowacc[rl + h], sum);
+                        } else {
+                            atomicAdd(&rowacc[rl + h], e[h]);
+                        }
+                        if (left || right) {
+                            const int ri = top ? rr : rr - (mc - wm1);
+                            const int cj = right ? c - (nc - wm1) : c;
+                            const int q = (bot ? 2 : 0) + (right ? 1 : 0);
+                            const uint32_t bits = F32IN ? __float_as_uint(v[h]) : (uint32_t)(int32_t)v[h];
+                            corners[(f * 4 + q) * wm1sq + (size_t)ri * wm1 + cj] = bits;
+                        }
+                    }
+                }
+            }
+        } else {
         __syncthreads();
         if (active) {
             for (int rl = rl0; rl < rows; rl += RPI) {
@@ -179,22 +264,23 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
                             pl[k] = __float2bfloat16_rn(val[k] - __bfloat162float(hi));
                         }
                 } else {
-                    float* dst = reinterpret_cast<float*>(buf + (rl >> 1) * N) + (rl & 1);
+                    float* dst = reinterpret_cast<float*>(buf + (rl >> 1) * LD) + (rl & 1);
 #pragma unroll
                     for (int k = 0; k < 8; ++k)
                         if (k < CW) dst[2 * (g * CW + k)] = val[k];
                 }
             }
         }
+        }
         __syncthreads();
         if constexpr (!PLANES) {
-        fft4_fwd<N>(buf, N, nfft, tw, tid, nthr);
+        fft4_fwd<N>(buf, LD, nfft, tw, tid, nthr);
         // Two real rows were packed as one complex row: split the spectra.
         constexpr int NH = N / 2 + 1;
         for (int task = tid; task < NH * nfft; task += nthr) {
             const int v = task / nfft, fi = task - v * nfft;
-            const float2 zk = buf[fi * N + spec_pos<N>(v)];
-            const float2 zn = cconj(buf[fi * N + spec_pos<N>((N - v) % N)]);
+            const float2 zk = buf[fi * LD + sk<N>(spec_pos<N>(v))];
+            const float2 zn = cconj(buf[fi * LD + sk<N>(spec_pos<N>((N - v) % N))]);
             const float2 x1 = cscale(cadd(zk, zn), 0.5f);
             const float2 d = csub(zk, zn);
             const float2 x2 = make_float2(0.5f * d.y, -0.5f * d.x);
@@ -215,6 +301,22 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
         }
         __syncthreads();
     }
+    if constexpr (!PLANES) {
+#pragma unroll
+        for (int slot = 0; slot < 4; ++slot) {
+            if (slot >= CS) break;
+            int c;
+            if (nc <= nthr) {
+                c = tid % nc;
+                if (tid / nc >= PPI) break;
+            } else {
+                c = tid + slot * nthr;
+                if (c >= nc) break;
+            }
+            if (c < wm1 || c >= nc - wm1) atomicAdd(&colacc[c], colreg[slot]);
+        }
+    }
+    __syncthreads();
     tacc = warp_sum(tacc);
     if ((tid & 31) == 0) red[tid >> 5] = tacc;
     __syncthreads();
@@ -334,8 +436,9 @@ k_cols(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv
        const float2* __restrict__ tw_g, const float2* __restrict__ bspec, float2* __restrict__ Y,
        int64_t y_fstride, int wm1, float scale) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* buf = reinterpret_cast<float2*>(smem_raw);  // kColsVC x N
-    float2* tw = buf + kColsVC * N;
+    constexpr int LD = fft_ld<N>();                      // skewed, padded row
+    float2* buf = reinterpret_cast<float2*>(smem_raw);  // kColsVC x LD
+    float2* tw = buf + kColsVC * LD;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int v0 = blockIdx.y * kColsVC, nv = min(kColsVC, ncv - v0);
     const int64_t f = blockIdx.x;
@@ -343,29 +446,29 @@ k_cols(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv
     const float2* xs = X + f * x_fstride + (int64_t)v0 * ldx;
     for (int task = tid; task < nv * N; task += nthr) {
         const int vi = task / N, i = task - vi * N;
-        buf[vi * N + i] = (i < mc) ? xs[(int64_t)vi * ldx + i] : make_float2(0.f, 0.f);
+        buf[vi * LD + sk<N>(i)] = (i < mc) ? xs[(int64_t)vi * ldx + i] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    fft4_fwd<N>(buf, N, nv, tw, tid, nthr);
+    fft4_fwd<N>(buf, LD, nv, tw, tid, nthr);
     if (SPECTRUM) {
         for (int task = tid; task < nv * N; task += nthr) {
             const int vi = task / N, p = task - vi * N;
-            Y[(int64_t)(v0 + vi) * N + p] = cscale(cconj(buf[vi * N + p]), scale);
+            Y[(int64_t)(v0 + vi) * N + p] = cscale(cconj(buf[vi * LD + sk<N>(p)]), scale);
         }
         return;
     }
     for (int task = tid; task < nv * N; task += nthr) {
         const int vi = task / N, p = task - vi * N;
-        buf[vi * N + p] = cmul(buf[vi * N + p], bspec[(int64_t)(v0 + vi) * N + p]);
+        buf[vi * LD + sk<N>(p)] = cmul(buf[vi * LD + sk<N>(p)], bspec[(int64_t)(v0 + vi) * N + p]);
     }
     __syncthreads();
-    fft4_inv<N>(buf, N, nv, tw, tid, nthr);
+    fft4_inv<N>(buf, LD, nv, tw, tid, nthr);
     const int W = 2 * wm1 + 1;
     float2* ys = Y + f * y_fstride + v0;
     for (int task = tid; task < W * nv; task += nthr) {
         const int si = task / nv, vi = task - si * nv;
         const int pos = (si - wm1 + N) % N;
-        ys[(int64_t)si * ncv + vi] = buf[vi * N + pos];
+        ys[(int64_t)si * ncv + vi] = buf[vi * LD + sk<N>(pos)];
     }
 }
 
@@ -408,8 +511,9 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
            const double* __restrict__ inv_area, double unit, double* __restrict__ cost,
            int32_t* __restrict__ coarse, double* __restrict__ fbest, float* __restrict__ margin) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* buf = reinterpret_cast<float2*>(smem_raw);  // kInvPC x N
-    float2* tw = buf + kInvPC * N;
+    constexpr int LD = fft_ld<N>();                      // skewed, padded row
+    float2* buf = reinterpret_cast<float2*>(smem_raw);  // kInvPC x LD
+    float2* tw = buf + kInvPC * LD;
     const int W = 2 * wm1 + 1, WW = W * W;
     float* hbuf = reinterpret_cast<float*>(tw + N);     // W x W
     __shared__ Best red[32];
@@ -430,14 +534,14 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
             float2 B = (rb < W) ? ys[(int64_t)rb * ncv + kk] : make_float2(0.f, 0.f);
             if (k == 0 || k == NH) { A.y = 0.f; B.y = 0.f; }
             if (k > NH) { A.y = -A.y; B.y = -B.y; }
-            buf[pi * N + spec_pos<N>(k)] = make_float2(A.x - B.y, A.y + B.x);
+            buf[pi * LD + sk<N>(spec_pos<N>(k))] = make_float2(A.x - B.y, A.y + B.x);
         }
         __syncthreads();
-        fft4_inv<N>(buf, N, np, tw, tid, nthr);
+        fft4_inv<N>(buf, LD, np, tw, tid, nthr);
         for (int task = tid; task < np * W; task += nthr) {
             const int pi = task / W, ti = task - pi * W;
             const int pos = (ti - wm1 + N) % N;
-            const float2 z = buf[pi * N + pos];
+            const float2 z = buf[pi * LD + sk<N>(pos)];
             const int ra = 2 * (p0 + pi);
             hbuf[ra * W + ti] = z.x;
             if (ra + 1 < W) hbuf[(ra + 1) * W + ti] = z.y;

@@ -14,7 +14,7 @@ cudaError_t launch_frame_planes(bool f32, const void* src, int64_t src_fstride, 
                                 int ldp, cudaStream_t st) {
     if (nimg <= 0) return cudaSuccess;
     constexpr int N = 48;  // the FFT buffer is unused in this mode
-    const size_t smem = sizeof(float2) * ((kRC / 2) * N + N) + sizeof(u64) * (kRC + nc);
+    const size_t smem = sizeof(float2) * ((kRC / 2) * fft_ld<N>() + N) + sizeof(u64) * (kRC + nc);
     const void* fn = f32 ? (const void*)k_frame_rows<N, true, true> : (const void*)k_frame_rows<N, false, true>;
     cudaError_t e = ensure_smem(fn, smem);
     if (e != cudaSuccess) return e;

@@ -10,7 +10,7 @@ static cudaError_t frame_rows_n(const void* src, int64_t src_fstride, int64_t ni
                                 int mc, int nc, const int32_t* coff_i, const float* coff_f, const float2* tw,
                                 float2* X, int64_t x_fstride, int ldx, u64* rowE, u64* colE, u64* tot,
                                 uint32_t* corners, int wm1, cudaStream_t st) {
-    const size_t smem = sizeof(float2) * ((kRC / 2) * N + N) + sizeof(u64) * (kRC + nc);
+    const size_t smem = sizeof(float2) * ((kRC / 2) * fft_ld<N>() + N) + sizeof(u64) * (kRC + nc);
     const void* fn = (const void*)k_frame_rows<N, F32>;
     cudaError_t e = ensure_smem(fn, smem);
     if (e != cudaSuccess) return e;
@@ -46,7 +46,7 @@ static cudaError_t rows_inv_n(const float2* Y, int64_t y_fstride, int ncv, int w
                               double unit, double* cost, int32_t* coarse, double* fbest, float* margin,
                               cudaStream_t st) {
     const int W = 2 * wm1 + 1;
-    const size_t smem = sizeof(float2) * (kInvPC * N + N) + sizeof(float) * W * W;
+    const size_t smem = sizeof(float2) * (kInvPC * fft_ld<N>() + N) + sizeof(float) * W * W;
     const void* fn = (const void*)k_rows_inv<N>;
     cudaError_t e = ensure_smem(fn, smem);
     if (e != cudaSuccess) return e;
