@@ -209,11 +209,17 @@ __device__ __forceinline__ int spec_pos(int k) {
     return N2 * (k % N1) + k / N1;
 }
 
+// Twiddle tables (in shared memory), both holding omega_N^(n2*k1) =
+// exp(-2 pi i n2 k1 / N) for n2 < N2, k1 < N1, in the order the lanes of a
+// warp read them so that the reads are conflict-free:
+//   forward: twf[k1*N2 + n2] (lanes run over n2),
+//   inverse: twi[n2*N1 + k1] (lanes run over k1).
+// The global copy is [twf | twi], 2N entries.
+
 // Forward transform of `rows` rows at buf + r*ld (natural-order input).
-// tw[j] = omega_N^j = exp(-2 pi i j / N), j < N, in shared memory.
 // Every thread of the block must call this (it synchronises).
 template <int N>
-__device__ void fft4_fwd(float2* buf, int ld, int rows, const float2* tw, int tid, int nthr) {
+__device__ void fft4_fwd(float2* buf, int ld, int rows, const float2* twf, int tid, int nthr) {
     constexpr int N1 = Four<N>::N1, N2 = Four<N>::N2, B = N2 + Skew<N>::S;  // B: skewed block stride
     for (int task = tid; task < rows * N2; task += nthr) {
         int r = task / N2, n2 = task - r * N2;
@@ -223,7 +229,7 @@ __device__ void fft4_fwd(float2* buf, int ld, int rows, const float2* tw, int ti
         for (int n1 = 0; n1 < N1; ++n1) x[n1] = p[B * n1];
         Dft<N1, false>::run(x);
 #pragma unroll
-        for (int k1 = 1; k1 < N1; ++k1) x[k1] = cmul(x[k1], tw[n2 * k1]);
+        for (int k1 = 1; k1 < N1; ++k1) x[k1] = cmul(x[k1], twf[k1 * N2 + n2]);
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) p[B * k1] = x[k1];
     }
@@ -244,7 +250,7 @@ __device__ void fft4_fwd(float2* buf, int ld, int rows, const float2* tw, int ti
 // Inverse (unnormalised, omega^+) transform: input in the forward output
 // layout, output in natural order.
 template <int N>
-__device__ void fft4_inv(float2* buf, int ld, int rows, const float2* tw, int tid, int nthr) {
+__device__ void fft4_inv(float2* buf, int ld, int rows, const float2* twi, int tid, int nthr) {
     constexpr int N1 = Four<N>::N1, N2 = Four<N>::N2, B = N2 + Skew<N>::S;  // B: skewed block stride
     for (int task = tid; task < rows * N1; task += nthr) {
         int r = task / N1, k1 = task - r * N1;
@@ -254,7 +260,7 @@ __device__ void fft4_inv(float2* buf, int ld, int rows, const float2* tw, int ti
         for (int k2 = 0; k2 < N2; ++k2) x[k2] = p[k2];
         Dft<N2, true>::run(x);
 #pragma unroll
-        for (int n2 = 1; n2 < N2; ++n2) x[n2] = cmulc(x[n2], tw[n2 * k1]);
+        for (int n2 = 1; n2 < N2; ++n2) x[n2] = cmulc(x[n2], twi[n2 * N1 + k1]);
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) p[n2] = x[n2];
     }

@@ -11,6 +11,7 @@ typedef unsigned long long u64;
 // codelet sizes); fft_size_for returns the smallest one >= needed, or 0.
 int fft_size_for(int needed);
 bool fft_size_supported(int N);
+bool fft_split(int N, int* n1, int* n2);  // the four-step factors N = N1 * N2
 int fft_split_max(int N);  // max(N1, N2): threads per row of a four-step stage
 
 cudaError_t launch_frame_rows(int N, bool f32, const void* src, int64_t src_fstride, int64_t nimg, int m,

@@ -82,7 +82,7 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int LD = fft_ld<N>();                      // skewed, padded row
     float2* buf = reinterpret_cast<float2*>(smem_raw);  // (kRC/2) x LD
-    float2* tw = buf + (kRC / 2) * LD;                   // N
+    float2* tw = buf + (kRC / 2) * LD;                   // N: forward table
     Acc* rowacc = reinterpret_cast<Acc*>(tw + N);        // kRC
     Acc* colacc = rowacc + kRC;                          // nc
     __shared__ Acc red[32];
@@ -438,11 +438,11 @@ k_cols(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int LD = fft_ld<N>();                      // skewed, padded row
     float2* buf = reinterpret_cast<float2*>(smem_raw);  // kColsVC x LD
-    float2* tw = buf + kColsVC * LD;
+    float2* tw = buf + kColsVC * LD;                     // 2N: forward, then inverse table
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int v0 = blockIdx.y * kColsVC, nv = min(kColsVC, ncv - v0);
     const int64_t f = blockIdx.x;
-    for (int i = tid; i < N; i += nthr) tw[i] = tw_g[i];
+    for (int i = tid; i < 2 * N; i += nthr) tw[i] = tw_g[i];
     const float2* xs = X + f * x_fstride + (int64_t)v0 * ldx;
     for (int task = tid; task < nv * N; task += nthr) {
         const int vi = task / N, i = task - vi * N;
@@ -462,7 +462,7 @@ k_cols(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv
         buf[vi * LD + sk<N>(p)] = cmul(buf[vi * LD + sk<N>(p)], bspec[(int64_t)(v0 + vi) * N + p]);
     }
     __syncthreads();
-    fft4_inv<N>(buf, LD, nv, tw, tid, nthr);
+    fft4_inv<N>(buf, LD, nv, tw + N, tid, nthr);
     const int W = 2 * wm1 + 1;
     float2* ys = Y + f * y_fstride + v0;
     for (int task = tid; task < W * nv; task += nthr) {
@@ -513,13 +513,13 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int LD = fft_ld<N>();                      // skewed, padded row
     float2* buf = reinterpret_cast<float2*>(smem_raw);  // kInvPC x LD
-    float2* tw = buf + kInvPC * LD;
+    float2* tw = buf + kInvPC * LD;                      // N: inverse table
     const int W = 2 * wm1 + 1, WW = W * W;
     float* hbuf = reinterpret_cast<float*>(tw + N);     // W x W
     __shared__ Best red[32];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int64_t f = blockIdx.x;
-    for (int i = tid; i < N; i += nthr) tw[i] = tw_g[i];
+    for (int i = tid; i < N; i += nthr) tw[i] = tw_g[N + i];
     const float2* ys = Y + f * y_fstride;
     const int npairs = (W + 1) / 2;
     constexpr int NH = N / 2;

@@ -58,13 +58,20 @@ struct Carver {
     }
 };
 
+// The four-step twiddles omega_N^(n2*k1) = exp(-2 pi i n2 k1 / N), each in
+// FP64 and rounded once to FP32, in two orders: [k1*N2 + n2] for the forward
+// transform, then [n2*N1 + k1] for the inverse (2N entries).
 void host_roots(int N, std::vector<float2>& out) {
-    out.resize(N);
-    for (int j = 0; j < N; ++j) {
-        // exp(-2 pi i j / N) in FP64, rounded once to FP32.
-        const double a = 2.0 * M_PI * (double)j / (double)N;
-        out[j] = make_float2((float)std::cos(a), (float)-std::sin(a));
-    }
+    int N1 = 0, N2 = 0;
+    fft_split(N, &N1, &N2);
+    out.resize(2 * (size_t)N);
+    for (int k1 = 0; k1 < N1; ++k1)
+        for (int n2 = 0; n2 < N2; ++n2) {
+            const double a = 2.0 * M_PI * (double)(n2 * k1) / (double)N;
+            const float2 z = make_float2((float)std::cos(a), (float)-std::sin(a));
+            out[(size_t)k1 * N2 + n2] = z;
+            out[(size_t)N + (size_t)n2 * N1 + k1] = z;
+        }
 }
 
 }  // namespace
@@ -145,8 +152,8 @@ moco_status allocate_shape(ShapePlan& sp) {
     c.add(&sp.tmpl, (size_t)m * n * (sp.f32 ? 4 : 2));
     c.add(&sp.coff_i, 4);
     c.add(&sp.coff_f, 4);
-    c.add(&sp.twr, (size_t)sp.Nr * 8);
-    c.add(&sp.twc, (size_t)sp.Nc * 8);
+    c.add(&sp.twr, (size_t)sp.Nr * 16);
+    c.add(&sp.twc, (size_t)sp.Nc * 16);
     c.add(&sp.bspec, sp.has_fft ? (size_t)sp.ncv * sp.Nr * 8 : 0);
     c.add(&sp.dev_err, 4);
     if (sp.has_direct) {

@@ -57,8 +57,8 @@ struct ShapePlan {
     void* tmpl = nullptr;
     int32_t* coff_i = nullptr;
     float* coff_f = nullptr;
-    float2* twr = nullptr;
-    float2* twc = nullptr;
+    float2* twr = nullptr;  // 2*Nr four-step twiddles: forward order, then inverse order
+    float2* twc = nullptr;  // 2*Nc, same layout
     float2* bspec = nullptr;
     double* Sb = nullptr;
     double* inv_area = nullptr;

@@ -10,7 +10,7 @@ template <int N>
 static cudaError_t cols_n(bool spectrum, const float2* X, int64_t x_fstride, int ldx, int mc, int ncv,
                           int64_t nimg, const float2* tw, const float2* bspec, float2* Y, int64_t y_fstride,
                           int wm1, float scale, cudaStream_t st) {
-    const size_t smem = sizeof(float2) * (kColsVC * fft_ld<N>() + N);
+    const size_t smem = sizeof(float2) * (kColsVC * fft_ld<N>() + 2 * N);
     const void* fn = spectrum ? (const void*)k_cols<N, true> : (const void*)k_cols<N, false>;
     cudaError_t e = ensure_smem(fn, smem);
     if (e != cudaSuccess) return e;

@@ -24,6 +24,14 @@ int fft_size_for(int needed) {
     return best;
 }
 
+bool fft_split(int N, int* n1, int* n2) {
+#define MOCO_CASE(NN) \
+    if (N == NN) { *n1 = Four<NN>::N1; *n2 = Four<NN>::N2; return true; }
+    MOCO_FOR_EACH_FFT_SIZE(MOCO_CASE)
+#undef MOCO_CASE
+    return false;
+}
+
 int fft_split_max(int N) {
 #define MOCO_CASE(NN) if (N == NN) return Four<NN>::N1 > Four<NN>::N2 ? Four<NN>::N1 : Four<NN>::N2;
     MOCO_FOR_EACH_FFT_SIZE(MOCO_CASE)
