@@ -98,6 +98,9 @@ typedef struct {
     int32_t* shifts_dev;    /* out [T][2]: final (s, t) per frame */
     double* best_cost_dev;  /* out, nullable [T]: f at the searched-grid optimum (box-mean units) */
     float* margin_dev;      /* out, nullable [T]: (f2 - f1) / f1 on the searched grid; f2 = next smallest f */
+    double* final_cost_dev; /* out, nullable [T]: f at the final shift. With a level: S / Area(D) at full
+                               resolution from the exact integer sum S, in FP64 (the upsampling step of
+                               Section 2); without: equal to best_cost */
 } moco_stack;
 
 /* Creates a plan for `nshapes` shapes (Section 2's problem statement: the

@@ -54,7 +54,7 @@ class MocoStack(ctypes.Structure):
     _fields_ = [("shape_idx", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("frames_dev", ctypes.c_void_p), ("T", ctypes.c_int64),
                 ("shifts_dev", ctypes.c_void_p), ("best_cost_dev", ctypes.c_void_p),
-                ("margin_dev", ctypes.c_void_p)]
+                ("margin_dev", ctypes.c_void_p), ("final_cost_dev", ctypes.c_void_p)]
 
 
 class MocoKernelStat(ctypes.Structure):
@@ -167,7 +167,7 @@ def moco_set_template(plan, shape_idx, template, stream=None):
 
 
 def moco_align_stack(plan, stacks, stream=None):
-    """stacks: list of dicts {shape_idx, frames, shifts, best_cost=None, margin=None}."""
+    """stacks: list of dicts {shape_idx, frames, shifts, best_cost=None, margin=None, final_cost=None}."""
     import torch
     arr = (MocoStack * len(stacks))()
     for k, s in enumerate(stacks):
@@ -175,14 +175,18 @@ def moco_align_stack(plan, stacks, stream=None):
         sh = _need(s["shifts"], torch.int32, "shifts")
         bc = s.get("best_cost")
         mg = s.get("margin")
+        fc = s.get("final_cost")
         if bc is not None:
             _need(bc, torch.float64, "best_cost")
         if mg is not None:
             _need(mg, torch.float32, "margin")
+        if fc is not None:
+            _need(fc, torch.float64, "final_cost")
         T = fr.shape[0] if fr.dim() == 3 else 1
         arr[k] = MocoStack(int(s.get("shape_idx", 0)), 0, fr.data_ptr(), T, sh.data_ptr(),
                            bc.data_ptr() if bc is not None else None,
-                           mg.data_ptr() if mg is not None else None)
+                           mg.data_ptr() if mg is not None else None,
+                           fc.data_ptr() if fc is not None else None)
     _check(lib().moco_align_stack(plan, arr, len(stacks), _stream(stream)))
 
 
@@ -293,15 +297,20 @@ class Plan:
     def W(self, shape_idx=0) -> int:
         return 2 * int(self.shapes[shape_idx]["w"]) - 1
 
-    def align(self, frames, shape_idx=0, best_cost=False, margin=False, stream=None):
+    def align(self, frames, shape_idx=0, best_cost=False, margin=False, final_cost=False, stream=None):
+        """shifts; or (shifts, best_cost, margin) when either is asked for;
+        with final_cost, (shifts, best_cost, margin, final_cost)."""
         import torch
         T = frames.shape[0]
         dev = frames.device
         shifts = torch.empty((T, 2), dtype=torch.int32, device=dev)
         bc = torch.empty(T, dtype=torch.float64, device=dev) if best_cost else None
         mg = torch.empty(T, dtype=torch.float32, device=dev) if margin else None
+        fc = torch.empty(T, dtype=torch.float64, device=dev) if final_cost else None
         moco_align_stack(self.handle, [dict(shape_idx=shape_idx, frames=frames, shifts=shifts,
-                                            best_cost=bc, margin=mg)], stream)
+                                            best_cost=bc, margin=mg, final_cost=fc)], stream)
+        if final_cost:
+            return shifts, bc, mg, fc
         if best_cost or margin:
             return shifts, bc, mg
         return shifts

@@ -33,9 +33,14 @@ cudaError_t launch_energy(bool f32, bool out_double, const u64* rowE, const u64*
                           cudaStream_t st);
 
 // acc: nimg x 9 u64 and ticket: nimg u32 of scratch (cleared here).
+// bsq: the template's b^2 prefix table (launch_sq_prefix), or nullptr to sum
+// b^2 inside the kernel.
 cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg, const uint16_t* tmpl, int m,
-                          int n, const int32_t* coarse, int32_t* shifts, double* ffinal, u64* acc,
+                          int n, const u64* bsq, const int32_t* coarse, int32_t* shifts, double* ffinal, u64* acc,
                           unsigned int* ticket, cudaStream_t st);
+
+// P[(m+1) x (n+1)], P[i][j] = sum over i' < i, j' < j of tmpl^2 (exact u64).
+cudaError_t launch_sq_prefix(const uint16_t* tmpl, int m, int n, u64* P, cudaStream_t st);
 
 cudaError_t launch_copy_shifts(const int32_t* coarse, int32_t* shifts, const double* fbest, double* ffinal,
                                int64_t T, cudaStream_t st);

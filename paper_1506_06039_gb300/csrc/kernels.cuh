@@ -589,116 +589,256 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 
 // ---------------------------------------------------------------------------
 // k_jitter: the upsampling step of Section 2. For the nine candidates
-// (2 sc + u, 2 tc + v), u, v in {-1, 0, 1}, the exact int64
+// (s, t) = (2 sc + u - 1, 2 tc + v - 1), u, v in {0, 1, 2}, the exact
 //     S = sum over D of (a[i+s][j+t] - b[i][j])^2
+//       = sum_D a^2 + sum_D b^2 - 2 sum_D a b
 // at full resolution, all nine accumulated in one pass over the frame.
-// Grid (CTAs per frame, frames). Each thread owns 8 template columns of a
-// band of kJitRows rows and walks down it keeping the three frame rows it
-// needs (i+s0-1 .. i+s0+1, 10 columns each) in registers, so
-// every frame row is loaded once per thread.
-// Since 2 tc is even, the 10-column window starts at an odd column: six
-// 32-bit loads from the even column before it and five byte permutes give
-// the 10 values. The next row is prefetched one template row ahead. Columns
-// outside the frame are masked per thread (a fixed bit mask), rows outside
-// by a flag.
-// Per-CTA partial sums go to acc[f][9] by 64-bit atomics; the last CTA of a
-// frame (ticket counter) takes the minimum of S / Area with the tie-break,
-// compared as exact rationals. acc and ticket are zero on entry.
+//
+// Products are exact 32-bit integer dot products (dp2a: two 16-bit values
+// times two bytes, plus a 32-bit sum). With y = 256 y_hi + y_lo split into
+// bytes, x y = 256 x y_hi + x y_lo and the two halves are summed apart. Each
+// 16 x 8-bit product is below 2^24, so a band of at most 32 rows of 8
+// columns sums below 2^32 exactly; the halves meet in 64 bits once per band.
+//
+// Frame values outside the frame are read as zero, so sum a b and sum a^2
+// need no mask. sum_D b^2 depends on the template and (s, t) only: with a
+// 2-D prefix table of b^2 (TABLE) the frame's last CTA reads it at four
+// corners per shift; without one it is summed in the loop, a template
+// position counting only when its partner lies inside the frame.
+//
+// Grid (CTAs per frame, frames). Each thread owns the template columns
+// j0 .. j0+7 of a band of kJitRows rows and walks down it keeping the three
+// frame rows r = i + 2 sc - 1 + u (u = 0, 1, 2) as 16-bit pairs, columns
+// counted from lead = j0 + 2 tc - 1 (odd):
+//   pw[p] = columns (lead + 2p, lead + 2p + 1), p < 5   (v = 0: pw[0..3],
+//                                                        v = 2: pw[1..4])
+//   rw[p] = columns (lead + 2p + 1, lead + 2p + 2), p < 4 (v = 1)
+// rw are the aligned 32-bit words themselves; pw take one byte permute each.
+// An aligned word (even column c, c + 1; n even) lies wholly inside or
+// wholly outside the frame, so every thread runs the same code: a word
+// outside is a predicated-off load that leaves zero. A row outside the frame
+// is the same for the whole warp (one band, one frame).
+// The next frame and template rows are prefetched one row ahead, and the
+// loop is unrolled three times so that the window rotates without copies.
+//
+// sum a^2: the frame rows that all three u share accumulate once per row;
+// the two rows at each end of the band's frame range are added at the end.
+// In-loop sum b^2: template rows whose partner rows are valid for all three
+// u accumulate once; the at most four rows valid for only some u are added
+// at the end.
+// Per-CTA partial sums go to acc[f][9] by 64-bit atomics (two's complement
+// wrap-around: the total is exact); the last CTA of a frame (ticket counter)
+// adds sum_D b^2 (TABLE) and takes the minimum of S / Area with the
+// tie-break, compared as exact rationals. acc and ticket are zero on entry.
 constexpr int kJitRows = 32;
+static_assert(kJitRows <= 32, "32-bit dot-product sums are exact for at most 32 rows of 8 columns");
 
 // Raw words of one frame row: 6 x 32 bits = half-words lead-1 .. lead+10,
-// loaded from lead - 1 (even, so 4-byte aligned). Border threads load
-// element by element with zeros outside the frame.
+// loaded from lead - 1 (even, so 4-byte aligned); zeros outside the frame.
 struct JitRaw {
     uint32_t w[6];
 };
 
-__device__ __forceinline__ void jit_fetch(const uint16_t* __restrict__ arow, int lead, int n, bool interior,
-                                          bool ok, JitRaw& r) {
-    if (!ok) return;
-    if (interior) {
-        const uint32_t* p = reinterpret_cast<const uint32_t*>(arow + lead - 1);
+// One frame row of the window as 16-bit pairs (see above).
+struct JitWin {
+    uint32_t pw[5];
+    uint32_t rw[4];
+};
+
+// 2 x 32-bit partial sums (low and high byte half) of one quantity.
+struct Acc2 {
+    uint32_t lo, hi;
+};
+
+struct JitBand {
+    const uint16_t* a;     // frame
+    const uint16_t* tmpl;  // template
+    int m, n, s0, lead, j0, i_b, i_e;
+    uint32_t wvalid;       // bit k: raw word k (columns lead-1+2k, +1) inside the frame
+};
+
+// Row ar of the frame (zeros where outside).
+__device__ __forceinline__ void jit_fetch(const JitBand& B, int ar, JitRaw& r) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) r.w[k] = __ldg(p + k);
-    } else {
+    for (int k = 0; k < 6; ++k) r.w[k] = 0u;
+    if (ar < 0 || ar >= B.m) return;
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(B.a + (int64_t)ar * B.n + (B.lead - 1));
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const int c = lead - 1 + 2 * k;
-            const uint32_t lo = (c >= 0 && c < n) ? (uint32_t)__ldg(arow + c) : 0u;
-            const uint32_t hi = (c + 1 >= 0 && c + 1 < n) ? (uint32_t)__ldg(arow + c + 1) : 0u;
-            r.w[k] = lo | (hi << 16);
-        }
-    }
+    for (int k = 0; k < 6; ++k)
+        if ((B.wvalid >> k) & 1u) r.w[k] = __ldg(p + k);
 }
 
-// The 10 values at columns lead .. lead + 9: drop the first half-word.
-__device__ __forceinline__ void jit_unpack(const JitRaw& r, int32_t (&v)[10]) {
+__device__ __forceinline__ void jit_unpack(const JitRaw& r, JitWin& x) {
 #pragma unroll
-    for (int p = 0; p < 5; ++p) {
-        const uint32_t pr = __byte_perm(r.w[p], r.w[p + 1], 0x5432);
-        v[2 * p] = (int32_t)(pr & 0xffffu);
-        v[2 * p + 1] = (int32_t)(pr >> 16);
-    }
+    for (int p = 0; p < 5; ++p) x.pw[p] = __byte_perm(r.w[p], r.w[p + 1], 0x5432);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) x.rw[p] = r.w[p + 1];
 }
 
-template <bool MASKED>
-__device__ __forceinline__ void jit_band(const uint16_t* __restrict__ a, const uint16_t* __restrict__ tmpl, int m,
-                                         int n, int s0, int lead, int j0, bool interior, uint32_t mask,
-                                         int i_begin, int i_end, long long (&acc)[9]) {
-    int32_t win[3][10];
-    bool ok[3];
+// Byte planes of a 16-bit pair (y0, y1): bytes (y0_lo, y1_lo, y0_hi, y1_hi).
+__device__ __forceinline__ uint32_t byte_planes(uint32_t y) { return __byte_perm(y, 0u, 0x3120); }
+
+// acc += x . y for a 16-bit pair x and the byte planes yp of a pair y
+// (dp2a: the two 16-bit halves of x times bytes 0, 1 (lo) or 2, 3 (hi) of
+// yp, added to the 32-bit accumulator in place).
+__device__ __forceinline__ void dot_acc(uint32_t x, uint32_t yp, Acc2& acc) {
+    asm("dp2a.lo.u32.u32 %0, %1, %2, %0;" : "+r"(acc.lo) : "r"(x), "r"(yp));
+    asm("dp2a.hi.u32.u32 %0, %1, %2, %0;" : "+r"(acc.hi) : "r"(x), "r"(yp));
+}
+
+__device__ __forceinline__ u64 acc_value(const Acc2& a) { return (u64)a.lo + ((u64)a.hi << 8); }
+
+// Sum of squares of one window row over the columns of each v:
+// v = 0: columns 0..7, v = 1: 1..8, v = 2: 2..9 (of lead ..).
+__device__ __forceinline__ void row_energy(const JitWin& x, Acc2 (&e)[3]) {
+    uint32_t pl[5];
+#pragma unroll
+    for (int p = 0; p < 5; ++p) pl[p] = byte_planes(x.pw[p]);
+    Acc2 core = {0u, 0u};  // columns 2..7
+#pragma unroll
+    for (int p = 1; p < 4; ++p) dot_acc(x.pw[p], pl[p], core);
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        e[v].lo += core.lo;
+        e[v].hi += core.hi;
+    }
+    dot_acc(x.pw[0], pl[0], e[0]);                // columns 0, 1
+    dot_acc(x.pw[4], pl[4], e[2]);                // columns 8, 9
+    dot_acc(x.pw[0], pl[0] & 0xff00ff00u, e[1]);  // column 1
+    dot_acc(x.pw[4], pl[4] & 0x00ff00ffu, e[1]);  // column 8
+}
+
+// Byte masks of template pair p for shift v: the template columns whose
+// frame partner (column lead + 2p + v, + 1) lies inside the frame.
+__device__ __forceinline__ uint32_t col_mask(uint32_t mask, int v, int p) {
+    return (((mask >> (v * 8 + 2 * p)) & 1u) ? 0x00ff00ffu : 0u) |
+           (((mask >> (v * 8 + 2 * p + 1)) & 1u) ? 0xff00ff00u : 0u);
+}
+
+// In-loop template energy of one row (pairs bw, planes bp) for each v.
+__device__ __forceinline__ void tmpl_energy(const uint32_t (&bw)[4], const uint32_t (&bp)[4],
+                                            const uint32_t (&cm)[12], Acc2 (&e)[3]) {
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) dot_acc(bw[p], bp[p] & cm[v * 4 + p], e[v]);
+}
+
+// One template row i: w0, w1 hold frame rows i+s0-1, i+s0; w2 receives row
+// i+s0+1 from raw, and raw / braw are refilled for row i+1.
+template <bool TABLE>
+__device__ __forceinline__ void jit_step(const JitBand& B, int i, const JitWin& w0, const JitWin& w1, JitWin& w2,
+                                         JitRaw& raw, uint4& braw, Acc2 (&C)[9], Acc2 (&M)[3], Acc2 (&QB)[3],
+                                         const uint32_t (&cm)[12]) {
+    jit_unpack(raw, w2);
+    const uint32_t bw[4] = {braw.x, braw.y, braw.z, braw.w};
+    uint32_t bp[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) bp[p] = byte_planes(bw[p]);
+    if (i + 1 < B.i_e) {
+        jit_fetch(B, i + B.s0 + 2, raw);
+        braw = __ldg(reinterpret_cast<const uint4*>(B.tmpl + (int64_t)(i + 1) * B.n + B.j0));
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        dot_acc(w0.pw[p], bp[p], C[0]);
+        dot_acc(w0.rw[p], bp[p], C[1]);
+        dot_acc(w0.pw[p + 1], bp[p], C[2]);
+        dot_acc(w1.pw[p], bp[p], C[3]);
+        dot_acc(w1.rw[p], bp[p], C[4]);
+        dot_acc(w1.pw[p + 1], bp[p], C[5]);
+        dot_acc(w2.pw[p], bp[p], C[6]);
+        dot_acc(w2.rw[p], bp[p], C[7]);
+        dot_acc(w2.pw[p + 1], bp[p], C[8]);
+    }
+    if (i <= B.i_e - 3) row_energy(w2, M);  // frame row shared by all three u
+    if (!TABLE)
+        if (i + B.s0 - 1 >= 0 && i + B.s0 + 1 <= B.m - 1) tmpl_energy(bw, bp, cm, QB);
+}
+
+// The nine partial sums of one thread's band, X[u*3+v] (mod 2^64).
+template <bool TABLE>
+__device__ __forceinline__ void jit_band(const JitBand& B, uint32_t mask, u64 (&X)[9]) {
+    Acc2 C[9], M[3], QB[3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) C[k] = Acc2{0u, 0u};
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        M[v] = Acc2{0u, 0u};
+        QB[v] = Acc2{0u, 0u};
+    }
+    uint32_t cm[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) cm[k] = TABLE ? 0u : col_mask(mask, k / 4, k % 4);
+    const int first = B.i_b + B.s0 - 1, L = B.i_e - B.i_b;
+    JitWin wa, wb, wc;
     JitRaw raw;
-    // window rows i_begin + s0 - 1, i_begin + s0
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const int ar = i_begin + s0 - 1 + u;
-        ok[u] = ar >= 0 && ar < m;
-        jit_fetch(a + (int64_t)ar * n, lead, n, interior, ok[u], raw);
-        if (ok[u]) jit_unpack(raw, win[u]);
+    jit_fetch(B, first, raw);
+    jit_unpack(raw, wa);
+    jit_fetch(B, first + 1, raw);
+    jit_unpack(raw, wb);
+    jit_fetch(B, first + 2, raw);
+    uint4 braw = __ldg(reinterpret_cast<const uint4*>(B.tmpl + (int64_t)B.i_b * B.n + B.j0));
+    for (int i = B.i_b;;) {
+        jit_step<TABLE>(B, i, wa, wb, wc, raw, braw, C, M, QB, cm);
+        if (++i >= B.i_e) break;
+        jit_step<TABLE>(B, i, wb, wc, wa, raw, braw, C, M, QB, cm);
+        if (++i >= B.i_e) break;
+        jit_step<TABLE>(B, i, wc, wa, wb, raw, braw, C, M, QB, cm);
+        if (++i >= B.i_e) break;
     }
-    // prefetch the first new row and template row
-    int ar = i_begin + s0 + 1;
-    bool okn = ar >= 0 && ar < m;
-    jit_fetch(a + (int64_t)ar * n, lead, n, interior, okn, raw);
-    uint4 braw = __ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)i_begin * n + j0));
-    for (int i = i_begin; i < i_end; ++i) {
-        ok[2] = okn;
-        if (okn) jit_unpack(raw, win[2]);
-        int32_t bv[8];
-        {
-            const uint32_t w[4] = {braw.x, braw.y, braw.z, braw.w};
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                bv[2 * k] = (int32_t)lo16(w[k]);
-                bv[2 * k + 1] = (int32_t)hi16(w[k]);
-            }
-        }
-        if (i + 1 < i_end) {  // prefetch for the next template row
-            ar = i + s0 + 2;
-            okn = ar >= 0 && ar < m;
-            jit_fetch(a + (int64_t)ar * n, lead, n, interior, okn, raw);
-            braw = __ldg(reinterpret_cast<const uint4*>(tmpl + (int64_t)(i + 1) * n + j0));
-        }
+    for (int u = 0; u < 3; ++u)
+#pragma unroll
+        for (int v = 0; v < 3; ++v)
+            X[u * 3 + v] = acc_value(M[v]) + acc_value(QB[v]) - 2ull * acc_value(C[u * 3 + v]);
+
+    // Frame rows at the ends of the band's range first .. first + L + 1:
+    // row r belongs to u when first + u <= r <= first + u + L - 1.
+    for (int k = 0; k < 4; ++k) {
+        const int r = (k < 2) ? first + k : first + L + k - 2;
+        if (k == 2 && L < 2) continue;  // L = 1: first + L is row first + 1
+        JitRaw rr;
+        jit_fetch(B, r, rr);
+        JitWin x;
+        jit_unpack(rr, x);
+        Acc2 e[3] = {{0u, 0u}, {0u, 0u}, {0u, 0u}};
+        row_energy(x, e);
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+            if (r >= first + u && r <= first + u + L - 1)
+#pragma unroll
+                for (int v = 0; v < 3; ++v) X[u * 3 + v] += acc_value(e[v]);
+    }
+    if (TABLE) return;
+    // In-loop sum b^2: template rows whose partner row is valid for some but
+    // not all u, i + s0 in {-1, 0, m - 1, m}.
+    for (int k = 0; k < 4; ++k) {
+        const int i = (k < 2 ? -1 + k : B.m - 3 + k) - B.s0;
+        if (i < B.i_b || i >= B.i_e || i < 0 || i >= B.m) continue;
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(B.tmpl + (int64_t)i * B.n + B.j0));
+        const uint32_t bw[4] = {q.x, q.y, q.z, q.w};
+        uint32_t bp[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) bp[p] = byte_planes(bw[p]);
+        Acc2 e[3] = {{0u, 0u}, {0u, 0u}, {0u, 0u}};
+        tmpl_energy(bw, bp, cm, e);
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
-            if (!ok[u]) continue;
+            const int r = i + B.s0 - 1 + u;
+            if (r >= 0 && r < B.m)
 #pragma unroll
-            for (int v = 0; v < 3; ++v)
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    int d = win[u][k + v] - bv[k];
-                    if (MASKED) d = ((mask >> (v * 8 + k)) & 1u) ? d : 0;
-                    acc[u * 3 + v] += (long long)d * d;
-                }
+                for (int v = 0; v < 3; ++v) X[u * 3 + v] += acc_value(e[v]);
         }
-#pragma unroll
-        for (int k = 0; k < 10; ++k) {
-            win[0][k] = win[1][k];
-            win[1][k] = win[2][k];
-        }
-        ok[0] = ok[1];
-        ok[1] = ok[2];
     }
+}
+
+// sum of b^2 over the template rows [i0, i1) x columns [j0, j1) from the
+// prefix table P[i][j] = sum_{i' < i, j' < j} b^2, (m+1) x (n+1).
+__device__ __forceinline__ u64 rect_sum(const u64* __restrict__ P, int n, int i0, int i1, int j0, int j1) {
+    if (i1 <= i0 || j1 <= j0) return 0ull;
+    const int64_t ld = n + 1;
+    return P[i1 * ld + j1] - P[i0 * ld + j1] - P[i1 * ld + j0] + P[i0 * ld + j0];
 }
 
 // Returns 1 when S1/A1 < S2/A2 exactly (A > 0); *eq when equal.
@@ -709,46 +849,56 @@ __device__ __forceinline__ int ratio_lt(u64 S1, u64 A1, u64 S2, u64 A2, int* eq)
     return (l_hi < r_hi) || (l_hi == r_hi && l_lo < r_lo);
 }
 
-static __global__ void __launch_bounds__(kJitterThreads, 2)
+// bsq: the prefix table of b^2 (TABLE) or nullptr (sum b^2 in the loop).
+template <bool TABLE>
+__global__ void __launch_bounds__(kJitterThreads, 2)
 k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* __restrict__ tmpl, int m, int n,
-         const int32_t* __restrict__ coarse, int32_t* __restrict__ shifts, double* __restrict__ ffinal,
-         u64* __restrict__ acc_g, unsigned int* __restrict__ ticket) {
+         const u64* __restrict__ bsq, const int32_t* __restrict__ coarse, int32_t* __restrict__ shifts,
+         double* __restrict__ ffinal, u64* __restrict__ acc_g, unsigned int* __restrict__ ticket) {
     __shared__ u64 red[kJitterThreads / 32][9];
     __shared__ bool last;
     const int tid = threadIdx.x;
     const int64_t f = blockIdx.y;
     const int s0 = 2 * coarse[2 * f], t0 = 2 * coarse[2 * f + 1];
-    const uint16_t* a = frames + f * fstride;
-    long long acc[9];
+    u64 X[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) acc[k] = 0;
+    for (int k = 0; k < 9; ++k) X[k] = 0;
     const int G = n / 8;
     const int nb = (m + kJitRows - 1) / kJitRows;
     const int task = blockIdx.x * kJitterThreads + tid;
     if (task < G * nb) {
         const int g = task % G, band = task / G;
-        const int j0 = 8 * g;
-        // Frame columns lead .. lead + 9 (lead = j0 + t0 - 1 is odd, so
-        // lead - 1 is 4-byte aligned).
-        const int lead = j0 + t0 - 1;
-        const bool interior = (lead - 1 >= 0) && (lead + 11 <= n);
-        uint32_t mask = 0;
+        JitBand B;
+        B.a = frames + f * fstride;
+        B.tmpl = tmpl;
+        B.m = m;
+        B.n = n;
+        B.s0 = s0;
+        B.j0 = 8 * g;
+        B.lead = B.j0 + t0 - 1;  // odd: lead - 1 is 4-byte aligned
+        B.i_b = band * kJitRows;
+        B.i_e = min(m, B.i_b + kJitRows);
+        B.wvalid = 0;
 #pragma unroll
-        for (int v = 0; v < 3; ++v)
+        for (int k = 0; k < 6; ++k) {
+            const int c = B.lead - 1 + 2 * k;
+            if (c >= 0 && c <= n - 2) B.wvalid |= 1u << k;
+        }
+        uint32_t mask = 0;  // bit v*8+k: frame column lead+k+v inside the frame
+        if (!TABLE) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int c = lead + k + v;
-                if (c >= 0 && c < n) mask |= 1u << (v * 8 + k);
-            }
-        const int i_begin = band * kJitRows, i_end = min(m, i_begin + kJitRows);
-        if (interior && mask == 0xffffffu)
-            jit_band<false>(a, tmpl, m, n, s0, lead, j0, true, mask, i_begin, i_end, acc);
-        else
-            jit_band<true>(a, tmpl, m, n, s0, lead, j0, interior, mask, i_begin, i_end, acc);
+            for (int v = 0; v < 3; ++v)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int c = B.lead + k + v;
+                    if (c >= 0 && c < n) mask |= 1u << (v * 8 + k);
+                }
+        }
+        jit_band<TABLE>(B, mask, X);
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        u64 v = (u64)acc[k];
+        u64 v = X[k];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         if ((tid & 31) == 0) red[tid >> 5][k] = v;
@@ -772,7 +922,8 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
         for (int v = 0; v < 3; ++v) {
             const int s = s0 + u - 1, t = t0 + v - 1;
             const u64 A = (u64)(m - abs(s)) * (u64)(n - abs(t));
-            const u64 Sk = atomicAdd(&acc_g[f * 9 + u * 3 + v], 0ull);
+            u64 Sk = atomicAdd(&acc_g[f * 9 + u * 3 + v], 0ull);
+            if (TABLE) Sk += rect_sum(bsq, n, max(0, -s), m - max(0, s), max(0, -t), n - max(0, t));
             bool take = (bk < 0);
             if (!take) {
                 int eq;
@@ -788,6 +939,32 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     shifts[2 * f] = bs;
     shifts[2 * f + 1] = bt;
     if (ffinal) ffinal[f] = (double)bS / (double)bA;
+}
+
+// Prefix table of b^2 for k_jitter, P[(m+1) x (n+1)] (exact u64), in two
+// passes: k_sq_prefix_rows (one thread per row, row 0 all zero), then
+// k_sq_prefix_cols (one thread per column).
+static __global__ void k_sq_prefix_rows(const uint16_t* __restrict__ tmpl, int m, int n, u64* __restrict__ P) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t ld = n + 1;
+    if (i == 0)
+        for (int j = 0; j <= n; ++j) P[j] = 0;
+    if (i >= m) return;
+    u64 run = 0;
+    u64* row = P + (int64_t)(i + 1) * ld;
+    row[0] = 0;
+    for (int j = 0; j < n; ++j) {
+        const u64 v = tmpl[(int64_t)i * n + j];
+        run += v * v;
+        row[j + 1] = run;
+    }
+}
+
+static __global__ void k_sq_prefix_cols(int m, int n, u64* __restrict__ P) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > n) return;
+    const int64_t ld = n + 1;
+    for (int i = 1; i <= m; ++i) P[i * ld + j] += P[(i - 1) * ld + j];
 }
 
 // For searches without a level: the searched optimum is the answer.

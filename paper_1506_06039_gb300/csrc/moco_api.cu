@@ -164,6 +164,7 @@ moco_status allocate_shape(ShapePlan& sp) {
     c.add(&sp.inv_area, (size_t)W * W * 8);
     c.add(&sp.grad_acc, (size_t)(m * n * 4));
     c.add(&sp.grad_Q, (size_t)(W * W * 4));
+    if (sp.levels && !sp.f32) c.add(&sp.bsq, (size_t)(m + 1) * (n + 1) * 8);
     sp.x_fstride = (int64_t)sp.ncv * sp.ldx;
     sp.y_fstride = W * sp.ncv;
     sp.bytes = c.off;
@@ -267,6 +268,10 @@ moco_status prepare_template(ShapePlan& sp, const void* tmpl_dev, cudaStream_t s
                             sp.coff_f, sp.bprime, sp.dtiles, st);
         if (e != cudaSuccess) return cuda_fail(e, "template Toeplitz tiles");
     }
+    if (sp.bsq) {
+        e = launch_sq_prefix(static_cast<const uint16_t*>(sp.tmpl), sp.desc.m, sp.desc.n, sp.bsq, st);
+        if (e != cudaSuccess) return cuda_fail(e, "template square prefix table");
+    }
     return MOCO_OK;
 }
 
@@ -325,7 +330,7 @@ moco_status search_group(ShapePlan& sp, const uint16_t* frames, int64_t g, doubl
 moco_status autotune(ShapePlan& sp, cudaStream_t st);
 
 moco_status align_frames(ShapePlan& sp, const uint16_t* frames, int64_t T, int32_t* shifts, double* best_cost,
-                         float* margin, cudaStream_t st) {
+                         float* margin, double* final_cost, cudaStream_t st) {
     const int64_t mn = (int64_t)sp.desc.m * sp.desc.n;
     for (int64_t f0 = 0; f0 < T; f0 += sp.group) {
         const int64_t g = std::min<int64_t>(sp.group, T - f0);
@@ -336,9 +341,11 @@ moco_status align_frames(ShapePlan& sp, const uint16_t* frames, int64_t T, int32
         sp.prof->begin(sp.levels ? K_JITTER : K_COPY_SHIFTS, st);
         if (sp.levels)
             e = launch_jitter(frames + f0 * mn, mn, g, static_cast<const uint16_t*>(sp.tmpl), sp.desc.m,
-                              sp.desc.n, sp.coarse, shifts + 2 * f0, nullptr, sp.jit_acc, sp.jit_ticket, st);
+                              sp.desc.n, sp.bsq, sp.coarse, shifts + 2 * f0, final_cost ? final_cost + f0 : nullptr,
+                              sp.jit_acc, sp.jit_ticket, st);
         else
-            e = launch_copy_shifts(sp.coarse, shifts + 2 * f0, nullptr, nullptr, g, st);
+            e = launch_copy_shifts(sp.coarse, shifts + 2 * f0, best_cost ? best_cost + f0 : sp.fbest,
+                                   final_cost ? final_cost + f0 : nullptr, g, st);
         sp.prof->end(st);
         if (e != cudaSuccess) return cuda_fail(e, sp.levels ? "k_jitter" : "k_copy_shifts");
     }
@@ -511,7 +518,7 @@ moco_status moco_align_stack(moco_plan_t plan, const moco_stack* stacks, int32_t
         const moco_stack& s = stacks[k];
         if (s.T == 0) continue;
         moco_status r = align_frames(plan->shapes[s.shape_idx], s.frames_dev, s.T, s.shifts_dev, s.best_cost_dev,
-                                     s.margin_dev, st);
+                                     s.margin_dev, s.final_cost_dev, st);
         if (r != MOCO_OK) return r;
     }
     return MOCO_OK;
@@ -682,7 +689,7 @@ moco_status moco_align_host(moco_plan_t plan, int32_t shape_idx, const uint16_t*
         if (e == cudaSuccess) e = cudaEventRecord(copied[k], cp);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, copied[k], 0);
         if (e != cudaSuccess) return cuda_fail(e, "host-to-device staging");
-        moco_status s = align_frames(sp, sp.stage[k], g, sp.stage_shifts[k], nullptr, nullptr, st);
+        moco_status s = align_frames(sp, sp.stage[k], g, sp.stage_shifts[k], nullptr, nullptr, nullptr, st);
         if (s != MOCO_OK) return s;
         e = cudaMemcpyAsync(shifts_host + 2 * f0, sp.stage_shifts[k], (size_t)(g * 8), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaEventRecord(done[k], st);

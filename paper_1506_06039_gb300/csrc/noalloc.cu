@@ -73,8 +73,9 @@ extern "C" moco_status moco_jitter_noalloc(const uint16_t* frames_dev, int64_t T
     u64* acc = static_cast<u64*>(base);
     unsigned int* ticket = reinterpret_cast<unsigned int*>(acc + 9 * kNoallocMaxFrames);
     // launch_jitter clears the T frames' sums and tickets before the kernel.
-    e = launch_jitter(frames_dev, (int64_t)m * n, T, template_dev, m, n, coarse_dev, shifts_dev, nullptr, acc, ticket,
-                      static_cast<cudaStream_t>(stream));
+    // No template table without a plan: the kernel sums b^2 itself.
+    e = launch_jitter(frames_dev, (int64_t)m * n, T, template_dev, m, n, nullptr, coarse_dev, shifts_dev, nullptr, acc,
+                      ticket, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "moco_jitter_noalloc");
     return MOCO_OK;
 }

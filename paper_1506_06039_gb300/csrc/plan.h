@@ -62,6 +62,7 @@ struct ShapePlan {
     float2* bspec = nullptr;
     double* Sb = nullptr;
     double* inv_area = nullptr;
+    u64* bsq = nullptr;  // with a level: prefix table of b^2, (m+1) x (n+1)
     // direct form
     float* bprime = nullptr;        // mc x nc offset template
     void* dtiles = nullptr;         // Toeplitz tiles (hi, lo)

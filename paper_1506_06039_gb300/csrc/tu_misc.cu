@@ -77,7 +77,7 @@ cudaError_t launch_energy(bool f32, bool out_double, const u64* rowE, const u64*
 }
 
 cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg, const uint16_t* tmpl, int m,
-                          int n, const int32_t* coarse, int32_t* shifts, double* ffinal, u64* acc,
+                          int n, const u64* bsq, const int32_t* coarse, int32_t* shifts, double* ffinal, u64* acc,
                           unsigned int* ticket, cudaStream_t st) {
     if (nimg <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(u64) * 9 * nimg, st);
@@ -86,7 +86,19 @@ cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg,
     const int tasks = (n / 8) * ((m + kJitRows - 1) / kJitRows);
     const int ctas = (tasks + kJitterThreads - 1) / kJitterThreads;
     dim3 grid((unsigned)ctas, (unsigned)nimg);
-    k_jitter<<<grid, kJitterThreads, 0, st>>>(frames, fstride, tmpl, m, n, coarse, shifts, ffinal, acc, ticket);
+    if (bsq)
+        k_jitter<true><<<grid, kJitterThreads, 0, st>>>(frames, fstride, tmpl, m, n, bsq, coarse, shifts, ffinal, acc,
+                                                        ticket);
+    else
+        k_jitter<false><<<grid, kJitterThreads, 0, st>>>(frames, fstride, tmpl, m, n, nullptr, coarse, shifts, ffinal,
+                                                         acc, ticket);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sq_prefix(const uint16_t* tmpl, int m, int n, u64* P, cudaStream_t st) {
+    const int threads = 128;
+    k_sq_prefix_rows<<<(m + threads - 1) / threads, threads, 0, st>>>(tmpl, m, n, P);
+    k_sq_prefix_cols<<<(n + 1 + threads - 1) / threads, threads, 0, st>>>(m, n, P);
     return cudaGetLastError();
 }
 

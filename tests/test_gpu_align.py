@@ -97,6 +97,53 @@ def test_jitter_every_column_offset():
     check_align(frames, b, 10, -1, shifts, best)
 
 
+def brute_ssd(a, b, s, t):
+    """Exact sum over D of (a[i+s][j+t] - b[i][j])^2 by direct int64 evaluation."""
+    m, n = b.shape
+    i0, i1, j0, j1 = max(0, -s), min(m, m - s), max(0, -t), min(n, n - t)
+    d = a[i0 + s:i1 + s, j0 + t:j1 + t].astype(np.int64) - b[i0:i1, j0:j1].astype(np.int64)
+    return int((d * d).sum()), (i1 - i0) * (j1 - j0)
+
+
+@pytest.mark.parametrize("m,n,w", [(264, 264, 40), (330, 296, 9)])
+def test_full_range_values_final_cost_exact(m, n, w):
+    # Values over the whole 16-bit range (both byte halves of every product
+    # busy), planted shifts out to the window's edge (whole row bands of the
+    # frame outside the overlap), a saturated and an all-zero frame. The
+    # full-resolution cost at the returned shift must be S / Area with S the
+    # exact integer sum, to the last bit.
+    rng = np.random.default_rng(m * 7 + n + w)
+    b = rng.integers(0, 65536, (m, n)).astype(np.uint16)
+    e = 2 * (w - 1) - 1
+    planted = [(-e, e), (e, -e), (5, -7), (0, 1), (-e, 0), (e - 2, e)]
+    frames = []
+    for s0, t0 in planted:
+        a = rng.integers(0, 65536, (m, n)).astype(np.int64)
+        a[max(0, s0):min(m, m + s0), max(0, t0):min(n, n + t0)] = \
+            b[max(0, -s0):min(m, m - s0), max(0, -t0):min(n, n - t0)]
+        a += rng.integers(-3000, 3001, (m, n))
+        frames.append(np.clip(a, 0, 65535).astype(np.uint16))
+    frames += [np.full((m, n), 65535, np.uint16), np.zeros((m, n), np.uint16)]
+    frames = np.stack(frames)
+    with Plan(dict(m=m, n=n, w=w, levels=1), dev(b)) as plan:
+        shifts, best, _, final = plan.align(dev(frames), best_cost=True, final_cost=True)
+        torch.cuda.synchronize()
+        shifts, best, final = shifts.cpu().numpy(), best.cpu().numpy(), final.cpu().numpy()
+    check_align(frames, b, w, 1, shifts, best)
+    assert [tuple(x) for x in shifts[:len(planted)]] == planted
+    for f in range(frames.shape[0]):
+        S, A = brute_ssd(frames[f], b, int(shifts[f, 0]), int(shifts[f, 1]))
+        assert final[f] == S / A, (f, final[f], S, A)
+
+
+def test_final_cost_equals_oracle_without_level():
+    st = synth.make_stack_np(96, 80, 5, 30, 4, seed=77, template="clean")
+    with Plan(dict(m=96, n=80, w=6, levels=0), dev(st.template)) as plan:
+        shifts, best, _, final = plan.align(dev(st.frames), best_cost=True, final_cost=True)
+        torch.cuda.synchronize()
+    assert np.array_equal(final.cpu().numpy(), best.cpu().numpy())
+
+
 def test_identity_and_constant_frames():
     rng = np.random.default_rng(3)
     b = rng.integers(0, 3000, (64, 64)).astype(np.uint16)
