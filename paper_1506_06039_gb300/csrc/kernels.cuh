@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "fft.cuh"
+#include "ptx.cuh"
 
 namespace moco {
 
@@ -633,16 +634,16 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 constexpr int kJitRows = 32;
 static_assert(kJitRows <= 32, "32-bit dot-product sums are exact for at most 32 rows of 8 columns");
 
-// Raw words of one frame row: 6 x 32 bits = half-words lead-1 .. lead+10,
-// loaded from lead - 1 (even, so 4-byte aligned); zeros outside the frame.
-struct JitRaw {
-    uint32_t w[6];
-};
-
-// One frame row of the window as 16-bit pairs (see above).
-struct JitWin {
+// One frame row of a thread's window. raw: the 16-byte chunks that hold
+// half-words lead-1 .. lead+10, i.e. 32-bit words O .. O+5 of raw, where
+// O = ((lead - 1) / 2) mod 4 is the same for every thread of a frame (lead =
+// 8 j + 2 tc - 1); a ninth word when O = 3. pw as described above; rw[p] is
+// raw[O + 1 + p] itself. Chunks (8 half-words from a multiple of 8; n % 8 ==
+// 0) lie wholly inside or outside the frame: outside ones stay zero.
+template <int O>
+struct JitSlot {
+    uint32_t raw[O == 3 ? 9 : 8];
     uint32_t pw[5];
-    uint32_t rw[4];
 };
 
 // 2 x 32-bit partial sums (low and high byte half) of one quantity.
@@ -653,26 +654,36 @@ struct Acc2 {
 struct JitBand {
     const uint16_t* a;     // frame
     const uint16_t* tmpl;  // template
-    int m, n, s0, lead, j0, i_b, i_e;
-    uint32_t wvalid;       // bit k: raw word k (columns lead-1+2k, +1) inside the frame
+    int m, n, s0, j0, i_b, i_e;
+    int first;             // frame row of window row 0 at the band's first template row
+    int c0;                // first column of raw chunk 0 (multiple of 8, may be negative)
+    uint32_t cvalid;       // bit c: raw chunk c (columns c0 + 8c .. + 7) inside the frame
 };
 
-// Row ar of the frame (zeros where outside).
-__device__ __forceinline__ void jit_fetch(const JitBand& B, int ar, JitRaw& r) {
+// Frame row ar into slot x (zeros where outside the frame).
+template <int O>
+__device__ __forceinline__ void jit_fetch(const JitBand& B, int ar, JitSlot<O>& x) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) r.w[k] = 0u;
-    if (ar < 0 || ar >= B.m) return;
-    const uint32_t* p = reinterpret_cast<const uint32_t*>(B.a + (int64_t)ar * B.n + (B.lead - 1));
+    for (int k = 0; k < (O == 3 ? 9 : 8); ++k) x.raw[k] = 0u;
+    if (ar < 0 || ar >= B.m) return;  // the same for the whole warp
+    const uint16_t* row = B.a + (int64_t)ar * B.n;
 #pragma unroll
-    for (int k = 0; k < 6; ++k)
-        if ((B.wvalid >> k) & 1u) r.w[k] = __ldg(p + k);
+    for (int c = 0; c < 2; ++c)
+        if ((B.cvalid >> c) & 1u) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4*>(row + B.c0 + 8 * c));
+            x.raw[4 * c] = q.x;
+            x.raw[4 * c + 1] = q.y;
+            x.raw[4 * c + 2] = q.z;
+            x.raw[4 * c + 3] = q.w;
+        }
+    if (O == 3)
+        if ((B.cvalid >> 2) & 1u) x.raw[(O == 3) ? 8 : 0] = __ldg(reinterpret_cast<const uint32_t*>(row + B.c0 + 16));
 }
 
-__device__ __forceinline__ void jit_unpack(const JitRaw& r, JitWin& x) {
+template <int O>
+__device__ __forceinline__ void jit_unpack(JitSlot<O>& x) {
 #pragma unroll
-    for (int p = 0; p < 5; ++p) x.pw[p] = __byte_perm(r.w[p], r.w[p + 1], 0x5432);
-#pragma unroll
-    for (int p = 0; p < 4; ++p) x.rw[p] = r.w[p + 1];
+    for (int p = 0; p < 5; ++p) x.pw[p] = __byte_perm(x.raw[O + p], x.raw[O + p + 1], 0x5432);
 }
 
 // Byte planes of a 16-bit pair (y0, y1): bytes (y0_lo, y1_lo, y0_hi, y1_hi).
@@ -690,7 +701,8 @@ __device__ __forceinline__ u64 acc_value(const Acc2& a) { return (u64)a.lo + ((u
 
 // Sum of squares of one window row over the columns of each v:
 // v = 0: columns 0..7, v = 1: 1..8, v = 2: 2..9 (of lead ..).
-__device__ __forceinline__ void row_energy(const JitWin& x, Acc2 (&e)[3]) {
+template <int O>
+__device__ __forceinline__ void row_energy(const JitSlot<O>& x, Acc2 (&e)[3]) {
     uint32_t pl[5];
 #pragma unroll
     for (int p = 0; p < 5; ++p) pl[p] = byte_planes(x.pw[p]);
@@ -724,41 +736,112 @@ __device__ __forceinline__ void tmpl_energy(const uint32_t (&bw)[4], const uint3
         for (int p = 0; p < 4; ++p) dot_acc(bw[p], bp[p] & cm[v * 4 + p], e[v]);
 }
 
-// One template row i: w0, w1 hold frame rows i+s0-1, i+s0; w2 receives row
-// i+s0+1 from raw, and raw / braw are refilled for row i+1.
-template <bool TABLE>
-__device__ __forceinline__ void jit_step(const JitBand& B, int i, const JitWin& w0, const JitWin& w1, JitWin& w2,
-                                         JitRaw& raw, uint4& braw, Acc2 (&C)[9], Acc2 (&M)[3], Acc2 (&QB)[3],
-                                         const uint32_t (&cm)[12]) {
-    jit_unpack(raw, w2);
-    const uint32_t bw[4] = {braw.x, braw.y, braw.z, braw.w};
+__device__ __forceinline__ uint4 jit_tmpl_row(const JitBand& B, int i) {
+    return __ldg(reinterpret_cast<const uint4*>(B.tmpl + (int64_t)i * B.n + B.j0));
+}
+
+// Shared-memory ring of rows in flight: stage q % kJitRing holds, per thread,
+// the raw chunks of frame row first + q and (q >= 2) template row
+// i_b + q - 2, as ring[((stage * 4) + c) * kJitterThreads + tid], c = 0, 1, 2
+// frame chunks, 3 template; each thread copies and reads only its own column
+// (cp.async, one commit group per row), so no barrier is needed.
+constexpr int kJitRing = 4;
+constexpr size_t kJitRingBytes = (size_t)kJitRing * 4 * kJitterThreads * 16;
+
+template <int O>
+__device__ __forceinline__ void jit_issue(const JitBand& B, uint4* ring, int q) {
+    uint4* st = ring + (q & (kJitRing - 1)) * 4 * kJitterThreads;
+    if (q <= B.i_e - B.i_b + 1) {
+        const int ar = B.first + q;
+        const bool rok = ar >= 0 && ar < B.m;  // the same for the whole warp
+        const uint16_t* row = B.a + (int64_t)(rok ? ar : 0) * B.n;
+#pragma unroll
+        for (int c = 0; c < (O == 3 ? 3 : 2); ++c) {
+            const bool ok = rok && ((B.cvalid >> c) & 1u);
+            cp16z(st + c * kJitterThreads, ok ? row + B.c0 + 8 * c : B.a, ok ? 16u : 0u);
+        }
+        if (q >= 2) cp16z(st + 3 * kJitterThreads, B.tmpl + (int64_t)(B.i_b + q - 2) * B.n + B.j0, 16u);
+    }
+    cp_commit();
+}
+
+// Row q from the ring (its copy group complete) into slot x; its template row
+// into *tr when asked.
+template <int O>
+__device__ __forceinline__ void jit_take(const uint4* ring, int q, JitSlot<O>& x, uint4* tr) {
+    const uint4* st = ring + (q & (kJitRing - 1)) * 4 * kJitterThreads;
+    const uint4 c0 = st[0], c1 = st[kJitterThreads];
+    x.raw[0] = c0.x;
+    x.raw[1] = c0.y;
+    x.raw[2] = c0.z;
+    x.raw[3] = c0.w;
+    x.raw[4] = c1.x;
+    x.raw[5] = c1.y;
+    x.raw[6] = c1.z;
+    x.raw[7] = c1.w;
+    if (O == 3) x.raw[(O == 3) ? 8 : 0] = st[2 * kJitterThreads].x;
+    if (tr) *tr = st[3 * kJitterThreads];
+    jit_unpack(x);
+}
+
+// Step j of a band (K = j mod 3), template row i = i_b + j: slots K, K+1
+// hold frame rows i+s0-1, i+s0; slot K+2 receives row i+s0+1 (ring row j+2)
+// with template row i, and ring row j+2+kJitRing is issued into its stage.
+template <bool TABLE, int O, int K>
+__device__ __forceinline__ void jit_step(const JitBand& B, int i, uint4* ring, JitSlot<O> (&S)[3], Acc2 (&C)[9],
+                                         Acc2 (&M)[3], Acc2 (&QB)[3], const uint32_t (&cm)[12]) {
+    const int j = i - B.i_b;
+    JitSlot<O>& w0 = S[K];
+    JitSlot<O>& w1 = S[(K + 1) % 3];
+    JitSlot<O>& w2 = S[(K + 2) % 3];
+    uint4 tr;
+    cp_wait<kJitRing - 1>();
+    jit_take(ring, j + 2, w2, &tr);
+    const uint32_t bw[4] = {tr.x, tr.y, tr.z, tr.w};
     uint32_t bp[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) bp[p] = byte_planes(bw[p]);
-    if (i + 1 < B.i_e) {
-        jit_fetch(B, i + B.s0 + 2, raw);
-        braw = __ldg(reinterpret_cast<const uint4*>(B.tmpl + (int64_t)(i + 1) * B.n + B.j0));
-    }
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         dot_acc(w0.pw[p], bp[p], C[0]);
-        dot_acc(w0.rw[p], bp[p], C[1]);
+        dot_acc(w0.raw[O + 1 + p], bp[p], C[1]);
         dot_acc(w0.pw[p + 1], bp[p], C[2]);
         dot_acc(w1.pw[p], bp[p], C[3]);
-        dot_acc(w1.rw[p], bp[p], C[4]);
+        dot_acc(w1.raw[O + 1 + p], bp[p], C[4]);
         dot_acc(w1.pw[p + 1], bp[p], C[5]);
         dot_acc(w2.pw[p], bp[p], C[6]);
-        dot_acc(w2.rw[p], bp[p], C[7]);
+        dot_acc(w2.raw[O + 1 + p], bp[p], C[7]);
         dot_acc(w2.pw[p + 1], bp[p], C[8]);
     }
     if (i <= B.i_e - 3) row_energy(w2, M);  // frame row shared by all three u
     if (!TABLE)
         if (i + B.s0 - 1 >= 0 && i + B.s0 + 1 <= B.m - 1) tmpl_energy(bw, bp, cm, QB);
+    jit_issue<O>(B, ring, j + 2 + kJitRing);  // the stage just read (its data is consumed)
+}
+
+// X[u*3+v] += energy e of frame row r for each u whose range
+// first + u .. first + u + L - 1 holds r.
+__device__ __forceinline__ void jit_add_row(int r, int first, int L, const Acc2 (&e)[3], u64 (&X)[9]) {
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+        if (r >= first + u && r <= first + u + L - 1)
+#pragma unroll
+            for (int v = 0; v < 3; ++v) X[u * 3 + v] += acc_value(e[v]);
+}
+
+template <int O, int A, int B2>
+__device__ __forceinline__ void jit_last_rows(const JitSlot<O> (&S)[3], int first, int L, u64 (&X)[9]) {
+    Acc2 e[3] = {{0u, 0u}, {0u, 0u}, {0u, 0u}};
+    row_energy(S[A], e);
+    jit_add_row(first + L, first, L, e, X);
+    Acc2 f[3] = {{0u, 0u}, {0u, 0u}, {0u, 0u}};
+    row_energy(S[B2], f);
+    jit_add_row(first + L + 1, first, L, f, X);
 }
 
 // The nine partial sums of one thread's band, X[u*3+v] (mod 2^64).
-template <bool TABLE>
-__device__ __forceinline__ void jit_band(const JitBand& B, uint32_t mask, u64 (&X)[9]) {
+template <bool TABLE, int O>
+__device__ __forceinline__ void jit_band(const JitBand& B, uint4* ring, uint32_t mask, u64 (&X)[9]) {
     Acc2 C[9], M[3], QB[3];
 #pragma unroll
     for (int k = 0; k < 9; ++k) C[k] = Acc2{0u, 0u};
@@ -770,45 +853,52 @@ __device__ __forceinline__ void jit_band(const JitBand& B, uint32_t mask, u64 (&
     uint32_t cm[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) cm[k] = TABLE ? 0u : col_mask(mask, k / 4, k % 4);
-    const int first = B.i_b + B.s0 - 1, L = B.i_e - B.i_b;
-    JitWin wa, wb, wc;
-    JitRaw raw;
-    jit_fetch(B, first, raw);
-    jit_unpack(raw, wa);
-    jit_fetch(B, first + 1, raw);
-    jit_unpack(raw, wb);
-    jit_fetch(B, first + 2, raw);
-    uint4 braw = __ldg(reinterpret_cast<const uint4*>(B.tmpl + (int64_t)B.i_b * B.n + B.j0));
+    const int first = B.first, L = B.i_e - B.i_b;
+    JitSlot<O> S[3];
+#pragma unroll
+    for (int q = 0; q < kJitRing; ++q) jit_issue<O>(B, ring, q);
+    cp_wait<kJitRing - 1>();
+    jit_take(ring, 0, S[0], nullptr);
+    jit_issue<O>(B, ring, kJitRing);
+    cp_wait<kJitRing - 1>();
+    jit_take(ring, 1, S[1], nullptr);
+    jit_issue<O>(B, ring, kJitRing + 1);
     for (int i = B.i_b;;) {
-        jit_step<TABLE>(B, i, wa, wb, wc, raw, braw, C, M, QB, cm);
+        jit_step<TABLE, O, 0>(B, i, ring, S, C, M, QB, cm);
         if (++i >= B.i_e) break;
-        jit_step<TABLE>(B, i, wb, wc, wa, raw, braw, C, M, QB, cm);
+        jit_step<TABLE, O, 1>(B, i, ring, S, C, M, QB, cm);
         if (++i >= B.i_e) break;
-        jit_step<TABLE>(B, i, wc, wa, wb, raw, braw, C, M, QB, cm);
+        jit_step<TABLE, O, 2>(B, i, ring, S, C, M, QB, cm);
         if (++i >= B.i_e) break;
     }
+    cp_wait<0>();  // the groups still open hold no copies; none stays in flight
 #pragma unroll
     for (int u = 0; u < 3; ++u)
 #pragma unroll
         for (int v = 0; v < 3; ++v)
             X[u * 3 + v] = acc_value(M[v]) + acc_value(QB[v]) - 2ull * acc_value(C[u * 3 + v]);
 
-    // Frame rows at the ends of the band's range first .. first + L + 1:
-    // row r belongs to u when first + u <= r <= first + u + L - 1.
-    for (int k = 0; k < 4; ++k) {
-        const int r = (k < 2) ? first + k : first + L + k - 2;
-        if (k == 2 && L < 2) continue;  // L = 1: first + L is row first + 1
-        JitRaw rr;
-        jit_fetch(B, r, rr);
-        JitWin x;
-        jit_unpack(rr, x);
+    // Frame rows at the ends of the band's range first .. first + L + 1.
+    // The last two are still in slots L and L + 1 (mod 3).
+    switch (L % 3) {
+        case 0: jit_last_rows<O, 0, 1>(S, first, L, X); break;
+        case 1: jit_last_rows<O, 1, 2>(S, first, L, X); break;
+        default: jit_last_rows<O, 2, 0>(S, first, L, X); break;
+    }
+    // The first two are loaded again (row first + 1 is row first + L when L = 1).
+    jit_fetch(B, first, S[0]);
+    if (L >= 2) jit_fetch(B, first + 1, S[1]);
+    jit_unpack(S[0]);
+    {
         Acc2 e[3] = {{0u, 0u}, {0u, 0u}, {0u, 0u}};
-        row_energy(x, e);
-#pragma unroll
-        for (int u = 0; u < 3; ++u)
-            if (r >= first + u && r <= first + u + L - 1)
-#pragma unroll
-                for (int v = 0; v < 3; ++v) X[u * 3 + v] += acc_value(e[v]);
+        row_energy(S[0], e);
+        jit_add_row(first, first, L, e, X);
+    }
+    if (L >= 2) {
+        jit_unpack(S[1]);
+        Acc2 e[3] = {{0u, 0u}, {0u, 0u}, {0u, 0u}};
+        row_energy(S[1], e);
+        jit_add_row(first + 1, first, L, e, X);
     }
     if (TABLE) return;
     // In-loop sum b^2: template rows whose partner row is valid for some but
@@ -816,7 +906,7 @@ __device__ __forceinline__ void jit_band(const JitBand& B, uint32_t mask, u64 (&
     for (int k = 0; k < 4; ++k) {
         const int i = (k < 2 ? -1 + k : B.m - 3 + k) - B.s0;
         if (i < B.i_b || i >= B.i_e || i < 0 || i >= B.m) continue;
-        const uint4 q = __ldg(reinterpret_cast<const uint4*>(B.tmpl + (int64_t)i * B.n + B.j0));
+        const uint4 q = jit_tmpl_row(B, i);
         const uint32_t bw[4] = {q.x, q.y, q.z, q.w};
         uint32_t bp[4];
 #pragma unroll
@@ -851,12 +941,14 @@ __device__ __forceinline__ int ratio_lt(u64 S1, u64 A1, u64 S2, u64 A2, int* eq)
 
 // bsq: the prefix table of b^2 (TABLE) or nullptr (sum b^2 in the loop).
 template <bool TABLE>
-__global__ void __launch_bounds__(kJitterThreads, 2)
+__global__ void __launch_bounds__(kJitterThreads, TABLE ? 2 : 1)
 k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* __restrict__ tmpl, int m, int n,
          const u64* __restrict__ bsq, const int32_t* __restrict__ coarse, int32_t* __restrict__ shifts,
          double* __restrict__ ffinal, u64* __restrict__ acc_g, unsigned int* __restrict__ ticket) {
     __shared__ u64 red[kJitterThreads / 32][9];
     __shared__ bool last;
+    extern __shared__ __align__(16) unsigned char jit_smem[];
+    uint4* ring = reinterpret_cast<uint4*>(jit_smem) + threadIdx.x;  // kJitRingBytes
     const int tid = threadIdx.x;
     const int64_t f = blockIdx.y;
     const int s0 = 2 * coarse[2 * f], t0 = 2 * coarse[2 * f + 1];
@@ -875,26 +967,33 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
         B.n = n;
         B.s0 = s0;
         B.j0 = 8 * g;
-        B.lead = B.j0 + t0 - 1;  // odd: lead - 1 is 4-byte aligned
+        const int lead = B.j0 + t0 - 1;  // odd
+        // Word (lead - 1) / 2 of the row is word O of chunk 0.
+        const int O = ((t0 >> 1) - 1) & 3;  // the same for the whole frame
+        B.c0 = lead - 1 - 2 * O;
         B.i_b = band * kJitRows;
         B.i_e = min(m, B.i_b + kJitRows);
-        B.wvalid = 0;
+        B.first = B.i_b + s0 - 1;
+        B.cvalid = 0;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const int c = B.lead - 1 + 2 * k;
-            if (c >= 0 && c <= n - 2) B.wvalid |= 1u << k;
-        }
+        for (int c = 0; c < 3; ++c)
+            if (B.c0 + 8 * c >= 0 && B.c0 + 8 * c + 8 <= n) B.cvalid |= 1u << c;
         uint32_t mask = 0;  // bit v*8+k: frame column lead+k+v inside the frame
         if (!TABLE) {
 #pragma unroll
             for (int v = 0; v < 3; ++v)
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    const int c = B.lead + k + v;
+                    const int c = lead + k + v;
                     if (c >= 0 && c < n) mask |= 1u << (v * 8 + k);
                 }
         }
-        jit_band<TABLE>(B, mask, X);
+        switch (O) {
+            case 0: jit_band<TABLE, 0>(B, ring, mask, X); break;
+            case 1: jit_band<TABLE, 1>(B, ring, mask, X); break;
+            case 2: jit_band<TABLE, 2>(B, ring, mask, X); break;
+            default: jit_band<TABLE, 3>(B, ring, mask, X); break;
+        }
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {

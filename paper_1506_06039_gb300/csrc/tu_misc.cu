@@ -86,12 +86,15 @@ cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg,
     const int tasks = (n / 8) * ((m + kJitRows - 1) / kJitRows);
     const int ctas = (tasks + kJitterThreads - 1) / kJitterThreads;
     dim3 grid((unsigned)ctas, (unsigned)nimg);
+    const void* fn = bsq ? reinterpret_cast<const void*>(k_jitter<true>) : reinterpret_cast<const void*>(k_jitter<false>);
+    e = ensure_smem(fn, kJitRingBytes);
+    if (e != cudaSuccess) return e;
     if (bsq)
-        k_jitter<true><<<grid, kJitterThreads, 0, st>>>(frames, fstride, tmpl, m, n, bsq, coarse, shifts, ffinal, acc,
-                                                        ticket);
+        k_jitter<true><<<grid, kJitterThreads, kJitRingBytes, st>>>(frames, fstride, tmpl, m, n, bsq, coarse, shifts,
+                                                                    ffinal, acc, ticket);
     else
-        k_jitter<false><<<grid, kJitterThreads, 0, st>>>(frames, fstride, tmpl, m, n, nullptr, coarse, shifts, ffinal,
-                                                         acc, ticket);
+        k_jitter<false><<<grid, kJitterThreads, kJitRingBytes, st>>>(frames, fstride, tmpl, m, n, nullptr, coarse,
+                                                                     shifts, ffinal, acc, ticket);
     return cudaGetLastError();
 }
 
