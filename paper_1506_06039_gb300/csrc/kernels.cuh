@@ -71,25 +71,64 @@ __device__ __forceinline__ uint32_t hi16(uint32_t w) { return w >> 16; }
 // PLANES (the direct form): no FFT; the offset searched-grid image is written
 // as BF16 hi and lo planes instead, planes[f][r][c] with row length ldp
 // (columns nc .. ldp-1 written as zeros).
-template <int N, bool F32IN, bool PLANES = false>
+// STAGED (uint16 frames, FFT mode; n % 8 == 0): the full-resolution rows of
+// each chunk of kRC searched rows are brought into shared memory by bulk
+// asynchronous copies (one mbarrier), the next chunk's while this chunk's
+// transforms run; the loader then reads shared memory. A wait that gives up
+// (about a second) sets *err and ends the CTA after one more bounded wait.
+template <int N, bool F32IN>
+__host__ __device__ constexpr size_t frame_rows_smem_base(int nc) {
+    return (sizeof(float2) * ((kRC / 2) * fft_ld<N>() + N) + sizeof(typename AccT<F32IN>::type) * (kRC + nc) + 127) /
+           128 * 128;
+}
+__host__ __device__ constexpr size_t frame_rows_stage_bytes(int n, int levels) {
+    return (size_t)(levels ? 2 : 1) * kRC * n * 2;
+}
+constexpr uint32_t kStageCopyBytes = 16384;  // bulk copies of at most 16 KiB each
+
+template <int N, bool F32IN, bool PLANES = false, bool STAGED = false>
 __global__ void __launch_bounds__(kRowsThreads, 2)
 k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, int levels, int mc,
              int nc, const int32_t* __restrict__ coff_i, const float* __restrict__ coff_f,
              const float2* __restrict__ tw_g, float2* __restrict__ X, int64_t x_fstride, int ldx,
              u64* __restrict__ rowE, u64* __restrict__ colE, u64* __restrict__ tot,
              uint32_t* __restrict__ corners, int wm1, __nv_bfloat16* __restrict__ p_hi = nullptr,
-             __nv_bfloat16* __restrict__ p_lo = nullptr, int ldp = 0) {
+             __nv_bfloat16* __restrict__ p_lo = nullptr, int ldp = 0, unsigned int* __restrict__ err = nullptr) {
+    static_assert(!STAGED || (!F32IN && !PLANES), "staging is for uint16 frames in FFT mode");
     typedef typename AccT<F32IN>::type Acc;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int LD = fft_ld<N>();                      // skewed, padded row
     float2* buf = reinterpret_cast<float2*>(smem_raw);  // (kRC/2) x LD
     float2* tw = buf + (kRC / 2) * LD;                   // N: forward table
     Acc* rowacc = reinterpret_cast<Acc*>(tw + N);        // kRC
     Acc* colacc = rowacc + kRC;                          // nc
     __shared__ Acc red[32];
+    __shared__ __align__(8) uint64_t stage_bar;
+    __shared__ int s_abort;
+    const uint16_t* stage = reinterpret_cast<const uint16_t*>(smem_raw + frame_rows_smem_base<N, F32IN>(nc));
+    // Issues the bulk copies of the chunk at searched row c0 (one thread).
+    auto issue_chunk = [&](int c0) {
+        const int rows = min(kRC, mc - c0) * (levels ? 2 : 1);
+        const uint32_t bytes = (uint32_t)rows * (uint32_t)n * 2u;
+        const unsigned char* g = reinterpret_cast<const unsigned char*>(static_cast<const uint16_t*>(src) +
+                                                                        blockIdx.x * src_fstride +
+                                                                        (int64_t)c0 * (levels ? 2 : 1) * n);
+        unsigned char* d = smem_raw + frame_rows_smem_base<N, F32IN>(nc);
+        mbar_expect_tx(&stage_bar, bytes);
+        for (uint32_t off = 0; off < bytes; off += kStageCopyBytes)
+            bulk_g2s(d + off, g + off, min(kStageCopyBytes, bytes - off), &stage_bar);
+    };
 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int64_t f = blockIdx.x;
+    if (STAGED) {
+        if (tid == 0) {
+            mbar_init(&stage_bar, 1);
+            s_abort = 0;
+            fence_async_smem();
+            issue_chunk(0);
+        }
+    }
     for (int i = tid; i < N; i += nthr) tw[i] = tw_g[i];
     for (int i = tid; i < nc; i += nthr) colacc[i] = 0;
     for (int i = tid; i < kRC; i += nthr) rowacc[i] = 0;
@@ -120,6 +159,15 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
                 const int pr = i / (N - nc), cc = nc + (i - pr * (N - nc));
                 buf[pr * LD + sk<N>(cc)] = make_float2(0.f, 0.f);
             }
+            if (STAGED) {
+                __syncthreads();  // s_abort and the barrier's set-up are visible
+                if (!mbar_wait(&stage_bar, (uint32_t)((r0 / kRC) & 1), err)) s_abort = 1;
+                __syncthreads();
+                if (s_abort) {
+                    if (tid == 0) mbar_wait(&stage_bar, (uint32_t)((r0 / kRC) & 1), err);
+                    return;
+                }
+            }
 #pragma unroll
             for (int slot = 0; slot < 4; ++slot) {
                 if (slot >= CS) break;
@@ -145,10 +193,20 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
                                 if (h == 1 && !has1) break;
-                                const uint32_t w0 = __ldg(reinterpret_cast<const uint32_t*>(base + (int64_t)(2 * (r + h)) * n + 2 * c));
-                                const uint32_t w1 = __ldg(reinterpret_cast<const uint32_t*>(base + (int64_t)(2 * (r + h) + 1) * n + 2 * c));
+                                uint32_t w0, w1;
+                                if (STAGED) {
+                                    const uint32_t* s32 = reinterpret_cast<const uint32_t*>(stage);
+                                    w0 = s32[(2 * (rl + h)) * (n / 2) + c];
+                                    w1 = s32[(2 * (rl + h) + 1) * (n / 2) + c];
+                                } else {
+                                    w0 = __ldg(reinterpret_cast<const uint32_t*>(base + (int64_t)(2 * (r + h)) * n + 2 * c));
+                                    w1 = __ldg(reinterpret_cast<const uint32_t*>(base + (int64_t)(2 * (r + h) + 1) * n + 2 * c));
+                                }
                                 iv[h] = (int32_t)(lo16(w0) + hi16(w0) + lo16(w1) + hi16(w1));
                             }
+                        } else if (STAGED) {
+                            iv[0] = (int32_t)stage[rl * n + c];
+                            if (has1) iv[1] = (int32_t)stage[(rl + 1) * n + c];
                         } else {
                             iv[0] = (int32_t)__ldg(base + (int64_t)r * n + c);
                             if (has1) iv[1] = (int32_t)__ldg(base + (int64_t)(r + 1) * n + c);
@@ -274,6 +332,10 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
         }
         }
         __syncthreads();
+        if (STAGED && tid == 0 && r0 + kRC < mc) {
+            fence_async_smem();  // this chunk's reads of the stage come before the next copies
+            issue_chunk(r0 + kRC);
+        }
         if constexpr (!PLANES) {
         fft4_fwd<N>(buf, LD, nfft, tw, tid, nthr);
         // Two real rows were packed as one complex row: split the spectra.

@@ -250,7 +250,7 @@ moco_status prepare_template(ShapePlan& sp, const void* tmpl_dev, cudaStream_t s
     if (sp.has_fft)
         e = launch_frame_rows(sp.Nc, sp.f32, sp.tmpl, 0, 1, sp.desc.m, sp.desc.n, sp.levels, sp.mc, sp.nc,
                               sp.coff_i, sp.coff_f, sp.twc, sp.X, sp.x_fstride, sp.ldx, sp.rowE, sp.colE, sp.tot,
-                              sp.corners, sp.wm1, st);
+                              sp.corners, sp.wm1, sp.dev_err, st);
     else
         e = launch_frame_planes(sp.f32, sp.tmpl, 0, 1, sp.desc.m, sp.desc.n, sp.levels, sp.mc, sp.nc, sp.coff_i,
                                 sp.coff_f, sp.twc, sp.rowE, sp.colE, sp.tot, sp.corners, sp.wm1, sp.planes_hi,
@@ -307,7 +307,7 @@ moco_status search_group(ShapePlan& sp, const uint16_t* frames, int64_t g, doubl
     P.begin(K_FRAME_ROWS, st);
     cudaError_t e = launch_frame_rows(sp.Nc, false, frames, (int64_t)m * n, g, m, n, sp.levels, sp.mc, sp.nc,
                                       sp.coff_i, nullptr, sp.twc, sp.X, sp.x_fstride, sp.ldx, sp.rowE, sp.colE,
-                                      sp.tot, sp.corners, sp.wm1, st);
+                                      sp.tot, sp.corners, sp.wm1, sp.dev_err, st);
     P.end(st);
     if (e != cudaSuccess) return cuda_fail(e, "k_frame_rows");
     P.begin(K_ENERGY, st);

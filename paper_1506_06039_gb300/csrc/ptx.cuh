@@ -27,7 +27,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsign
             : "memory");
         if (ok) return true;
         if (clock64() - t0 > (2ll << 30)) {
-            atomicExch(err, 1u);
+            if (err) atomicExch(err, 1u);
             return false;
         }
     }
