@@ -589,15 +589,37 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
     for (int p0 = 0; p0 < npairs; p0 += kInvPC) {
         const int np = min(kInvPC, npairs - p0);
         __syncthreads();
-        for (int task = tid; task < np * N; task += nthr) {
-            const int pi = task / N, k = task - pi * N;
-            const int ra = 2 * (p0 + pi), rb = ra + 1;
-            const int kk = (k <= NH) ? k : N - k;
-            float2 A = ys[(int64_t)ra * ncv + kk];
-            float2 B = (rb < W) ? ys[(int64_t)rb * ncv + kk] : make_float2(0.f, 0.f);
-            if (k == 0 || k == NH) { A.y = 0.f; B.y = 0.f; }
-            if (k > NH) { A.y = -A.y; B.y = -B.y; }
-            buf[pi * LD + sk<N>(spec_pos<N>(k))] = make_float2(A.x - B.y, A.y + B.x);
+        // Two real rows ra, rb = ra + 1 as one complex row: Z[k] = A[k] + i B[k]
+        // from the half spectra (k <= N/2; A[N-k] = conj A[k]). Each stored
+        // value is read once; four tasks' loads are issued before any store.
+        constexpr int NK = NH + 1;
+        const int ntask = np * NK;
+        for (int t0 = tid; t0 < ntask; t0 += 4 * nthr) {
+            float2 A[4], B[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int task = t0 + q * nthr;
+                A[q] = make_float2(0.f, 0.f);
+                B[q] = make_float2(0.f, 0.f);
+                if (task < ntask) {
+                    const int pi = task / NK, kk = task - pi * NK;
+                    const int ra = 2 * (p0 + pi), rb = ra + 1;
+                    A[q] = ys[(int64_t)ra * ncv + kk];
+                    if (rb < W) B[q] = ys[(int64_t)rb * ncv + kk];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int task = t0 + q * nthr;
+                if (task < ntask) {
+                    const int pi = task / NK, kk = task - pi * NK;
+                    float2 a = A[q], b = B[q];
+                    if (kk == 0 || kk == NH) { a.y = 0.f; b.y = 0.f; }
+                    buf[pi * LD + sk<N>(spec_pos<N>(kk))] = make_float2(a.x - b.y, a.y + b.x);
+                    if (kk != 0 && kk != NH)  // k = N - kk: conj A + i conj B
+                        buf[pi * LD + sk<N>(spec_pos<N>(N - kk))] = make_float2(a.x + b.y, b.x - a.y);
+                }
+            }
         }
         __syncthreads();
         fft4_inv<N>(buf, LD, np, tw, tid, nthr);
