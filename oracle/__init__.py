@@ -69,6 +69,8 @@ def lib():
             L.oracle_median.argtypes = [P, i32]
             L.oracle_softmin_loss.restype = dbl
             L.oracle_softmin_loss.argtypes = [P, i64, P, i32, i32, i32, P, P, P, P, i32]
+            L.oracle_apply_shifts.restype = None
+            L.oracle_apply_shifts.argtypes = [P, i64, i32, i32, P, ctypes.c_uint16, P, P]
             _lib = L
     return _lib
 
@@ -179,3 +181,17 @@ def softmin_loss(frames, template, w, tau, grad_template=False, grad_frames=Fals
     L = lib().oracle_softmin_loss(_p(frames), T, _p(template), m, n, w, _p(tau), _p(lf), _p(gb),
                                   _p(ga), nthreads)
     return float(L), lf, gb, ga
+
+
+def apply_shifts(frames, shifts, fill=0, corrected=True, mean=True):
+    """Corrected frames (T, m, n) uint16 and the corrected mean image (m, n)
+    FP64 (see moco_oracle.c); returns (corrected or None, mean or None)."""
+    frames = _c(frames, np.uint16)
+    if frames.ndim == 2:
+        frames = frames[None]
+    T, m, n = frames.shape
+    shifts = _c(shifts, np.int32).reshape(T, 2)
+    out = np.empty((T, m, n), np.uint16) if corrected else None
+    mu = np.empty((m, n)) if mean else None
+    lib().oracle_apply_shifts(_p(frames), T, m, n, _p(shifts), int(fill), _p(out), _p(mu))
+    return out, mu

@@ -24,6 +24,12 @@
  *   - Ties (the paper is silent): among equal f the shift with the smallest
  *     |s| + |t| wins, then the smallest s, then the smallest t. Costs are
  *     compared as exact rationals S1 * A2 vs S2 * A1 in 128-bit integers.
+ *   - Correction (Section 2: the found shifts "motion correct" the video; the
+ *     paper gives no formula, so the definition below is this project's
+ *     reading): corrected[f][i][j] = a_f[i + s_f][j + t_f] where that pixel
+ *     lies in the frame, else a fill value; the corrected mean image averages,
+ *     per pixel, the frames whose source pixel lies in the frame (exact integer
+ *     sum / count in FP64; the fill value where no frame covers the pixel).
  *   - Soft-min and its gradient (not in the paper; the differentiable form):
  *     L_f = -tau_f log sum_{s,t} exp(-f_{s,t} / tau_f), tau_f given, in FP64;
  *     the gradient is the chain rule through Section 2's f.
@@ -362,4 +368,36 @@ double oracle_softmin_loss(const double *frames, int64_t T, const double *tmpl, 
         free(gb);
     }
     return total;
+}
+
+/* ---- Correction: apply the found shifts (Section 2, "motion corrected") ---- */
+
+/* corrected[f][i][j] = frames[f][i+s_f][j+t_f] when 0 <= i+s_f < m and
+ * 0 <= j+t_f < n, else fill. mean[i][j] = (sum of the in-frame source pixels
+ * over f) / (their count), in FP64 from the exact integer sum; fill where the
+ * count is 0. Either output may be NULL. */
+void oracle_apply_shifts(const uint16_t *frames, int64_t T, int m, int n, const int32_t *shifts,
+                         uint16_t fill, uint16_t *corrected, double *mean) {
+    uint64_t *sum = mean ? (uint64_t *)calloc((size_t)m * n, sizeof(uint64_t)) : NULL;
+    int64_t *cnt = mean ? (int64_t *)calloc((size_t)m * n, sizeof(int64_t)) : NULL;
+    for (int64_t f = 0; f < T; ++f) {
+        const int s = shifts[2 * f], t = shifts[2 * f + 1];
+        const uint16_t *a = frames + f * (int64_t)m * n;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < n; ++j) {
+                const int si = i + s, sj = j + t;
+                const int inside = si >= 0 && si < m && sj >= 0 && sj < n;
+                const uint16_t v = inside ? a[(int64_t)si * n + sj] : fill;
+                if (corrected) corrected[(f * m + i) * (int64_t)n + j] = v;
+                if (mean && inside) {
+                    sum[(int64_t)i * n + j] += v;
+                    cnt[(int64_t)i * n + j] += 1;
+                }
+            }
+    }
+    if (mean)
+        for (int64_t p = 0; p < (int64_t)m * n; ++p)
+            mean[p] = cnt[p] ? (double)sum[p] / (double)cnt[p] : (double)fill;
+    free(sum);
+    free(cnt);
 }
