@@ -160,6 +160,26 @@ moco_status moco_align_host(moco_plan_t plan, int32_t shape_idx, const uint16_t*
  * flag then cleared); MOCO_OK otherwise. */
 moco_status moco_plan_status(moco_plan_t plan);
 
+/* The correction step: applies each frame's shift (Section 2: the found
+ * shifts "motion correct" the video; the paper gives no formula, this is the
+ * library's definition). For frames_dev [T][m][n] uint16 (shape shape_idx,
+ * n % 8 == 0, 16-byte aligned) and shifts_dev [T][2] int32 (s, t) as
+ * returned by moco_align_stack (any values; a shift past the frame leaves no
+ * source pixel):
+ *   corrected_dev [T][m][n] uint16 (nullable, 16-byte aligned):
+ *       corrected[f][i][j] = frames[f][i + s_f][j + t_f] where 0 <= i + s_f < m
+ *       and 0 <= j + t_f < n, else fill;
+ *   mean_dev [m][n] double (nullable): per pixel, the sum of the in-frame
+ *       source pixels over all frames divided by their count, from the exact
+ *       integer sum in FP64; fill where no frame covers the pixel (all of the
+ *       image when T == 0).
+ * Enqueued on `stream`; no allocation (the sums live in the plan), no
+ * synchronisation. Two calls on one shape must not overlap on the GPU when
+ * both ask for the mean (they share the plan's sums). */
+moco_status moco_apply_shifts(moco_plan_t plan, int32_t shape_idx, const uint16_t* frames_dev, int64_t T,
+                              const int32_t* shifts_dev, uint16_t fill, uint16_t* corrected_dev, double* mean_dev,
+                              void* stream);
+
 /* The full-resolution 3x3 refinement on its own, allocating nothing (the
  * paper has no counterpart: this exists for callers that cannot call
  * cudaMalloc, such as code inside a host application that owns all device

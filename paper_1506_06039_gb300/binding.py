@@ -32,7 +32,7 @@ EXPORTS = (
     "moco_plan", "moco_set_template", "moco_align_stack", "moco_cost_surface", "moco_softmin",
     "moco_cost_backward", "moco_align_host", "moco_plan_query", "moco_plan_destroy",
     "moco_status_string", "moco_last_error", "moco_profile_enable", "moco_profile_read", "moco_plan_status",
-    "moco_jitter_noalloc",
+    "moco_jitter_noalloc", "moco_apply_shifts",
 )
 
 
@@ -98,6 +98,7 @@ def lib():
             L.moco_profile_enable.argtypes = [P, i32]
             L.moco_plan_status.argtypes = [P]
             L.moco_jitter_noalloc.argtypes = [P, i64, i32, i32, P, P, P, P]
+            L.moco_apply_shifts.argtypes = [P, i32, P, i64, P, ctypes.c_uint16, P, P, P]
             L.moco_profile_read.argtypes = [P, ctypes.POINTER(MocoKernelStat), i32, ctypes.POINTER(i32), i32]
             for name in EXPORTS:
                 if name not in ("moco_status_string", "moco_last_error"):
@@ -196,6 +197,22 @@ def moco_cost_surface(plan, shape_idx, frames, cost, stream=None):
     _need(cost, torch.float64, "cost")
     T = frames.shape[0] if frames.dim() == 3 else 1
     _check(lib().moco_cost_surface(plan, shape_idx, _ptr(frames), T, _ptr(cost), _stream(stream)))
+
+
+def moco_apply_shifts(plan, shape_idx, frames, shifts, fill=0, corrected=None, mean=None, stream=None):
+    """Corrected frames (uint16, like frames) and/or the corrected mean image
+    (float64 [m, n]) into the given tensors (either may be None)."""
+    import torch
+    _need(frames, torch.uint16, "frames")
+    _need(shifts, torch.int32, "shifts")
+    if corrected is not None:
+        _need(corrected, torch.uint16, "corrected")
+    if mean is not None:
+        _need(mean, torch.float64, "mean")
+    T = frames.shape[0] if frames.dim() == 3 else 1
+    _check(lib().moco_apply_shifts(plan, shape_idx, _ptr(frames), T, _ptr(shifts), int(fill),
+                                   corrected.data_ptr() if corrected is not None else None,
+                                   mean.data_ptr() if mean is not None else None, _stream(stream)))
 
 
 def moco_softmin(plan, shape_idx, cost, tau_scale, loss, weights, stream=None):
@@ -314,6 +331,15 @@ class Plan:
         if best_cost or margin:
             return shifts, bc, mg
         return shifts
+
+    def apply_shifts(self, frames, shifts, fill=0, corrected=True, mean=True, shape_idx=0, stream=None):
+        """(corrected frames or None, corrected mean image float64 or None)."""
+        import torch
+        m, n = int(self.shapes[shape_idx]["m"]), int(self.shapes[shape_idx]["n"])
+        out = torch.empty_like(frames) if corrected else None
+        mu = torch.empty((m, n), dtype=torch.float64, device=frames.device) if mean else None
+        moco_apply_shifts(self.handle, shape_idx, frames, shifts, fill, out, mu, stream)
+        return out, mu
 
     def cost_surface(self, frames, shape_idx=0, stream=None):
         import torch

@@ -39,6 +39,12 @@ cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg,
                           int n, const u64* bsq, const int32_t* coarse, int32_t* shifts, double* ffinal, u64* acc,
                           unsigned int* ticket, cudaStream_t st);
 
+// The correction step: corrected frames and/or the corrected mean image;
+// sum (u64) and cnt (u32) are m*n scratch, cleared here.
+cudaError_t launch_apply(const uint16_t* frames, int64_t fstride, int64_t T, int m, int n, const int32_t* shifts,
+                         uint16_t fill, uint16_t* corrected, double* mean, u64* sum, unsigned int* cnt,
+                         int num_sms, cudaStream_t st);
+
 // P[(m+1) x (n+1)], P[i][j] = sum over i' < i, j' < j of tmpl^2 (exact u64).
 cudaError_t launch_sq_prefix(const uint16_t* tmpl, int m, int n, u64* P, cudaStream_t st);
 

@@ -17,7 +17,7 @@
 namespace moco {
 
 const char* const kKernelNames[K_COUNT] = {"k_frame_rows", "k_energy", "k_cols", "k_rows_inv", "k_jitter",
-                                           "k_copy_shifts", "k_softmin", "k_backward", "k_direct"};
+                                           "k_copy_shifts", "k_softmin", "k_backward", "k_direct", "k_apply"};
 
 thread_local std::string g_last_error;
 
@@ -165,6 +165,8 @@ moco_status allocate_shape(ShapePlan& sp) {
     c.add(&sp.grad_acc, (size_t)(m * n * 4));
     c.add(&sp.grad_Q, (size_t)(W * W * 4));
     if (sp.levels && !sp.f32) c.add(&sp.bsq, (size_t)(m + 1) * (n + 1) * 8);
+    c.add(&sp.apply_sum, (size_t)m * n * 8);
+    c.add(&sp.apply_cnt, (size_t)m * n * 4);
     sp.x_fstride = (int64_t)sp.ncv * sp.ldx;
     sp.y_fstride = W * sp.ncv;
     sp.bytes = c.off;
@@ -521,6 +523,34 @@ moco_status moco_align_stack(moco_plan_t plan, const moco_stack* stacks, int32_t
                                      s.margin_dev, s.final_cost_dev, st);
         if (r != MOCO_OK) return r;
     }
+    return MOCO_OK;
+}
+
+moco_status moco_apply_shifts(moco_plan_t plan, int32_t shape_idx, const uint16_t* frames_dev, int64_t T,
+                              const int32_t* shifts_dev, uint16_t fill, uint16_t* corrected_dev, double* mean_dev,
+                              void* stream) {
+    if (!plan) return fail(MOCO_ERR_INVALID_ARG, "null plan");
+    if (shape_idx < 0 || shape_idx >= (int)plan->shapes.size()) return fail(MOCO_ERR_INVALID_ARG, "bad shape_idx");
+    if (T < 0) return fail(MOCO_ERR_INVALID_ARG, "T < 0");
+    ShapePlan& sp = plan->shapes[shape_idx];
+    const int m = sp.desc.m, n = sp.desc.n;
+    if (n % 8 != 0) return fail(MOCO_ERR_UNSUPPORTED, "moco_apply_shifts needs n % 8 == 0");
+    if (T == 0 && mean_dev == nullptr) return MOCO_OK;
+    if (T > 0 && (!frames_dev || !shifts_dev)) return fail(MOCO_ERR_INVALID_ARG, "null frames or shifts");
+    if (T > 0 && !aligned16(frames_dev)) return fail(MOCO_ERR_INVALID_ARG, "frames must be 16-byte aligned");
+    if (corrected_dev && !aligned16(corrected_dev))
+        return fail(MOCO_ERR_INVALID_ARG, "corrected frames must be 16-byte aligned");
+    DeviceGuard guard(plan->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, plan->device);
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
+    sp.prof->begin(K_APPLY, st);
+    e = launch_apply(frames_dev, (int64_t)m * n, T, m, n, shifts_dev, fill, corrected_dev, mean_dev, sp.apply_sum,
+                     sp.apply_cnt, sms, st);
+    sp.prof->end(st);
+    if (e != cudaSuccess) return cuda_fail(e, "k_apply");
     return MOCO_OK;
 }
 

@@ -14,7 +14,7 @@ namespace moco {
 // Optional per-kernel timing: CUDA events recorded on the launching stream
 // around every kernel launch (enabled by moco_profile_enable).
 enum KernelId { K_FRAME_ROWS = 0, K_ENERGY, K_COLS, K_ROWS_INV, K_JITTER, K_COPY_SHIFTS, K_SOFTMIN,
-                K_BACKWARD, K_DIRECT, K_COUNT };
+                K_BACKWARD, K_DIRECT, K_APPLY, K_COUNT };
 extern const char* const kKernelNames[K_COUNT];
 
 struct Profiler {
@@ -63,6 +63,8 @@ struct ShapePlan {
     double* Sb = nullptr;
     double* inv_area = nullptr;
     u64* bsq = nullptr;  // with a level: prefix table of b^2, (m+1) x (n+1)
+    u64* apply_sum = nullptr;           // m x n: the correction step's per-pixel sums
+    unsigned int* apply_cnt = nullptr;  // m x n: and counts
     // direct form
     float* bprime = nullptr;        // mc x nc offset template
     void* dtiles = nullptr;         // Toeplitz tiles (hi, lo)
