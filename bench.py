@@ -28,6 +28,7 @@ if ROOT not in sys.path:
 METRIC = "frames/s aligned (256², w=32, full search+upsample), plain vs chosen form"
 UNIT = "frames/s"
 FP32_LANES_PER_SM = 128
+INT_MAD_LANES_PER_SM = 64  # 32-bit integer multiply-add (and dp2a) pipe
 NUM_SMS = 152
 SM_MAX_MHZ = 2070.0
 
@@ -46,6 +47,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-correction", action="store_true", help="skip the correction-step measurement")
+    p.add_argument("--correction-steps", type=int, default=50)
     return p.parse_args()
 
 
@@ -145,19 +148,28 @@ def fft_flops(N):
 
 
 def kernel_work(info, wl, frames):
-    """Per-kernel algorithmic work for `frames` frames: (bytes, flops)."""
+    """Per-kernel algorithmic work for `frames` frames: (bytes, flops, exact
+    integer multiply-adds)."""
     m, n, w = wl.m, wl.n, wl.w
     mc, nc, Nr, Nc = info["mc"], info["nc"], info["fft_rows"], info["fft_cols"]
     W = 2 * w - 1
     ncv = Nc // 2 + 1
     per = {
-        "k_frame_rows": (2 * m * n + 8 * ncv * mc, (mc / 2) * fft_flops(Nc)),
-        "k_energy": (8 * (mc + nc) + 8 * W * W, 0.0),
-        "k_cols": (8 * ncv * mc + 8 * W * ncv, ncv * (2 * fft_flops(Nr) + 6 * Nr)),
-        "k_rows_inv": (8 * W * ncv + 8 * W * W, math.ceil(W / 2) * fft_flops(Nc)),
-        "k_jitter": (2 * m * n, 0.0),
+        "k_frame_rows": (2 * m * n + 8 * ncv * mc, (mc / 2) * fft_flops(Nc), 0.0),
+        "k_energy": (8 * (mc + nc) + 8 * W * W, 0.0, 0.0),
+        "k_cols": (8 * ncv * mc + 8 * W * ncv, ncv * (2 * fft_flops(Nr) + 6 * Nr), 0.0),
+        "k_rows_inv": (8 * W * ncv + 8 * W * W, math.ceil(W / 2) * fft_flops(Nc), 0.0),
+        # nine exact squared differences per full-resolution pixel
+        "k_jitter": (2 * m * n, 0.0, 9.0 * m * n),
     }
-    return {k: (b * frames, f * frames) for k, (b, f) in per.items()}
+    return {k: (b * frames, f * frames, i * frames) for k, (b, f, i) in per.items()}
+
+
+# DRAM bytes (read + write) per frame of the current kernels, from one ncu
+# capture of 512 frames of the std512 workload (profiles/kernels_std512_fft.md),
+# scaled to a launch by its frame count.
+TRAFFIC_PER_FRAME = {"k_frame_rows": (268.626432e6 + 123.891712e6) / 512,
+                     "k_jitter": (261.744896e6 + 4.0e6) / 512}
 
 
 def roofline(profile, info, wl, frames_per_step, steps, peaks, clocks):
@@ -166,22 +178,35 @@ def roofline(profile, info, wl, frames_per_step, steps, peaks, clocks):
     name = max(profile, key=lambda k: profile[k][1])
     launches, ms = profile[name]
     work = kernel_work(info, wl, frames_per_step * steps)
-    byts, flops = work.get(name, (0.0, 0.0))
+    byts, flops, imads = work.get(name, (0.0, 0.0, 0.0))
     dur_s = ms / 1e3
     hbm = peaks.get("hbm_gbs", 6800.0)
     fp32_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s at max clock
-    frac_h = (byts / dur_s / 1e9) / hbm if byts else 0.0
-    frac_a = (flops / dur_s / 1e12) / fp32_peak if flops else 0.0
-    if frac_a >= frac_h:
-        rf = {"bound": "alu", "achieved": flops / launches / (dur_s / launches) / 1e12, "peak": fp32_peak,
-              "unit": "TFLOP/s", "frac": frac_a,
-              "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"}
+    imad_peak = NUM_SMS * INT_MAD_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12  # T multiply-adds/s
+    fracs = {"hbm": (byts / dur_s / 1e9) / hbm if byts else 0.0,
+             "fp32": (flops / dur_s / 1e12) / fp32_peak if flops else 0.0,
+             "int": (imads / dur_s / 1e12) / imad_peak if imads else 0.0}
+    bound = max(fracs, key=fracs.get)
+    if bound == "fp32":
+        rf = {"bound": "alu", "achieved": flops / dur_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+              "frac": fracs["fp32"], "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)"}
+    elif bound == "int":
+        rf = {"bound": "alu", "achieved": imads / dur_s / 1e12, "peak": imad_peak, "unit": "T int-MAD/s",
+              "frac": fracs["int"],
+              "peak_source": "32-bit integer multiply-add pipe: 152 SMs x 64 lanes x 2070 MHz (derived)"}
     else:
-        rf = {"bound": "hbm", "achieved": byts / dur_s / 1e9, "peak": hbm, "unit": "GB/s", "frac": frac_h,
+        rf = {"bound": "hbm", "achieved": byts / dur_s / 1e9, "peak": hbm, "unit": "GB/s", "frac": fracs["hbm"],
               "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    per_launch_frames = frames_per_step * steps / launches
+    traffic = TRAFFIC_PER_FRAME.get(name)
     rf.update({"kernel": name, "launches": launches, "avg_launch_ms": ms / launches,
-               "share": ms / total, "traffic": None,
-               "algorithmic_per_launch": {"bytes": byts / launches, "flops": flops / launches}})
+               "share": ms / total,
+               "traffic": traffic * per_launch_frames if traffic else None,
+               "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum on 512 frames, scaled to "
+                                  "%d frames per launch" % per_launch_frames) if traffic else None,
+               "algorithmic_per_launch": {"bytes": byts / launches, "flops": flops / launches,
+                                          "int_mads": imads / launches},
+               "fractions": fracs})
     return rf
 
 
@@ -324,6 +349,10 @@ def main():
                "h2d_bytes_per_step": int(wl.T * wl.m * wl.n * 2), "d2h_bytes_per_step": int(wl.T * 8),
                "steps": args.e2e_steps, "api": "moco_align_host (pinned host buffers)"}
 
+    correction = None
+    if not args.no_correction:
+        correction = measure_correction(plan, st.frames, shifts, wl, args.correction_steps, peaks, pg)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         idx = np.random.default_rng(0).choice(wl.T, 256, replace=False)
@@ -338,12 +367,49 @@ def main():
                "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic", "config": cfg,
                "plain_form": {"form": "fft_fp32", "value": value if form_name == "fft_fp32" else None},
                "roofline": rf, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clocks,
+               "clocks": clocks, "correction": correction,
                "kernels": {k: {"launches": l, "ms": t, "share": t / tot_ms} for k, (l, t) in profile.items()}}
         print(json.dumps(out), flush=True)
     plan.close()
     if pg:
         pg.destroy_process_group()
+
+
+def measure_correction(plan, frames, shifts, wl, steps, peaks, pg):
+    """The correction step on the aligned stack (corrected frames + mean
+    image), timed alone with CUDA events on the launching stream."""
+    import torch
+    from paper_1506_06039_gb300 import moco_apply_shifts
+    corrected = torch.empty_like(frames)
+    mean = torch.empty((wl.m, wl.n), dtype=torch.float64, device=frames.device)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        moco_apply_shifts(plan.handle, 0, frames, shifts, 100, corrected, mean, stream)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), pg, "cuda") / steps
+    world = pg.get_world_size() if pg else 1
+    byts = 4.0 * wl.m * wl.n * wl.T  # read each frame once, write its corrected copy
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    del corrected
+    return {"metric": "frames/s corrected (corrected stack + corrected mean image)",
+            "value": wl.T * world / (ms / 1e3), "unit": "frames/s", "ms_per_step": ms, "steps": steps,
+            "roofline": {"bound": "hbm", "kernel": "k_apply", "achieved": byts / (ms / 1e3) / 1e9, "peak": hbm,
+                         "unit": "GB/s", "frac": byts / (ms / 1e3) / 1e9 / hbm, "traffic": None,
+                         "algorithmic_per_launch": {"bytes": byts},
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+            "api": "moco_apply_shifts (device buffers; fill 100)"}
 
 
 def run_mixed(args, world, rank, local):

@@ -141,7 +141,11 @@ moco_status resolve_shape(const moco_shape& d, ShapePlan& sp) {
         const int64_t target = 1ll << 30;
         sp.group = (int)std::max<int64_t>(1, std::min<int64_t>(2048, target / per_frame_scratch_bytes(sp)));
     }
-    sp.stage_frames = std::min(sp.group, 512);
+    // Host staging chunks of ~64 MiB: the copy engine (the bound of the
+    // host path) keeps streaming while each chunk is searched, and the last
+    // chunk's search after the final copy stays short.
+    const int64_t frame_bytes = (int64_t)d.m * d.n * 2;
+    sp.stage_frames = (int)std::max<int64_t>(16, std::min<int64_t>(sp.group, (64ll << 20) / frame_bytes));
     return MOCO_OK;
 }
 

@@ -51,55 +51,75 @@ k_apply(const uint16_t* __restrict__ frames, int64_t fstride, int64_t T, int m, 
         num[k] = 0;
     }
     const uint32_t fill2 = (uint32_t)fill | ((uint32_t)fill << 16);
-    for (int64_t f = f_begin; f < f_end; ++f) {
-        // Shifts beyond the frame are clamped: every source pixel is outside.
-        const int s = max(-m, min(m, shifts[2 * f])), t = max(-n, min(n, shifts[2 * f + 1]));
-        const int r = i + s;
-        const int c = j0 + t;                 // first source column
-        const int o = c & 7, cb = c - o;      // aligned chunk start (multiple of 8)
-        uint4 q0 = make_uint4(0, 0, 0, 0), q1 = make_uint4(0, 0, 0, 0);
-        const bool row_in = r >= 0 && r < m;
-        if (row_in) {
-            const uint16_t* src = frames + f * fstride + (int64_t)r * n;
-            if (cb >= 0 && cb + 8 <= n) q0 = __ldg(reinterpret_cast<const uint4*>(src + cb));
-            if (o != 0 && cb + 8 >= 0 && cb + 16 <= n) q1 = __ldg(reinterpret_cast<const uint4*>(src + cb + 8));
-        }
-        uint32_t v[4];
-        switch (o) {
-            case 0: apply_extract<0>(q0, q1, v); break;
-            case 1: apply_extract<1>(q0, q1, v); break;
-            case 2: apply_extract<2>(q0, q1, v); break;
-            case 3: apply_extract<3>(q0, q1, v); break;
-            case 4: apply_extract<4>(q0, q1, v); break;
-            case 5: apply_extract<5>(q0, q1, v); break;
-            case 6: apply_extract<6>(q0, q1, v); break;
-            default: apply_extract<7>(q0, q1, v); break;
-        }
-        // Pixels whose source lies outside the frame take the fill value.
-        uint32_t inside = 0;  // bit k: pixel j0 + k has an in-frame source
-        if (row_in) {
+    // Four frames per iteration: all their loads are issued before any is used.
+    constexpr int kF = 4;
+    for (int64_t fb = f_begin; fb < f_end; fb += kF) {
+        uint4 q0[kF], q1[kF];
+        int c[kF];
+        bool row_in[kF];
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (c + k >= 0 && c + k < n) inside |= 1u << k;
-        }
-        if (inside != 0xffu) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t keep = (((inside >> (2 * k)) & 1u) ? 0x0000ffffu : 0u) |
-                                      (((inside >> (2 * k + 1)) & 1u) ? 0xffff0000u : 0u);
-                v[k] = (v[k] & keep) | (fill2 & ~keep);
+        for (int u = 0; u < kF; ++u) {
+            const int64_t f = fb + u;
+            q0[u] = make_uint4(0, 0, 0, 0);
+            q1[u] = make_uint4(0, 0, 0, 0);
+            row_in[u] = false;
+            c[u] = 0;
+            if (f < f_end) {
+                // Shifts beyond the frame are clamped: every source pixel is outside.
+                const int s = max(-m, min(m, shifts[2 * f])), t = max(-n, min(n, shifts[2 * f + 1]));
+                const int r = i + s;
+                c[u] = j0 + t;  // first source column
+                const int o = c[u] & 7, cb = c[u] - o;
+                row_in[u] = r >= 0 && r < m;
+                if (row_in[u]) {
+                    const uint16_t* src = frames + f * fstride + (int64_t)r * n;
+                    if (cb >= 0 && cb + 8 <= n) q0[u] = __ldg(reinterpret_cast<const uint4*>(src + cb));
+                    if (o != 0 && cb + 8 >= 0 && cb + 16 <= n)
+                        q1[u] = __ldg(reinterpret_cast<const uint4*>(src + cb + 8));
+                }
             }
         }
-        if (corrected)
-            *reinterpret_cast<uint4*>(corrected + f * (int64_t)m * n + (int64_t)i * n + j0) =
-                make_uint4(v[0], v[1], v[2], v[3]);
-        if (sum) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const uint32_t in = (inside >> k) & 1u;
-                const uint32_t x = (k & 1) ? (v[k / 2] >> 16) : (v[k / 2] & 0xffffu);
-                acc[k] += in ? x : 0u;
-                num[k] += in;
+        for (int u = 0; u < kF; ++u) {
+            const int64_t f = fb + u;
+            if (f >= f_end) break;
+            uint32_t v[4];
+            switch (c[u] & 7) {
+                case 0: apply_extract<0>(q0[u], q1[u], v); break;
+                case 1: apply_extract<1>(q0[u], q1[u], v); break;
+                case 2: apply_extract<2>(q0[u], q1[u], v); break;
+                case 3: apply_extract<3>(q0[u], q1[u], v); break;
+                case 4: apply_extract<4>(q0[u], q1[u], v); break;
+                case 5: apply_extract<5>(q0[u], q1[u], v); break;
+                case 6: apply_extract<6>(q0[u], q1[u], v); break;
+                default: apply_extract<7>(q0[u], q1[u], v); break;
+            }
+            // Pixels whose source lies outside the frame take the fill value.
+            uint32_t inside = 0;  // bit k: pixel j0 + k has an in-frame source
+            if (row_in[u]) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (c[u] + k >= 0 && c[u] + k < n) inside |= 1u << k;
+            }
+            if (inside != 0xffu) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t keep = (((inside >> (2 * k)) & 1u) ? 0x0000ffffu : 0u) |
+                                          (((inside >> (2 * k + 1)) & 1u) ? 0xffff0000u : 0u);
+                    v[k] = (v[k] & keep) | (fill2 & ~keep);
+                }
+            }
+            if (corrected)
+                *reinterpret_cast<uint4*>(corrected + f * (int64_t)m * n + (int64_t)i * n + j0) =
+                    make_uint4(v[0], v[1], v[2], v[3]);
+            if (sum) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t in = (inside >> k) & 1u;
+                    const uint32_t x = (k & 1) ? (v[k / 2] >> 16) : (v[k / 2] & 0xffffu);
+                    acc[k] += in ? x : 0u;
+                    num[k] += in;
+                }
             }
         }
     }
