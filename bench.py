@@ -276,6 +276,8 @@ def main():
         return run_reference(args, world, rank)
     if args.workload == "mixed":
         return run_mixed(args, world, rank, local)
+    if args.workload == "refine256":
+        return run_grad(args, world, rank, local)
 
     import numpy as np
     import torch
@@ -468,6 +470,67 @@ def run_mixed(args, world, rank, local):
                           "forms": {"fft_fp32": forms.count(1), "direct_bf16x3": forms.count(2)},
                           "graph": "one captured moco_align_stack call"},
                "clocks": clocks}
+        print(json.dumps(out), flush=True)
+    plan.close()
+
+
+def run_grad(args, world, rank, local):
+    """The differentiable form: per step, the soft-min loss of every frame and
+    its gradient with respect to a float template (set template, cost
+    surface, soft-min, adjoint), all through the C ABI."""
+    import torch
+    from paper_1506_06039_gb300 import (build, moco_cost_backward, moco_cost_surface, moco_set_template,
+                                        moco_softmin, synth)
+    from paper_1506_06039_gb300.autograd import softmin_plan
+
+    build.build()
+    torch.cuda.set_device(local)
+    wl = synth.WORKLOADS["refine256"]
+    T = args.frames or wl.T
+    st = synth.make_stack_torch(wl.m, wl.n, T, wl.nblobs, wl.shift_max, rank_seed(wl.seed, rank), template="clean")
+    gen = torch.Generator(device="cuda").manual_seed(wl.seed)
+    tmpl = st.frames.float().mean(0) + 50.0 * torch.randn((wl.m, wl.n), generator=gen, device="cuda")
+    plan = softmin_plan(st.frames, tmpl, wl.w)
+    W = 2 * wl.w - 1
+    cost = torch.empty((T, W, W), dtype=torch.float64, device="cuda")
+    loss = torch.empty(T, dtype=torch.float64, device="cuda")
+    weights = torch.empty((T, W, W), dtype=torch.float32, device="cuda")
+    grad = torch.zeros((wl.m, wl.n), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        moco_set_template(plan.handle, 0, tmpl, stream)
+        moco_cost_surface(plan.handle, 0, st.frames, cost, stream)
+        moco_softmin(plan.handle, 0, cost, 0.05, loss, weights, stream)
+        moco_cost_backward(plan.handle, 0, st.frames, weights, grad, None, 1.0, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    plan.profile(max_launches=args.steps * 64 + 64)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    profile = plan.profile_read(reset=True)
+    plan.profile(0)
+    if rank == 0:
+        tot = sum(t for _, t in profile.values()) or 1.0
+        out = {"metric": "frames/s, soft-min loss and template gradient (differentiable form)",
+               "value": world * T * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+               "config": {"workload": "refine256: %d frames of 256x256, w=16 (31^2 shifts), float template "
+                                      "(mean frame + N(0, 50^2)), tau = 0.05 x median" % T, "frames": T},
+               "gpu_launches": sum(l for l, _ in profile.values()), "clocks": clocks,
+               "kernels": {k: {"launches": l, "ms": t, "share": t / tot} for k, (l, t) in profile.items()}}
         print(json.dumps(out), flush=True)
     plan.close()
 
