@@ -168,8 +168,7 @@ def kernel_work(info, wl, frames):
 # DRAM bytes (read + write) per frame of the current kernels, from one ncu
 # capture of 512 frames of the std512 workload (profiles/kernels_std512_fft.md),
 # scaled to a launch by its frame count.
-TRAFFIC_PER_FRAME = {"k_frame_rows": (268.626432e6 + 123.891712e6) / 512,
-                     "k_jitter": (261.744896e6 + 4.0e6) / 512}
+TRAFFIC_PER_FRAME = {"k_jitter": (261.744896e6 + 4.0e6) / 512}
 
 
 def roofline(profile, info, wl, frames_per_step, steps, peaks, clocks):

@@ -52,6 +52,15 @@ __device__ __forceinline__ u64 sq64(int32_t d) {
     return (u64)a * (u64)a;
 }
 __device__ __forceinline__ uint32_t hi16(uint32_t w) { return w >> 16; }
+// acc + (low half-word of w) + (high half-word of w), one dp2a.
+__device__ __forceinline__ uint32_t add_halves(uint32_t w, uint32_t acc) {
+    asm("dp2a.lo.u32.u32 %0, %1, %2, %0;" : "+r"(acc) : "r"(w), "r"(0x0101u));
+    return acc;
+}
+// acc += d * d exactly (|d| < 2^31), one 32 x 32 -> 64-bit multiply-add.
+__device__ __forceinline__ void add_sq(u64& acc, int32_t d) {
+    asm("mad.wide.s32 %0, %1, %1, %0;" : "+l"(acc) : "r"(d));
+}
 
 // ---------------------------------------------------------------------------
 // k_frame_rows: one CTA per image (frame or template).
@@ -105,6 +114,7 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
     __shared__ Acc red[32];
     __shared__ __align__(8) uint64_t stage_bar;
     __shared__ int s_abort;
+    __shared__ int spos[PLANES ? 1 : N];  // buffer slot of spectral index k
     const uint16_t* stage = reinterpret_cast<const uint16_t*>(smem_raw + frame_rows_smem_base<N, F32IN>(nc));
     // Issues the bulk copies of the chunk at searched row c0 (one thread).
     auto issue_chunk = [&](int c0) {
@@ -130,6 +140,8 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
         }
     }
     for (int i = tid; i < N; i += nthr) tw[i] = tw_g[i];
+    if (!PLANES)
+        for (int k = tid; k < N; k += nthr) spos[k] = sk<N>(spec_pos<N>(k));
     for (int i = tid; i < nc; i += nthr) colacc[i] = 0;
     for (int i = tid; i < kRC; i += nthr) rowacc[i] = 0;
 
@@ -168,6 +180,66 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
                     return;
                 }
             }
+            if constexpr (STAGED) {
+                // Staged uint16 frames (the host guarantees nc <= nthr): one
+                // column c per thread, row pairs p0, p0 + PPI, ... of the chunk.
+                // The 2x2 box sums come from dp2a, the float value from the
+                // exact 2^23 bias (|d| < 2^19), the squares from 64-bit
+                // multiply-adds; an edge row's sum over a warp is two 32-bit
+                // reductions of the 18-bit halves of d^2 (< 2^36).
+                const int c = tid % nc, p0 = tid / nc;
+                if (p0 < PPI) {
+                    const int skc = sk<N>(c);
+                    const bool ecol = c < wm1 || c >= nc - wm1;
+                    const int hw = n >> 1;
+                    const uint32_t* s32 = reinterpret_cast<const uint32_t*>(stage);
+                    const int bias = 0x4B400000 - ci_off;  // float bits of 2^23 + 2^22 + d
+                    for (int pr = p0; pr < nfft; pr += PPI) {
+                        const int rl = 2 * pr;
+                        const bool has1 = rl + 1 < rows;  // the same for the whole warp
+                        int s0, s1;
+                        if (levels) {
+                            const uint32_t* q = s32 + (2 * rl) * hw + c;
+                            s0 = (int)add_halves(q[0], add_halves(q[hw], 0u));
+                            s1 = has1 ? (int)add_halves(q[2 * hw], add_halves(q[3 * hw], 0u)) : ci_off;
+                        } else {
+                            s0 = stage[rl * n + c];
+                            s1 = has1 ? (int)stage[(rl + 1) * n + c] : ci_off;
+                        }
+                        const int d0 = s0 - ci_off, d1 = s1 - ci_off;  // d1 = 0 past the last row
+                        buf[pr * LD + skc] = make_float2(__int_as_float(s0 + bias) - 12582912.0f,
+                                                         __int_as_float(s1 + bias) - 12582912.0f);
+                        add_sq(tacc, d0);
+                        add_sq(tacc, d1);
+                        if (ecol) {
+                            add_sq(colreg[0], d0);
+                            add_sq(colreg[0], d1);
+                        }
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            if (h == 1 && !has1) break;
+                            const int rr = r0 + rl + h;
+                            const bool top = rr < wm1, bot = rr >= mc - wm1;
+                            if (!(top || bot)) continue;
+                            const int dh = h ? d1 : d0;
+                            const u64 eh = (u64)((long long)dh * dh);
+                            if (warp_rows) {
+                                const uint32_t lo = __reduce_add_sync(0xffffffffu, (uint32_t)(eh & 0x3ffffu));
+                                const uint32_t hi = __reduce_add_sync(0xffffffffu, (uint32_t)(eh >> 18));
+                                if ((tid & 31) == 0) atomicAdd(&rowacc[rl + h], ((u64)hi << 18) + lo);
+                            } else {
+                                atomicAdd(&rowacc[rl + h], eh);
+                            }
+                            if (ecol) {
+                                const int ri = top ? rr : rr - (mc - wm1);
+                                const int cj = c >= nc - wm1 ? c - (nc - wm1) : c;
+                                const int q = (bot ? 2 : 0) + (c >= nc - wm1 ? 1 : 0);
+                                corners[(f * 4 + q) * wm1sq + (size_t)ri * wm1 + cj] = (uint32_t)dh;
+                            }
+                        }
+                    }
+                }
+            } else
 #pragma unroll
             for (int slot = 0; slot < 4; ++slot) {
                 if (slot >= CS) break;
@@ -340,10 +412,12 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
         fft4_fwd<N>(buf, LD, nfft, tw, tid, nthr);
         // Two real rows were packed as one complex row: split the spectra.
         constexpr int NH = N / 2 + 1;
-        for (int task = tid; task < NH * nfft; task += nthr) {
-            const int v = task / nfft, fi = task - v * nfft;
-            const float2 zk = buf[fi * LD + sk<N>(spec_pos<N>(v))];
-            const float2 zn = cconj(buf[fi * LD + sk<N>(spec_pos<N>((N - v) % N))]);
+        constexpr int PC = kRC / 2;  // row pairs of a full chunk
+        for (int task = tid; task < NH * PC; task += nthr) {
+            const int v = task / PC, fi = task % PC;
+            if (fi >= nfft) continue;
+            const float2 zk = buf[fi * LD + spos[v]];
+            const float2 zn = cconj(buf[fi * LD + spos[v == 0 ? 0 : N - v]]);
             const float2 x1 = cscale(cadd(zk, zn), 0.5f);
             const float2 d = csub(zk, zn);
             const float2 x2 = make_float2(0.5f * d.y, -0.5f * d.x);
