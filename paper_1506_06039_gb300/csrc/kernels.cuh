@@ -567,8 +567,19 @@ k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* 
 // layout), inverse DFT, and only the 2w-1 rows s in [-(w-1), w-1] kept:
 // Y[f*y_fstride + (s+w-1)*ncv + v]. With SPECTRUM set, the forward transform
 // is written out conjugated and scaled instead (template preparation).
+// Threads of a k_cols CTA: one per task of the wider four-step stage.
+template <int N>
+__host__ __device__ constexpr int cols_threads() {
+    return (kColsVC * (Four<N>::N1 > Four<N>::N2 ? Four<N>::N1 : Four<N>::N2) + 31) / 32 * 32;
+}
+
+template <int N>
+__host__ __device__ constexpr int cols_min_blocks() {
+    return cols_threads<N>() <= 256 ? 4 : (cols_threads<N>() <= 320 ? 3 : 1);
+}
+
 template <int N, bool SPECTRUM>
-__global__ void __launch_bounds__(576)
+__global__ void __launch_bounds__(cols_threads<N>(), cols_min_blocks<N>())
 k_cols(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv,
        const float2* __restrict__ tw_g, const float2* __restrict__ bspec, float2* __restrict__ Y,
        int64_t y_fstride, int wm1, float scale) {
@@ -580,31 +591,54 @@ k_cols(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv
     const int v0 = blockIdx.y * kColsVC, nv = min(kColsVC, ncv - v0);
     const int64_t f = blockIdx.x;
     for (int i = tid; i < 2 * N; i += nthr) tw[i] = tw_g[i];
+    // A thread owns positions i (one slot sk(i)) of all the CTA's columns;
+    // each column's loads are issued before any is stored.
     const float2* xs = X + f * x_fstride + (int64_t)v0 * ldx;
-    for (int task = tid; task < nv * N; task += nthr) {
-        const int vi = task / N, i = task - vi * N;
-        buf[vi * LD + sk<N>(i)] = (i < mc) ? xs[(int64_t)vi * ldx + i] : make_float2(0.f, 0.f);
+    for (int i = tid; i < N; i += nthr) {
+        const int ski = sk<N>(i);
+#pragma unroll
+        for (int v8 = 0; v8 < kColsVC; v8 += 8) {
+            float2 t[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                t[u] = (v8 + u < nv && i < mc) ? xs[(int64_t)(v8 + u) * ldx + i] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (v8 + u < nv) buf[(v8 + u) * LD + ski] = t[u];
+        }
     }
     __syncthreads();
     fft4_fwd<N>(buf, LD, nv, tw, tid, nthr);
     if (SPECTRUM) {
-        for (int task = tid; task < nv * N; task += nthr) {
-            const int vi = task / N, p = task - vi * N;
-            Y[(int64_t)(v0 + vi) * N + p] = cscale(cconj(buf[vi * LD + sk<N>(p)]), scale);
+        for (int p = tid; p < N; p += nthr) {
+            const int skp = sk<N>(p);
+#pragma unroll
+            for (int vi = 0; vi < kColsVC; ++vi)
+                if (vi < nv) Y[(int64_t)(v0 + vi) * N + p] = cscale(cconj(buf[vi * LD + skp]), scale);
         }
         return;
     }
-    for (int task = tid; task < nv * N; task += nthr) {
-        const int vi = task / N, p = task - vi * N;
-        buf[vi * LD + sk<N>(p)] = cmul(buf[vi * LD + sk<N>(p)], bspec[(int64_t)(v0 + vi) * N + p]);
+    for (int p = tid; p < N; p += nthr) {
+        const int skp = sk<N>(p);
+#pragma unroll
+        for (int v8 = 0; v8 < kColsVC; v8 += 8) {
+            float2 b[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                b[u] = v8 + u < nv ? bspec[(int64_t)(v0 + v8 + u) * N + p] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (v8 + u < nv) buf[(v8 + u) * LD + skp] = cmul(buf[(v8 + u) * LD + skp], b[u]);
+        }
     }
     __syncthreads();
     fft4_inv<N>(buf, LD, nv, tw + N, tid, nthr);
     const int W = 2 * wm1 + 1;
     float2* ys = Y + f * y_fstride + v0;
-    for (int task = tid; task < W * nv; task += nthr) {
-        const int si = task / nv, vi = task - si * nv;
-        const int pos = (si - wm1 + N) % N;
+    for (int task = tid; task < W * kColsVC; task += nthr) {
+        const int si = task / kColsVC, vi = task % kColsVC;
+        if (vi >= nv) continue;
+        const int pos = si - wm1 < 0 ? si - wm1 + N : si - wm1;
         ys[(int64_t)si * ncv + vi] = buf[vi * LD + sk<N>(pos)];
     }
 }

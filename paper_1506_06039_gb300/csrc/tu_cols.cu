@@ -14,8 +14,7 @@ static cudaError_t cols_n(bool spectrum, const float2* X, int64_t x_fstride, int
     const void* fn = spectrum ? (const void*)k_cols<N, true> : (const void*)k_cols<N, false>;
     cudaError_t e = ensure_smem(fn, smem);
     if (e != cudaSuccess) return e;
-    int threads = kColsVC * (Four<N>::N1 > Four<N>::N2 ? Four<N>::N1 : Four<N>::N2);
-    threads = (threads + 31) / 32 * 32;
+    const int threads = cols_threads<N>();
     dim3 grid((unsigned)nimg, (unsigned)((ncv + kColsVC - 1) / kColsVC));
     if (spectrum)
         k_cols<N, true><<<grid, threads, smem, st>>>(X, x_fstride, ldx, mc, ncv, tw, bspec, Y, y_fstride, wm1, scale);
