@@ -490,24 +490,36 @@ k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* 
     Acc* exR = reinterpret_cast<Acc*>(smem_raw);  // W
     Acc* exC = exR + W;                            // W
     Acc* P = exC + W;                              // w x w
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
     const int64_t f = blockIdx.x;
     const u64* rE = rowE + f * mc;
     const u64* cE = colE + f * nc;
     auto ld = [](const u64* p) { u64 v = *p; return *reinterpret_cast<Acc*>(&v); };
-    if (tid == 0) {
-        exR[wm1] = 0;
-        Acc s = 0;
-        for (int k = 1; k <= wm1; ++k) { s += ld(rE + k - 1); exR[wm1 + k] = s; }
-        s = 0;
-        for (int k = 1; k <= wm1; ++k) { s += ld(rE + mc - k); exR[wm1 - k] = s; }
-    }
-    if (tid == 32) {  // (launched with kEnergyThreads > 32)
-        exC[wm1] = 0;
-        Acc s = 0;
-        for (int k = 1; k <= wm1; ++k) { s += ld(cE + k - 1); exC[wm1 + k] = s; }
-        s = 0;
-        for (int k = 1; k <= wm1; ++k) { s += ld(cE + nc - k); exC[wm1 - k] = s; }
+    // Inclusive warp scan of one 32-wide segment (lane order).
+    auto scan32 = [&](Acc v) {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const Acc u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        return v;
+    };
+    // Edge strips: exR[wm1 + k] = energy of the first k rows, exR[wm1 - k] of
+    // the last k rows (k = 1 .. wm1); the same for columns. Warps 0-3.
+    if (warp < 4) {
+        const u64* src = warp < 2 ? rE : cE;
+        const int len = warp < 2 ? mc : nc;
+        Acc* dst = warp < 2 ? exR : exC;
+        const bool from_end = warp & 1;
+        Acc carry = 0;
+        if (lane == 0) dst[wm1] = 0;
+        for (int k0 = 0; k0 < wm1; k0 += 32) {
+            const int k = k0 + lane;  // k + 1 rows or columns
+            Acc v = k < wm1 ? ld(src + (from_end ? len - 1 - k : k)) : Acc(0);
+            v = scan32(v) + carry;
+            if (k < wm1) dst[from_end ? wm1 - 1 - k : wm1 + 1 + k] = v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
+        }
     }
     const Acc T = ld(tot + f);
     const size_t wm1sq = (size_t)wm1 * wm1;
@@ -515,7 +527,7 @@ k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* 
         const bool bottom = q >= 2, right = q & 1;
         __syncthreads();
         // P[a][b] = sum over the a rows nearest the corner's horizontal edge
-        // and the b columns nearest its vertical edge.
+        // and the b columns nearest its vertical edge: squares first ...
         for (int i = tid; i < w * w; i += nthr) {
             const int a = i / w, b = i - a * w;
             Acc v = 0;
@@ -535,14 +547,28 @@ k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* 
             P[i] = v;
         }
         __syncthreads();
-        for (int a = tid; a < w; a += nthr) {
-            Acc s = 0;
-            for (int b = 0; b < w; ++b) { s += P[a * w + b]; P[a * w + b] = s; }
+        // ... then a scan along each row (one warp per row) ...
+        for (int a = warp; a < w; a += nwarps) {
+            Acc carry = 0;
+            for (int b0 = 0; b0 < w; b0 += 32) {
+                const int b = b0 + lane;
+                Acc v = b < w ? P[a * w + b] : Acc(0);
+                v = scan32(v) + carry;
+                if (b < w) P[a * w + b] = v;
+                carry = __shfl_sync(0xffffffffu, v, 31);
+            }
         }
         __syncthreads();
-        for (int b = tid; b < w; b += nthr) {
-            Acc s = 0;
-            for (int a = 0; a < w; ++a) { s += P[a * w + b]; P[a * w + b] = s; }
+        // ... and along each column.
+        for (int b = warp; b < w; b += nwarps) {
+            Acc carry = 0;
+            for (int a0 = 0; a0 < w; a0 += 32) {
+                const int a = a0 + lane;
+                Acc v = a < w ? P[a * w + b] : Acc(0);
+                v = scan32(v) + carry;
+                if (a < w) P[a * w + b] = v;
+                carry = __shfl_sync(0xffffffffu, v, 31);
+            }
         }
         __syncthreads();
         // Shifts of this quadrant: s >= 0 (top) or s < 0 (bottom), same for t.
