@@ -168,7 +168,9 @@ def kernel_work(info, wl, frames):
 # DRAM bytes (read + write) per frame of the current kernels, from one ncu
 # capture of 512 frames of the std512 workload (profiles/kernels_std512_fft.md),
 # scaled to a launch by its frame count.
-TRAFFIC_PER_FRAME = {"k_jitter": (261.744896e6 + 4.0e6) / 512}
+TRAFFIC_PER_FRAME = {"k_frame_rows": (269.646848e6 + 124.598016e6) / 512,
+                     "k_cols": (153.365504e6 + 20.268544e6) / 512,
+                     "k_jitter": (261.745152e6 + 3.996928e6) / 512}
 
 
 def roofline(profile, info, wl, frames_per_step, steps, peaks, clocks):

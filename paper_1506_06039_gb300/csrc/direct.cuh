@@ -336,8 +336,8 @@ __global__ void k_coarse_image(const void* __restrict__ src, int m, int n, int l
 // f = (Sa + Sb - 2 h) / Area * unit with the argmin and margin, from an h
 // computed by the direct form. One CTA per frame.
 static __global__ void __launch_bounds__(256)
-k_combine_h(const float* __restrict__ hh, int wm1, const u64* __restrict__ Sa, const double* __restrict__ Sb,
-            const double* __restrict__ inv_area, double unit, double* __restrict__ cost, int32_t* __restrict__ coarse,
+k_combine_h(const float* __restrict__ hh, int wm1, const float2* __restrict__ Sa2, const float2* __restrict__ Sb2,
+            const float* __restrict__ ia32, double* __restrict__ cost, int32_t* __restrict__ coarse,
             double* __restrict__ fbest, float* __restrict__ margin) {
     __shared__ Best red[8];
     const int W = 2 * wm1 + 1, WW = W * W;
@@ -349,9 +349,8 @@ k_combine_h(const float* __restrict__ hh, int wm1, const u64* __restrict__ Sa, c
     b.f2 = INFINITY;
     for (int k = tid; k < WW; k += nthr) {
         const int s = k / W - wm1, t = k % W - wm1;
-        const double num = ((double)Sa[f * WW + k] + Sb[k]) - 2.0 * (double)hh[f * WW + k];
-        const double fv = num * inv_area[k] * unit;
-        if (cost) cost[f * WW + k] = fv;
+        const float fv = combine_f32(Sa2[f * WW + k], Sb2[k], hh[f * WW + k], ia32[k]);
+        if (cost) cost[f * WW + k] = (double)fv;
         best_push(b, fv, (abs(s) + abs(t)) * WW + k);
     }
 #pragma unroll
@@ -369,10 +368,10 @@ k_combine_h(const float* __restrict__ hh, int wm1, const u64* __restrict__ Sa, c
         const int k = b.r1 % WW;
         coarse[2 * f] = k / W - wm1;
         coarse[2 * f + 1] = k % W - wm1;
-        if (fbest) fbest[f] = b.f1;
+        if (fbest) fbest[f] = (double)b.f1;
         if (margin) {
             float mg;
-            if (b.f1 > 0) mg = (float)((b.f2 - b.f1) / b.f1);
+            if (b.f1 > 0) mg = (b.f2 - b.f1) / b.f1;
             else mg = (b.f2 > 0) ? INFINITY : 0.f;
             margin[f] = mg;
         }

@@ -23,10 +23,11 @@ cudaError_t launch_cols(int N, bool spectrum, const float2* X, int64_t x_fstride
                         int64_t nimg, const float2* tw, const float2* bspec, float2* Y, int64_t y_fstride,
                         int wm1, float scale, cudaStream_t st);
 
+// Sa2 [nimg][W^2] and Sb2 [W^2]: exact energies as FP32 pairs (hi, lo);
+// ia32 [W^2]: unit / Area.
 cudaError_t launch_rows_inv(int N, const float2* Y, int64_t y_fstride, int ncv, int wm1, int64_t nimg,
-                            const float2* tw, const u64* Sa, const double* Sb, const double* inv_area,
-                            double unit, double* cost, int32_t* coarse, double* fbest, float* margin,
-                            cudaStream_t st);
+                            const float2* tw, const float2* Sa2, const float2* Sb2, const float* ia32,
+                            double* cost, int32_t* coarse, double* fbest, float* margin, cudaStream_t st);
 
 cudaError_t launch_energy(bool f32, bool out_double, const u64* rowE, const u64* colE, const u64* tot,
                           const uint32_t* corners, int64_t nimg, int mc, int nc, int wm1, void* out, int flip,
@@ -77,9 +78,12 @@ cudaError_t launch_toeplitz(bool f32, const void* tmpl, int m, int n, int levels
                             const int32_t* coff_i, const float* coff_f, float* bprime, void* tiles, cudaStream_t st);
 cudaError_t launch_direct(const void* a_hi, const void* a_lo, int64_t T, int mc, int ncp, int nqc, int wm1,
                           const void* tiles, float* h, unsigned int* err, cudaStream_t st);
-cudaError_t launch_combine_h(const float* h, int64_t nimg, int wm1, const u64* Sa, const double* Sb,
-                             const double* inv_area, double unit, double* cost, int32_t* coarse, double* fbest,
-                             float* margin, cudaStream_t st);
+cudaError_t launch_combine_h(const float* h, int64_t nimg, int wm1, const float2* Sa2, const float2* Sb2,
+                             const float* ia32, double* cost, int32_t* coarse, double* fbest, float* margin,
+                             cudaStream_t st);
+
+// out[k] = (hi, lo): hi the nearest float of x[k], lo the rounded remainder.
+cudaError_t launch_pair_from_double(const double* x, float2* out, int64_t count, cudaStream_t st);
 
 // Sets the dynamic shared-memory limit of `func` on the current device once.
 cudaError_t ensure_smem(const void* func, size_t bytes);

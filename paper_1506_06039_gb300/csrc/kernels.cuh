@@ -478,7 +478,10 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
 // where the corner term is a 2-D prefix sum over one (w-1)^2 corner block
 // (the recurrence of Section 2 restricted to the window). With flip set the
 // result is stored at (-s,-t): the template's energy over the b-side of D.
-// OUT_DOUBLE stores doubles, else u64 (both exact for integer images).
+// OUT_DOUBLE stores doubles (exact for integer images); otherwise (uint16
+// frames) each exact integer energy is stored as an FP32 pair hi + lo with
+// hi = the nearest float and lo = the rounded remainder (|error| <= 8 for
+// energies below 2^53, i.e. 2^-48 relative), which the FP32 combine uses.
 template <bool F32, bool OUT_DOUBLE>
 __global__ void __launch_bounds__(kEnergyThreads)
 k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* __restrict__ tot,
@@ -489,7 +492,8 @@ k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* 
     const int W = 2 * wm1 + 1, w = wm1 + 1;
     Acc* exR = reinterpret_cast<Acc*>(smem_raw);  // W
     Acc* exC = exR + W;                            // W
-    Acc* P = exC + W;                              // w x w
+    Acc* P = exC + W;                              // w x (w + 1): padded rows
+    const int PL = w + 1;
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
     const int64_t f = blockIdx.x;
     const u64* rE = rowE + f * mc;
@@ -544,7 +548,7 @@ k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* 
                     v = (Acc)(x * x);
                 }
             }
-            P[i] = v;
+            P[a * PL + b] = v;
         }
         __syncthreads();
         // ... then a scan along each row (one warp per row) ...
@@ -552,9 +556,9 @@ k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* 
             Acc carry = 0;
             for (int b0 = 0; b0 < w; b0 += 32) {
                 const int b = b0 + lane;
-                Acc v = b < w ? P[a * w + b] : Acc(0);
+                Acc v = b < w ? P[a * PL + b] : Acc(0);
                 v = scan32(v) + carry;
-                if (b < w) P[a * w + b] = v;
+                if (b < w) P[a * PL + b] = v;
                 carry = __shfl_sync(0xffffffffu, v, 31);
             }
         }
@@ -564,9 +568,9 @@ k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* 
             Acc carry = 0;
             for (int a0 = 0; a0 < w; a0 += 32) {
                 const int a = a0 + lane;
-                Acc v = a < w ? P[a * w + b] : Acc(0);
+                Acc v = a < w ? P[a * PL + b] : Acc(0);
                 v = scan32(v) + carry;
-                if (a < w) P[a * w + b] = v;
+                if (a < w) P[a * PL + b] = v;
                 carry = __shfl_sync(0xffffffffu, v, 31);
             }
         }
@@ -577,11 +581,17 @@ k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* 
             if (bottom && a == 0) continue;
             if (right && b == 0) continue;
             const int s = bottom ? -a : a, t = right ? -b : b;
-            const Acc val = T - exR[s + wm1] - exC[t + wm1] + P[i];
+            const Acc val = T - exR[s + wm1] - exC[t + wm1] + P[a * PL + b];
             const int so = flip ? -s : s, to = flip ? -t : t;
             const int64_t k = f * (int64_t)W * W + (int64_t)(so + wm1) * W + (to + wm1);
-            if (OUT_DOUBLE) static_cast<double*>(out)[k] = (double)val;
-            else static_cast<u64*>(out)[k] = *reinterpret_cast<const u64*>(&val);
+            if (OUT_DOUBLE) {
+                static_cast<double*>(out)[k] = (double)val;
+            } else {
+                const u64 e = *reinterpret_cast<const u64*>(&val);
+                const float hi = __ull2float_rn(e);
+                const long long r = (long long)(e - __float2ull_rn(hi));  // |r| <= ulp(hi) / 2
+                static_cast<float2*>(out)[k] = make_float2(hi, __ll2float_rn(r));
+            }
         }
     }
 }
@@ -670,42 +680,54 @@ k_cols(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv
 }
 
 // ---------------------------------------------------------------------------
+// The combine f = (Sa + Sb - 2h) / Area * unit in FP32 from the exact
+// energies as FP32 pairs: Sa_hi + Sb_hi by an error-free sum (TwoSum), so
+// the only roundings are h's own (the FP32 cross term), one in the
+// difference and one in the final product (~1e-7 relative each).
+__device__ __forceinline__ float combine_f32(float2 sa, float2 sb, float h, float ia) {
+    const float s = sa.x + sb.x;
+    const float bb = s - sa.x;
+    const float err = (sa.x - (s - bb)) + (sb.x - bb);
+    const float num = (s - 2.0f * h) + (err + (sa.y + sb.y));
+    return num * ia;
+}
+
 // k_rows_inv: one CTA per frame. Inverse real DFTs along the image columns
 // (length Nc) of Y's 2w-1 rows, two rows per complex transform, keeping the
-// 2w-1 columns t in [-(w-1), w-1] -> h[s][t]. Then, in FP64,
-//     f_st = (Sa_st + Sb_st - 2 h_st) / Area_st * unit
+// 2w-1 columns t in [-(w-1), w-1] -> h[s][t]. Then
+//     f_st = (Sa_st + Sb_st - 2 h_st) / Area_st * unit   (combine_f32)
 // and the argmin over the window with the tie-break: smallest f, then
 // smallest |s|+|t|, then smallest s, then smallest t. Also the second-best
 // value for the margin (f2 - f1) / f1.
 struct Best {
-    double f1;
+    float f1;
     int r1;
-    double f2;
+    float f2;
 };
-__device__ __forceinline__ void best_push(Best& b, double f, int r) {
+__device__ __forceinline__ void best_push(Best& b, float f, int r) {
     if (f < b.f1 || (f == b.f1 && r < b.r1)) {
-        b.f2 = fmin(b.f2, b.f1);
+        b.f2 = fminf(b.f2, b.f1);
         b.f1 = f;
         b.r1 = r;
     } else {
-        b.f2 = fmin(b.f2, f);
+        b.f2 = fminf(b.f2, f);
     }
 }
 __device__ __forceinline__ void best_merge(Best& a, const Best& o) {
     if (o.f1 < a.f1 || (o.f1 == a.f1 && o.r1 < a.r1)) {
-        a.f2 = fmin(o.f2, a.f1);
+        a.f2 = fminf(o.f2, a.f1);
         a.f1 = o.f1;
         a.r1 = o.r1;
     } else {
-        a.f2 = fmin(a.f2, o.f1);
+        a.f2 = fminf(a.f2, o.f1);
     }
 }
 
 template <int N>
 __global__ void __launch_bounds__(576)
 k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
-           const float2* __restrict__ tw_g, const u64* __restrict__ Sa, const double* __restrict__ Sb,
-           const double* __restrict__ inv_area, double unit, double* __restrict__ cost,
+           const float2* __restrict__ tw_g, const float2* __restrict__ Sa2, const float2* __restrict__ Sb2,
+           const float* __restrict__ ia32, double* __restrict__ cost,
            int32_t* __restrict__ coarse, double* __restrict__ fbest, float* __restrict__ margin) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int LD = fft_ld<N>();                      // skewed, padded row
@@ -771,13 +793,12 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
     b.f1 = INFINITY;
     b.r1 = 0x7fffffff;
     b.f2 = INFINITY;
-    const u64* sa = Sa + f * WW;
+    const float2* sa = Sa2 + f * WW;
     for (int k = tid; k < WW; k += nthr) {
         const int si = k / W, ti = k - si * W;
         const int s = si - wm1, t = ti - wm1;
-        const double num = ((double)sa[k] + Sb[k]) - 2.0 * (double)hbuf[k];
-        const double fv = num * inv_area[k] * unit;
-        if (cost) cost[f * WW + k] = fv;
+        const float fv = combine_f32(sa[k], Sb2[k], hbuf[k], ia32[k]);
+        if (cost) cost[f * WW + k] = (double)fv;
         best_push(b, fv, (abs(s) + abs(t)) * WW + k);
     }
 #pragma unroll
@@ -796,10 +817,10 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
         const int s = k / W - wm1, t = k % W - wm1;
         coarse[2 * f] = s;
         coarse[2 * f + 1] = t;
-        if (fbest) fbest[f] = b.f1;
+        if (fbest) fbest[f] = (double)b.f1;
         if (margin) {
             float mg;
-            if (b.f1 > 0) mg = (float)((b.f2 - b.f1) / b.f1);
+            if (b.f1 > 0) mg = (b.f2 - b.f1) / b.f1;
             else mg = (b.f2 > 0) ? INFINITY : 0.f;
             margin[f] = mg;
         }

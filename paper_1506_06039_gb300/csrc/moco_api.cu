@@ -166,6 +166,8 @@ moco_status allocate_shape(ShapePlan& sp) {
     }
     c.add(&sp.Sb, (size_t)W * W * 8);
     c.add(&sp.inv_area, (size_t)W * W * 8);
+    c.add(&sp.Sb2, (size_t)W * W * 8);
+    c.add(&sp.ia32, (size_t)W * W * 4);
     c.add(&sp.grad_acc, (size_t)(m * n * 4));
     c.add(&sp.grad_Q, (size_t)(W * W * 4));
     if (sp.levels && !sp.f32) c.add(&sp.bsq, (size_t)(m + 1) * (n + 1) * 8);
@@ -198,6 +200,10 @@ moco_status allocate_shape(ShapePlan& sp) {
                 1.0 / ((double)(sp.mc - std::abs(s)) * (double)(sp.nc - std::abs(t)));
     e = cudaMemcpy(sp.inv_area, ia.data(), ia.size() * 8, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "upload of 1/Area");
+    std::vector<float> ia32(ia.size());
+    for (size_t k = 0; k < ia.size(); ++k) ia32[k] = (float)(ia[k] * sp.unit);
+    e = cudaMemcpy(sp.ia32, ia32.data(), ia32.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload of unit/Area");
     return MOCO_OK;
 }
 
@@ -263,6 +269,7 @@ moco_status prepare_template(ShapePlan& sp, const void* tmpl_dev, cudaStream_t s
                                 sp.planes_lo, sp.ncp, st);
     if (e != cudaSuccess) return cuda_fail(e, "template rows");
     e = launch_energy(sp.f32, true, sp.rowE, sp.colE, sp.tot, sp.corners, 1, sp.mc, sp.nc, sp.wm1, sp.Sb, 1, st);
+    if (e == cudaSuccess) e = launch_pair_from_double(sp.Sb, sp.Sb2, (int64_t)sp.W * sp.W, st);
     if (e != cudaSuccess) return cuda_fail(e, "template energies");
     if (sp.has_fft) {
         e = launch_cols(sp.Nr, true, sp.X, sp.x_fstride, sp.ldx, sp.mc, sp.ncv, 1, sp.twr, nullptr, sp.bspec, 0,
@@ -304,7 +311,7 @@ moco_status search_group(ShapePlan& sp, const uint16_t* frames, int64_t g, doubl
         P.end(st);
         if (e != cudaSuccess) return cuda_fail(e, "k_direct");
         P.begin(K_ROWS_INV, st);
-        e = launch_combine_h(sp.hbuf, g, sp.wm1, sp.Sa, sp.Sb, sp.inv_area, sp.unit, cost, sp.coarse,
+        e = launch_combine_h(sp.hbuf, g, sp.wm1, reinterpret_cast<const float2*>(sp.Sa), sp.Sb2, sp.ia32, cost, sp.coarse,
                              fbest ? fbest : sp.fbest, margin ? margin : sp.margin, st);
         P.end(st);
         if (e != cudaSuccess) return cuda_fail(e, "k_combine_h");
@@ -326,7 +333,8 @@ moco_status search_group(ShapePlan& sp, const uint16_t* frames, int64_t g, doubl
     P.end(st);
     if (e != cudaSuccess) return cuda_fail(e, "k_cols");
     P.begin(K_ROWS_INV, st);
-    e = launch_rows_inv(sp.Nc, sp.Y, sp.y_fstride, sp.ncv, sp.wm1, g, sp.twc, sp.Sa, sp.Sb, sp.inv_area, sp.unit,
+    e = launch_rows_inv(sp.Nc, sp.Y, sp.y_fstride, sp.ncv, sp.wm1, g, sp.twc, reinterpret_cast<const float2*>(sp.Sa),
+                        sp.Sb2, sp.ia32,
                         cost, sp.coarse, fbest ? fbest : sp.fbest, margin ? margin : sp.margin, st);
     P.end(st);
     if (e != cudaSuccess) return cuda_fail(e, "k_rows_inv");

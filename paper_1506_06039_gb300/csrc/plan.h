@@ -62,6 +62,8 @@ struct ShapePlan {
     float2* bspec = nullptr;
     double* Sb = nullptr;
     double* inv_area = nullptr;
+    float2* Sb2 = nullptr;  // Sb as FP32 pairs (hi, lo), W^2
+    float* ia32 = nullptr;  // unit / Area, W^2
     u64* bsq = nullptr;  // with a level: prefix table of b^2, (m+1) x (n+1)
     u64* apply_sum = nullptr;           // m x n: the correction step's per-pixel sums
     unsigned int* apply_cnt = nullptr;  // m x n: and counts

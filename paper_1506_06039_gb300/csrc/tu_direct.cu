@@ -60,11 +60,11 @@ cudaError_t launch_direct(const void* a_hi, const void* a_lo, int64_t T, int mc,
     return cudaGetLastError();
 }
 
-cudaError_t launch_combine_h(const float* h, int64_t nimg, int wm1, const u64* Sa, const double* Sb,
-                             const double* inv_area, double unit, double* cost, int32_t* coarse, double* fbest,
-                             float* margin, cudaStream_t st) {
+cudaError_t launch_combine_h(const float* h, int64_t nimg, int wm1, const float2* Sa2, const float2* Sb2,
+                             const float* ia32, double* cost, int32_t* coarse, double* fbest, float* margin,
+                             cudaStream_t st) {
     if (nimg <= 0) return cudaSuccess;
-    k_combine_h<<<(unsigned)nimg, 256, 0, st>>>(h, wm1, Sa, Sb, inv_area, unit, cost, coarse, fbest, margin);
+    k_combine_h<<<(unsigned)nimg, 256, 0, st>>>(h, wm1, Sa2, Sb2, ia32, cost, coarse, fbest, margin);
     return cudaGetLastError();
 }
 

@@ -61,7 +61,7 @@ cudaError_t launch_energy(bool f32, bool out_double, const u64* rowE, const u64*
                           cudaStream_t st) {
     if (nimg <= 0) return cudaSuccess;
     const int W = 2 * wm1 + 1, w = wm1 + 1;
-    const size_t smem = sizeof(u64) * (2 * W + w * w);
+    const size_t smem = sizeof(u64) * (2 * W + w * (w + 1));  // exR, exC, P with padded rows
     const void* fn = f32 ? (out_double ? (const void*)k_energy<true, true> : (const void*)k_energy<true, false>)
                          : (out_double ? (const void*)k_energy<false, true> : (const void*)k_energy<false, false>);
     cudaError_t e = ensure_smem(fn, smem);
@@ -73,6 +73,19 @@ cudaError_t launch_energy(bool f32, bool out_double, const u64* rowE, const u64*
         if (out_double) k_energy<false, true><<<(unsigned)nimg, kEnergyThreads, smem, st>>>(rowE, colE, tot, corners, mc, nc, wm1, out, flip);
         else k_energy<false, false><<<(unsigned)nimg, kEnergyThreads, smem, st>>>(rowE, colE, tot, corners, mc, nc, wm1, out, flip);
     }
+    return cudaGetLastError();
+}
+
+static __global__ void k_pair_from_double(const double* __restrict__ x, float2* __restrict__ out, int64_t count) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const float hi = (float)x[k];
+    out[k] = make_float2(hi, (float)(x[k] - (double)hi));
+}
+
+cudaError_t launch_pair_from_double(const double* x, float2* out, int64_t count, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    k_pair_from_double<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(x, out, count);
     return cudaGetLastError();
 }
 

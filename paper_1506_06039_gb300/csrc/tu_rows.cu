@@ -56,8 +56,8 @@ cudaError_t launch_frame_rows(int N, bool f32, const void* src, int64_t src_fstr
 
 template <int N>
 static cudaError_t rows_inv_n(const float2* Y, int64_t y_fstride, int ncv, int wm1, int64_t nimg,
-                              const float2* tw, const u64* Sa, const double* Sb, const double* inv_area,
-                              double unit, double* cost, int32_t* coarse, double* fbest, float* margin,
+                              const float2* tw, const float2* Sa2, const float2* Sb2, const float* ia32,
+                              double* cost, int32_t* coarse, double* fbest, float* margin,
                               cudaStream_t st) {
     const int W = 2 * wm1 + 1;
     const size_t smem = sizeof(float2) * (kInvPC * fft_ld<N>() + N) + sizeof(float) * W * W;
@@ -66,19 +66,18 @@ static cudaError_t rows_inv_n(const float2* Y, int64_t y_fstride, int ncv, int w
     if (e != cudaSuccess) return e;
     int threads = kInvPC * (Four<N>::N1 > Four<N>::N2 ? Four<N>::N1 : Four<N>::N2);
     threads = (threads + 31) / 32 * 32;
-    k_rows_inv<N><<<(unsigned)nimg, threads, smem, st>>>(Y, y_fstride, ncv, wm1, tw, Sa, Sb, inv_area, unit,
+    k_rows_inv<N><<<(unsigned)nimg, threads, smem, st>>>(Y, y_fstride, ncv, wm1, tw, Sa2, Sb2, ia32,
                                                          cost, coarse, fbest, margin);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rows_inv(int N, const float2* Y, int64_t y_fstride, int ncv, int wm1, int64_t nimg,
-                            const float2* tw, const u64* Sa, const double* Sb, const double* inv_area,
-                            double unit, double* cost, int32_t* coarse, double* fbest, float* margin,
-                            cudaStream_t st) {
+                            const float2* tw, const float2* Sa2, const float2* Sb2, const float* ia32,
+                            double* cost, int32_t* coarse, double* fbest, float* margin, cudaStream_t st) {
     if (nimg <= 0) return cudaSuccess;
 #define MOCO_CASE(NN) \
     case NN:          \
-        return rows_inv_n<NN>(Y, y_fstride, ncv, wm1, nimg, tw, Sa, Sb, inv_area, unit, cost, coarse, fbest, margin, st);
+        return rows_inv_n<NN>(Y, y_fstride, ncv, wm1, nimg, tw, Sa2, Sb2, ia32, cost, coarse, fbest, margin, st);
     switch (N) {
         MOCO_FOR_EACH_FFT_SIZE(MOCO_CASE)
         default:
