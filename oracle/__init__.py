@@ -110,8 +110,11 @@ def downsample(a) -> np.ndarray:
 
 
 def align(frames, template, w, levels=-1, nthreads=0):
-    """Exhaustive search + upsampling jitter. Returns a dict of numpy arrays:
-    shifts (T,2), coarse (T,2), fbest (T,), margin (T,), ffinal (T,)."""
+    """Exhaustive search + upsampling jitter. levels: -1 the paper's rule (one
+    level above 256x256), else 0..4 (the search on level L, then one 3x3
+    refinement per level down to full resolution). Returns a dict of numpy
+    arrays: shifts (T,2), coarse (T,2) on the searched level, fbest (T,),
+    margin (T,), ffinal (T,) at full resolution."""
     frames = _c(frames, np.uint16)
     template = _c(template, np.uint16)
     if frames.ndim == 2:

@@ -21,6 +21,13 @@
  *   - Upsampling (Section 2): the coarse optimum (s,t) is doubled and f is
  *     evaluated at full resolution for (2s+u, 2t+v), u, v in {-1, 0, 1}; the
  *     minimum is kept.
+ *   - More levels (Section 2 says the resolution is "multiplied by two
+ *     multiple times"; Section 3 reports that three or four downsamplings
+ *     cause severe errors): with L levels, level l is the 2x2 sum of level
+ *     l - 1 (floor sizes; level 0 is the image), the exhaustive search runs
+ *     on level L, and for l = L-1 down to 0 the doubled optimum is refined by
+ *     the 3x3 search on level l's images (exact sums, the same tie-break).
+ *     Costs on level L are reported per pixel of the full image (/ 16^L).
  *   - Ties (the paper is silent): among equal f the shift with the smallest
  *     |s| + |t| wins, then the smallest s, then the smallest t. Costs are
  *     compared as exact rationals S1 * A2 vs S2 * A1 in 128-bit integers.
@@ -96,6 +103,36 @@ static void widen(const uint16_t *a, int64_t count, int32_t *out) {
     for (int64_t k = 0; k < count; ++k) out[k] = (int32_t)a[k];
 }
 
+/* 2x2 sums of an int32 image (m x n -> m/2 x n/2, floor). */
+static void downsample32(const int32_t *a, int m, int n, int32_t *out) {
+    int mc = m / 2, nc = n / 2;
+    for (int i = 0; i < mc; ++i)
+        for (int j = 0; j < nc; ++j)
+            out[(int64_t)i * nc + j] = a[(int64_t)(2 * i) * n + 2 * j] + a[(int64_t)(2 * i + 1) * n + 2 * j] +
+                                       a[(int64_t)(2 * i) * n + 2 * j + 1] + a[(int64_t)(2 * i + 1) * n + 2 * j + 1];
+}
+
+#define ORACLE_MAX_LEVELS 4
+
+/* The level images of a (lev[0] = a widened, lev[l] = 2x2 sums of lev[l-1])
+ * into one buffer; off[l] is level l's start, ml[l] x nl[l] its size. */
+static void pyramid(const uint16_t *a, int m, int n, int L, int32_t *buf, int64_t *off, int *ml, int *nl) {
+    ml[0] = m; nl[0] = n; off[0] = 0;
+    widen(a, (int64_t)m * n, buf);
+    for (int l = 1; l <= L; ++l) {
+        ml[l] = ml[l - 1] / 2; nl[l] = nl[l - 1] / 2;
+        off[l] = off[l - 1] + (int64_t)ml[l - 1] * nl[l - 1];
+        downsample32(buf + off[l - 1], ml[l - 1], nl[l - 1], buf + off[l]);
+    }
+}
+
+/* Elements of a pyramid buffer of L levels. */
+static int64_t pyramid_size(int m, int n, int L) {
+    int64_t total = 0;
+    for (int l = 0; l <= L; ++l) { total += (int64_t)m * n; m /= 2; n /= 2; }
+    return total;
+}
+
 /* Paper rule for the number of levels: one iff the image is larger than 256x256. */
 int oracle_levels(int m, int n) { return (m > 256 || n > 256) ? 1 : 0; }
 
@@ -122,25 +159,18 @@ typedef struct {
     double ffinal;       /* full-resolution f at the final shift (= fbest w/o levels) */
 } oracle_result;
 
-/* a, b are the full-resolution frame and template (uint16, m x n). */
-static void align_one(const uint16_t *a, const uint16_t *b, const int32_t *bc, int m, int n,
-                      int w, int levels, int32_t *ac, int32_t *afull, int32_t *bfull,
-                      int64_t *Sbuf, oracle_result *res) {
-    int mc = levels ? m / 2 : m, nc = levels ? n / 2 : n;
-    const int32_t *A, *B;
-    widen(a, (int64_t)m * n, afull);
-    widen(b, (int64_t)m * n, bfull);
-    if (levels) {
-        oracle_downsample(a, m, n, ac);
-        A = ac;
-        B = bc;
-    } else {
-        A = afull;
-        B = bfull;
-    }
-    double unit = levels ? 16.0 : 1.0;
+/* a is the frame; bp the template's pyramid (offsets boff, sizes ml x nl). */
+static void align_one(const uint16_t *a, const int32_t *bp, const int64_t *boff, int m, int n, int w, int L,
+                      int32_t *ap, int64_t *Sbuf, oracle_result *res) {
+    int64_t off[ORACLE_MAX_LEVELS + 1];
+    int ml[ORACLE_MAX_LEVELS + 1], nl[ORACLE_MAX_LEVELS + 1];
+    pyramid(a, m, n, L, ap, off, ml, nl);
+    const int32_t *A = ap + off[L], *B = bp + boff[L];
+    const int mc = ml[L], nc = nl[L];
+    double unit = 1.0;
+    for (int l = 0; l < L; ++l) unit *= 16.0;
     int W = 2 * w - 1;
-    /* Coarse exhaustive search over max(|s|,|t|) < w. */
+    /* Exhaustive search over max(|s|,|t|) < w on the searched level. */
     oracle_ssd_all(A, B, mc, nc, w, Sbuf);
     int bs = 0, bt = 0;
     int64_t bS = -1, bA = 1;
@@ -164,24 +194,24 @@ static void align_one(const uint16_t *a, const uint16_t *b, const int32_t *bc, i
     res->fbest = f1;
     if (f1 > 0) res->margin = (f2 - f1) / f1;
     else res->margin = (f2 > 0) ? INFINITY : 0.0;
-    if (!levels) {
-        res->s = bs; res->t = bt; res->ffinal = f1;
-        return;
-    }
-    /* Upsampling: double, then the 3x3 local search on the full grid. */
-    int fs = 0, ft = 0;
-    int64_t fS = -1, fA = 1;
-    for (int u = -1; u <= 1; ++u)
-        for (int v = -1; v <= 1; ++v) {
-            int s = 2 * bs + u, t = 2 * bt + v;
-            int64_t S = oracle_ssd_one(afull, bfull, m, n, s, t);
-            int64_t Ar = oracle_area(m, n, s, t);
-            if (fS < 0 || better(S, Ar, s, t, fS, fA, fs, ft)) {
-                fS = S; fA = Ar; fs = s; ft = t;
+    res->ffinal = f1;
+    /* Upsampling, one level at a time: double, then the 3x3 search. */
+    int64_t fS = bS, fA = bA;
+    for (int l = L - 1; l >= 0; --l) {
+        int ps = bs, pt = bt;
+        int first = 1;
+        for (int u = -1; u <= 1; ++u)
+            for (int v = -1; v <= 1; ++v) {
+                int s = 2 * ps + u, t = 2 * pt + v;
+                int64_t S = oracle_ssd_one(ap + off[l], bp + boff[l], ml[l], nl[l], s, t);
+                int64_t Ar = oracle_area(ml[l], nl[l], s, t);
+                if (first || better(S, Ar, s, t, fS, fA, bs, bt)) {
+                    fS = S; fA = Ar; bs = s; bt = t; first = 0;
+                }
             }
-        }
-    res->s = fs; res->t = ft;
-    res->ffinal = (double)fS / (double)fA;
+    }
+    res->s = bs; res->t = bt;
+    if (L > 0) res->ffinal = (double)fS / (double)fA;
 }
 
 /* Align T frames (uint16, T x m x n) against the template (uint16, m x n).
@@ -192,28 +222,29 @@ int oracle_align(const uint16_t *frames, int64_t T, const uint16_t *tmpl, int m,
                  int levels, int32_t *shifts, int32_t *coarse, double *fbest, double *margin,
                  double *ffinal, int nthreads) {
     if (levels < 0) levels = oracle_levels(m, n);
-    int mc = levels ? m / 2 : m, nc = levels ? n / 2 : n;
-    if (w < 1 || 2 * w - 1 > mc || 2 * w - 1 > nc || levels > 1) return -1;
-    int32_t *bc = (int32_t *)malloc(sizeof(int32_t) * (size_t)mc * nc);
-    if (levels) oracle_downsample(tmpl, m, n, bc);
+    if (levels > ORACLE_MAX_LEVELS) return -1;
+    int mc = m >> levels, nc = n >> levels;
+    if (w < 1 || 2 * w - 1 > mc || 2 * w - 1 > nc) return -1;
+    int64_t boff[ORACLE_MAX_LEVELS + 1];
+    int bml[ORACLE_MAX_LEVELS + 1], bnl[ORACLE_MAX_LEVELS + 1];
+    int32_t *bp = (int32_t *)malloc(sizeof(int32_t) * (size_t)pyramid_size(m, n, levels));
+    pyramid(tmpl, m, n, levels, bp, boff, bml, bnl);
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
     int failed = 0;
 #pragma omp parallel
     {
-        int32_t *ac = (int32_t *)malloc(sizeof(int32_t) * (size_t)mc * nc);
-        int32_t *af = (int32_t *)malloc(sizeof(int32_t) * (size_t)m * n);
-        int32_t *bf = (int32_t *)malloc(sizeof(int32_t) * (size_t)m * n);
+        int32_t *ap = (int32_t *)malloc(sizeof(int32_t) * (size_t)pyramid_size(m, n, levels));
         int64_t *Sb = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * w - 1) * (2 * w - 1));
-        if (!ac || !af || !bf || !Sb) {
+        if (!ap || !Sb) {
 #pragma omp atomic write
             failed = 1;
         } else {
 #pragma omp for schedule(dynamic, 1)
             for (int64_t f = 0; f < T; ++f) {
                 oracle_result r;
-                align_one(frames + f * (int64_t)m * n, tmpl, bc, m, n, w, levels, ac, af, bf, Sb, &r);
+                align_one(frames + f * (int64_t)m * n, bp, boff, m, n, w, levels, ap, Sb, &r);
                 shifts[2 * f] = r.s; shifts[2 * f + 1] = r.t;
                 if (coarse) { coarse[2 * f] = r.sc; coarse[2 * f + 1] = r.tc; }
                 if (fbest) fbest[f] = r.fbest;
@@ -221,9 +252,9 @@ int oracle_align(const uint16_t *frames, int64_t T, const uint16_t *tmpl, int m,
                 if (ffinal) ffinal[f] = r.ffinal;
             }
         }
-        free(ac); free(af); free(bf); free(Sb);
+        free(ap); free(Sb);
     }
-    free(bc);
+    free(bp);
     return failed ? -2 : 0;
 }
 
@@ -232,25 +263,31 @@ int oracle_align(const uint16_t *frames, int64_t T, const uint16_t *tmpl, int m,
 int oracle_cost_surface(const uint16_t *frames, int64_t T, const uint16_t *tmpl, int m, int n,
                         int w, int levels, double *cost, int64_t *S_out, int nthreads) {
     if (levels < 0) levels = oracle_levels(m, n);
-    int mc = levels ? m / 2 : m, nc = levels ? n / 2 : n;
-    if (w < 1 || 2 * w - 1 > mc || 2 * w - 1 > nc || levels > 1) return -1;
+    if (levels > ORACLE_MAX_LEVELS) return -1;
+    int mc = m >> levels, nc = n >> levels;
+    if (w < 1 || 2 * w - 1 > mc || 2 * w - 1 > nc) return -1;
     int W = 2 * w - 1;
-    double unit = levels ? 16.0 : 1.0;
-    int32_t *bc = (int32_t *)malloc(sizeof(int32_t) * (size_t)mc * nc);
-    if (levels) oracle_downsample(tmpl, m, n, bc);
-    else widen(tmpl, (int64_t)m * n, bc);
+    double unit = 1.0;
+    for (int l = 0; l < levels; ++l) unit *= 16.0;
+    int64_t boff[ORACLE_MAX_LEVELS + 1];
+    int bml[ORACLE_MAX_LEVELS + 1], bnl[ORACLE_MAX_LEVELS + 1];
+    int32_t *bp = (int32_t *)malloc(sizeof(int32_t) * (size_t)pyramid_size(m, n, levels));
+    pyramid(tmpl, m, n, levels, bp, boff, bml, bnl);
+    const int32_t *bc = bp + boff[levels];
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
 #pragma omp parallel
     {
-        int32_t *ac = (int32_t *)malloc(sizeof(int32_t) * (size_t)mc * nc);
+        int32_t *ap = (int32_t *)malloc(sizeof(int32_t) * (size_t)pyramid_size(m, n, levels));
         int64_t *S = (int64_t *)malloc(sizeof(int64_t) * (size_t)W * W);
 #pragma omp for schedule(dynamic, 1)
         for (int64_t f = 0; f < T; ++f) {
             const uint16_t *a = frames + f * (int64_t)m * n;
-            if (levels) oracle_downsample(a, m, n, ac);
-            else widen(a, (int64_t)m * n, ac);
+            int64_t off[ORACLE_MAX_LEVELS + 1];
+            int ml[ORACLE_MAX_LEVELS + 1], nl[ORACLE_MAX_LEVELS + 1];
+            pyramid(a, m, n, levels, ap, off, ml, nl);
+            const int32_t *ac = ap + off[levels];
             oracle_ssd_all(ac, bc, mc, nc, w, S);
             for (int s = -(w - 1); s <= w - 1; ++s)
                 for (int t = -(w - 1); t <= w - 1; ++t) {
@@ -259,9 +296,9 @@ int oracle_cost_surface(const uint16_t *frames, int64_t T, const uint16_t *tmpl,
                     if (S_out) S_out[f * (int64_t)W * W + k] = S[k];
                 }
         }
-        free(ac); free(S);
+        free(ap); free(S);
     }
-    free(bc);
+    free(bp);
     return 0;
 }
 
