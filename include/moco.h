@@ -69,7 +69,11 @@ typedef enum {
 typedef struct {
     int32_t m, n;           /* full-resolution rows and columns (n % 8 == 0, n <= 4096) */
     int32_t w;              /* window on the searched grid: max(|s|,|t|) < w, 2w-1 <= min(mc, nc) */
-    int32_t levels;         /* -1: the paper's rule (1 if m > 256 or n > 256, else 0); 0; or 1 */
+    int32_t levels;         /* -1: the paper's rule (1 if m > 256 or n > 256, else 0); or 0 .. 4:
+                               the search runs on level L (2^L x 2^L box sums), then each
+                               finer level refines the doubled optimum by a 3x3 search with
+                               exact sums (Section 2, "multiplied by two multiple times");
+                               L >= 2 uses the FFT form only */
     int32_t template_dtype; /* moco_template_dtype */
     int32_t xcorr;          /* moco_xcorr */
     int32_t group_frames;   /* frames per internal batch (workspace size); 0 = chosen by the plan */

@@ -40,6 +40,13 @@ cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg,
                           int n, const u64* bsq, const int32_t* coarse, int32_t* shifts, double* ffinal, u64* acc,
                           unsigned int* ticket, cudaStream_t st);
 
+// More than one level: level-l images (int32 box sums of 2^l x 2^l pixels)
+// and the 3x3 refinement on level l of the doubled level-(l+1) optimum.
+size_t level_image_elems(int m, int n, int l);
+cudaError_t launch_box_level(const uint16_t* img, int m, int n, int l, int32_t* out, cudaStream_t st);
+cudaError_t launch_jitter_level(const uint16_t* frames, int64_t fstride, int64_t nimg, int m, int n, int l,
+                                const int32_t* bl, const int32_t* cin, int32_t* cout, cudaStream_t st);
+
 // The correction step: corrected frames and/or the corrected mean image;
 // sum (u64) and cnt (u32) are m*n scratch, cleared here.
 cudaError_t launch_apply(const uint16_t* frames, int64_t fstride, int64_t T, int m, int n, const int32_t* shifts,

@@ -57,6 +57,16 @@ __device__ __forceinline__ uint32_t add_halves(uint32_t w, uint32_t acc) {
     asm("dp2a.lo.u32.u32 %0, %1, %2, %0;" : "+r"(acc) : "r"(w), "r"(0x0101u));
     return acc;
 }
+// Sum of the 2^L x 2^L full-resolution pixels behind level-L pixel (r, c)
+// (L >= 1; below 2^32 for L <= 4).
+__device__ __forceinline__ uint32_t box_sum_l(const uint16_t* __restrict__ img, int n, int r, int c, int L) {
+    const int B = 1 << L;
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(img + ((int64_t)r << L) * n + ((int64_t)c << L));
+    uint32_t s = 0;
+    for (int dr = 0; dr < B; ++dr)
+        for (int k = 0; k < B / 2; ++k) s = add_halves(__ldg(p + (int64_t)dr * (n / 2) + k), s);
+    return s;
+}
 // acc += d * d exactly (|d| < 2^31), one 32 x 32 -> 64-bit multiply-add.
 __device__ __forceinline__ void add_sq(u64& acc, int32_t d) {
     asm("mad.wide.s32 %0, %1, %1, %0;" : "+l"(acc) : "r"(d));
@@ -270,6 +280,9 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
                                     const uint32_t* s32 = reinterpret_cast<const uint32_t*>(stage);
                                     w0 = s32[(2 * (rl + h)) * (n / 2) + c];
                                     w1 = s32[(2 * (rl + h) + 1) * (n / 2) + c];
+                                } else if (levels > 1) {
+                                    iv[h] = (int32_t)box_sum_l(base, n, r + h, c, levels);
+                                    continue;
                                 } else {
                                     w0 = __ldg(reinterpret_cast<const uint32_t*>(base + (int64_t)(2 * (r + h)) * n + 2 * c));
                                     w1 = __ldg(reinterpret_cast<const uint32_t*>(base + (int64_t)(2 * (r + h) + 1) * n + 2 * c));
@@ -1323,8 +1336,8 @@ k_template_offset(const void* __restrict__ tmpl, int m, int n, int levels, int32
     __shared__ double redd[32];
     __shared__ u64 redu[32];
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int mc = levels ? m / 2 : m, nc = levels ? n / 2 : n;
-    const int rows = levels ? 2 * mc : mc, cols = levels ? 2 * nc : nc;
+    const int mc = m >> levels, nc = n >> levels;
+    const int rows = mc << levels, cols = nc << levels;  // the pixels the searched grid covers
     u64 su = 0;
     double sd = 0.0;
     for (int64_t k = tid; k < (int64_t)rows * cols; k += nthr) {

@@ -17,7 +17,8 @@
 namespace moco {
 
 const char* const kKernelNames[K_COUNT] = {"k_frame_rows", "k_energy", "k_cols", "k_rows_inv", "k_jitter",
-                                           "k_copy_shifts", "k_softmin", "k_backward", "k_direct", "k_apply"};
+                                           "k_copy_shifts", "k_softmin", "k_backward", "k_direct", "k_apply",
+                                           "k_jitter_level"};
 
 thread_local std::string g_last_error;
 
@@ -87,6 +88,7 @@ int64_t per_frame_scratch_bytes(const ShapePlan& sp) {
     b += 4 * wm1 * wm1 * 4;                    // corners
     b += W * W * 8;                            // Sa
     b += 8 + 8 + 4;                            // coarse, fbest, margin
+    if (sp.levels > 1) b += 8;                 // the refinement's second shift buffer
     b += 9 * 8 + 4;                            // jitter sums and tickets
     return b;
 }
@@ -95,7 +97,7 @@ moco_status resolve_shape(const moco_shape& d, ShapePlan& sp) {
     if (d.reserved != 0) return fail(MOCO_ERR_INVALID_ARG, "moco_shape.reserved must be 0");
     if (d.m < 1 || d.n < 8 || d.n % 8 != 0 || d.m > 4096 || d.n > 4096)
         return fail(MOCO_ERR_INVALID_ARG, "need 1 <= m <= 4096, 8 <= n <= 4096 and n % 8 == 0");
-    if (d.levels < -1 || d.levels > 1) return fail(MOCO_ERR_INVALID_ARG, "levels must be -1, 0 or 1");
+    if (d.levels < -1 || d.levels > 4) return fail(MOCO_ERR_INVALID_ARG, "levels must be -1 or 0 .. 4");
     if (d.template_dtype != MOCO_TEMPLATE_U16 && d.template_dtype != MOCO_TEMPLATE_F32)
         return fail(MOCO_ERR_INVALID_ARG, "bad template_dtype");
     if (d.xcorr < MOCO_XCORR_AUTO || d.xcorr > MOCO_XCORR_DIRECT_BF16X3)
@@ -106,9 +108,9 @@ moco_status resolve_shape(const moco_shape& d, ShapePlan& sp) {
     sp.f32 = d.template_dtype == MOCO_TEMPLATE_F32;
     if (sp.f32 && sp.levels != 0)
         return fail(MOCO_ERR_UNSUPPORTED, "a float template needs levels == 0");
-    sp.mc = sp.levels ? d.m / 2 : d.m;
-    sp.nc = sp.levels ? d.n / 2 : d.n;
-    if (sp.mc < 1) return fail(MOCO_ERR_INVALID_ARG, "image too small for a 2x2 level");
+    sp.mc = d.m >> sp.levels;
+    sp.nc = d.n >> sp.levels;
+    if (sp.mc < 1 || sp.nc < 1) return fail(MOCO_ERR_INVALID_ARG, "image too small for its levels");
     sp.w = d.w;
     if (d.w < 1 || 2 * d.w - 1 > sp.mc || 2 * d.w - 1 > sp.nc)
         return fail(MOCO_ERR_INVALID_ARG, "need w >= 1 and 2w-1 <= min(mc, nc)");
@@ -117,7 +119,8 @@ moco_status resolve_shape(const moco_shape& d, ShapePlan& sp) {
     sp.Nr = fft_size_for(sp.mc + d.w - 1);
     sp.Nc = fft_size_for(sp.nc + d.w - 1);
     const bool fft_ok = sp.Nr && sp.Nc;
-    const bool direct_ok = direct_smem(sp.W) <= 227 * 1024 && sp.W <= 256;
+    // (the direct form reads 2x2 sums: at most one level)
+    const bool direct_ok = direct_smem(sp.W) <= 227 * 1024 && sp.W <= 256 && sp.levels <= 1;
     sp.nqc = (sp.nc + 63) / 64;
     sp.ncp = sp.nqc * 64;
     if (d.xcorr == MOCO_XCORR_FFT_FP32 && !fft_ok)
@@ -132,7 +135,8 @@ moco_status resolve_shape(const moco_shape& d, ShapePlan& sp) {
     if (!sp.Nc) sp.Nc = 48;
     sp.ncv = sp.Nc / 2 + 1;
     sp.ldx = sp.mc + (sp.mc & 1);
-    sp.unit = sp.levels ? 1.0 / 16.0 : 1.0;
+    sp.unit = 1.0;
+    for (int l = 0; l < sp.levels; ++l) sp.unit /= 16.0;  // costs per full-resolution pixel
     if (d.group_frames > 0) {
         sp.group = d.group_frames;
     } else {
@@ -171,6 +175,7 @@ moco_status allocate_shape(ShapePlan& sp) {
     c.add(&sp.grad_acc, (size_t)(m * n * 4));
     c.add(&sp.grad_Q, (size_t)(W * W * 4));
     if (sp.levels && !sp.f32) c.add(&sp.bsq, (size_t)(m + 1) * (n + 1) * 8);
+    for (int l = 1; l < sp.levels; ++l) c.add(&sp.tlev[l], level_image_elems((int)m, (int)n, l) * 4);
     c.add(&sp.apply_sum, (size_t)m * n * 8);
     c.add(&sp.apply_cnt, (size_t)m * n * 4);
     sp.x_fstride = (int64_t)sp.ncv * sp.ldx;
@@ -229,6 +234,7 @@ size_t bind_scratch(ShapePlan& sp, void* base) {
     c.add(&sp.corners, (size_t)(G * 4 * sp.wm1 * sp.wm1 * 4));
     c.add(&sp.Sa, (size_t)(G * W * W * 8));
     c.add(&sp.coarse, (size_t)(G * 2 * 4));
+    if (sp.levels > 1) c.add(&sp.coarse2, (size_t)(G * 2 * 4));
     c.add(&sp.fbest, (size_t)(G * 8));
     c.add(&sp.margin, (size_t)(G * 4));
     c.add(&sp.jit_acc, (size_t)(G * 9 * 8));
@@ -284,6 +290,10 @@ moco_status prepare_template(ShapePlan& sp, const void* tmpl_dev, cudaStream_t s
     if (sp.bsq) {
         e = launch_sq_prefix(static_cast<const uint16_t*>(sp.tmpl), sp.desc.m, sp.desc.n, sp.bsq, st);
         if (e != cudaSuccess) return cuda_fail(e, "template square prefix table");
+    }
+    for (int l = 1; l < sp.levels; ++l) {
+        e = launch_box_level(static_cast<const uint16_t*>(sp.tmpl), sp.desc.m, sp.desc.n, l, sp.tlev[l], st);
+        if (e != cudaSuccess) return cuda_fail(e, "template level image");
     }
     return MOCO_OK;
 }
@@ -352,10 +362,21 @@ moco_status align_frames(ShapePlan& sp, const uint16_t* frames, int64_t T, int32
                                      margin ? margin + f0 : nullptr, st);
         if (s != MOCO_OK) return s;
         cudaError_t e;
+        // Levels L-1 .. 1: the 3x3 refinement on each level's box sums; the
+        // shifts alternate between the two buffers.
+        const int32_t* cin = sp.coarse;
+        for (int l = sp.levels - 1; l >= 1; --l) {
+            int32_t* cout = (cin == sp.coarse) ? sp.coarse2 : sp.coarse;
+            sp.prof->begin(K_JITTER_LEVEL, st);
+            e = launch_jitter_level(frames + f0 * mn, mn, g, sp.desc.m, sp.desc.n, l, sp.tlev[l], cin, cout, st);
+            sp.prof->end(st);
+            if (e != cudaSuccess) return cuda_fail(e, "k_jitter_level");
+            cin = cout;
+        }
         sp.prof->begin(sp.levels ? K_JITTER : K_COPY_SHIFTS, st);
         if (sp.levels)
             e = launch_jitter(frames + f0 * mn, mn, g, static_cast<const uint16_t*>(sp.tmpl), sp.desc.m,
-                              sp.desc.n, sp.bsq, sp.coarse, shifts + 2 * f0, final_cost ? final_cost + f0 : nullptr,
+                              sp.desc.n, sp.bsq, cin, shifts + 2 * f0, final_cost ? final_cost + f0 : nullptr,
                               sp.jit_acc, sp.jit_ticket, st);
         else
             e = launch_copy_shifts(sp.coarse, shifts + 2 * f0, best_cost ? best_cost + f0 : sp.fbest,

@@ -14,7 +14,7 @@ namespace moco {
 // Optional per-kernel timing: CUDA events recorded on the launching stream
 // around every kernel launch (enabled by moco_profile_enable).
 enum KernelId { K_FRAME_ROWS = 0, K_ENERGY, K_COLS, K_ROWS_INV, K_JITTER, K_COPY_SHIFTS, K_SOFTMIN,
-                K_BACKWARD, K_DIRECT, K_APPLY, K_COUNT };
+                K_BACKWARD, K_DIRECT, K_APPLY, K_JITTER_LEVEL, K_COUNT };
 extern const char* const kKernelNames[K_COUNT];
 
 struct Profiler {
@@ -65,6 +65,7 @@ struct ShapePlan {
     float2* Sb2 = nullptr;  // Sb as FP32 pairs (hi, lo), W^2
     float* ia32 = nullptr;  // unit / Area, W^2
     u64* bsq = nullptr;  // with a level: prefix table of b^2, (m+1) x (n+1)
+    int32_t* tlev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // template level images 1 .. levels-1
     u64* apply_sum = nullptr;           // m x n: the correction step's per-pixel sums
     unsigned int* apply_cnt = nullptr;  // m x n: and counts
     // direct form
@@ -83,6 +84,7 @@ struct ShapePlan {
     uint32_t* corners = nullptr;
     u64* Sa = nullptr;
     int32_t* coarse = nullptr;
+    int32_t* coarse2 = nullptr;  // levels > 1: the refinement's other buffer
     double* fbest = nullptr;
     float* margin = nullptr;
     float* grad_acc = nullptr;         // m x n (adjoint scratch)

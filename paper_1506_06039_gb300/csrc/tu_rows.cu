@@ -16,7 +16,7 @@ static cudaError_t frame_rows_n(const void* src, int64_t src_fstride, int64_t ni
                                 uint32_t* corners, int wm1, unsigned int* err, cudaStream_t st) {
     const size_t smem = sizeof(float2) * ((kRC / 2) * fft_ld<N>() + N) + sizeof(u64) * (kRC + nc);
     const size_t smem_staged = frame_rows_smem_base<N, F32>(nc) + frame_rows_stage_bytes(n, levels);
-    if (!F32 && n % 8 == 0 && smem_staged <= kStagedSmemMax) {
+    if (!F32 && n % 8 == 0 && levels <= 1 && smem_staged <= kStagedSmemMax) {
         const void* fn = (const void*)k_frame_rows<N, false, false, true>;
         cudaError_t e = ensure_smem(fn, smem_staged);
         if (e != cudaSuccess) return e;

@@ -57,7 +57,8 @@ def _plan_status(lib, shape, template_ptr=0x1000):
     (binding.MocoShape(128, 128, 0, -1, 0, 0, 0, 0), "w >= 1"),        # empty window
     (binding.MocoShape(128, 128, 65, -1, 0, 0, 0, 0), "2w-1"),         # window larger than the image
     (binding.MocoShape(512, 512, 129, -1, 0, 0, 0, 0), "2w-1"),        # on the searched grid
-    (binding.MocoShape(128, 128, 10, 2, 0, 0, 0, 0), "levels"),
+    (binding.MocoShape(128, 128, 10, 5, 0, 0, 0, 0), "levels"),          # at most four levels
+    (binding.MocoShape(128, 128, 10, 3, 0, 0, 0, 0), "2w-1"),            # 16 x 16 level-3 grid
     (binding.MocoShape(128, 128, 10, -1, 7, 0, 0, 0), "template_dtype"),
     (binding.MocoShape(128, 128, 10, -1, 0, 9, 0, 0), "xcorr"),
     (binding.MocoShape(128, 128, 10, -1, 0, 0, 0, 1), "reserved"),
