@@ -44,8 +44,10 @@ cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg,
 // and the 3x3 refinement on level l of the doubled level-(l+1) optimum.
 size_t level_image_elems(int m, int n, int l);
 cudaError_t launch_box_level(const uint16_t* img, int m, int n, int l, int32_t* out, cudaStream_t st);
+// acc: nimg x 9 u64 and ticket: nimg u32 of scratch (cleared here).
 cudaError_t launch_jitter_level(const uint16_t* frames, int64_t fstride, int64_t nimg, int m, int n, int l,
-                                const int32_t* bl, const int32_t* cin, int32_t* cout, cudaStream_t st);
+                                const int32_t* bl, const int32_t* cin, int32_t* cout, u64* acc,
+                                unsigned int* ticket, cudaStream_t st);
 
 // The correction step: corrected frames and/or the corrected mean image;
 // sum (u64) and cnt (u32) are m*n scratch, cleared here.

@@ -368,7 +368,8 @@ moco_status align_frames(ShapePlan& sp, const uint16_t* frames, int64_t T, int32
         for (int l = sp.levels - 1; l >= 1; --l) {
             int32_t* cout = (cin == sp.coarse) ? sp.coarse2 : sp.coarse;
             sp.prof->begin(K_JITTER_LEVEL, st);
-            e = launch_jitter_level(frames + f0 * mn, mn, g, sp.desc.m, sp.desc.n, l, sp.tlev[l], cin, cout, st);
+            e = launch_jitter_level(frames + f0 * mn, mn, g, sp.desc.m, sp.desc.n, l, sp.tlev[l], cin, cout,
+                                    sp.jit_acc, sp.jit_ticket, st);
             sp.prof->end(st);
             if (e != cudaSuccess) return cuda_fail(e, "k_jitter_level");
             cin = cout;

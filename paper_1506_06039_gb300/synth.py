@@ -122,7 +122,7 @@ def _translate_fill(x: np.ndarray, s: int, t: int) -> np.ndarray:
 
 def make_stack_torch(m: int, n: int, T: int, nblobs: int, shift_max: int, seed: int,
                      device="cuda", template: str = "mean100", chunk: int = 256,
-                     activity_sigma: float = 0.3) -> Stack:
+                     activity_sigma: float = 0.3, sigma_range=(3.0, 6.0)) -> Stack:
     """Device stack for the large workloads (2000 x 512^2 is 1 GiB of uint16).
 
     Blob parameters, activities and shifts come from the same numpy PCG64
@@ -131,7 +131,7 @@ def make_stack_torch(m: int, n: int, T: int, nblobs: int, shift_max: int, seed: 
     import torch
 
     rng = np.random.Generator(np.random.PCG64(seed))
-    blobs = draw_blobs(rng, m, n, nblobs)
+    blobs = draw_blobs(rng, m, n, nblobs, sigma_range=sigma_range)
     alpha, shifts = draw_frame_params(rng, T, nblobs, shift_max, activity_sigma)
     gy, gx = _profiles(blobs, m, n)
     dev = torch.device(device)
