@@ -184,6 +184,26 @@ moco_status moco_apply_shifts(moco_plan_t plan, int32_t shape_idx, const uint16_
                               const int32_t* shifts_dev, uint16_t fill, uint16_t* corrected_dev, double* mean_dev,
                               void* stream);
 
+/* The closed-loop single-frame mode (Section 1: real-time, closed-loop
+ * experiments): a handle that aligns one frame at a time from host memory.
+ * moco_stream_create registers frame_host (m x n uint16 of shape shape_idx)
+ * and shift_host (2 int32); both should be page-locked (cudaHostAlloc) for
+ * the shortest copies, and must stay valid until the handle is destroyed.
+ * It allocates one frame and one shift on the device and captures, once,
+ * the copy of frame_host to the device, the plan's alignment of that frame
+ * (moco_align_stack with T = 1) and the copy of the shift to shift_host into
+ * a CUDA graph (running the step once eagerly first).
+ * moco_stream_align replays that graph on `stream` and waits for it: on
+ * return shift_host holds (s, t) of the frame that was in frame_host, which
+ * the caller may then overwrite with the next frame. The handle shares the
+ * plan's batch scratch: it must not run concurrently with other calls on the
+ * same plan. The plan must outlive the handle. */
+typedef struct moco_stream_s* moco_stream_t;
+moco_status moco_stream_create(moco_plan_t plan, int32_t shape_idx, const uint16_t* frame_host, int32_t* shift_host,
+                               moco_stream_t* out);
+moco_status moco_stream_align(moco_stream_t handle, void* stream);
+moco_status moco_stream_destroy(moco_stream_t handle);
+
 /* The full-resolution 3x3 refinement on its own, allocating nothing (the
  * paper has no counterpart: this exists for callers that cannot call
  * cudaMalloc, such as code inside a host application that owns all device

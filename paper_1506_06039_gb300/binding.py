@@ -32,7 +32,7 @@ EXPORTS = (
     "moco_plan", "moco_set_template", "moco_align_stack", "moco_cost_surface", "moco_softmin",
     "moco_cost_backward", "moco_align_host", "moco_plan_query", "moco_plan_destroy",
     "moco_status_string", "moco_last_error", "moco_profile_enable", "moco_profile_read", "moco_plan_status",
-    "moco_jitter_noalloc", "moco_apply_shifts",
+    "moco_jitter_noalloc", "moco_apply_shifts", "moco_stream_create", "moco_stream_align", "moco_stream_destroy",
 )
 
 
@@ -99,6 +99,9 @@ def lib():
             L.moco_plan_status.argtypes = [P]
             L.moco_jitter_noalloc.argtypes = [P, i64, i32, i32, P, P, P, P]
             L.moco_apply_shifts.argtypes = [P, i32, P, i64, P, ctypes.c_uint16, P, P, P]
+            L.moco_stream_create.argtypes = [P, i32, P, P, ctypes.POINTER(P)]
+            L.moco_stream_align.argtypes = [P, P]
+            L.moco_stream_destroy.argtypes = [P]
             L.moco_profile_read.argtypes = [P, ctypes.POINTER(MocoKernelStat), i32, ctypes.POINTER(i32), i32]
             for name in EXPORTS:
                 if name not in ("moco_status_string", "moco_last_error"):
@@ -213,6 +216,37 @@ def moco_apply_shifts(plan, shape_idx, frames, shifts, fill=0, corrected=None, m
     _check(lib().moco_apply_shifts(plan, shape_idx, _ptr(frames), T, _ptr(shifts), int(fill),
                                    corrected.data_ptr() if corrected is not None else None,
                                    mean.data_ptr() if mean is not None else None, _stream(stream)))
+
+
+class FrameStream:
+    """The closed-loop single-frame mode: write a frame into .frame (pinned
+    host, uint16 [m, n]), call align(), read .shift (pinned host, int32 [2])."""
+
+    def __init__(self, plan, shape_idx=0):
+        import torch
+        m, n = int(plan.shapes[shape_idx]["m"]), int(plan.shapes[shape_idx]["n"])
+        self.frame = torch.zeros((m, n), dtype=torch.uint16).pin_memory()
+        self.shift = torch.zeros(2, dtype=torch.int32).pin_memory()
+        self._plan = plan  # the plan must outlive the handle
+        h = ctypes.c_void_p()
+        _check(lib().moco_stream_create(plan.handle, shape_idx, self.frame.data_ptr(), self.shift.data_ptr(),
+                                        ctypes.byref(h)))
+        self.handle = h
+
+    def align(self, stream=None):
+        _check(lib().moco_stream_align(self.handle, _stream(stream)))
+        return int(self.shift[0]), int(self.shift[1])
+
+    def close(self):
+        if self.handle:
+            _check(lib().moco_stream_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def moco_softmin(plan, shape_idx, cost, tau_scale, loss, weights, stream=None):
