@@ -147,7 +147,7 @@ moco_status moco_softmin(moco_plan_t plan, int32_t shape_idx, const double* cost
  * with dL/da. Uses the plan's current template. The correlation parts run
  * as direct FP32 contractions with FP32 atomics across frame chunks, so the
  * last bits vary from run to run. MOCO_ERR_UNSUPPORTED when levels != 0 or
- * the window needs more shared memory than a CTA has (w > 48). */
+ * the window needs more shared memory than a CTA has (w > 56). */
 moco_status moco_cost_backward(moco_plan_t plan, int32_t shape_idx, const uint16_t* frames_dev, int64_t T,
                                const float* grad_cost_dev, float grad_scale, float* grad_template_dev,
                                float* grad_frames_dev, void* stream);

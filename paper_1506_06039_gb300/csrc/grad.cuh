@@ -132,14 +132,17 @@ k_softmin(const double* __restrict__ cost, int K, double tau_scale, double* __re
     for (int k = tid; k < K; k += nthr) wf[k] = (float)(exp(-(c[k] - fmin_v) / tau) / Z);
 }
 
-// Q[k] = scale * inv_area[k] * sum_f G[f][k] (k < K), one thread per k.
+// Q[k] += scale * inv_area[k] * sum_f G[f][k] (k < K) over one chunk of
+// kQsumFrames frames: grid (k blocks, frame chunks); Q is zero on entry.
+constexpr int kQsumFrames = 32;
 static __global__ void k_grad_qsum(const float* __restrict__ G, int64_t T, int K, const double* __restrict__ inv_area,
                             float scale, float* __restrict__ Q) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
-    double s = 0.0;
-    for (int64_t f = 0; f < T; ++f) s += (double)G[f * K + k];
-    Q[k] = (float)(s * inv_area[k] * (double)scale);
+    const int64_t f0 = (int64_t)blockIdx.y * kQsumFrames, f1 = (T < f0 + kQsumFrames) ? T : f0 + kQsumFrames;
+    float s = 0.f;
+    for (int64_t f = f0; f < f1; ++f) s += G[f * K + k];
+    atomicAdd(&Q[k], s * (float)inv_area[k] * scale);
 }
 
 // 2-D inclusive prefix of a W x W table into P ((W+1) x (W+1), P[0][*] =
@@ -172,54 +175,88 @@ __device__ __forceinline__ float rect(const float* P, int W, int wm1, int slo, i
 }
 
 // Correlation part of dL/db: acc[i][j] += sum_{f in chunk} sum_st q_f,st a'_f[i+s][j+t]
-// for one 32 x 32 tile; q_f = scale * G_f * inv_area. Grid (tiles_x, tiles_y, frame chunks).
+// for one kGradTY x kGradTX tile; q_f = scale * G_f * inv_area. Grid
+// (tiles_x, tiles_y, chunks of kGradTmplFrames frames). Each of the 16 x 16
+// threads owns 4 rows x 8 columns of outputs; for every shift row s it slides
+// 12-value windows of its four halo rows along t, four taps at a time from
+// 16-byte shared loads (q's rows are zero-padded to Wp, a multiple of 4, so
+// the last taps add zeros).
+constexpr int kGradTY = 64, kGradTX = 128, kGradTmplFrames = 8;
+
+__host__ __device__ constexpr int grad_wp(int W) { return (W + 3) / 4 * 4; }
+
 static __global__ void __launch_bounds__(kGradThreads)
 k_grad_tmpl(const uint16_t* __restrict__ frames, int64_t T, int m, int n, int wm1, const float* __restrict__ G,
             const double* __restrict__ inv_area, float scale, const int32_t* __restrict__ coff,
             float* __restrict__ acc_out) {
     extern __shared__ __align__(16) float sm[];
-    const int W = 2 * wm1 + 1, K = W * W;
-    const int H = kGradTile + 2 * wm1;  // halo edge
-    float* halo = sm;                   // H x H
-    float* q = sm + H * H;              // K
+    const int W = 2 * wm1 + 1, K = W * W, Wp = grad_wp(W);
+    const int Hy = kGradTY + 2 * wm1, Hx = kGradTX + Wp;  // halo rows, padded halo row length
+    float* halo = sm;                                      // Hy x Hx
+    float* q = sm + Hy * Hx;                               // W x Wp
     const int tid = threadIdx.x;
-    const int i0 = blockIdx.y * kGradTile, j0 = blockIdx.x * kGradTile;
-    const int ty = tid >> 3, tx = (tid & 7) * 4;  // output row ty, columns tx..tx+3
+    const int i0 = blockIdx.y * kGradTY, j0 = blockIdx.x * kGradTX;
+    const int ty = tid >> 4, tx = tid & 15;  // outputs (ty*4 + r, tx*8 + x)
     const float c = (float)*coff;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    const int64_t f_begin = (int64_t)blockIdx.z * kGradFramesPerCta;
-    const int64_t f_end = (T < f_begin + kGradFramesPerCta) ? T : f_begin + kGradFramesPerCta;
+    float acc[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int x = 0; x < 8; ++x) acc[r][x] = 0.f;
+    const int64_t f_begin = (int64_t)blockIdx.z * kGradTmplFrames;
+    const int64_t f_end = (T < f_begin + kGradTmplFrames) ? T : f_begin + kGradTmplFrames;
     for (int64_t f = f_begin; f < f_end; ++f) {
         __syncthreads();
         const uint16_t* a = frames + f * (int64_t)m * n;
-        for (int k = tid; k < H * H; k += kGradThreads) {
-            const int r = k / H, cc = k - r * H;
-            const int ai = i0 - wm1 + r, aj = j0 - wm1 + cc;
-            halo[k] = (ai >= 0 && ai < m && aj >= 0 && aj < n) ? (float)a[(int64_t)ai * n + aj] - c : 0.f;
+        for (int r = tid >> 5; r < Hy; r += kGradThreads / 32) {
+            const int ai = i0 - wm1 + r;
+            for (int cc = tid & 31; cc < Hx; cc += 32) {
+                const int aj = j0 - wm1 + cc;
+                halo[r * Hx + cc] = (cc < kGradTX + W - 1 && ai >= 0 && ai < m && aj >= 0 && aj < n)
+                                        ? (float)a[(int64_t)ai * n + aj] - c : 0.f;
+            }
         }
-        for (int k = tid; k < K; k += kGradThreads) q[k] = scale * G[f * K + k] * (float)inv_area[k];
+        for (int k = tid; k < W * Wp; k += kGradThreads) {
+            const int si = k / Wp, ti = k - si * Wp;
+            q[k] = ti < W ? scale * G[f * K + si * W + ti] * (float)inv_area[si * W + ti] : 0.f;
+        }
         __syncthreads();
         for (int s = 0; s < W; ++s) {
-            const float* hrow = halo + (ty + s) * H + tx;
-            const float* qrow = q + s * W;
-            float seg[4];
+            const float* qrow = q + s * Wp;
+            float win[4][12];
 #pragma unroll
-            for (int x = 0; x < 3; ++x) seg[x] = hrow[x];
-            for (int t = 0; t < W; ++t) {
-                seg[3] = hrow[t + 3];
-                const float qv = qrow[t];
+            for (int r = 0; r < 4; ++r) {
+                const float* hp = halo + (ty * 4 + r + s) * Hx + tx * 8;
+                const float4 v0 = *reinterpret_cast<const float4*>(hp);
+                const float4 v1 = *reinterpret_cast<const float4*>(hp + 4);
+                win[r][0] = v0.x; win[r][1] = v0.y; win[r][2] = v0.z; win[r][3] = v0.w;
+                win[r][4] = v1.x; win[r][5] = v1.y; win[r][6] = v1.z; win[r][7] = v1.w;
+            }
+            for (int t0 = 0; t0 < Wp; t0 += 4) {
+                const float4 q4 = *reinterpret_cast<const float4*>(qrow + t0);
+                const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
 #pragma unroll
-                for (int x = 0; x < 4; ++x) acc[x] = fmaf(qv, seg[x], acc[x]);
+                for (int r = 0; r < 4; ++r) {
+                    const float4 v = *reinterpret_cast<const float4*>(halo + (ty * 4 + r + s) * Hx + tx * 8 + t0 + 8);
+                    win[r][8] = v.x; win[r][9] = v.y; win[r][10] = v.z; win[r][11] = v.w;
 #pragma unroll
-                for (int x = 0; x < 3; ++x) seg[x] = seg[x + 1];
+                    for (int dt = 0; dt < 4; ++dt)
+#pragma unroll
+                        for (int x = 0; x < 8; ++x) acc[r][x] = fmaf(qv[dt], win[r][x + dt], acc[r][x]);
+#pragma unroll
+                    for (int x = 0; x < 8; ++x) win[r][x] = win[r][x + 4];
+                }
             }
         }
     }
-    const int i = i0 + ty;
 #pragma unroll
-    for (int x = 0; x < 4; ++x) {
-        const int j = j0 + tx + x;
-        if (i < m && j < n) atomicAdd(&acc_out[(int64_t)i * n + j], acc[x]);
+    for (int r = 0; r < 4; ++r) {
+        const int i = i0 + ty * 4 + r;
+#pragma unroll
+        for (int x = 0; x < 8; ++x) {
+            const int j = j0 + tx * 8 + x;
+            if (i < m && j < n) atomicAdd(&acc_out[(int64_t)i * n + j], acc[r][x]);
+        }
     }
 }
 

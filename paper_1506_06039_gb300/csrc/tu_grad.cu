@@ -13,9 +13,14 @@ cudaError_t launch_softmin(const double* cost, int64_t T, int K, double tau_scal
     return cudaGetLastError();
 }
 
+static size_t grad_tmpl_smem(int wm1) {
+    const int W = 2 * wm1 + 1, Wp = grad_wp(W);
+    return sizeof(float) * ((size_t)(kGradTY + 2 * wm1) * (kGradTX + Wp) + (size_t)W * Wp);
+}
+
 size_t grad_smem_bytes(int wm1) {
     const int W = 2 * wm1 + 1, K = W * W, L = W + 1, H = kGradTile + 2 * wm1;
-    const size_t tmpl = sizeof(float) * ((size_t)H * H + K);
+    const size_t tmpl = grad_tmpl_smem(wm1);
     const size_t frames = sizeof(float) * ((size_t)H * H + 2 * (size_t)K + (size_t)L * L);
     const size_t fin = sizeof(float) * (size_t)L * L;
     return std::max(tmpl, std::max(frames, fin));
@@ -28,12 +33,15 @@ cudaError_t launch_grad(const uint16_t* frames, int64_t T, int m, int n, int wm1
     const int W = 2 * wm1 + 1, K = W * W, L = W + 1, H = kGradTile + 2 * wm1;
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)m * n, st);
     if (e != cudaSuccess) return e;
-    k_grad_qsum<<<(K + 255) / 256, 256, 0, st>>>(G, T, K, inv_area, scale, Q);
+    if ((e = cudaMemsetAsync(Q, 0, sizeof(float) * (size_t)K, st)) != cudaSuccess) return e;
+    k_grad_qsum<<<dim3((K + 255) / 256, (unsigned)((T + kQsumFrames - 1) / kQsumFrames)), 256, 0, st>>>(
+        G, T, K, inv_area, scale, Q);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const dim3 tiles((n + kGradTile - 1) / kGradTile, (m + kGradTile - 1) / kGradTile);
-    const size_t sm_t = sizeof(float) * ((size_t)H * H + K);
+    const size_t sm_t = grad_tmpl_smem(wm1);
     if ((e = ensure_smem((const void*)k_grad_tmpl, sm_t)) != cudaSuccess) return e;
-    const dim3 g1(tiles.x, tiles.y, (unsigned)((T + kGradFramesPerCta - 1) / kGradFramesPerCta));
+    const dim3 g1((n + kGradTX - 1) / kGradTX, (m + kGradTY - 1) / kGradTY,
+                  (unsigned)((T + kGradTmplFrames - 1) / kGradTmplFrames));
     k_grad_tmpl<<<g1, kGradThreads, sm_t, st>>>(frames, T, m, n, wm1, G, inv_area, scale, coff, acc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const size_t sm_f = sizeof(float) * (size_t)L * L;
