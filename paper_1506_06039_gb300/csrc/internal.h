@@ -71,10 +71,24 @@ cudaError_t launch_softmin(const double* cost, int64_t T, int K, double tau_scal
 size_t grad_smem_bytes(int wm1);
 
 // Adjoint of f (levels = 0): grad_template += dL/db, grad_frames = dL/da
-// (if non-null). acc (m*n floats) and Q (W*W floats) are scratch.
+// (if non-null). acc (m*n floats) and Q (W*W floats) are scratch. With corr
+// set the correlation part of dL/db is formed here by the tiled direct
+// contraction; with corr clear acc already holds it (the FFT route below).
 cudaError_t launch_grad(const uint16_t* frames, int64_t T, int m, int n, int wm1, const float* G, float scale,
-                        const double* inv_area, const int32_t* coff, const void* tmpl, int tmpl_f32,
+                        const double* inv_area, const int32_t* coff, const void* tmpl, int tmpl_f32, int corr,
                         float* acc, float* Q, float* grad_template, float* grad_frames, cudaStream_t st);
+
+// The correlation part of dL/db through FFTs (FFT form, levels = 0):
+// QX[f][v][k] = row spectra of q_f = scale * G_f / Area (k = s + w - 1);
+// Acc (ncv x Nr, four-step order, zero before the first group) += sum_f
+// DFT_cols(X_f) * conj(DFT_cols(QX_f)); the inverse writes acc[r][j] for
+// r < mc, j < nc, through Yt (mc x ncv complex scratch).
+cudaError_t launch_q_rows(int Nc, const float* G, const double* inv_area, float scale, int wm1, int64_t T,
+                          const float2* twc, float2* QX, cudaStream_t st);
+cudaError_t launch_adj_cols(int Nr, const float2* X, int64_t x_fstride, int ldx, int mc, int ncv, const float2* QX,
+                            int wm1, int64_t T, const float2* twr, float2* Acc, cudaStream_t st);
+cudaError_t launch_adj_inverse(int Nr, int Nc, const float2* Acc, int ncv, int mc, int nc, const float2* twr,
+                               const float2* twc, float2* Yt, float* out, cudaStream_t st);
 
 // ---- the direct (tensor-core) form -----------------------------------------
 size_t direct_tiles_bytes(int mc, int nqc, int W);  // hi + lo Toeplitz tiles

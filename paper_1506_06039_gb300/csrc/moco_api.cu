@@ -174,6 +174,7 @@ moco_status allocate_shape(ShapePlan& sp) {
     c.add(&sp.ia32, (size_t)W * W * 4);
     c.add(&sp.grad_acc, (size_t)(m * n * 4));
     c.add(&sp.grad_Q, (size_t)(W * W * 4));
+    c.add(&sp.grad_spec, sp.has_fft ? (size_t)sp.ncv * sp.Nr * 8 : 0);
     if (sp.levels && !sp.f32) c.add(&sp.bsq, (size_t)(m + 1) * (n + 1) * 8);
     for (int l = 1; l < sp.levels; ++l) c.add(&sp.tlev[l], level_image_elems((int)m, (int)n, l) * 4);
     c.add(&sp.apply_sum, (size_t)m * n * 8);
@@ -640,9 +641,31 @@ moco_status moco_cost_backward(moco_plan_t plan, int32_t shape_idx, const uint16
     DeviceGuard guard(plan->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     plan->prof.begin(K_BACKWARD, st);
-    cudaError_t e = launch_grad(frames_dev, T, sp.desc.m, sp.desc.n, sp.wm1, grad_cost_dev, grad_scale, sp.inv_area,
-                                sp.coff_i, sp.tmpl, sp.f32 ? 1 : 0, sp.grad_acc, sp.grad_Q, grad_template_dev,
-                                grad_frames_dev, st);
+    cudaError_t e = cudaSuccess;
+    if (sp.has_fft) {
+        // sum_f a'_f (correlated with) q_f = IDFT2(sum_f A_f conj(Q_f)), group by group
+        // through the search's own row spectra X; QX takes Y's place.
+        const int64_t mn = (int64_t)sp.desc.m * sp.desc.n, K = (int64_t)sp.W * sp.W;
+        e = cudaMemsetAsync(sp.grad_spec, 0, (size_t)sp.ncv * sp.Nr * 8, st);
+        for (int64_t f0 = 0; f0 < T && e == cudaSuccess; f0 += sp.group) {
+            const int64_t g = std::min<int64_t>(sp.group, T - f0);
+            e = launch_frame_rows(sp.Nc, false, frames_dev + f0 * mn, mn, g, sp.desc.m, sp.desc.n, 0, sp.mc, sp.nc,
+                                  sp.coff_i, nullptr, sp.twc, sp.X, sp.x_fstride, sp.ldx, sp.rowE, sp.colE, sp.tot,
+                                  sp.corners, sp.wm1, sp.dev_err, st);
+            if (e == cudaSuccess)
+                e = launch_q_rows(sp.Nc, grad_cost_dev + f0 * K, sp.inv_area, grad_scale, sp.wm1, g, sp.twc, sp.Y, st);
+            if (e == cudaSuccess)
+                e = launch_adj_cols(sp.Nr, sp.X, sp.x_fstride, sp.ldx, sp.mc, sp.ncv, sp.Y, sp.wm1, g, sp.twr,
+                                    sp.grad_spec, st);
+        }
+        if (e == cudaSuccess)
+            e = launch_adj_inverse(sp.Nr, sp.Nc, sp.grad_spec, sp.ncv, sp.mc, sp.nc, sp.twr, sp.twc, sp.X,
+                                   sp.grad_acc, st);
+    }
+    if (e == cudaSuccess)
+        e = launch_grad(frames_dev, T, sp.desc.m, sp.desc.n, sp.wm1, grad_cost_dev, grad_scale, sp.inv_area,
+                        sp.coff_i, sp.tmpl, sp.f32 ? 1 : 0, sp.has_fft ? 0 : 1, sp.grad_acc, sp.grad_Q,
+                        grad_template_dev, grad_frames_dev, st);
     plan->prof.end(st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint kernels");
     return MOCO_OK;

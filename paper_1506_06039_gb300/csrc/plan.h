@@ -89,6 +89,7 @@ struct ShapePlan {
     float* margin = nullptr;
     float* grad_acc = nullptr;         // m x n (adjoint scratch)
     float* grad_Q = nullptr;           // W x W
+    float2* grad_spec = nullptr;       // ncv x Nr (FFT form): sum_f A_f conj(Q_f) of the adjoint
     u64* jit_acc = nullptr;            // group x 9
     unsigned int* jit_ticket = nullptr;  // group
     // staging for moco_align_host (double-buffered)

@@ -27,23 +27,25 @@ size_t grad_smem_bytes(int wm1) {
 }
 
 cudaError_t launch_grad(const uint16_t* frames, int64_t T, int m, int n, int wm1, const float* G, float scale,
-                        const double* inv_area, const int32_t* coff, const void* tmpl, int tmpl_f32,
+                        const double* inv_area, const int32_t* coff, const void* tmpl, int tmpl_f32, int corr,
                         float* acc, float* Q, float* grad_template, float* grad_frames, cudaStream_t st) {
     if (T <= 0) return cudaSuccess;
     const int W = 2 * wm1 + 1, K = W * W, L = W + 1, H = kGradTile + 2 * wm1;
-    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)m * n, st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (corr && (e = cudaMemsetAsync(acc, 0, sizeof(float) * (size_t)m * n, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(Q, 0, sizeof(float) * (size_t)K, st)) != cudaSuccess) return e;
     k_grad_qsum<<<dim3((K + 255) / 256, (unsigned)((T + kQsumFrames - 1) / kQsumFrames)), 256, 0, st>>>(
         G, T, K, inv_area, scale, Q);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const dim3 tiles((n + kGradTile - 1) / kGradTile, (m + kGradTile - 1) / kGradTile);
-    const size_t sm_t = grad_tmpl_smem(wm1);
-    if ((e = ensure_smem((const void*)k_grad_tmpl, sm_t)) != cudaSuccess) return e;
-    const dim3 g1((n + kGradTX - 1) / kGradTX, (m + kGradTY - 1) / kGradTY,
-                  (unsigned)((T + kGradTmplFrames - 1) / kGradTmplFrames));
-    k_grad_tmpl<<<g1, kGradThreads, sm_t, st>>>(frames, T, m, n, wm1, G, inv_area, scale, coff, acc);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (corr) {
+        const size_t sm_t = grad_tmpl_smem(wm1);
+        if ((e = ensure_smem((const void*)k_grad_tmpl, sm_t)) != cudaSuccess) return e;
+        const dim3 g1((n + kGradTX - 1) / kGradTX, (m + kGradTY - 1) / kGradTY,
+                      (unsigned)((T + kGradTmplFrames - 1) / kGradTmplFrames));
+        k_grad_tmpl<<<g1, kGradThreads, sm_t, st>>>(frames, T, m, n, wm1, G, inv_area, scale, coff, acc);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     const size_t sm_f = sizeof(float) * (size_t)L * L;
     if ((e = ensure_smem((const void*)k_grad_tmpl_finish, sm_f)) != cudaSuccess) return e;
     const int64_t blocks = std::min<int64_t>(1024, ((int64_t)m * n + 255) / 256);

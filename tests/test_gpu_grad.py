@@ -15,7 +15,8 @@ import pytest
 import torch
 
 import oracle
-from paper_1506_06039_gb300 import build, synth
+from paper_1506_06039_gb300 import Plan, build, synth
+from paper_1506_06039_gb300.binding import TEMPLATE_F32, XCORR_DIRECT_BF16X3, XCORR_FFT_FP32
 from paper_1506_06039_gb300.autograd import MocoSoftMin, refine_template, softmin_plan
 
 pytestmark = pytest.mark.gpu
@@ -36,10 +37,15 @@ def stack(m, n, T, w, seed, shift=None):
     return st.frames, tmpl.astype(np.float32)
 
 
-def gpu_loss_grad(frames, tmpl, w, grad_frames=False):
+def gpu_loss_grad(frames, tmpl, w, grad_frames=False, xcorr=None, group_frames=0):
     fr = torch.from_numpy(frames).cuda()
     tb = torch.from_numpy(tmpl).cuda()
-    plan = softmin_plan(fr, tb, w)
+    if xcorr is None:
+        plan = softmin_plan(fr, tb, w, group_frames=group_frames)
+    else:
+        m, n = tmpl.shape
+        plan = Plan(dict(m=m, n=n, w=w, levels=0, template_dtype=TEMPLATE_F32, xcorr=xcorr,
+                         group_frames=group_frames), tb)
     try:
         cost = plan.cost_surface(fr)
         loss, weights = plan.softmin(cost, TAU)
@@ -72,6 +78,23 @@ def test_softmin_loss_and_gradients_match_oracle():
     check_loss(loss, lf, frames, tmpl, 8)
     assert np.abs(gt - gb).max() <= 1e-3 * np.abs(gb).max()
     assert np.abs(gf - ga).max() <= 1e-3 * np.abs(ga).max()
+
+
+@pytest.mark.parametrize("route", ["fft", "direct"])
+def test_template_adjoint_routes_ragged_groups(route):
+    # The correlation part of dL/db through the FFTs (FFT form) and through
+    # the tiled direct contraction (direct form), on a ragged frame size that
+    # spans several column blocks and FFT tiles, with frame groups of 4 (three
+    # groups, the last one short).
+    m, n, w, T = 90, 88, 7, 10
+    frames, tmpl = stack(m, n, T, w, seed=33)
+    xc = XCORR_FFT_FP32 if route == "fft" else XCORR_DIRECT_BF16X3
+    _, loss, gt, _ = gpu_loss_grad(frames, tmpl, w, xcorr=xc, group_frames=4)
+    tau = oracle_tau(frames, tmpl, w)
+    _, lf, gb, _ = oracle.softmin_loss(frames.astype(np.float64), tmpl.astype(np.float64), w, tau,
+                                       grad_template=True)
+    check_loss(loss, lf, frames, tmpl, w)
+    assert np.abs(gt - gb).max() <= 1e-3 * np.abs(gb).max()
 
 
 def test_gradient_central_differences_64_pixels():
