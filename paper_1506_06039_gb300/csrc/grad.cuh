@@ -11,8 +11,10 @@
 //   dL/da_f[k][l] = 2 a'_f[k][l] sum_st q_f,st 1[0<=k-s<m] 1[0<=l-t<n] - 2 sum_st q_f,st b'[k-s][l-t]
 // with Q = sum_f q_f, a' = a - c, b' = b - c (the plan's offset; f does not
 // depend on it), and a', b' taken as zero outside the image (that zero
-// carries the 1[(i,j) in D_st] of each sum). The correlation sums run as
-// tiled direct FP32 contractions; the indicator sums are rectangle sums of a
+// carries the 1[(i,j) in D_st] of each sum). The template side's correlation
+// sum runs through FFTs where the plan has the FFT form (tu_adjoint.cu) and
+// as the tiled direct FP32 contraction below otherwise; the frame side's is
+// a direct contraction per frame; the indicator sums are rectangle sums of a
 // 2-D prefix table of q (or Q).
 #pragma once
 #include <cuda_runtime.h>

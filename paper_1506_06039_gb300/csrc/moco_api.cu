@@ -18,7 +18,7 @@ namespace moco {
 
 const char* const kKernelNames[K_COUNT] = {"k_frame_rows", "k_energy", "k_cols", "k_rows_inv", "k_jitter",
                                            "k_copy_shifts", "k_softmin", "k_backward", "k_direct", "k_apply",
-                                           "k_jitter_level"};
+                                           "k_jitter_level", "k_adj_rows", "k_adj_cols", "k_adj_inverse"};
 
 thread_local std::string g_last_error;
 
@@ -640,7 +640,7 @@ moco_status moco_cost_backward(moco_plan_t plan, int32_t shape_idx, const uint16
         return fail(MOCO_ERR_INVALID_ARG, "null frames, grad_cost or grad_template");
     DeviceGuard guard(plan->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    plan->prof.begin(K_BACKWARD, st);
+    Profiler& P = plan->prof;
     cudaError_t e = cudaSuccess;
     if (sp.has_fft) {
         // sum_f a'_f (correlated with) q_f = IDFT2(sum_f A_f conj(Q_f)), group by group
@@ -649,24 +649,31 @@ moco_status moco_cost_backward(moco_plan_t plan, int32_t shape_idx, const uint16
         e = cudaMemsetAsync(sp.grad_spec, 0, (size_t)sp.ncv * sp.Nr * 8, st);
         for (int64_t f0 = 0; f0 < T && e == cudaSuccess; f0 += sp.group) {
             const int64_t g = std::min<int64_t>(sp.group, T - f0);
+            P.begin(K_ADJ_ROWS, st);
             e = launch_frame_rows(sp.Nc, false, frames_dev + f0 * mn, mn, g, sp.desc.m, sp.desc.n, 0, sp.mc, sp.nc,
                                   sp.coff_i, nullptr, sp.twc, sp.X, sp.x_fstride, sp.ldx, sp.rowE, sp.colE, sp.tot,
                                   sp.corners, sp.wm1, sp.dev_err, st);
             if (e == cudaSuccess)
                 e = launch_q_rows(sp.Nc, grad_cost_dev + f0 * K, sp.inv_area, grad_scale, sp.wm1, g, sp.twc, sp.Y, st);
+            P.end(st);
+            P.begin(K_ADJ_COLS, st);
             if (e == cudaSuccess)
                 e = launch_adj_cols(sp.Nr, sp.X, sp.x_fstride, sp.ldx, sp.mc, sp.ncv, sp.Y, sp.wm1, g, sp.twr,
                                     sp.grad_spec, st);
+            P.end(st);
         }
+        P.begin(K_ADJ_INV, st);
         if (e == cudaSuccess)
             e = launch_adj_inverse(sp.Nr, sp.Nc, sp.grad_spec, sp.ncv, sp.mc, sp.nc, sp.twr, sp.twc, sp.X,
                                    sp.grad_acc, st);
+        P.end(st);
     }
+    P.begin(K_BACKWARD, st);
     if (e == cudaSuccess)
         e = launch_grad(frames_dev, T, sp.desc.m, sp.desc.n, sp.wm1, grad_cost_dev, grad_scale, sp.inv_area,
                         sp.coff_i, sp.tmpl, sp.f32 ? 1 : 0, sp.has_fft ? 0 : 1, sp.grad_acc, sp.grad_Q,
                         grad_template_dev, grad_frames_dev, st);
-    plan->prof.end(st);
+    P.end(st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint kernels");
     return MOCO_OK;
 }

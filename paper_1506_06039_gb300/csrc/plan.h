@@ -14,7 +14,7 @@ namespace moco {
 // Optional per-kernel timing: CUDA events recorded on the launching stream
 // around every kernel launch (enabled by moco_profile_enable).
 enum KernelId { K_FRAME_ROWS = 0, K_ENERGY, K_COLS, K_ROWS_INV, K_JITTER, K_COPY_SHIFTS, K_SOFTMIN,
-                K_BACKWARD, K_DIRECT, K_APPLY, K_JITTER_LEVEL, K_COUNT };
+                K_BACKWARD, K_DIRECT, K_APPLY, K_JITTER_LEVEL, K_ADJ_ROWS, K_ADJ_COLS, K_ADJ_INV, K_COUNT };
 extern const char* const kKernelNames[K_COUNT];
 
 struct Profiler {

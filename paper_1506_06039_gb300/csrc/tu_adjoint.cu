@@ -75,7 +75,7 @@ k_q_rows(const float* __restrict__ G, const double* __restrict__ inv_area, float
 // Grid (column blocks of kColsVC, chunks of kAdjFramesPerCta frames). Thread
 // p owns position p of every column of the block and keeps its sum.
 template <int N>
-__global__ void __launch_bounds__(cols_threads<N>())
+__global__ void __launch_bounds__(cols_threads<N>(), cols_threads<N>() <= 320 ? 2 : 1)
 k_adj_cols(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv, const float2* __restrict__ QX,
            int wm1, int64_t T, const float2* __restrict__ tw_g, float2* __restrict__ Acc) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
