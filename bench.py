@@ -141,7 +141,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ---- algorithmic work per kernel launch -------------------------
+# ---- algorithmic work per kernel launch ----------------------------------------
 
 def fft_flops(N):
     return 5.0 * N * math.log2(N)
@@ -166,11 +166,11 @@ def kernel_work(info, wl, frames):
 
 
 # DRAM bytes (read + write) per frame of the current kernels, from one ncu
-# capture of 512 frames of the std512 workload (profiles/kernels_std512_fft.md),
-# scaled to a launch by its frame count.
-TRAFFIC_PER_FRAME = {"k_frame_rows": (269.646848e6 + 124.598016e6) / 512,
-                     "k_cols": (153.365504e6 + 20.268544e6) / 512,
-                     "k_jitter": (261.745152e6 + 3.996928e6) / 512}
+# capture of 512 frames of the std512 workload (dram__bytes_read.sum +
+# dram__bytes_write.sum), scaled to a launch by its frame count.
+TRAFFIC_PER_FRAME = {"k_frame_rows": (269.648128e6 + 125.167104e6) / 512,
+                     "k_cols": (153.365760e6 + 20.226048e6) / 512,
+                     "k_jitter": (261.750016e6 + 4.341248e6) / 512}
 
 
 def roofline(profile, info, wl, frames_per_step, steps, peaks, clocks):
