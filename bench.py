@@ -158,7 +158,9 @@ def kernel_work(info, wl, frames):
         "k_frame_rows": (2 * m * n + 8 * ncv * mc, (mc / 2) * fft_flops(Nc), 0.0),
         "k_energy": (8 * (mc + nc) + 8 * W * W, 0.0, 0.0),
         "k_cols": (8 * ncv * mc + 8 * W * ncv, ncv * (2 * fft_flops(Nr) + 6 * Nr), 0.0),
-        "k_rows_inv": (8 * W * ncv + 8 * W * W, math.ceil(W / 2) * fft_flops(Nc), 0.0),
+        # h's row spectra in, the energies' edge sums and corner blocks in, the costs out
+        "k_rows_inv": (8 * W * ncv + 8 * (mc + nc) + 16 * (w - 1) ** 2 + 8 * W * W,
+                       math.ceil(W / 2) * fft_flops(Nc), 0.0),
         # nine exact squared differences per full-resolution pixel
         "k_jitter": (2 * m * n, 0.0, 9.0 * m * n),
     }

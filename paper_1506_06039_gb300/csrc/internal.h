@@ -25,8 +25,12 @@ cudaError_t launch_cols(int N, bool spectrum, const float2* X, int64_t x_fstride
 
 // Sa2 [nimg][W^2] and Sb2 [W^2]: exact energies as FP32 pairs (hi, lo);
 // ia32 [W^2]: unit / Area.
+// Dynamic shared memory of k_rows_inv for transform length N (all-ones if N
+// is not a supported length).
+size_t rows_inv_smem_bytes(int N, int wm1);
 cudaError_t launch_rows_inv(int N, const float2* Y, int64_t y_fstride, int ncv, int wm1, int64_t nimg,
-                            const float2* tw, const float2* Sa2, const float2* Sb2, const float* ia32,
+                            const float2* tw, const u64* rowE, const u64* colE, const u64* tot,
+                            const uint32_t* corners, int mc, int nc, const float2* Sb2, const float* ia32,
                             double* cost, int32_t* coarse, double* fbest, float* margin, cudaStream_t st);
 
 cudaError_t launch_energy(bool f32, bool out_double, const u64* rowE, const u64* colE, const u64* tot,

@@ -8,11 +8,13 @@
 // cross-correlation, computed through zero-padded 2-D FFTs (Section 2):
 //   k_frame_rows : 2x2 box (exact integer 4-sum), subtract c, energies of the
 //                  edge strips and corners, real row FFTs (length Nc) -> X
-//   k_energy     : Sa for every shift from totals, edge strips and corners
 //   k_cols       : column FFT (length Nr), x conj(template spectrum), inverse
 //                  column FFT kept on the 2w-1 needed rows -> Y
 //   k_rows_inv   : inverse row FFTs kept on the 2w-1 needed columns -> h;
-//                  f = (Sa + Sb - 2h) / Area in FP64; argmin with tie-break
+//                  Sa for every shift from totals, edge strips and corners
+//                  (energy_frame); f = (Sa + Sb - 2h) / Area in FP32 from
+//                  exact energies; argmin with tie-break
+//   k_energy     : the same energies stored (template, direct form)
 //   k_jitter     : Section 2's upsampling step: the 3x3 candidates around the
 //                  doubled optimum, exact int64 sums at full resolution
 #pragma once
@@ -495,32 +497,34 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
 // frames) each exact integer energy is stored as an FP32 pair hi + lo with
 // hi = the nearest float and lo = the rounded remainder (|error| <= 8 for
 // energies below 2^53, i.e. 2^-48 relative), which the FP32 combine uses.
-template <bool F32, bool OUT_DOUBLE>
-__global__ void __launch_bounds__(kEnergyThreads)
-k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* __restrict__ tot,
-         const uint32_t* __restrict__ corners, int mc, int nc, int wm1, void* __restrict__ out,
-         int flip) {
+// The energies of one frame for every shift, computed by the whole block:
+// emit(s, t, Sa) once per shift (s, t), |s|, |t| <= wm1. qp corner tables
+// (1 or 4) are built per pass: their squares, a prefix along each table row
+// (one thread per row), then along each column (one thread per column), so a
+// pass takes three barriers. smem (energy_smem): exR, exC (W each) and qp
+// tables of w rows x PL of Acc. Every thread of the block must call it (it
+// synchronises).
+__host__ __device__ constexpr int energy_pl(int wm1) { return (wm1 + 1) | 1; }  // odd row stride
+__host__ __device__ constexpr size_t energy_smem(int wm1, size_t acc_bytes, int qp) {
+    return acc_bytes * (2 * (2 * wm1 + 1) + (size_t)qp * (wm1 + 1) * energy_pl(wm1));
+}
+// Quadrants per pass: all four while their tables stay within 64 KiB.
+__host__ __device__ constexpr int energy_qp(int wm1, size_t acc_bytes) {
+    return energy_smem(wm1, acc_bytes, 4) <= 64 * 1024 ? 4 : 1;
+}
+
+template <bool F32, typename Emit>
+__device__ __forceinline__ void energy_frame(const u64* __restrict__ rE, const u64* __restrict__ cE, u64 tot_bits,
+                                             const uint32_t* __restrict__ corners_f, int mc, int nc, int wm1,
+                                             unsigned char* smem, Emit emit) {
     typedef typename AccT<F32>::type Acc;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int W = 2 * wm1 + 1, w = wm1 + 1;
-    Acc* exR = reinterpret_cast<Acc*>(smem_raw);  // W
-    Acc* exC = exR + W;                            // W
-    Acc* P = exC + W;                              // w x (w + 1): padded rows
-    const int PL = w + 1;
+    const int W = 2 * wm1 + 1, w = wm1 + 1, PL = energy_pl(wm1);
+    const int qp = energy_qp(wm1, sizeof(Acc));
+    Acc* exR = reinterpret_cast<Acc*>(smem);  // W
+    Acc* exC = exR + W;                       // W
+    Acc* P = exC + W;                         // qp x w x PL
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
-    const int64_t f = blockIdx.x;
-    const u64* rE = rowE + f * mc;
-    const u64* cE = colE + f * nc;
     auto ld = [](const u64* p) { u64 v = *p; return *reinterpret_cast<Acc*>(&v); };
-    // Inclusive warp scan of one 32-wide segment (lane order).
-    auto scan32 = [&](Acc v) {
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const Acc u = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += u;
-        }
-        return v;
-    };
     // Edge strips: exR[wm1 + k] = energy of the first k rows, exR[wm1 - k] of
     // the last k rows (k = 1 .. wm1); the same for columns. Warps 0-3.
     if (warp < 4) {
@@ -533,80 +537,105 @@ k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* 
         for (int k0 = 0; k0 < wm1; k0 += 32) {
             const int k = k0 + lane;  // k + 1 rows or columns
             Acc v = k < wm1 ? ld(src + (from_end ? len - 1 - k : k)) : Acc(0);
-            v = scan32(v) + carry;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const Acc u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            v += carry;
             if (k < wm1) dst[from_end ? wm1 - 1 - k : wm1 + 1 + k] = v;
             carry = __shfl_sync(0xffffffffu, v, 31);
         }
     }
-    const Acc T = ld(tot + f);
+    const Acc T = *reinterpret_cast<const Acc*>(&tot_bits);
     const size_t wm1sq = (size_t)wm1 * wm1;
-    for (int q = 0; q < 4; ++q) {
-        const bool bottom = q >= 2, right = q & 1;
+    for (int q0 = 0; q0 < 4; q0 += qp) {
+        const int rows = qp * w;  // table rows of this pass: (q - q0) * w + a
         __syncthreads();
-        // P[a][b] = sum over the a rows nearest the corner's horizontal edge
+        // P_q[a][b] = sum over the a rows nearest the corner's horizontal edge
         // and the b columns nearest its vertical edge: squares first ...
-        for (int i = tid; i < w * w; i += nthr) {
-            const int a = i / w, b = i - a * w;
-            Acc v = 0;
-            if (a > 0 && b > 0) {
-                const int di = a - 1, dj = b - 1;  // distances from the outer edges
-                const int ri = bottom ? wm1 - 1 - di : di;
-                const int cj = right ? wm1 - 1 - dj : dj;
-                const uint32_t bits = corners[(f * 4 + q) * wm1sq + (size_t)ri * wm1 + cj];
-                if (F32) {
-                    const double x = (double)__uint_as_float(bits);
-                    v = (Acc)(x * x);
-                } else {
-                    const long long x = (int32_t)bits;
-                    v = (Acc)(x * x);
+        for (int r = warp; r < rows; r += nwarps) {
+            const int q = q0 + r / w, a = r % w;
+            const bool bottom = q >= 2, right = q & 1;
+            for (int b = lane; b < w; b += 32) {
+                Acc v = 0;
+                if (a > 0 && b > 0) {
+                    const int ri = bottom ? wm1 - a : a - 1;  // distances from the outer edges
+                    const int cj = right ? wm1 - b : b - 1;
+                    const uint32_t bits = corners_f[q * wm1sq + (size_t)ri * wm1 + cj];
+                    if (F32) {
+                        const double x = (double)__uint_as_float(bits);
+                        v = (Acc)(x * x);
+                    } else {
+                        const long long x = (int32_t)bits;
+                        v = (Acc)(x * x);
+                    }
                 }
+                P[r * PL + b] = v;
             }
-            P[a * PL + b] = v;
         }
         __syncthreads();
-        // ... then a scan along each row (one warp per row) ...
-        for (int a = warp; a < w; a += nwarps) {
-            Acc carry = 0;
-            for (int b0 = 0; b0 < w; b0 += 32) {
-                const int b = b0 + lane;
-                Acc v = b < w ? P[a * PL + b] : Acc(0);
-                v = scan32(v) + carry;
-                if (b < w) P[a * PL + b] = v;
-                carry = __shfl_sync(0xffffffffu, v, 31);
+        // ... then along each table row ...
+        for (int r = tid; r < rows; r += nthr) {
+            Acc* row = P + r * PL;
+            Acc run = 0;
+            for (int b = 0; b < w; ++b) {
+                run += row[b];
+                row[b] = run;
             }
         }
         __syncthreads();
         // ... and along each column.
-        for (int b = warp; b < w; b += nwarps) {
-            Acc carry = 0;
-            for (int a0 = 0; a0 < w; a0 += 32) {
-                const int a = a0 + lane;
-                Acc v = a < w ? P[a * PL + b] : Acc(0);
-                v = scan32(v) + carry;
-                if (a < w) P[a * PL + b] = v;
-                carry = __shfl_sync(0xffffffffu, v, 31);
+        for (int c = tid; c < rows; c += nthr) {
+            Acc* col = P + (c / w) * w * PL + c % w;
+            Acc run = 0;
+            for (int a = 0; a < w; ++a) {
+                run += col[a * PL];
+                col[a * PL] = run;
             }
         }
         __syncthreads();
-        // Shifts of this quadrant: s >= 0 (top) or s < 0 (bottom), same for t.
-        for (int i = tid; i < w * w; i += nthr) {
-            const int a = i / w, b = i - a * w;
+        // Shifts of these quadrants: s >= 0 (top) or s < 0 (bottom), same for t.
+        for (int r = warp; r < rows; r += nwarps) {
+            const int q = q0 + r / w, a = r % w;
+            const bool bottom = q >= 2, right = q & 1;
             if (bottom && a == 0) continue;
-            if (right && b == 0) continue;
-            const int s = bottom ? -a : a, t = right ? -b : b;
-            const Acc val = T - exR[s + wm1] - exC[t + wm1] + P[a * PL + b];
-            const int so = flip ? -s : s, to = flip ? -t : t;
-            const int64_t k = f * (int64_t)W * W + (int64_t)(so + wm1) * W + (to + wm1);
-            if (OUT_DOUBLE) {
-                static_cast<double*>(out)[k] = (double)val;
-            } else {
-                const u64 e = *reinterpret_cast<const u64*>(&val);
-                const float hi = __ull2float_rn(e);
-                const long long r = (long long)(e - __float2ull_rn(hi));  // |r| <= ulp(hi) / 2
-                static_cast<float2*>(out)[k] = make_float2(hi, __ll2float_rn(r));
+            const int s = bottom ? -a : a;
+            for (int b = lane; b < w; b += 32) {
+                if (right && b == 0) continue;
+                const int t = right ? -b : b;
+                emit(s, t, T - exR[s + wm1] - exC[t + wm1] + P[r * PL + b]);
             }
         }
     }
+}
+
+// The exact energy e as the FP32 pair (nearest float, rounded remainder).
+__device__ __forceinline__ float2 energy_pair(u64 e) {
+    const float hi = __ull2float_rn(e);
+    const long long r = (long long)(e - __float2ull_rn(hi));  // |r| <= ulp(hi) / 2
+    return make_float2(hi, __ll2float_rn(r));
+}
+
+template <bool F32, bool OUT_DOUBLE>
+__global__ void __launch_bounds__(kEnergyThreads)
+k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* __restrict__ tot,
+         const uint32_t* __restrict__ corners, int mc, int nc, int wm1, void* __restrict__ out,
+         int flip) {
+    typedef typename AccT<F32>::type Acc;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int W = 2 * wm1 + 1;
+    const int64_t f = blockIdx.x;
+    energy_frame<F32>(rowE + f * mc, colE + f * nc, tot[f], corners + f * 4 * (size_t)wm1 * wm1, mc, nc, wm1,
+                      smem_raw, [&](int s, int t, Acc val) {
+                          const int so = flip ? -s : s, to = flip ? -t : t;
+                          const int64_t k = f * (int64_t)W * W + (int64_t)(so + wm1) * W + (to + wm1);
+                          if (OUT_DOUBLE) {
+                              static_cast<double*>(out)[k] = (double)val;
+                          } else {
+                              static_cast<float2*>(out)[k] = energy_pair(*reinterpret_cast<const u64*>(&val));
+                          }
+                      });
 }
 
 // ---------------------------------------------------------------------------
@@ -736,16 +765,30 @@ __device__ __forceinline__ void best_merge(Best& a, const Best& o) {
     }
 }
 
+// Shared memory of k_rows_inv: the transform buffer (later the energies'
+// tables), the inverse roots, h.
+template <int N>
+__host__ __device__ constexpr size_t rows_inv_region(int wm1) {
+    return (sizeof(float2) * kInvPC * fft_ld<N>() > energy_smem(wm1, 8, energy_qp(wm1, 8))
+                ? sizeof(float2) * kInvPC * fft_ld<N>()
+                : (energy_smem(wm1, 8, energy_qp(wm1, 8)) + 15) / 16 * 16);
+}
+template <int N>
+__host__ __device__ constexpr size_t rows_inv_smem(int wm1) {
+    return rows_inv_region<N>(wm1) + sizeof(float2) * N + sizeof(float) * (2 * wm1 + 1) * (2 * wm1 + 1);
+}
+
 template <int N>
 __global__ void __launch_bounds__(576)
 k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
-           const float2* __restrict__ tw_g, const float2* __restrict__ Sa2, const float2* __restrict__ Sb2,
-           const float* __restrict__ ia32, double* __restrict__ cost,
+           const float2* __restrict__ tw_g, const u64* __restrict__ rowE, const u64* __restrict__ colE,
+           const u64* __restrict__ tot, const uint32_t* __restrict__ corners, int mc, int nc,
+           const float2* __restrict__ Sb2, const float* __restrict__ ia32, double* __restrict__ cost,
            int32_t* __restrict__ coarse, double* __restrict__ fbest, float* __restrict__ margin) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int LD = fft_ld<N>();                      // skewed, padded row
     float2* buf = reinterpret_cast<float2*>(smem_raw);  // kInvPC x LD
-    float2* tw = buf + kInvPC * LD;                      // N: inverse table
+    float2* tw = reinterpret_cast<float2*>(smem_raw + rows_inv_region<N>(wm1));  // N: inverse table
     const int W = 2 * wm1 + 1, WW = W * W;
     float* hbuf = reinterpret_cast<float*>(tw + N);     // W x W
     __shared__ Best red[32];
@@ -801,19 +844,20 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
             if (ra + 1 < W) hbuf[(ra + 1) * W + ti] = z.y;
         }
     }
-    __syncthreads();
+    __syncthreads();  // the transform buffer is read for the last time above
     Best b;
     b.f1 = INFINITY;
     b.r1 = 0x7fffffff;
     b.f2 = INFINITY;
-    const float2* sa = Sa2 + f * WW;
-    for (int k = tid; k < WW; k += nthr) {
-        const int si = k / W, ti = k - si * W;
-        const int s = si - wm1, t = ti - wm1;
-        const float fv = combine_f32(sa[k], Sb2[k], hbuf[k], ia32[k]);
-        if (cost) cost[f * WW + k] = (double)fv;
-        best_push(b, fv, (abs(s) + abs(t)) * WW + k);
-    }
+    // The frame's energies Sa (exact) straight into the combine; their tables
+    // take the transform buffer's place.
+    energy_frame<false>(rowE + f * mc, colE + f * nc, tot[f], corners + f * 4 * (size_t)wm1 * wm1, mc, nc, wm1,
+                        smem_raw, [&](int s, int t, u64 sa) {
+                            const int k = (s + wm1) * W + (t + wm1);
+                            const float fv = combine_f32(energy_pair(sa), Sb2[k], hbuf[k], ia32[k]);
+                            if (cost) cost[f * WW + k] = (double)fv;
+                            best_push(b, fv, (abs(s) + abs(t)) * WW + k);
+                        });
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         Best o2;

@@ -118,13 +118,15 @@ moco_status resolve_shape(const moco_shape& d, ShapePlan& sp) {
     sp.W = 2 * d.w - 1;
     sp.Nr = fft_size_for(sp.mc + d.w - 1);
     sp.Nc = fft_size_for(sp.nc + d.w - 1);
-    const bool fft_ok = sp.Nr && sp.Nc;
+    // (k_rows_inv keeps h, W x W floats, next to a transform buffer)
+    const bool fft_ok = sp.Nr && sp.Nc && rows_inv_smem_bytes(sp.Nc, sp.wm1) <= 227 * 1024;
     // (the direct form reads 2x2 sums: at most one level)
     const bool direct_ok = direct_smem(sp.W) <= 227 * 1024 && sp.W <= 256 && sp.levels <= 1;
     sp.nqc = (sp.nc + 63) / 64;
     sp.ncp = sp.nqc * 64;
     if (d.xcorr == MOCO_XCORR_FFT_FP32 && !fft_ok)
-        return fail(MOCO_ERR_UNSUPPORTED, "searched grid + window exceeds the largest FFT length (576)");
+        return fail(MOCO_ERR_UNSUPPORTED,
+                    "searched grid + window exceeds the largest FFT length (576), or the window its shared memory");
     if (d.xcorr == MOCO_XCORR_DIRECT_BF16X3 && !direct_ok)
         return fail(MOCO_ERR_UNSUPPORTED, "window too large for the direct form");
     if (!fft_ok && !direct_ok) return fail(MOCO_ERR_UNSUPPORTED, "no cross-term form supports this shape");
@@ -334,19 +336,15 @@ moco_status search_group(ShapePlan& sp, const uint16_t* frames, int64_t g, doubl
                                       sp.tot, sp.corners, sp.wm1, sp.dev_err, st);
     P.end(st);
     if (e != cudaSuccess) return cuda_fail(e, "k_frame_rows");
-    P.begin(K_ENERGY, st);
-    e = launch_energy(false, false, sp.rowE, sp.colE, sp.tot, sp.corners, g, sp.mc, sp.nc, sp.wm1, sp.Sa, 0, st);
-    P.end(st);
-    if (e != cudaSuccess) return cuda_fail(e, "k_energy");
     P.begin(K_COLS, st);
     e = launch_cols(sp.Nr, false, sp.X, sp.x_fstride, sp.ldx, sp.mc, sp.ncv, g, sp.twr, sp.bspec, sp.Y,
                     sp.y_fstride, sp.wm1, 0.f, st);
     P.end(st);
     if (e != cudaSuccess) return cuda_fail(e, "k_cols");
     P.begin(K_ROWS_INV, st);
-    e = launch_rows_inv(sp.Nc, sp.Y, sp.y_fstride, sp.ncv, sp.wm1, g, sp.twc, reinterpret_cast<const float2*>(sp.Sa),
-                        sp.Sb2, sp.ia32,
-                        cost, sp.coarse, fbest ? fbest : sp.fbest, margin ? margin : sp.margin, st);
+    e = launch_rows_inv(sp.Nc, sp.Y, sp.y_fstride, sp.ncv, sp.wm1, g, sp.twc, sp.rowE, sp.colE, sp.tot, sp.corners,
+                        sp.mc, sp.nc, sp.Sb2, sp.ia32, cost, sp.coarse, fbest ? fbest : sp.fbest,
+                        margin ? margin : sp.margin, st);
     P.end(st);
     if (e != cudaSuccess) return cuda_fail(e, "k_rows_inv");
     return MOCO_OK;

@@ -112,7 +112,7 @@ moco_status cuda_fail(cudaError_t e, const char* what);
 struct moco_plan_s {
     int device = 0;
     std::vector<moco::ShapePlan> shapes;
-    cudaStream_t aux = nullptr;
+    cudaStream_t aux = nullptr;  // host staging copies (moco_align_host)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     moco::Profiler prof;
     void* scratch = nullptr;  // per-batch scratch shared by all shapes

@@ -56,28 +56,40 @@ cudaError_t launch_frame_rows(int N, bool f32, const void* src, int64_t src_fstr
 
 template <int N>
 static cudaError_t rows_inv_n(const float2* Y, int64_t y_fstride, int ncv, int wm1, int64_t nimg,
-                              const float2* tw, const float2* Sa2, const float2* Sb2, const float* ia32,
+                              const float2* tw, const u64* rowE, const u64* colE, const u64* tot,
+                              const uint32_t* corners, int mc, int nc, const float2* Sb2, const float* ia32,
                               double* cost, int32_t* coarse, double* fbest, float* margin,
                               cudaStream_t st) {
-    const int W = 2 * wm1 + 1;
-    const size_t smem = sizeof(float2) * (kInvPC * fft_ld<N>() + N) + sizeof(float) * W * W;
+    const size_t smem = rows_inv_smem<N>(wm1);
     const void* fn = (const void*)k_rows_inv<N>;
     cudaError_t e = ensure_smem(fn, smem);
     if (e != cudaSuccess) return e;
     int threads = kInvPC * (Four<N>::N1 > Four<N>::N2 ? Four<N>::N1 : Four<N>::N2);
     threads = (threads + 31) / 32 * 32;
-    k_rows_inv<N><<<(unsigned)nimg, threads, smem, st>>>(Y, y_fstride, ncv, wm1, tw, Sa2, Sb2, ia32,
-                                                         cost, coarse, fbest, margin);
+    k_rows_inv<N><<<(unsigned)nimg, threads, smem, st>>>(Y, y_fstride, ncv, wm1, tw, rowE, colE, tot, corners, mc,
+                                                         nc, Sb2, ia32, cost, coarse, fbest, margin);
     return cudaGetLastError();
 }
 
+size_t rows_inv_smem_bytes(int N, int wm1) {
+#define MOCO_CASE(NN) \
+    case NN: return rows_inv_smem<NN>(wm1);
+    switch (N) {
+        MOCO_FOR_EACH_FFT_SIZE(MOCO_CASE)
+        default: return ~(size_t)0;
+    }
+#undef MOCO_CASE
+}
+
 cudaError_t launch_rows_inv(int N, const float2* Y, int64_t y_fstride, int ncv, int wm1, int64_t nimg,
-                            const float2* tw, const float2* Sa2, const float2* Sb2, const float* ia32,
+                            const float2* tw, const u64* rowE, const u64* colE, const u64* tot,
+                            const uint32_t* corners, int mc, int nc, const float2* Sb2, const float* ia32,
                             double* cost, int32_t* coarse, double* fbest, float* margin, cudaStream_t st) {
     if (nimg <= 0) return cudaSuccess;
 #define MOCO_CASE(NN) \
     case NN:          \
-        return rows_inv_n<NN>(Y, y_fstride, ncv, wm1, nimg, tw, Sa2, Sb2, ia32, cost, coarse, fbest, margin, st);
+        return rows_inv_n<NN>(Y, y_fstride, ncv, wm1, nimg, tw, rowE, colE, tot, corners, mc, nc, Sb2, ia32, cost, \
+                              coarse, fbest, margin, st);
     switch (N) {
         MOCO_FOR_EACH_FFT_SIZE(MOCO_CASE)
         default:

@@ -175,6 +175,24 @@ def test_group_boundaries_do_not_change_results():
     check_align(st.frames, st.template, 8, -1, a)
 
 
+@pytest.mark.parametrize("group_frames", [0, 96])
+def test_large_calls_match_separate_calls(group_frames):
+    # 1100 frames with a level in one call (one group, or 12 groups of 96 with
+    # a short last one) against calls of 100 frames: identical shifts, best
+    # and final costs; the oracle checks a sample.
+    T, m, n, w = 1100, 64, 72, 6
+    st = synth.make_stack_np(m, n, T, 12, 8, seed=1234, template="clean")
+    with Plan(dict(m=m, n=n, w=w, levels=1, group_frames=group_frames), dev(st.template)) as plan:
+        a, ab, _, af = plan.align(dev(st.frames), best_cost=True, final_cost=True)
+        parts = [plan.align(dev(st.frames[k:k + 100]), best_cost=True, final_cost=True) for k in range(0, T, 100)]
+        torch.cuda.synchronize()
+    assert np.array_equal(a.cpu().numpy(), np.concatenate([p[0].cpu().numpy() for p in parts]))
+    assert np.array_equal(ab.cpu().numpy(), np.concatenate([p[1].cpu().numpy() for p in parts]))
+    assert np.array_equal(af.cpu().numpy(), np.concatenate([p[3].cpu().numpy() for p in parts]))
+    sample = np.random.default_rng(5).choice(T, 40, replace=False)
+    check_align(st.frames[sample], st.template, w, 1, a.cpu().numpy()[sample], ab.cpu().numpy()[sample])
+
+
 def test_align_host_matches_device_path():
     st = synth.make_stack_np(264, 264, 11, 40, 6, seed=8, template="clean")
     with Plan(dict(m=264, n=264, w=8, group_frames=4), dev(st.template)) as plan:
