@@ -501,6 +501,11 @@ def run_grad(args, world, rank, local):
 
     build.build()
     torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
     wl = synth.WORKLOADS["refine256"]
     T = args.frames or wl.T
     st = synth.make_stack_torch(wl.m, wl.n, T, wl.nblobs, wl.shift_max, rank_seed(wl.seed, rank), template="clean")
@@ -519,6 +524,9 @@ def run_grad(args, world, rank, local):
         moco_cost_surface(plan.handle, 0, st.frames, cost, stream)
         moco_softmin(plan.handle, 0, cost, 0.05, loss, weights, stream)
         moco_cost_backward(plan.handle, 0, st.frames, weights, grad, None, 1.0, stream)
+        if pg:
+            # data-parallel refinement: the template gradient summed over the ranks' frames
+            pg.all_reduce(grad)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -528,27 +536,35 @@ def run_grad(args, world, rank, local):
     sampler.start()
     time.sleep(0.3)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
     ev0.record(stream)
     for _ in range(args.steps):
         step()
     ev1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), pg, "cuda")
     profile = plan.profile_read(reset=True)
     plan.profile(0)
     if rank == 0:
         tot = sum(t for _, t in profile.values()) or 1.0
         out = {"metric": "frames/s, soft-min loss and template gradient (differentiable form)",
-               "value": world * T * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "value": job_value(world, T, args.steps, ms / 1e3), "unit": UNIT, "n_gpus": world,
+               "steps": args.steps,
                "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
                "config": {"workload": "refine256: %d frames of 256x256, w=16 (31^2 shifts), float template "
                                       "(mean frame + N(0, 50^2)), tau = 0.05 x median" % T, "frames": T},
                "gpu_launches": sum(l for l, _ in profile.values()), "clocks": clocks,
                "kernels": {k: {"launches": l, "ms": t, "share": t / tot} for k, (l, t) in profile.items()}}
+        if world > 1:
+            out["config"]["parallelism"] = "dp%d: frames sharded, template gradient all-reduced every step" % world
         print(json.dumps(out), flush=True)
     plan.close()
+    if pg:
+        pg.destroy_process_group()
 
 
 def run_pyramid(args, world, rank, local):

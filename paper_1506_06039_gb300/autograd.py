@@ -38,22 +38,47 @@ def softmin_plan(frames, template, w, group_frames=0):
                 template.detach().float().contiguous())
 
 
-def refine_template(frames, template0, w, steps=50, lr=1.0, tau_scale=0.05, plan=None):
-    """Gradient-based template refinement with Adam. Returns (template, losses)."""
+def adam_refine(template0, step, steps=50, lr=1.0, group=None):
+    """Adam on a float template. step(t) returns (loss, gradient) of this
+    process's frames at template t. With a torch.distributed process group
+    (one rank per GPU, each holding its own frames) the gradient and the loss
+    are summed over the ranks before every update, so every rank applies the
+    same update to the same template: the data-parallel form of the
+    refinement, whose only exchange is this all-reduce of m x n floats.
+    Returns (template, losses)."""
     tmpl = template0.detach().clone().float().requires_grad_(True)
-    own = plan is None
-    if own:
-        plan = softmin_plan(frames, tmpl, w)
     opt = torch.optim.Adam([tmpl], lr=lr)
     losses = []
+    for _ in range(steps):
+        opt.zero_grad(set_to_none=True)
+        loss, grad = step(tmpl)
+        grad = grad.detach().to(tmpl.dtype).clone()
+        loss = loss.detach().reshape(1).double().clone()
+        if group is not None:
+            import torch.distributed as dist
+            dist.all_reduce(grad, group=group)
+            dist.all_reduce(loss, group=group)
+        tmpl.grad = grad
+        opt.step()
+        losses.append(float(loss))
+    return tmpl.detach(), losses
+
+
+def refine_template(frames, template0, w, steps=50, lr=1.0, tau_scale=0.05, plan=None, group=None):
+    """Gradient-based template refinement with Adam (see adam_refine; group:
+    an optional process group over which the frames are sharded). Returns
+    (template, losses)."""
+    own = plan is None
+    if own:
+        plan = softmin_plan(frames, template0, w)
+
+    def step(t):
+        loss = MocoSoftMin.apply(t, frames, plan, tau_scale, 0)
+        (g,) = torch.autograd.grad(loss, t)
+        return loss, g
+
     try:
-        for _ in range(steps):
-            opt.zero_grad(set_to_none=True)
-            loss = MocoSoftMin.apply(tmpl, frames, plan, tau_scale, 0)
-            loss.backward()
-            opt.step()
-            losses.append(float(loss))
+        return adam_refine(template0, step, steps=steps, lr=lr, group=group)
     finally:
         if own:
             plan.close()
-    return tmpl.detach(), losses

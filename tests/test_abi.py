@@ -76,6 +76,13 @@ def test_plan_rejects_unsupported(lib):
     assert st == binding.MOCO_ERR_UNSUPPORTED and "levels" in err
     st, handle, err = _plan_status(lib, binding.MocoShape(4096, 4096, 64, 0, 0, binding.XCORR_FFT_FP32, 0, 0))
     assert st == binding.MOCO_ERR_UNSUPPORTED and "FFT" in err
+    # 384 x 384 without a level, w = 150: the FFT length fits (576) but the
+    # combine's W x W costs (299^2 floats) do not fit in shared memory, and
+    # W > 256 rules out the direct form.
+    st, handle, err = _plan_status(lib, binding.MocoShape(384, 384, 150, 0, 0, binding.XCORR_FFT_FP32, 0, 0))
+    assert st == binding.MOCO_ERR_UNSUPPORTED and "shared memory" in err
+    st, handle, err = _plan_status(lib, binding.MocoShape(384, 384, 150, 0, 0, 0, 0, 0))
+    assert st == binding.MOCO_ERR_UNSUPPORTED and "no cross-term form" in err
 
 
 def test_null_arguments(lib):

@@ -50,3 +50,66 @@ def test_two_ranks_max_time_and_job_value():
 def test_single_rank_passthrough():
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.job_value(1, 2000, 10, 2.0) == 10000.0
+
+
+# ---- data-parallel template refinement: the all-reduce of the gradient ------
+
+def _refine_problem():
+    import numpy as np
+    from paper_1506_06039_gb300 import synth
+    st = synth.make_stack_np(24, 32, 6, 5, 2, seed=44, template="clean")
+    rng = np.random.default_rng(3)
+    tmpl = st.frames.astype(np.float64).mean(0) + rng.normal(0, 20, (24, 32))
+    return st.frames, tmpl.astype(np.float32), 4
+
+
+def _oracle_step(frames, w):
+    """Loss and template gradient of these frames (FP64 oracle, tau = 0.05 x
+    median at the current template, held constant)."""
+    import numpy as np
+    import torch
+    import oracle
+
+    def step(t):
+        tb = t.detach().double().numpy()
+        tau = oracle.softmin_tau(frames, tb, w, 0.05)
+        L, _, gb, _ = oracle.softmin_loss(frames.astype(np.float64), tb, w, tau, grad_template=True)
+        return torch.tensor(L, dtype=torch.float64), torch.from_numpy(gb)
+    return step
+
+
+def _refine_worker(rank, world, port, q):
+    import torch
+    from paper_1506_06039_gb300.autograd import adam_refine
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        frames, tmpl, w = _refine_problem()
+        t, losses = adam_refine(torch.from_numpy(tmpl), _oracle_step(frames[rank::world], w), steps=3, lr=2.0,
+                                group=dist.group.WORLD)
+        q.put((rank, t.numpy(), losses))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_refinement_equals_one_process_over_all_frames():
+    import numpy as np
+    import torch
+    from paper_1506_06039_gb300.autograd import adam_refine
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_refine_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    res = sorted((q.get(timeout=5) for _ in range(world)), key=lambda r: r[0])
+    frames, tmpl, w = _refine_problem()
+    t1, l1 = adam_refine(torch.from_numpy(tmpl), _oracle_step(frames, w), steps=3, lr=2.0)
+    # every rank holds the same template: the one-process refinement over all frames
+    assert np.array_equal(res[0][1], res[1][1])
+    np.testing.assert_allclose(res[0][1], t1.numpy(), rtol=0, atol=1e-4)
+    np.testing.assert_allclose(res[0][2], l1, rtol=1e-8)  # float32 gradients summed in another order
+    assert not np.array_equal(t1.numpy(), tmpl)  # the template moved
