@@ -216,6 +216,47 @@ __device__ __forceinline__ int spec_pos(int k) {
 //   inverse: twi[n2*N1 + k1] (lanes run over k1).
 // The global copy is [twf | twi], 2N entries.
 
+// Second stage of the forward transform (after a barrier that follows the
+// first): N1 tasks per row, one N2-point codelet each; ends with a barrier.
+template <int N>
+__device__ void fft4_fwd_stage2(float2* buf, int ld, int rows, int tid, int nthr) {
+    constexpr int N1 = Four<N>::N1, N2 = Four<N>::N2, B = N2 + Skew<N>::S;
+    for (int task = tid; task < rows * N1; task += nthr) {
+        int r = task / N1, k1 = task - r * N1;
+        float2* p = buf + r * ld + B * k1;
+        float2 x[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) x[n2] = p[n2];
+        Dft<N2, false>::run(x);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) p[k2] = x[k2];
+    }
+    __syncthreads();
+}
+
+// First stage of the forward transform with the input read from a plain
+// (unskewed) array: row r's x[n] = src[r * lds + n] for n < valid, zero
+// beyond; the stage's output goes to buf (rows at buf + r * ld) in the
+// layout fft4_fwd_stage2 continues from. No barrier.
+template <int N>
+__device__ void fft4_fwd_stage1_from(const float2* src, int lds, int valid, float2* buf, int ld, int rows,
+                                     const float2* twf, int tid, int nthr) {
+    constexpr int N1 = Four<N>::N1, N2 = Four<N>::N2, B = N2 + Skew<N>::S;
+    for (int task = tid; task < rows * N2; task += nthr) {
+        int r = task / N2, n2 = task - r * N2;
+        const float2* q = src + r * lds + n2;
+        float2 x[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) x[n1] = (n1 * N2 + n2 < valid) ? q[N2 * n1] : make_float2(0.f, 0.f);
+        Dft<N1, false>::run(x);
+#pragma unroll
+        for (int k1 = 1; k1 < N1; ++k1) x[k1] = cmul(x[k1], twf[k1 * N2 + n2]);
+        float2* p = buf + r * ld + n2;
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) p[B * k1] = x[k1];
+    }
+}
+
 // Forward transform of `rows` rows at buf + r*ld (natural-order input).
 // Every thread of the block must call this (it synchronises).
 template <int N>
@@ -234,17 +275,7 @@ __device__ void fft4_fwd(float2* buf, int ld, int rows, const float2* twf, int t
         for (int k1 = 0; k1 < N1; ++k1) p[B * k1] = x[k1];
     }
     __syncthreads();
-    for (int task = tid; task < rows * N1; task += nthr) {
-        int r = task / N1, k1 = task - r * N1;
-        float2* p = buf + r * ld + B * k1;
-        float2 x[N2];
-#pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) x[n2] = p[n2];
-        Dft<N2, false>::run(x);
-#pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) p[k2] = x[k2];
-    }
-    __syncthreads();
+    fft4_fwd_stage2<N>(buf, ld, rows, tid, nthr);
 }
 
 // Inverse (unnormalised, omega^+) transform: input in the forward output

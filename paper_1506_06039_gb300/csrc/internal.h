@@ -21,7 +21,7 @@ cudaError_t launch_frame_rows(int N, bool f32, const void* src, int64_t src_fstr
 
 cudaError_t launch_cols(int N, bool spectrum, const float2* X, int64_t x_fstride, int ldx, int mc, int ncv,
                         int64_t nimg, const float2* tw, const float2* bspec, float2* Y, int64_t y_fstride,
-                        int wm1, float scale, cudaStream_t st);
+                        int wm1, float scale, unsigned int* err, cudaStream_t st);
 
 // Sa2 [nimg][W^2] and Sb2 [W^2]: exact energies as FP32 pairs (hi, lo);
 // ia32 [W^2]: unit / Area.

@@ -721,6 +721,85 @@ k_cols(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv
     }
 }
 
+// k_cols_stream: the k_cols product for many frames per CTA. Grid (column
+// blocks, frame slices): CTA (x, y) owns spectral columns [v0, v1) (the ncv
+// columns split evenly over gridDim.x blocks of at most kColsVC) and walks
+// frames f = y, y + gridDim.y, ... Its columns' template spectrum stays in
+// shared memory; each frame's block of row spectra X[f][v0 .. v1) (contiguous,
+// v1 - v0 rows of ldx) arrives by one bulk copy into a staging buffer, issued
+// as soon as the previous frame's first transform stage has read the buffer,
+// so the copy runs under the rest of that frame's transforms. The bounded
+// wait on the copy sets *err and ends the CTA (after the copy in flight).
+template <int N>
+__host__ __device__ constexpr size_t cols_stream_smem(int ldx) {
+    return sizeof(float2) * ((size_t)kColsVC * ldx + (size_t)kColsVC * fft_ld<N>() + (size_t)kColsVC * N + 2 * N);
+}
+
+template <int N>
+__global__ void __launch_bounds__(cols_threads<N>(), 2)
+k_cols_stream(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv, int64_t T,
+              const float2* __restrict__ tw_g, const float2* __restrict__ bspec, float2* __restrict__ Y,
+              int64_t y_fstride, int wm1, unsigned int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int LD = fft_ld<N>();
+    float2* stg = reinterpret_cast<float2*>(smem_raw);  // kColsVC x ldx: the frame's block (ldx even)
+    float2* buf = stg + kColsVC * ldx;                   // kColsVC x LD
+    float2* bs = buf + kColsVC * LD;                     // kColsVC x N: template spectrum, forward output layout
+    float2* tw = bs + kColsVC * N;                       // 2N: forward, then inverse table
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int v0 = (int)((int64_t)blockIdx.x * ncv / gridDim.x);
+    const int nv = (int)((int64_t)(blockIdx.x + 1) * ncv / gridDim.x) - v0;  // <= kColsVC (host)
+    const uint32_t bytes = (uint32_t)(sizeof(float2) * nv * ldx);
+    const int W = 2 * wm1 + 1;
+    int64_t f = blockIdx.y;
+    if (f >= T) return;  // the same for the whole CTA
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        s_abort = 0;
+        fence_async_smem();
+        mbar_expect_tx(&bar, bytes);
+        bulk_g2s(stg, X + f * x_fstride + (int64_t)v0 * ldx, bytes, &bar);
+    }
+    for (int i = tid; i < 2 * N; i += nthr) tw[i] = tw_g[i];
+    for (int i = tid; i < nv * N; i += nthr) bs[i] = bspec[(int64_t)v0 * N + i];
+    uint32_t phase = 0;
+    for (; f < T; f += gridDim.y) {
+        __syncthreads();  // set-up / the previous frame's outputs are read from buf
+        if (!mbar_wait(&bar, phase, err)) s_abort = 1;
+        __syncthreads();
+        if (s_abort) {
+            if (tid == 0) mbar_wait(&bar, phase, err);  // the copy in flight lands before the CTA ends
+            return;
+        }
+        phase ^= 1u;
+        fft4_fwd_stage1_from<N>(stg, ldx, mc, buf, LD, nv, tw, tid, nthr);
+        __syncthreads();
+        if (tid == 0 && f + gridDim.y < T) {
+            fence_async_smem();  // this frame's reads of the staging buffer come before the next copy
+            mbar_expect_tx(&bar, bytes);
+            bulk_g2s(stg, X + (f + gridDim.y) * x_fstride + (int64_t)v0 * ldx, bytes, &bar);
+        }
+        fft4_fwd_stage2<N>(buf, LD, nv, tid, nthr);
+        for (int p = tid; p < N; p += nthr) {
+            const int skp = sk<N>(p);
+#pragma unroll
+            for (int vi = 0; vi < kColsVC; ++vi)
+                if (vi < nv) buf[vi * LD + skp] = cmul(buf[vi * LD + skp], bs[vi * N + p]);
+        }
+        __syncthreads();
+        fft4_inv<N>(buf, LD, nv, tw + N, tid, nthr);
+        float2* ys = Y + f * y_fstride + v0;
+        for (int task = tid; task < W * kColsVC; task += nthr) {
+            const int si = task / kColsVC, vi = task % kColsVC;
+            if (vi >= nv) continue;
+            const int pos = si - wm1 < 0 ? si - wm1 + N : si - wm1;
+            ys[(int64_t)si * ncv + vi] = buf[vi * LD + sk<N>(pos)];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // The combine f = (Sa + Sb - 2h) / Area * unit in FP32 from the exact
 // energies as FP32 pairs: Sa_hi + Sb_hi by an error-free sum (TwoSum), so

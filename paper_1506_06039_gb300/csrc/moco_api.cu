@@ -282,7 +282,7 @@ moco_status prepare_template(ShapePlan& sp, const void* tmpl_dev, cudaStream_t s
     if (e != cudaSuccess) return cuda_fail(e, "template energies");
     if (sp.has_fft) {
         e = launch_cols(sp.Nr, true, sp.X, sp.x_fstride, sp.ldx, sp.mc, sp.ncv, 1, sp.twr, nullptr, sp.bspec, 0,
-                        sp.wm1, (float)(1.0 / ((double)sp.Nr * (double)sp.Nc)), st);
+                        sp.wm1, (float)(1.0 / ((double)sp.Nr * (double)sp.Nc)), sp.dev_err, st);
         if (e != cudaSuccess) return cuda_fail(e, "template spectrum");
     }
     if (sp.has_direct) {
@@ -338,7 +338,7 @@ moco_status search_group(ShapePlan& sp, const uint16_t* frames, int64_t g, doubl
     if (e != cudaSuccess) return cuda_fail(e, "k_frame_rows");
     P.begin(K_COLS, st);
     e = launch_cols(sp.Nr, false, sp.X, sp.x_fstride, sp.ldx, sp.mc, sp.ncv, g, sp.twr, sp.bspec, sp.Y,
-                    sp.y_fstride, sp.wm1, 0.f, st);
+                    sp.y_fstride, sp.wm1, 0.f, sp.dev_err, st);
     P.end(st);
     if (e != cudaSuccess) return cuda_fail(e, "k_cols");
     P.begin(K_ROWS_INV, st);
