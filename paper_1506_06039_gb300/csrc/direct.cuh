@@ -16,8 +16,8 @@
 // bytes, core matrices 128 bytes apart along K and 1024 bytes apart along
 // M/N), so a K step copies them with one bulk copy each. A tiles (128
 // frames x 64 pixels, BF16 hi and lo planes written by the frame pass) come
-// in with 16-byte asynchronous copies. Two stages: the copies for step k+1
-// run while the MMAs of step k do. One thread issues the MMAs; every
+// in with 16-byte asynchronous copies. Three stages: the copies for steps
+// k+1 and k+2 run while the MMAs of step k do. One thread issues the MMAs; every
 // mbarrier wait is bounded (about a second) and sets an error flag instead
 // of hanging.
 //
@@ -46,7 +46,8 @@ __host__ __device__ inline size_t direct_tile_bytes(int W) { return (size_t)dire
 __host__ __device__ inline size_t direct_stage_bytes(int W) {
     return 2 * (size_t)kDirM * kDirK * 2 + 2 * (size_t)direct_ns(W) * direct_tile_bytes(W);
 }
-__host__ __device__ inline size_t direct_smem_bytes(int W) { return 1024 + 2 * direct_stage_bytes(W) + 64; }
+constexpr int kDirStages = 3;  // copies run two K steps ahead of the MMAs
+__host__ __device__ inline size_t direct_smem_bytes(int W) { return 1024 + kDirStages * direct_stage_bytes(W) + 64; }
 
 // Byte offset of element (row, k) in a K-major core-matrix tile with 64 K.
 __device__ __forceinline__ uint32_t core_off(int row, int k) {
@@ -149,7 +150,7 @@ k_direct(const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict
          unsigned int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char dsm_raw[];
     unsigned char* dsm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t load_bar[2];
+    __shared__ __align__(8) uint64_t load_bar[kDirStages];
     __shared__ __align__(8) uint64_t mma_bar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_abort;
@@ -164,8 +165,7 @@ k_direct(const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict
     constexpr uint32_t kTmemCols = 2 * kDirNmax;  // two accumulators
 
     if (tid == 0) {
-        mbar_init(&load_bar[0], 1);
-        mbar_init(&load_bar[1], 1);
+        for (int i = 0; i < kDirStages; ++i) mbar_init(&load_bar[i], 1);
         mbar_init(&mma_bar[0], 1);
         mbar_init(&mma_bar[1], 1);
         s_abort = 0;
@@ -237,34 +237,42 @@ k_direct(const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict
     for (int c = 0; c < kDirNmax; ++c) hsum[c] = 0.f;
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 
+    int issued = 0, loaded = 0;  // K steps whose copies were issued / have landed
     issue(0, 0);
+    if (ksteps > 1) issue(1, 1);
+    issued = ksteps > 1 ? 2 : 1;
     for (int k = 0; k < ksteps; ++k) {
-        const int st = k & 1;
+        const int st = k % kDirStages;  // copy stage of step k
+        const int ab = k & 1;           // accumulator of step k
         if (k >= 1) {
-            // Step k-1's MMAs (stage and accumulator st^1) are done: drain them,
-            // then reuse the stage for step k+1.
-            if (!mbar_wait(&mma_bar[st ^ 1], ((k - 1) >> 1) & 1, err)) s_abort = 1;
+            // Step k-1's MMAs (its stage and accumulator ab^1) are done: drain
+            // them, then reuse that stage for step k+2.
+            if (!mbar_wait(&mma_bar[ab ^ 1], ((k - 1) >> 1) & 1, err)) s_abort = 1;
             __syncthreads();
             if (s_abort) break;
-            drain_acc(lane_addr + (uint32_t)((st ^ 1) * kDirNmax), N, hsum);
+            drain_acc(lane_addr + (uint32_t)((ab ^ 1) * kDirNmax), N, hsum);
         }
-        if (k + 1 < ksteps) {
-            issue(k + 1, st ^ 1);
+        if (k + 2 < ksteps) {
+            issue(k + 2, (k + 2) % kDirStages);
+            issued = k + 3;
+            cp_wait<2>();
+        } else if (k + 1 < ksteps) {
             cp_wait<1>();
         } else {
             cp_wait<0>();
         }
-        if (!mbar_wait(&load_bar[st], (k >> 1) & 1, err)) s_abort = 1;
+        if (!mbar_wait(&load_bar[st], (k / kDirStages) & 1, err)) s_abort = 1;
         fence_async_smem();
         __syncthreads();
         if (s_abort) break;
+        loaded = k + 1;
         if (tid == 0) {
             tc_fence_after();
             const unsigned char* A0 = sA(st, 0);
             const unsigned char* A1 = sA(st, 1);
             const unsigned char* B0 = sB(st, 0);
             const unsigned char* B1 = sB(st, 1);
-            const uint32_t d = tmem + (uint32_t)(st * kDirNmax);
+            const uint32_t d = tmem + (uint32_t)(ab * kDirNmax);
             // small terms first, then hi*hi: a fresh accumulator every K step
 #pragma unroll
             for (int kk = 0; kk < kDirK / 16; ++kk) {
@@ -277,7 +285,7 @@ k_direct(const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict
                 const uint32_t off = kk * 256;
                 mma_bf16(d, smem_desc(A0 + off), smem_desc(B0 + off), idesc, 1u);
             }
-            mma_commit(&mma_bar[st]);
+            mma_commit(&mma_bar[ab]);
         }
     }
     // Drain the last step (its commit covers every earlier MMA).
@@ -289,6 +297,8 @@ k_direct(const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict
     if (s_abort) {
         // Leave no copy in flight into this CTA's shared memory.
         cp_wait<0>();
+        if (tid == 0)
+            for (int j = loaded; j < issued; ++j) mbar_wait(&load_bar[j % kDirStages], (j / kDirStages) & 1, err);
     }
     if (!s_abort) {
         const int64_t f = f0 + warp * 32 + (tid & 31);
