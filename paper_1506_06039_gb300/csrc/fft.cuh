@@ -234,20 +234,19 @@ __device__ void fft4_fwd_stage2(float2* buf, int ld, int rows, int tid, int nthr
     __syncthreads();
 }
 
-// First stage of the forward transform with the input read from a plain
-// (unskewed) array: row r's x[n] = src[r * lds + n] for n < valid, zero
-// beyond; the stage's output goes to buf (rows at buf + r * ld) in the
-// layout fft4_fwd_stage2 continues from. No barrier.
-template <int N>
-__device__ void fft4_fwd_stage1_from(const float2* src, int lds, int valid, float2* buf, int ld, int rows,
-                                     const float2* twf, int tid, int nthr) {
+// First stage of the forward transform with row r's natural-order input
+// x[n] = fetch(r, n) taken from anywhere; the stage's output goes to buf
+// (rows at buf + r * ld) in the layout fft4_fwd_stage2 continues from. No
+// barrier.
+template <int N, typename Fetch>
+__device__ void fft4_fwd_stage1_gen(Fetch fetch, float2* buf, int ld, int rows, const float2* twf, int tid,
+                                    int nthr) {
     constexpr int N1 = Four<N>::N1, N2 = Four<N>::N2, B = N2 + Skew<N>::S;
     for (int task = tid; task < rows * N2; task += nthr) {
         int r = task / N2, n2 = task - r * N2;
-        const float2* q = src + r * lds + n2;
         float2 x[N1];
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) x[n1] = (n1 * N2 + n2 < valid) ? q[N2 * n1] : make_float2(0.f, 0.f);
+        for (int n1 = 0; n1 < N1; ++n1) x[n1] = fetch(r, n1 * N2 + n2);
         Dft<N1, false>::run(x);
 #pragma unroll
         for (int k1 = 1; k1 < N1; ++k1) x[k1] = cmul(x[k1], twf[k1 * N2 + n2]);
@@ -255,6 +254,16 @@ __device__ void fft4_fwd_stage1_from(const float2* src, int lds, int valid, floa
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) p[B * k1] = x[k1];
     }
+}
+
+// The same with the input read from a plain (unskewed) array: row r's
+// x[n] = src[r * lds + n] for n < valid, zero beyond.
+template <int N>
+__device__ void fft4_fwd_stage1_from(const float2* src, int lds, int valid, float2* buf, int ld, int rows,
+                                     const float2* twf, int tid, int nthr) {
+    fft4_fwd_stage1_gen<N>(
+        [&](int r, int n) { return n < valid ? src[r * lds + n] : make_float2(0.f, 0.f); }, buf, ld, rows, twf, tid,
+        nthr);
 }
 
 // Forward transform of `rows` rows at buf + r*ld (natural-order input).

@@ -90,7 +90,7 @@ cudaError_t launch_grad(const uint16_t* frames, int64_t T, int m, int n, int wm1
 cudaError_t launch_q_rows(int Nc, const float* G, const double* inv_area, float scale, int wm1, int64_t T,
                           const float2* twc, float2* QX, cudaStream_t st);
 cudaError_t launch_adj_cols(int Nr, const float2* X, int64_t x_fstride, int ldx, int mc, int ncv, const float2* QX,
-                            int wm1, int64_t T, const float2* twr, float2* Acc, cudaStream_t st);
+                            int wm1, int64_t T, const float2* twr, float2* Acc, unsigned int* err, cudaStream_t st);
 cudaError_t launch_adj_inverse(int Nr, int Nc, const float2* Acc, int ncv, int mc, int nc, const float2* twr,
                                const float2* twc, float2* Yt, float* out, cudaStream_t st);
 

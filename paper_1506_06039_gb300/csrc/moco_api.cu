@@ -657,7 +657,7 @@ moco_status moco_cost_backward(moco_plan_t plan, int32_t shape_idx, const uint16
             P.begin(K_ADJ_COLS, st);
             if (e == cudaSuccess)
                 e = launch_adj_cols(sp.Nr, sp.X, sp.x_fstride, sp.ldx, sp.mc, sp.ncv, sp.Y, sp.wm1, g, sp.twr,
-                                    sp.grad_spec, st);
+                                    sp.grad_spec, sp.dev_err, st);
             P.end(st);
         }
         P.begin(K_ADJ_INV, st);

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "fft_sizes.h"
 #include "internal.h"
 #include "kernels.cuh"
@@ -21,6 +23,7 @@
 namespace moco {
 
 constexpr int kAdjFramesPerCta = 16;
+constexpr size_t kAdjStreamSmemMax = 113 * 1024 + 512;  // two CTAs per SM
 
 // One CTA per frame: the 2w-1 rows of q_f (q = scale * G * inv_area), two
 // rows per complex transform of length N (= Nc), spectra split and written
@@ -132,6 +135,98 @@ k_adj_cols(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int
     }
 }
 
+// The same sum with persistent CTAs: grid (column blocks, frame slices),
+// CTA (x, y) owns columns [v0, v0 + nv) (ncv split evenly over gridDim.x)
+// and walks frames f = y, y + gridDim.y, ..., keeping its sums in registers
+// and adding them once at the end. Each frame's X block (contiguous) arrives
+// by one bulk copy issued when the previous frame's first stage has read the
+// staging buffer; q's few nonzero rows are read straight from QX. The
+// bounded wait on the copy sets *err and ends the CTA (after the copy).
+template <int N>
+__host__ __device__ constexpr size_t adj_stream_smem(int ldx) {
+    return sizeof(float2) * ((size_t)kColsVC * ldx + 2 * (size_t)kColsVC * fft_ld<N>() + N);
+}
+
+template <int N>
+__global__ void __launch_bounds__(cols_threads<N>(), 2)
+k_adj_cols_stream(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv,
+                  const float2* __restrict__ QX, int wm1, int64_t T, const float2* __restrict__ tw_g,
+                  float2* __restrict__ Acc, unsigned int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    constexpr int LD = fft_ld<N>();
+    float2* stg = reinterpret_cast<float2*>(smem_raw);  // kColsVC x ldx (ldx even)
+    float2* bufA = stg + kColsVC * ldx;                  // kColsVC x LD
+    float2* bufQ = bufA + kColsVC * LD;                  // kColsVC x LD
+    float2* tw = bufQ + kColsVC * LD;                    // N: forward table
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int W = 2 * wm1 + 1;
+    const int v0 = (int)((int64_t)blockIdx.x * ncv / gridDim.x);
+    const int nv = (int)((int64_t)(blockIdx.x + 1) * ncv / gridDim.x) - v0;  // <= kColsVC (host)
+    const uint32_t bytes = (uint32_t)(sizeof(float2) * nv * ldx);
+    int64_t f = blockIdx.y;
+    if (f >= T) return;  // the same for the whole CTA
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        s_abort = 0;
+        fence_async_smem();
+        mbar_expect_tx(&bar, bytes);
+        bulk_g2s(stg, X + f * x_fstride + (int64_t)v0 * ldx, bytes, &bar);
+    }
+    for (int i = tid; i < N; i += nthr) tw[i] = tw_g[i];
+    float2 acc[kColsVC];
+#pragma unroll
+    for (int vi = 0; vi < kColsVC; ++vi) acc[vi] = make_float2(0.f, 0.f);
+    uint32_t phase = 0;
+    for (; f < T; f += gridDim.y) {
+        __syncthreads();  // set-up / the previous frame's products are read from the buffers
+        if (!mbar_wait(&bar, phase, err)) s_abort = 1;
+        __syncthreads();
+        if (s_abort) {
+            if (tid == 0) mbar_wait(&bar, phase, err);  // the copy in flight lands before the CTA ends
+            return;
+        }
+        phase ^= 1u;
+        fft4_fwd_stage1_from<N>(stg, ldx, mc, bufA, LD, nv, tw, tid, nthr);
+        // row i of q's column holds shift s = i (i <= wm1) or i - N (i >= N - wm1)
+        const float2* qs = QX + f * (int64_t)ncv * W + (int64_t)v0 * W;
+        fft4_fwd_stage1_gen<N>(
+            [&](int r, int i) {
+                const int k = i <= wm1 ? i + wm1 : (i >= N - wm1 ? i - N + wm1 : -1);
+                return k >= 0 ? qs[(int64_t)r * W + k] : make_float2(0.f, 0.f);
+            },
+            bufQ, LD, nv, tw, tid, nthr);
+        __syncthreads();
+        if (tid == 0 && f + gridDim.y < T) {
+            fence_async_smem();  // this frame's reads of the staging buffer come before the next copy
+            mbar_expect_tx(&bar, bytes);
+            bulk_g2s(stg, X + (f + gridDim.y) * x_fstride + (int64_t)v0 * ldx, bytes, &bar);
+        }
+        fft4_fwd_stage2<N>(bufA, LD, nv, tid, nthr);
+        fft4_fwd_stage2<N>(bufQ, LD, nv, tid, nthr);
+        if (tid < N) {
+            const int skp = sk<N>(tid);
+#pragma unroll
+            for (int vi = 0; vi < kColsVC; ++vi) {
+                if (vi >= nv) break;
+                const float2 a = bufA[vi * LD + skp], q = bufQ[vi * LD + skp];
+                acc[vi].x += a.x * q.x + a.y * q.y;  // a * conj(q)
+                acc[vi].y += a.y * q.x - a.x * q.y;
+            }
+        }
+    }
+    if (tid < N) {
+#pragma unroll
+        for (int vi = 0; vi < kColsVC; ++vi) {
+            if (vi >= nv) break;
+            float* dst = reinterpret_cast<float*>(Acc + (int64_t)(v0 + vi) * N + tid);
+            atomicAdd(dst, acc[vi].x);
+            atomicAdd(dst + 1, acc[vi].y);
+        }
+    }
+}
+
 // Inverse column transforms of Acc (columns of the block), rows [0, mc)
 // scaled by `scale`, written transposed: Yt[r][v].
 template <int N>
@@ -216,10 +311,27 @@ static cudaError_t adj_rows_n(int which, const float* G, const double* inv_area,
 template <int N>
 static cudaError_t adj_cols_n(int which, const float2* X, int64_t x_fstride, int ldx, int mc, int ncv,
                               const float2* QX, int wm1, int64_t T, const float2* tw, float2* Acc, float scale,
-                              float2* Yt, cudaStream_t st) {
+                              float2* Yt, unsigned int* err, cudaStream_t st) {
     const int threads = cols_threads<N>();
     const unsigned vblocks = (unsigned)((ncv + kColsVC - 1) / kColsVC);
     if (which == 0) {
+        // Persistent form when two CTAs fit on an SM and each walks several frames.
+        const size_t ssm = adj_stream_smem<N>(ldx);
+        if (ssm <= kAdjStreamSmemMax) {
+            const void* fn = reinterpret_cast<const void*>(k_adj_cols_stream<N>);
+            cudaError_t e = ensure_smem(fn, ssm);
+            if (e != cudaSuccess) return e;
+            int dev = 0, sms = 0, per_sm = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, ssm)) != cudaSuccess) return e;
+            const int64_t slices = std::max(1, std::max(1, per_sm) * sms / (int)vblocks);
+            if (T >= 4 * slices) {
+                k_adj_cols_stream<N><<<dim3(vblocks, (unsigned)slices), threads, ssm, st>>>(X, x_fstride, ldx, mc, ncv,
+                                                                                         QX, wm1, T, tw, Acc, err);
+                return cudaGetLastError();
+            }
+        }
         const size_t smem = sizeof(float2) * (2 * kColsVC * fft_ld<N>() + N);
         cudaError_t e = ensure_smem(reinterpret_cast<const void*>(k_adj_cols<N>), smem);
         if (e != cudaSuccess) return e;
@@ -247,10 +359,10 @@ cudaError_t launch_q_rows(int Nc, const float* G, const double* inv_area, float 
 }
 
 cudaError_t launch_adj_cols(int Nr, const float2* X, int64_t x_fstride, int ldx, int mc, int ncv, const float2* QX,
-                            int wm1, int64_t T, const float2* twr, float2* Acc, cudaStream_t st) {
+                            int wm1, int64_t T, const float2* twr, float2* Acc, unsigned int* err, cudaStream_t st) {
     if (T <= 0) return cudaSuccess;
 #define MOCO_CASE(NN) \
-    case NN: return adj_cols_n<NN>(0, X, x_fstride, ldx, mc, ncv, QX, wm1, T, twr, Acc, 0.f, nullptr, st);
+    case NN: return adj_cols_n<NN>(0, X, x_fstride, ldx, mc, ncv, QX, wm1, T, twr, Acc, 0.f, nullptr, err, st);
     switch (Nr) {
         MOCO_FOR_EACH_FFT_SIZE(MOCO_CASE)
         default: return cudaErrorInvalidValue;
@@ -263,7 +375,7 @@ cudaError_t launch_adj_inverse(int Nr, int Nc, const float2* Acc, int ncv, int m
     const float scale = (float)(1.0 / ((double)Nr * (double)Nc));
     cudaError_t e = cudaErrorInvalidValue;
 #define MOCO_CASE(NN) \
-    case NN: e = adj_cols_n<NN>(1, nullptr, 0, 0, mc, ncv, nullptr, 0, 0, twr, const_cast<float2*>(Acc), scale, Yt, st); break;
+    case NN: e = adj_cols_n<NN>(1, nullptr, 0, 0, mc, ncv, nullptr, 0, 0, twr, const_cast<float2*>(Acc), scale, Yt, nullptr, st); break;
     switch (Nr) {
         MOCO_FOR_EACH_FFT_SIZE(MOCO_CASE)
         default: break;
