@@ -37,47 +37,107 @@ __device__ __forceinline__ double dkey_inv(unsigned long long k) {
     return __longlong_as_double((long long)u);
 }
 
-// One CTA per frame: exact median by 8-bit radix select, then the stable
-// log-sum-exp and the softmax weights.
+// Order-preserving map of floats to unsigned keys (and back).
+__device__ __forceinline__ unsigned int fkey(float x) {
+    const unsigned int u = __float_as_uint(x);
+    return (u >> 31) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(unsigned int k) {
+    return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k);
+}
+
+// One step of the radix select: hist holds the counts of the current digit
+// among the keys that match the prefix; the digit of the element of rank
+// *rank (0-based) is found by warp 0 (lane L owns bins 8L .. 8L + 7: a scan
+// of the lanes' totals, then the owning lane walks its eight bins), and
+// *rank becomes the rank within that digit. Returns the digit (all threads,
+// after the call's barrier).
+__device__ __forceinline__ unsigned int radix_digit(const unsigned int* hist, int* s_rank, unsigned int* s_digit) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        unsigned int c[8], tot = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            c[j] = hist[lane * 8 + j];
+            tot += c[j];
+        }
+        unsigned int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const unsigned int excl = incl - tot;
+        const unsigned int r = (unsigned int)*s_rank;
+        const unsigned int own = __ballot_sync(0xffffffffu, r >= excl && r < incl);
+        if (lane == __ffs(own) - 1) {
+            unsigned int rr = r - excl, b = lane * 8;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (c[j] > rr) break;
+                rr -= c[j];
+                ++b;
+            }
+            *s_rank = (int)rr;
+            *s_digit = b;
+        }
+    }
+    __syncthreads();
+    return *s_digit;
+}
+
+// One CTA per frame: the exact median (the element of rank K/2) by 8-bit
+// radix select on order-preserving keys (32-bit keys when every cost of the
+// frame is a float value, as the search's own costs are; 64-bit otherwise),
+// then the stable log-sum-exp and the softmax weights (exponentials in FP32,
+// their sum in FP64).
 static __global__ void __launch_bounds__(kSoftminThreads)
 k_softmin(const double* __restrict__ cost, int K, double tau_scale, double* __restrict__ loss,
           float* __restrict__ weights) {
     __shared__ unsigned int hist[256];
-    __shared__ unsigned long long s_prefix;
     __shared__ int s_rank;
+    __shared__ unsigned int s_digit;
     __shared__ double s_red[32];
     __shared__ int s_cnt[32];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int64_t f = blockIdx.x;
     const double* c = cost + f * K;
-    if (tid == 0) {
-        s_prefix = 0;
-        s_rank = K / 2;
-    }
-    unsigned long long mask = 0;
-    for (int shift = 56; shift >= 0; shift -= 8) {
-        for (int i = tid; i < 256; i += nthr) hist[i] = 0;
-        __syncthreads();
-        const unsigned long long prefix = s_prefix;
-        for (int k = tid; k < K; k += nthr) {
-            const unsigned long long key = dkey(c[k]);
-            if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int r = s_rank;
-            unsigned int b = 0;
-            for (; b < 256; ++b) {
-                if ((int)hist[b] > r) break;
-                r -= (int)hist[b];
+    if (tid == 0) s_rank = K / 2;
+    int exact = 1;
+    for (int k = tid; k < K; k += nthr) exact &= ((double)(float)c[k] == c[k]);
+    exact = __syncthreads_and(exact);
+    double med;
+    if (exact) {
+        unsigned int prefix = 0, mask = 0;
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            for (int i = tid; i < 256; i += nthr) hist[i] = 0;
+            __syncthreads();
+            for (int k = tid; k < K; k += nthr) {
+                const unsigned int key = fkey((float)c[k]);
+                if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
             }
-            s_rank = r;
-            s_prefix = prefix | ((unsigned long long)b << shift);
+            __syncthreads();
+            prefix |= radix_digit(hist, &s_rank, &s_digit) << shift;
+            mask |= 255u << shift;
+            __syncthreads();  // s_digit is read before the next pass writes it
         }
-        mask |= 255ull << shift;
-        __syncthreads();
+        med = (double)fkey_inv(prefix);
+    } else {
+        unsigned long long prefix = 0, mask = 0;
+        for (int shift = 56; shift >= 0; shift -= 8) {
+            for (int i = tid; i < 256; i += nthr) hist[i] = 0;
+            __syncthreads();
+            for (int k = tid; k < K; k += nthr) {
+                const unsigned long long key = dkey(c[k]);
+                if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+            }
+            __syncthreads();
+            prefix |= (unsigned long long)radix_digit(hist, &s_rank, &s_digit) << shift;
+            mask |= 255ull << shift;
+            __syncthreads();
+        }
+        med = dkey_inv(prefix);
     }
-    const double med = dkey_inv(s_prefix);
     const double tau = tau_scale * med;
     double vmin = INFINITY;
     for (int k = tid; k < K; k += nthr) vmin = vmin < c[k] ? vmin : c[k];
@@ -117,8 +177,9 @@ k_softmin(const double* __restrict__ cost, int K, double tau_scale, double* __re
         for (int k = tid; k < K; k += nthr) wf[k] = (c[k] == fmin_v) ? wv : 0.0f;
         return;
     }
+    const double itau = 1.0 / tau;
     double z = 0.0;
-    for (int k = tid; k < K; k += nthr) z += exp(-(c[k] - fmin_v) / tau);
+    for (int k = tid; k < K; k += nthr) z += (double)expf(-(float)((c[k] - fmin_v) * itau));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
     if ((tid & 31) == 0) s_red[tid >> 5] = z;
@@ -130,8 +191,8 @@ k_softmin(const double* __restrict__ cost, int K, double tau_scale, double* __re
         loss[f] = fmin_v - tau * log(t);
     }
     __syncthreads();
-    const double Z = s_red[0];
-    for (int k = tid; k < K; k += nthr) wf[k] = (float)(exp(-(c[k] - fmin_v) / tau) / Z);
+    const float iZ = (float)(1.0 / s_red[0]);
+    for (int k = tid; k < K; k += nthr) wf[k] = expf(-(float)((c[k] - fmin_v) * itau)) * iZ;
 }
 
 // Q[k] += scale * inv_area[k] * sum_f G[f][k] (k < K) over one chunk of
