@@ -495,8 +495,7 @@ def run_grad(args, world, rank, local):
     its gradient with respect to a float template (set template, cost
     surface, soft-min, adjoint), all through the C ABI."""
     import torch
-    from paper_1506_06039_gb300 import (build, moco_cost_backward, moco_cost_surface, moco_set_template,
-                                        moco_softmin, synth)
+    from paper_1506_06039_gb300 import build, moco_set_template, moco_softmin_grad, synth
     from paper_1506_06039_gb300.autograd import softmin_plan
 
     build.build()
@@ -520,10 +519,9 @@ def run_grad(args, world, rank, local):
     stream = torch.cuda.current_stream()
 
     def step():
+        # one refinement step's device work: template in, per-frame loss and dL/db out
         moco_set_template(plan.handle, 0, tmpl, stream)
-        moco_cost_surface(plan.handle, 0, st.frames, cost, stream)
-        moco_softmin(plan.handle, 0, cost, 0.05, loss, weights, stream)
-        moco_cost_backward(plan.handle, 0, st.frames, weights, grad, None, 1.0, stream)
+        moco_softmin_grad(plan.handle, 0, st.frames, 0.05, cost, loss, weights, grad, 1.0, stream)
         if pg:
             # data-parallel refinement: the template gradient summed over the ranks' frames
             pg.all_reduce(grad)

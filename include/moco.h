@@ -144,13 +144,28 @@ moco_status moco_softmin(moco_plan_t plan, int32_t shape_idx, const double* cost
  * ([T][2w-1][2w-1] floats, dL/df_{s,t}), accumulates
  *   grad_template_dev[m][n] += dL/db  (float; the caller zeroes it first)
  * and, if grad_frames_dev is non-null, overwrites grad_frames_dev[T][m][n]
- * with dL/da. Uses the plan's current template. The correlation parts run
- * as direct FP32 contractions with FP32 atomics across frame chunks, so the
- * last bits vary from run to run. MOCO_ERR_UNSUPPORTED when levels != 0 or
- * the window needs more shared memory than a CTA has (w > 56). */
+ * with dL/da. Uses the plan's current template. The template side's
+ * correlation runs through FFTs on FFT-form plans (one inverse transform of
+ * the sum over frames) and as a direct FP32 contraction otherwise; both sum
+ * with FP32 atomics, so the last bits vary from run to run.
+ * MOCO_ERR_UNSUPPORTED when levels != 0 or the window needs more shared
+ * memory than a CTA has (w > 56). */
 moco_status moco_cost_backward(moco_plan_t plan, int32_t shape_idx, const uint16_t* frames_dev, int64_t T,
                                const float* grad_cost_dev, float grad_scale, float* grad_template_dev,
                                float* grad_frames_dev, void* stream);
+
+/* The differentiable form's forward pass and template adjoint in one call
+ * (shapes with levels == 0): the cost surface (as moco_cost_surface) into
+ * cost_dev [T][2w-1][2w-1] FP64, the soft-min (as moco_softmin) into
+ * loss_dev [T] and weights_dev [T][2w-1][2w-1], and
+ *   grad_template_dev[m][n] += grad_scale * d(sum_f L_f)/db
+ * (as moco_cost_backward with grad_cost = the weights). On FFT-form plans
+ * each batch's row spectra serve both the search and the adjoint (computed
+ * once); otherwise the three steps run one after another. All pointers are
+ * caller-owned device memory; no allocation, no synchronisation. */
+moco_status moco_softmin_grad(moco_plan_t plan, int32_t shape_idx, const uint16_t* frames_dev, int64_t T,
+                              double tau_scale, float grad_scale, double* cost_dev, double* loss_dev,
+                              float* weights_dev, float* grad_template_dev, void* stream);
 
 /* End-to-end alignment from host memory: copies frames_host [T][m][n] to the
  * device in batches, aligns them and copies shifts [T][2] back to

@@ -3,9 +3,10 @@
 MocoSoftMin computes, for a float template b and uint16 frames a_f,
     L = sum_f -tau_f log sum_{s,t} exp(-f_st(a_f, b) / tau_f),
     tau_f = tau_scale * median_{s,t} f_st (held constant),
-with f Section 2's cost. Forward: moco_set_template, moco_cost_surface and
-moco_softmin; backward: moco_cost_backward with the saved soft-min weights.
-Only the per-frame losses are summed here (a reduction of T numbers).
+with f Section 2's cost: moco_set_template, then moco_softmin_grad (cost
+surface, soft-min and template adjoint in one pass) when the template
+requires a gradient, else moco_cost_surface and moco_softmin. Only the
+per-frame losses are summed here (a reduction of T numbers).
 """
 from __future__ import annotations
 
@@ -15,20 +16,27 @@ from .binding import TEMPLATE_F32, Plan
 
 
 class MocoSoftMin(torch.autograd.Function):
+    """The summed soft-min loss. When the template requires a gradient, the
+    forward pass computes it too (moco_softmin_grad: the frames' row spectra
+    serve the search and the adjoint) and backward scales it by the incoming
+    gradient (the loss is a scalar, its gradient linear in that factor);
+    otherwise only the loss is computed."""
+
     @staticmethod
     def forward(ctx, template, frames, plan, tau_scale=0.05, shape_idx=0):
         plan.set_template(template.detach().contiguous(), shape_idx)
-        cost = plan.cost_surface(frames, shape_idx)
-        loss, weights = plan.softmin(cost, tau_scale, shape_idx)
-        ctx.save_for_backward(frames, weights)
-        ctx.plan, ctx.shape_idx = plan, shape_idx
+        if ctx.needs_input_grad[0]:
+            loss, grad_t, _, _ = plan.softmin_grad(frames, tau_scale, shape_idx=shape_idx)
+            ctx.save_for_backward(grad_t)
+        else:
+            cost = plan.cost_surface(frames, shape_idx)
+            loss, _ = plan.softmin(cost, tau_scale, shape_idx)
         return loss.sum()
 
     @staticmethod
     def backward(ctx, grad_out):
-        frames, weights = ctx.saved_tensors
-        grad_t = ctx.plan.cost_backward(frames, weights, grad_scale=float(grad_out), shape_idx=ctx.shape_idx)
-        return grad_t, None, None, None, None
+        (grad_t,) = ctx.saved_tensors
+        return grad_t * grad_out.to(grad_t.dtype), None, None, None, None
 
 
 def softmin_plan(frames, template, w, group_frames=0):

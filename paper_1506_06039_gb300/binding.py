@@ -33,6 +33,7 @@ EXPORTS = (
     "moco_cost_backward", "moco_align_host", "moco_plan_query", "moco_plan_destroy",
     "moco_status_string", "moco_last_error", "moco_profile_enable", "moco_profile_read", "moco_plan_status",
     "moco_jitter_noalloc", "moco_apply_shifts", "moco_stream_create", "moco_stream_align", "moco_stream_destroy",
+    "moco_softmin_grad",
 )
 
 
@@ -88,6 +89,7 @@ def lib():
             L.moco_cost_surface.argtypes = [P, i32, P, i64, P, P]
             L.moco_softmin.argtypes = [P, i32, P, i64, dbl, P, P, P]
             L.moco_cost_backward.argtypes = [P, i32, P, i64, P, ctypes.c_float, P, P, P]
+            L.moco_softmin_grad.argtypes = [P, i32, P, i64, dbl, ctypes.c_float, P, P, P, P, P]
             L.moco_align_host.argtypes = [P, i32, P, i64, P, P]
             L.moco_plan_query.argtypes = [P, i32, ctypes.POINTER(MocoShapeInfo)]
             L.moco_plan_destroy.argtypes = [P]
@@ -271,6 +273,19 @@ def moco_cost_backward(plan, shape_idx, frames, grad_cost, grad_template, grad_f
                                     _ptr(grad_template), _ptr(grad_frames), _stream(stream)))
 
 
+def moco_softmin_grad(plan, shape_idx, frames, tau_scale, cost, loss, weights, grad_template, grad_scale=1.0,
+                      stream=None):
+    import torch
+    _need(frames, torch.uint16, "frames")
+    _need(cost, torch.float64, "cost")
+    _need(loss, torch.float64, "loss")
+    _need(weights, torch.float32, "weights")
+    _need(grad_template, torch.float32, "grad_template")
+    T = frames.shape[0] if frames.dim() == 3 else 1
+    _check(lib().moco_softmin_grad(plan, shape_idx, _ptr(frames), T, float(tau_scale), float(grad_scale),
+                                   _ptr(cost), _ptr(loss), _ptr(weights), _ptr(grad_template), _stream(stream)))
+
+
 def moco_align_host(plan, shape_idx, frames_host, shifts_host, stream=None):
     import torch
     _need(frames_host, torch.uint16, "frames_host", device=False)
@@ -399,6 +414,23 @@ class Plan:
         gf = torch.empty(frames.shape, dtype=torch.float32, device=frames.device) if grad_frames else None
         moco_cost_backward(self.handle, shape_idx, frames, grad_cost, grad_template, gf, grad_scale, stream)
         return (grad_template, gf) if grad_frames else grad_template
+
+    def softmin_grad(self, frames, tau_scale, grad_template=None, grad_scale=1.0, shape_idx=0, stream=None):
+        """(loss[T] float64, grad_template[m, n] float32 (accumulated), cost, weights): the
+        soft-min loss of every frame and the gradient of their sum with respect to the
+        template, in one pass over the frames."""
+        import torch
+        W = self.W(shape_idx)
+        m, n = int(self.shapes[shape_idx]["m"]), int(self.shapes[shape_idx]["n"])
+        T = frames.shape[0]
+        cost = torch.empty((T, W, W), dtype=torch.float64, device=frames.device)
+        loss = torch.empty(T, dtype=torch.float64, device=frames.device)
+        weights = torch.empty((T, W, W), dtype=torch.float32, device=frames.device)
+        if grad_template is None:
+            grad_template = torch.zeros((m, n), dtype=torch.float32, device=frames.device)
+        moco_softmin_grad(self.handle, shape_idx, frames, tau_scale, cost, loss, weights, grad_template, grad_scale,
+                          stream)
+        return loss, grad_template, cost, weights
 
     def set_template(self, template, shape_idx=0, stream=None):
         moco_set_template(self.handle, shape_idx, template, stream)

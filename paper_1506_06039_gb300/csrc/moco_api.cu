@@ -676,6 +676,63 @@ moco_status moco_cost_backward(moco_plan_t plan, int32_t shape_idx, const uint16
     return MOCO_OK;
 }
 
+moco_status moco_softmin_grad(moco_plan_t plan, int32_t shape_idx, const uint16_t* frames_dev, int64_t T,
+                              double tau_scale, float grad_scale, double* cost_dev, double* loss_dev,
+                              float* weights_dev, float* grad_template_dev, void* stream) {
+    if (!plan) return fail(MOCO_ERR_INVALID_ARG, "null plan");
+    if (shape_idx < 0 || shape_idx >= (int)plan->shapes.size()) return fail(MOCO_ERR_INVALID_ARG, "bad shape_idx");
+    if (T < 0 || !(tau_scale >= 0.0)) return fail(MOCO_ERR_INVALID_ARG, "T < 0 or bad tau_scale");
+    ShapePlan& sp = plan->shapes[shape_idx];
+    if (sp.levels != 0) return fail(MOCO_ERR_UNSUPPORTED, "the adjoint needs levels == 0");
+    if (T == 0) return MOCO_OK;
+    if (!frames_dev || !cost_dev || !loss_dev || !weights_dev || !grad_template_dev)
+        return fail(MOCO_ERR_INVALID_ARG, "null frames, cost, loss, weights or grad_template");
+    if (!aligned16(frames_dev)) return fail(MOCO_ERR_INVALID_ARG, "frames must be 16-byte aligned");
+    if (sp.form != MOCO_XCORR_FFT_FP32 || !sp.has_fft) {
+        moco_status s = moco_cost_surface(plan, shape_idx, frames_dev, T, cost_dev, stream);
+        if (s == MOCO_OK) s = moco_softmin(plan, shape_idx, cost_dev, T, tau_scale, loss_dev, weights_dev, stream);
+        if (s == MOCO_OK)
+            s = moco_cost_backward(plan, shape_idx, frames_dev, T, weights_dev, grad_scale, grad_template_dev, nullptr,
+                                   stream);
+        return s;
+    }
+    DeviceGuard guard(plan->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Profiler& P = plan->prof;
+    const int64_t mn = (int64_t)sp.desc.m * sp.desc.n, WW = (int64_t)sp.W * sp.W;
+    cudaError_t e = cudaMemsetAsync(sp.grad_spec, 0, (size_t)sp.ncv * sp.Nr * 8, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint spectrum clear");
+    for (int64_t f0 = 0; f0 < T; f0 += sp.group) {
+        const int64_t g = std::min<int64_t>(sp.group, T - f0);
+        // the search leaves this batch's row spectra in X and frees Y
+        moco_status s = search_group(sp, frames_dev + f0 * mn, g, cost_dev + f0 * WW, nullptr, nullptr, st);
+        if (s != MOCO_OK) return s;
+        P.begin(K_SOFTMIN, st);
+        e = launch_softmin(cost_dev + f0 * WW, g, (int)WW, tau_scale, loss_dev + f0, weights_dev + f0 * WW, st);
+        P.end(st);
+        if (e != cudaSuccess) return cuda_fail(e, "k_softmin");
+        P.begin(K_ADJ_ROWS, st);
+        e = launch_q_rows(sp.Nc, weights_dev + f0 * WW, sp.inv_area, grad_scale, sp.wm1, g, sp.twc, sp.Y, st);
+        P.end(st);
+        if (e != cudaSuccess) return cuda_fail(e, "k_q_rows");
+        P.begin(K_ADJ_COLS, st);
+        e = launch_adj_cols(sp.Nr, sp.X, sp.x_fstride, sp.ldx, sp.mc, sp.ncv, sp.Y, sp.wm1, g, sp.twr, sp.grad_spec,
+                            sp.dev_err, st);
+        P.end(st);
+        if (e != cudaSuccess) return cuda_fail(e, "k_adj_cols");
+    }
+    P.begin(K_ADJ_INV, st);
+    e = launch_adj_inverse(sp.Nr, sp.Nc, sp.grad_spec, sp.ncv, sp.mc, sp.nc, sp.twr, sp.twc, sp.X, sp.grad_acc, st);
+    P.end(st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint inverse");
+    P.begin(K_BACKWARD, st);
+    e = launch_grad(frames_dev, T, sp.desc.m, sp.desc.n, sp.wm1, weights_dev, grad_scale, sp.inv_area, sp.coff_i,
+                    sp.tmpl, sp.f32 ? 1 : 0, 0, sp.grad_acc, sp.grad_Q, grad_template_dev, nullptr, st);
+    P.end(st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint kernels");
+    return MOCO_OK;
+}
+
 moco_status moco_plan_status(moco_plan_t plan) {
     if (!plan) return fail(MOCO_ERR_INVALID_ARG, "null plan");
     DeviceGuard guard(plan->device);

@@ -97,6 +97,35 @@ def test_template_adjoint_routes_ragged_groups(route):
     assert np.abs(gt - gb).max() <= 1e-3 * np.abs(gb).max()
 
 
+@pytest.mark.parametrize("route", ["fft", "direct"])
+def test_fused_softmin_grad_equals_separate_calls(route):
+    # moco_softmin_grad (one pass: the row spectra serve search and adjoint on
+    # FFT-form plans; the three calls in turn otherwise) against
+    # moco_cost_surface + moco_softmin + moco_cost_backward, over three frame
+    # groups with a short last one.
+    m, n, w, T = 64, 72, 6, 11
+    frames, tmpl = stack(m, n, T, w, seed=71)
+    fr = torch.from_numpy(frames).cuda()
+    xc = XCORR_FFT_FP32 if route == "fft" else XCORR_DIRECT_BF16X3
+    plan = Plan(dict(m=m, n=n, w=w, levels=0, template_dtype=TEMPLATE_F32, xcorr=xc, group_frames=4),
+                torch.from_numpy(tmpl).cuda())
+    try:
+        loss, grad, cost, weights = plan.softmin_grad(fr, TAU, grad_scale=0.5)
+        c2 = plan.cost_surface(fr)
+        l2, w2 = plan.softmin(c2, TAU)
+        g2 = plan.cost_backward(fr, w2, grad_scale=0.5)
+        torch.cuda.synchronize()
+    finally:
+        plan.close()
+    assert torch.equal(cost, c2) and torch.equal(loss, l2) and torch.equal(weights, w2)
+    g, g2 = grad.cpu().numpy(), g2.cpu().numpy()
+    assert np.abs(g - g2).max() <= 1e-5 * np.abs(g2).max()  # FP32 atomics: order of the sums only
+    tau = oracle_tau(frames, tmpl, w)
+    _, lf, gb, _ = oracle.softmin_loss(frames.astype(np.float64), tmpl.astype(np.float64), w, tau, grad_template=True)
+    check_loss(loss.cpu().numpy(), lf, frames, tmpl, w)
+    assert np.abs(g - 0.5 * gb).max() <= 1e-3 * np.abs(0.5 * gb).max()
+
+
 def test_gradient_central_differences_64_pixels():
     # 64 seeded pixels, FP64 central differences of the oracle loss (tau held
     # at the oracle's median rule), step 1e-2 (the loss is smooth in b).
