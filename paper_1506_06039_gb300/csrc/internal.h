@@ -14,10 +14,13 @@ bool fft_size_supported(int N);
 bool fft_split(int N, int* n1, int* n2);  // the four-step factors N = N1 * N2
 int fft_split_max(int N);  // max(N1, N2): threads per row of a four-step stage
 
+// capacity: image slots in colE and tot (a single image is split over chunk
+// CTAs when it covers their count).
 cudaError_t launch_frame_rows(int N, bool f32, const void* src, int64_t src_fstride, int64_t nimg, int m,
                               int n, int levels, int mc, int nc, const int32_t* coff_i, const float* coff_f,
                               const float2* tw, float2* X, int64_t x_fstride, int ldx, u64* rowE, u64* colE,
-                              u64* tot, uint32_t* corners, int wm1, unsigned int* err, cudaStream_t st);
+                              u64* tot, uint32_t* corners, int wm1, unsigned int* err, int64_t capacity,
+                              cudaStream_t st);
 
 cudaError_t launch_cols(int N, bool spectrum, const float2* X, int64_t x_fstride, int ldx, int mc, int ncv,
                         int64_t nimg, const float2* tw, const float2* bspec, float2* Y, int64_t y_fstride,

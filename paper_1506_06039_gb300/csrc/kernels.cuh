@@ -114,7 +114,8 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
              const float2* __restrict__ tw_g, float2* __restrict__ X, int64_t x_fstride, int ldx,
              u64* __restrict__ rowE, u64* __restrict__ colE, u64* __restrict__ tot,
              uint32_t* __restrict__ corners, int wm1, __nv_bfloat16* __restrict__ p_hi = nullptr,
-             __nv_bfloat16* __restrict__ p_lo = nullptr, int ldp = 0, unsigned int* __restrict__ err = nullptr) {
+             __nv_bfloat16* __restrict__ p_lo = nullptr, int ldp = 0, unsigned int* __restrict__ err = nullptr,
+             int split = 0) {
     static_assert(!STAGED || (!F32IN && !PLANES), "staging is for uint16 frames in FFT mode");
     typedef typename AccT<F32IN>::type Acc;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -133,7 +134,7 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
         const int rows = min(kRC, mc - c0) * (levels ? 2 : 1);
         const uint32_t bytes = (uint32_t)rows * (uint32_t)n * 2u;
         const unsigned char* g = reinterpret_cast<const unsigned char*>(static_cast<const uint16_t*>(src) +
-                                                                        blockIdx.x * src_fstride +
+                                                                        (split ? 0 : blockIdx.x) * src_fstride +
                                                                         (int64_t)c0 * (levels ? 2 : 1) * n);
         unsigned char* d = smem_raw + frame_rows_smem_base<N, F32IN>(nc);
         mbar_expect_tx(&stage_bar, bytes);
@@ -142,13 +143,18 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
     };
 
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int64_t f = blockIdx.x;
+    // split: one image, one chunk of kRC searched rows per CTA; its partial
+    // total and edge-column energies go to slot blockIdx.x.
+    const int64_t f = split ? 0 : blockIdx.x;
+    const int r_begin = split ? (int)blockIdx.x * kRC : 0;
+    const int r_end = split ? min(mc, r_begin + kRC) : mc;
+    const int64_t slot_out = blockIdx.x;
     if (STAGED) {
         if (tid == 0) {
             mbar_init(&stage_bar, 1);
             s_abort = 0;
             fence_async_smem();
-            issue_chunk(0);
+            issue_chunk(r_begin);
         }
     }
     for (int i = tid; i < N; i += nthr) tw[i] = tw_g[i];
@@ -176,7 +182,7 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
     const bool warp_rows = (nc % 32 == 0);  // every warp then shares one row pair
     Acc colreg[4] = {0, 0, 0, 0};
 
-    for (int r0 = 0; r0 < mc; r0 += kRC) {
+    for (int r0 = r_begin; r0 < r_end; r0 += kRC) {
         const int rows = min(kRC, mc - r0), nfft = (rows + 1) >> 1;
         if constexpr (!PLANES) {
             for (int i = tid; i < nfft * (N - nc); i += nthr) {
@@ -185,10 +191,10 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
             }
             if (STAGED) {
                 __syncthreads();  // s_abort and the barrier's set-up are visible
-                if (!mbar_wait(&stage_bar, (uint32_t)((r0 / kRC) & 1), err)) s_abort = 1;
+                if (!mbar_wait(&stage_bar, (uint32_t)(((r0 - r_begin) / kRC) & 1), err)) s_abort = 1;
                 __syncthreads();
                 if (s_abort) {
-                    if (tid == 0) mbar_wait(&stage_bar, (uint32_t)((r0 / kRC) & 1), err);
+                    if (tid == 0) mbar_wait(&stage_bar, (uint32_t)(((r0 - r_begin) / kRC) & 1), err);
                     return;
                 }
             }
@@ -419,7 +425,7 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
         }
         }
         __syncthreads();
-        if (STAGED && tid == 0 && r0 + kRC < mc) {
+        if (STAGED && tid == 0 && r0 + kRC < r_end) {
             fence_async_smem();  // this chunk's reads of the stage come before the next copies
             issue_chunk(r0 + kRC);
         }
@@ -475,13 +481,31 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
     if (tid == 0) {
         Acc s = 0;
         for (int i = 0; i < (nthr + 31) / 32; ++i) s += red[i];
-        tot[f] = *reinterpret_cast<u64*>(&s);
+        tot[slot_out] = *reinterpret_cast<u64*>(&s);
     }
     for (int c = tid; c < nc; c += nthr)
         if (c < wm1 || c >= nc - wm1) {
             Acc v = colacc[c];
-            colE[f * nc + c] = *reinterpret_cast<u64*>(&v);
+            colE[slot_out * nc + c] = *reinterpret_cast<u64*>(&v);
         }
+}
+
+// After a split single-image k_frame_rows: the slots' partial totals and
+// edge-column energies summed, in slot order, into slot 0.
+template <bool F32>
+__global__ void k_merge_chunks(u64* __restrict__ colE, u64* __restrict__ tot, int chunks, int nc, int wm1) {
+    typedef typename AccT<F32>::type Acc;
+    for (int c = threadIdx.x; c <= nc; c += blockDim.x) {
+        if (c < nc && !(c < wm1 || c >= nc - wm1)) continue;
+        u64* p = c < nc ? colE + c : tot;
+        const int64_t stride = c < nc ? nc : 1;
+        Acc s = 0;
+        for (int k = 0; k < chunks; ++k) {
+            const u64 b = p[k * stride];
+            s += *reinterpret_cast<const Acc*>(&b);
+        }
+        p[0] = *reinterpret_cast<u64*>(&s);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1438,7 +1462,11 @@ static __global__ void k_sq_prefix_cols(int m, int n, u64* __restrict__ P) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j > n) return;
     const int64_t ld = n + 1;
-    for (int i = 1; i <= m; ++i) P[i * ld + j] += P[(i - 1) * ld + j];
+    u64 run = 0;  // in a register: the loads down the column do not wait on the stores
+    for (int i = 1; i <= m; ++i) {
+        run += P[i * ld + j];
+        P[i * ld + j] = run;
+    }
 }
 
 // For searches without a level: the searched optimum is the answer.
@@ -1463,11 +1491,12 @@ k_template_offset(const void* __restrict__ tmpl, int m, int n, int levels, int32
     const int rows = mc << levels, cols = nc << levels;  // the pixels the searched grid covers
     u64 su = 0;
     double sd = 0.0;
-    for (int64_t k = tid; k < (int64_t)rows * cols; k += nthr) {
-        const int i = (int)(k / cols), j = (int)(k % cols);
-        if (F32) sd += (double)static_cast<const float*>(tmpl)[(int64_t)i * n + j];
-        else su += static_cast<const uint16_t*>(tmpl)[(int64_t)i * n + j];
-    }
+    // one warp per row at a time (coalesced; no per-element division)
+    for (int i = tid >> 5; i < rows; i += nthr >> 5)
+        for (int j = tid & 31; j < cols; j += 32) {
+            if (F32) sd += (double)static_cast<const float*>(tmpl)[(int64_t)i * n + j];
+            else su += static_cast<const uint16_t*>(tmpl)[(int64_t)i * n + j];
+        }
     su = warp_sum(su);
     sd = warp_sum(sd);
     if ((tid & 31) == 0) { redu[tid >> 5] = su; redd[tid >> 5] = sd; }

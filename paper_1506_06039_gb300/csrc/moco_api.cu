@@ -271,7 +271,7 @@ moco_status prepare_template(ShapePlan& sp, const void* tmpl_dev, cudaStream_t s
     if (sp.has_fft)
         e = launch_frame_rows(sp.Nc, sp.f32, sp.tmpl, 0, 1, sp.desc.m, sp.desc.n, sp.levels, sp.mc, sp.nc,
                               sp.coff_i, sp.coff_f, sp.twc, sp.X, sp.x_fstride, sp.ldx, sp.rowE, sp.colE, sp.tot,
-                              sp.corners, sp.wm1, sp.dev_err, st);
+                              sp.corners, sp.wm1, sp.dev_err, sp.group, st);
     else
         e = launch_frame_planes(sp.f32, sp.tmpl, 0, 1, sp.desc.m, sp.desc.n, sp.levels, sp.mc, sp.nc, sp.coff_i,
                                 sp.coff_f, sp.twc, sp.rowE, sp.colE, sp.tot, sp.corners, sp.wm1, sp.planes_hi,
@@ -280,12 +280,14 @@ moco_status prepare_template(ShapePlan& sp, const void* tmpl_dev, cudaStream_t s
     e = launch_energy(sp.f32, true, sp.rowE, sp.colE, sp.tot, sp.corners, 1, sp.mc, sp.nc, sp.wm1, sp.Sb, 1, st);
     if (e == cudaSuccess) e = launch_pair_from_double(sp.Sb, sp.Sb2, (int64_t)sp.W * sp.W, st);
     if (e != cudaSuccess) return cuda_fail(e, "template energies");
-    if (sp.has_fft) {
+    // Before the autotuner has fixed the form both forms' tables are built;
+    // afterwards only the chosen form's.
+    if (sp.has_fft && (!sp.tuned || sp.form == MOCO_XCORR_FFT_FP32)) {
         e = launch_cols(sp.Nr, true, sp.X, sp.x_fstride, sp.ldx, sp.mc, sp.ncv, 1, sp.twr, nullptr, sp.bspec, 0,
                         sp.wm1, (float)(1.0 / ((double)sp.Nr * (double)sp.Nc)), sp.dev_err, st);
         if (e != cudaSuccess) return cuda_fail(e, "template spectrum");
     }
-    if (sp.has_direct) {
+    if (sp.has_direct && (!sp.tuned || sp.form == MOCO_XCORR_DIRECT_BF16X3)) {
         e = launch_toeplitz(sp.f32, sp.tmpl, sp.desc.m, sp.desc.n, sp.levels, sp.mc, sp.nc, sp.nqc, sp.wm1, sp.coff_i,
                             sp.coff_f, sp.bprime, sp.dtiles, st);
         if (e != cudaSuccess) return cuda_fail(e, "template Toeplitz tiles");
@@ -333,7 +335,7 @@ moco_status search_group(ShapePlan& sp, const uint16_t* frames, int64_t g, doubl
     P.begin(K_FRAME_ROWS, st);
     cudaError_t e = launch_frame_rows(sp.Nc, false, frames, (int64_t)m * n, g, m, n, sp.levels, sp.mc, sp.nc,
                                       sp.coff_i, nullptr, sp.twc, sp.X, sp.x_fstride, sp.ldx, sp.rowE, sp.colE,
-                                      sp.tot, sp.corners, sp.wm1, sp.dev_err, st);
+                                      sp.tot, sp.corners, sp.wm1, sp.dev_err, sp.group, st);
     P.end(st);
     if (e != cudaSuccess) return cuda_fail(e, "k_frame_rows");
     P.begin(K_COLS, st);
@@ -392,7 +394,10 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 
 // MOCO_XCORR_AUTO: time both forms on one batch (zero frames in the staging
 // buffer: the work does not depend on the values) and keep the faster.
 moco_status autotune(ShapePlan& sp, cudaStream_t st) {
-    if (!(sp.has_fft && sp.has_direct)) return MOCO_OK;
+    if (!(sp.has_fft && sp.has_direct)) {
+        sp.tuned = true;
+        return MOCO_OK;
+    }
     const int64_t g = std::min<int64_t>(sp.stage_frames, sp.group);
     cudaError_t e = cudaMemsetAsync(sp.stage[0], 0, (size_t)(g * sp.desc.m * sp.desc.n * 2), st);
     if (e != cudaSuccess) return cuda_fail(e, "autotune clear");
@@ -423,6 +428,7 @@ moco_status autotune(ShapePlan& sp, cudaStream_t st) {
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     sp.form = best_form;
+    sp.tuned = true;
     return r;
 }
 
@@ -650,7 +656,7 @@ moco_status moco_cost_backward(moco_plan_t plan, int32_t shape_idx, const uint16
             P.begin(K_ADJ_ROWS, st);
             e = launch_frame_rows(sp.Nc, false, frames_dev + f0 * mn, mn, g, sp.desc.m, sp.desc.n, 0, sp.mc, sp.nc,
                                   sp.coff_i, nullptr, sp.twc, sp.X, sp.x_fstride, sp.ldx, sp.rowE, sp.colE, sp.tot,
-                                  sp.corners, sp.wm1, sp.dev_err, st);
+                                  sp.corners, sp.wm1, sp.dev_err, sp.group, st);
             if (e == cudaSuccess)
                 e = launch_q_rows(sp.Nc, grad_cost_dev + f0 * K, sp.inv_area, grad_scale, sp.wm1, g, sp.twc, sp.Y, st);
             P.end(st);

@@ -46,6 +46,7 @@ struct ShapePlan {
     bool has_fft = true, has_direct = false;  // which forms' buffers exist
     int ncp = 0, nqc = 0;                     // direct form: padded row length, 64-column chunks
     float tuned_ms[3] = {0, 0, 0};            // autotuner timings per form (ms per frame batch)
+    bool tuned = false;                       // form fixed: template changes prepare only its tables
     int group = 1;
     int stage_frames = 1;  // frames per host staging buffer
     bool f32 = false;

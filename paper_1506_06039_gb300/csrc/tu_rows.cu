@@ -13,39 +13,48 @@ template <int N, bool F32>
 static cudaError_t frame_rows_n(const void* src, int64_t src_fstride, int64_t nimg, int m, int n, int levels,
                                 int mc, int nc, const int32_t* coff_i, const float* coff_f, const float2* tw,
                                 float2* X, int64_t x_fstride, int ldx, u64* rowE, u64* colE, u64* tot,
-                                uint32_t* corners, int wm1, unsigned int* err, cudaStream_t st) {
+                                uint32_t* corners, int wm1, unsigned int* err, int64_t capacity, cudaStream_t st) {
     const size_t smem = sizeof(float2) * ((kRC / 2) * fft_ld<N>() + N) + sizeof(u64) * (kRC + nc);
     const size_t smem_staged = frame_rows_smem_base<N, F32>(nc) + frame_rows_stage_bytes(n, levels);
+    // A single image (the template, a closed-loop frame) is split over one CTA
+    // per chunk of rows when the buffers have a slot per chunk for the partial
+    // sums, which k_merge_chunks then adds up.
+    const int chunks = (mc + kRC - 1) / kRC;
+    const int split = (nimg == 1 && chunks > 1 && chunks <= capacity) ? 1 : 0;
+    const unsigned grid = split ? (unsigned)chunks : (unsigned)nimg;
+    cudaError_t e;
     if (!F32 && n % 8 == 0 && levels <= 1 && smem_staged <= kStagedSmemMax) {
         const void* fn = (const void*)k_frame_rows<N, false, false, true>;
-        cudaError_t e = ensure_smem(fn, smem_staged);
-        if (e != cudaSuccess) return e;
-        k_frame_rows<N, false, false, true><<<(unsigned)nimg, kRowsThreads, smem_staged, st>>>(
+        if ((e = ensure_smem(fn, smem_staged)) != cudaSuccess) return e;
+        k_frame_rows<N, false, false, true><<<grid, kRowsThreads, smem_staged, st>>>(
             src, src_fstride, m, n, levels, mc, nc, coff_i, coff_f, tw, X, x_fstride, ldx, rowE, colE, tot, corners,
-            wm1, nullptr, nullptr, 0, err);
-        return cudaGetLastError();
+            wm1, nullptr, nullptr, 0, err, split);
+    } else {
+        const void* fn = (const void*)k_frame_rows<N, F32>;
+        if ((e = ensure_smem(fn, smem)) != cudaSuccess) return e;
+        k_frame_rows<N, F32><<<grid, kRowsThreads, smem, st>>>(src, src_fstride, m, n, levels, mc, nc, coff_i, coff_f,
+                                                              tw, X, x_fstride, ldx, rowE, colE, tot, corners, wm1,
+                                                              nullptr, nullptr, 0, nullptr, split);
     }
-    const void* fn = (const void*)k_frame_rows<N, F32>;
-    cudaError_t e = ensure_smem(fn, smem);
-    if (e != cudaSuccess) return e;
-    k_frame_rows<N, F32><<<(unsigned)nimg, kRowsThreads, smem, st>>>(src, src_fstride, m, n, levels, mc, nc,
-                                                                      coff_i, coff_f, tw, X, x_fstride, ldx,
-                                                                      rowE, colE, tot, corners, wm1);
+    if ((e = cudaGetLastError()) != cudaSuccess || !split) return e;
+    k_merge_chunks<F32><<<1, 256, 0, st>>>(colE, tot, chunks, nc, wm1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_frame_rows(int N, bool f32, const void* src, int64_t src_fstride, int64_t nimg, int m,
                               int n, int levels, int mc, int nc, const int32_t* coff_i, const float* coff_f,
                               const float2* tw, float2* X, int64_t x_fstride, int ldx, u64* rowE, u64* colE,
-                              u64* tot, uint32_t* corners, int wm1, unsigned int* err, cudaStream_t st) {
+                              u64* tot, uint32_t* corners, int wm1, unsigned int* err, int64_t capacity,
+                              cudaStream_t st) {
     if (nimg <= 0) return cudaSuccess;
 #define MOCO_CASE(NN)                                                                                        \
     case NN:                                                                                                 \
         return f32 ? frame_rows_n<NN, true>(src, src_fstride, nimg, m, n, levels, mc, nc, coff_i, coff_f,    \
-                                            tw, X, x_fstride, ldx, rowE, colE, tot, corners, wm1, err, st)   \
+                                            tw, X, x_fstride, ldx, rowE, colE, tot, corners, wm1, err,       \
+                                            capacity, st)                                                    \
                    : frame_rows_n<NN, false>(src, src_fstride, nimg, m, n, levels, mc, nc, coff_i,           \
                                              coff_f, tw, X, x_fstride, ldx, rowE, colE, tot, corners, wm1,   \
-                                             err, st);
+                                             err, capacity, st);
     switch (N) {
         MOCO_FOR_EACH_FFT_SIZE(MOCO_CASE)
         default:
