@@ -259,3 +259,18 @@ def test_std512_clean_template_recovers_planted_shifts():
     assert (shifts == st.shifts).all(axis=1).mean() > 0.99
     sample = np.random.default_rng(1).choice(300, 8, replace=False)
     check_align(st.frames.cpu().numpy()[sample], st.template.cpu().numpy(), wl.w, -1, shifts[sample])
+
+
+def test_largest_fft_length_wide_window():
+    # 520 x 520 without a level and w = 57: searched grid + window = 576, the
+    # longest transform, and 113^2 shifts (the combine keeps 113^2 costs in
+    # shared memory beside the 576-point transform buffer).
+    m = n = 520
+    w = 57
+    st = synth.make_stack_np(m, n, 2, 300, 40, seed=5200, template="clean")
+    shifts, best, margin, info = run_align(st.frames, st.template, w, levels=0)
+    assert info["fft_rows"] == 576 and info["fft_cols"] == 576
+    check_align(st.frames, st.template, w, 0, shifts, best)
+    with Plan(dict(m=m, n=n, w=w, levels=0), dev(st.template)) as plan:
+        cost = plan.cost_surface(dev(st.frames[:1])).cpu().numpy()
+    assert cost_rel_err(cost, oracle.cost_surface(st.frames[:1], st.template, w, levels=0)) <= COST_RTOL

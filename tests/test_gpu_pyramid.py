@@ -72,3 +72,16 @@ def test_ragged_sizes_and_cost_surface():
     with Plan(dict(m=m, n=n, w=w, levels=L), dev(st.template)) as plan:
         cost = plan.cost_surface(dev(st.frames[:4])).cpu().numpy()
     assert cost_rel_err(cost, oracle.cost_surface(st.frames[:4], st.template, w, levels=L)) <= COST_RTOL
+
+
+def test_largest_frames_three_levels():
+    # 4096 x 4096 frames (the largest the plan takes) through three levels:
+    # the search on the 512 x 512 level-3 grid (576-point transforms), exact
+    # 3x3 refinements on levels 2 and 1, the jitter at full resolution.
+    m = n = 4096
+    st = synth.make_stack_np(m, n, 2, 2000, 60, seed=4096, template="clean")
+    got, best, final = run(st.frames, st.template, 12, 3)
+    ref, _ = check_align(st.frames, st.template, 12, 3, got, best)
+    same = np.all(got == ref["shifts"], axis=1)
+    assert same.all()
+    assert np.array_equal(final, ref["ffinal"])
