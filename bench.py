@@ -172,9 +172,10 @@ def kernel_work(info, wl, frames):
 # DRAM bytes (read + write) per frame of the current kernels, from one ncu
 # capture of 512 frames of the std512 workload (dram__bytes_read.sum +
 # dram__bytes_write.sum), scaled to a launch by its frame count.
-TRAFFIC_PER_FRAME = {"k_frame_rows": (269.648128e6 + 125.167104e6) / 512,
-                     "k_cols": (153.365760e6 + 20.226048e6) / 512,
-                     "k_jitter": (261.750016e6 + 4.341248e6) / 512}
+TRAFFIC_PER_FRAME = {"k_frame_rows": (269.646336e6 + 124.932352e6) / 512,
+                     "k_cols": (152.487936e6 + 19.695360e6) / 512,
+                     "k_rows_inv": (45.919744e6 + 0.0) / 512,
+                     "k_jitter": (261.832448e6 + 4.060416e6) / 512}
 
 
 def roofline(profile, info, wl, frames_per_step, steps, peaks, clocks):
