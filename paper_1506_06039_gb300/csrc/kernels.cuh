@@ -1152,14 +1152,18 @@ __device__ __forceinline__ void jit_issue(const JitBand& B, uint4* ring, int q) 
     uint4* st = ring + (q & (kJitRing - 1)) * 4 * kJitterThreads;
     if (q <= B.i_e - B.i_b + 1) {
         const int ar = B.first + q;
-        const bool rok = ar >= 0 && ar < B.m;  // the same for the whole warp
-        const uint16_t* row = B.a + (int64_t)(rok ? ar : 0) * B.n;
+        const bool rok = (unsigned)ar < (unsigned)B.m;  // the same for the whole warp
+        // 32-bit element offsets from the image bases (m n < 2^31): a chunk's
+        // offset is exact whenever the chunk is inside the frame (c0 may be
+        // negative, the sum then is not)
+        const uint32_t off = (uint32_t)(rok ? ar : 0) * (uint32_t)B.n + (uint32_t)B.c0;
 #pragma unroll
         for (int c = 0; c < (O == 3 ? 3 : 2); ++c) {
             const bool ok = rok && ((B.cvalid >> c) & 1u);
-            cp16z(st + c * kJitterThreads, ok ? row + B.c0 + 8 * c : B.a, ok ? 16u : 0u);
+            cp16z(st + c * kJitterThreads, B.a + (ok ? off + 8u * c : 0u), ok ? 16u : 0u);
         }
-        if (q >= 2) cp16z(st + 3 * kJitterThreads, B.tmpl + (int64_t)(B.i_b + q - 2) * B.n + B.j0, 16u);
+        if (q >= 2)
+            cp16z(st + 3 * kJitterThreads, B.tmpl + ((uint32_t)(B.i_b + q - 2) * (uint32_t)B.n + (uint32_t)B.j0), 16u);
     }
     cp_commit();
 }
