@@ -1147,23 +1147,32 @@ __device__ __forceinline__ uint4 jit_tmpl_row(const JitBand& B, int i) {
 constexpr int kJitRing = 4;
 constexpr size_t kJitRingBytes = (size_t)kJitRing * 4 * kJitterThreads * 16;
 
+// The next row to copy: its frame row ar, the 32-bit element offsets of its
+// first raw chunk in the frame and of its template row, rows left to issue.
+// The offsets advance by n per row (modular: exact whenever a chunk is inside
+// the frame, m n < 2^31).
+struct JitCursor {
+    uint32_t foff, toff;
+    int ar, left;
+};
+
 template <int O>
-__device__ __forceinline__ void jit_issue(const JitBand& B, uint4* ring, int q) {
+__device__ __forceinline__ void jit_issue(const JitBand& B, uint4* ring, int q, JitCursor& cur) {
     uint4* st = ring + (q & (kJitRing - 1)) * 4 * kJitterThreads;
-    if (q <= B.i_e - B.i_b + 1) {
-        const int ar = B.first + q;
-        const bool rok = (unsigned)ar < (unsigned)B.m;  // the same for the whole warp
-        // 32-bit element offsets from the image bases (m n < 2^31): a chunk's
-        // offset is exact whenever the chunk is inside the frame (c0 may be
-        // negative, the sum then is not)
-        const uint32_t off = (uint32_t)(rok ? ar : 0) * (uint32_t)B.n + (uint32_t)B.c0;
+    if (cur.left > 0) {
+        const bool rok = (unsigned)cur.ar < (unsigned)B.m;  // the same for the whole warp
 #pragma unroll
         for (int c = 0; c < (O == 3 ? 3 : 2); ++c) {
             const bool ok = rok && ((B.cvalid >> c) & 1u);
-            cp16z(st + c * kJitterThreads, B.a + (ok ? off + 8u * c : 0u), ok ? 16u : 0u);
+            cp16z(st + c * kJitterThreads, B.a + (ok ? cur.foff + 8u * c : 0u), ok ? 16u : 0u);
         }
-        if (q >= 2)
-            cp16z(st + 3 * kJitterThreads, B.tmpl + ((uint32_t)(B.i_b + q - 2) * (uint32_t)B.n + (uint32_t)B.j0), 16u);
+        if (q >= 2) {
+            cp16z(st + 3 * kJitterThreads, B.tmpl + cur.toff, 16u);
+            cur.toff += (uint32_t)B.n;
+        }
+        cur.foff += (uint32_t)B.n;
+        ++cur.ar;
+        --cur.left;
     }
     cp_commit();
 }
@@ -1191,7 +1200,8 @@ __device__ __forceinline__ void jit_take(const uint4* ring, int q, JitSlot<O>& x
 // hold frame rows i+s0-1, i+s0; slot K+2 receives row i+s0+1 (ring row j+2)
 // with template row i, and ring row j+2+kJitRing is issued into its stage.
 template <bool TABLE, int O, int K>
-__device__ __forceinline__ void jit_step(const JitBand& B, int i, uint4* ring, JitSlot<O> (&S)[3], Acc2 (&C)[9],
+__device__ __forceinline__ void jit_step(const JitBand& B, int i, uint4* ring, JitCursor& cur, JitSlot<O> (&S)[3],
+                                         Acc2 (&C)[9],
                                          Acc2 (&M)[3], Acc2 (&QB)[3], const uint32_t (&cm)[12]) {
     const int j = i - B.i_b;
     JitSlot<O>& w0 = S[K];
@@ -1219,7 +1229,7 @@ __device__ __forceinline__ void jit_step(const JitBand& B, int i, uint4* ring, J
     if (i <= B.i_e - 3) row_energy(w2, M);  // frame row shared by all three u
     if (!TABLE)
         if (i + B.s0 - 1 >= 0 && i + B.s0 + 1 <= B.m - 1) tmpl_energy(bw, bp, cm, QB);
-    jit_issue<O>(B, ring, j + 2 + kJitRing);  // the stage just read (its data is consumed)
+    jit_issue<O>(B, ring, j + 2 + kJitRing, cur);  // the stage just read (its data is consumed)
 }
 
 // X[u*3+v] += energy e of frame row r for each u whose range
@@ -1259,19 +1269,24 @@ __device__ __forceinline__ void jit_band(const JitBand& B, uint4* ring, uint32_t
     const int first = B.first, L = B.i_e - B.i_b;
     JitSlot<O> S[3];
 #pragma unroll
-    for (int q = 0; q < kJitRing; ++q) jit_issue<O>(B, ring, q);
+    JitCursor cur;
+    cur.ar = B.first;
+    cur.foff = (uint32_t)B.first * (uint32_t)B.n + (uint32_t)B.c0;
+    cur.toff = (uint32_t)B.i_b * (uint32_t)B.n + (uint32_t)B.j0;
+    cur.left = B.i_e - B.i_b + 2;  // rows first .. first + L + 1
+    for (int q = 0; q < kJitRing; ++q) jit_issue<O>(B, ring, q, cur);
     cp_wait<kJitRing - 1>();
     jit_take(ring, 0, S[0], nullptr);
-    jit_issue<O>(B, ring, kJitRing);
+    jit_issue<O>(B, ring, kJitRing, cur);
     cp_wait<kJitRing - 1>();
     jit_take(ring, 1, S[1], nullptr);
-    jit_issue<O>(B, ring, kJitRing + 1);
+    jit_issue<O>(B, ring, kJitRing + 1, cur);
     for (int i = B.i_b;;) {
-        jit_step<TABLE, O, 0>(B, i, ring, S, C, M, QB, cm);
+        jit_step<TABLE, O, 0>(B, i, ring, cur, S, C, M, QB, cm);
         if (++i >= B.i_e) break;
-        jit_step<TABLE, O, 1>(B, i, ring, S, C, M, QB, cm);
+        jit_step<TABLE, O, 1>(B, i, ring, cur, S, C, M, QB, cm);
         if (++i >= B.i_e) break;
-        jit_step<TABLE, O, 2>(B, i, ring, S, C, M, QB, cm);
+        jit_step<TABLE, O, 2>(B, i, ring, cur, S, C, M, QB, cm);
         if (++i >= B.i_e) break;
     }
     cp_wait<0>();  // the groups still open hold no copies; none stays in flight
