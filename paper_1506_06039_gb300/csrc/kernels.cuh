@@ -1007,7 +1007,7 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 // position counting only when its partner lies inside the frame.
 //
 // Grid (CTAs per frame, frames). Each thread owns the template columns
-// j0 .. j0+7 of a band of kJitRows rows and walks down it keeping the three
+// j0 .. j0+7 of a band of band_rows (<= kJitRows) rows and walks down it keeping the three
 // frame rows r = i + 2 sc - 1 + u (u = 0, 1, 2) as 16-bit pairs, columns
 // counted from lead = j0 + 2 tc - 1 (odd):
 //   pw[p] = columns (lead + 2p, lead + 2p + 1), p < 5   (v = 0: pw[0..3],
@@ -1030,7 +1030,7 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 // wrap-around: the total is exact); the last CTA of a frame (ticket counter)
 // adds sum_D b^2 (TABLE) and takes the minimum of S / Area with the
 // tie-break, compared as exact rationals. acc and ticket are zero on entry.
-constexpr int kJitRows = 32;
+constexpr int kJitRows = 32;  // band height (at most: the launcher may pick shorter bands)
 static_assert(kJitRows <= 32, "32-bit dot-product sums are exact for at most 32 rows of 8 columns");
 
 // One frame row of a thread's window. raw: the 16-byte chunks that hold
@@ -1362,7 +1362,7 @@ template <bool TABLE>
 __global__ void __launch_bounds__(kJitterThreads, TABLE ? 2 : 1)
 k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* __restrict__ tmpl, int m, int n,
          const u64* __restrict__ bsq, const int32_t* __restrict__ coarse, int32_t* __restrict__ shifts,
-         double* __restrict__ ffinal, u64* __restrict__ acc_g, unsigned int* __restrict__ ticket) {
+         double* __restrict__ ffinal, u64* __restrict__ acc_g, unsigned int* __restrict__ ticket, int band_rows) {
     __shared__ u64 red[kJitterThreads / 32][9];
     __shared__ bool last;
     extern __shared__ __align__(16) unsigned char jit_smem[];
@@ -1374,7 +1374,7 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
 #pragma unroll
     for (int k = 0; k < 9; ++k) X[k] = 0;
     const int G = n / 8;
-    const int nb = (m + kJitRows - 1) / kJitRows;
+    const int nb = (m + band_rows - 1) / band_rows;  // band_rows <= kJitRows
     const int task = blockIdx.x * kJitterThreads + tid;
     if (task < G * nb) {
         const int g = task % G, band = task / G;
@@ -1389,8 +1389,8 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
         // Word (lead - 1) / 2 of the row is word O of chunk 0.
         const int O = ((t0 >> 1) - 1) & 3;  // the same for the whole frame
         B.c0 = lead - 1 - 2 * O;
-        B.i_b = band * kJitRows;
-        B.i_e = min(m, B.i_b + kJitRows);
+        B.i_b = band * band_rows;
+        B.i_e = min(m, B.i_b + band_rows);
         B.first = B.i_b + s0 - 1;
         B.cvalid = 0;
 #pragma unroll

@@ -95,18 +95,22 @@ cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg,
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(u64) * 9 * nimg, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int) * nimg, st);
     if (e != cudaSuccess) return e;
-    const int tasks = (n / 8) * ((m + kJitRows - 1) / kJitRows);
-    const int ctas = (tasks + kJitterThreads - 1) / kJitterThreads;
+    // Bands of kJitRows rows; a small batch (fewer CTAs than two waves of
+    // 152 SMs) takes bands of 16 or 8 rows so that more CTAs share a frame.
+    int band_rows = kJitRows;
+    auto ctas_for = [&](int br) { return ((n / 8) * ((m + br - 1) / br) + kJitterThreads - 1) / kJitterThreads; };
+    while (band_rows > 8 && (int64_t)ctas_for(band_rows) * nimg < 2 * 152) band_rows /= 2;
+    const int ctas = ctas_for(band_rows);
     dim3 grid((unsigned)ctas, (unsigned)nimg);
     const void* fn = bsq ? reinterpret_cast<const void*>(k_jitter<true>) : reinterpret_cast<const void*>(k_jitter<false>);
     e = ensure_smem(fn, kJitRingBytes);
     if (e != cudaSuccess) return e;
     if (bsq)
         k_jitter<true><<<grid, kJitterThreads, kJitRingBytes, st>>>(frames, fstride, tmpl, m, n, bsq, coarse, shifts,
-                                                                    ffinal, acc, ticket);
+                                                                    ffinal, acc, ticket, band_rows);
     else
         k_jitter<false><<<grid, kJitterThreads, kJitRingBytes, st>>>(frames, fstride, tmpl, m, n, nullptr, coarse,
-                                                                     shifts, ffinal, acc, ticket);
+                                                                     shifts, ffinal, acc, ticket, band_rows);
     return cudaGetLastError();
 }
 
