@@ -517,10 +517,9 @@ def run_grad(args, world, rank, local):
     loss = torch.empty(T, dtype=torch.float64, device="cuda")
     weights = torch.empty((T, W, W), dtype=torch.float32, device="cuda")
     grad = torch.zeros((wl.m, wl.n), dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-
     def step():
         # one refinement step's device work: template in, per-frame loss and dL/db out
+        stream = torch.cuda.current_stream()
         moco_set_template(plan.handle, 0, tmpl, stream)
         moco_softmin_grad(plan.handle, 0, st.frames, 0.05, cost, loss, weights, grad, 1.0, stream)
         if pg:
@@ -530,7 +529,24 @@ def run_grad(args, world, rank, local):
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
+    # Per-kernel times from profiled eager steps (untimed) ...
     plan.profile(max_launches=args.steps * 64 + 64)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    profile = plan.profile_read(reset=True)
+    plan.profile(0)
+    # ... and the timed steps as replays of one captured step (the library's
+    # calls allocate and synchronise nothing, so the step captures as a whole;
+    # with several ranks the all-reduce stays eager).
+    graph = None
+    if not pg:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        graph.replay()
+        torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -540,13 +556,14 @@ def run_grad(args, world, rank, local):
     torch.cuda.synchronize()
     ev0.record(stream)
     for _ in range(args.steps):
-        step()
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
     ev1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = max_over_ranks(ev0.elapsed_time(ev1), pg, "cuda")
-    profile = plan.profile_read(reset=True)
-    plan.profile(0)
     if rank == 0:
         tot = sum(t for _, t in profile.values()) or 1.0
         out = {"metric": "frames/s, soft-min loss and template gradient (differentiable form)",
@@ -555,7 +572,10 @@ def run_grad(args, world, rank, local):
                "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
                "config": {"workload": "refine256: %d frames of 256x256, w=16 (31^2 shifts), float template "
-                                      "(mean frame + N(0, 50^2)), tau = 0.05 x median" % T, "frames": T},
+                                      "(mean frame + N(0, 50^2)), tau = 0.05 x median" % T, "frames": T,
+                          "timed": ("replays of one captured step (moco_set_template + moco_softmin_grad); "
+                                    "kernel times from as many profiled eager steps") if graph is not None
+                          else "eager steps"},
                "gpu_launches": sum(l for l, _ in profile.values()), "clocks": clocks,
                "kernels": {k: {"launches": l, "ms": t, "share": t / tot} for k, (l, t) in profile.items()}}
         if world > 1:
