@@ -68,8 +68,10 @@ cudaError_t launch_sq_prefix(const uint16_t* tmpl, int m, int n, u64* P, cudaStr
 cudaError_t launch_copy_shifts(const int32_t* coarse, int32_t* shifts, const double* fbest, double* ffinal,
                                int64_t T, cudaStream_t st);
 
+// The template offset c (two kernels: per-slice sums into part[0 .. nparts),
+// then their sum in order; part is scratch of at least one u64).
 cudaError_t launch_template_offset(bool f32, const void* tmpl, int m, int n, int levels, int32_t* coff_i,
-                                   float* coff_f, cudaStream_t st);
+                                   float* coff_f, u64* part, int64_t nparts, cudaStream_t st);
 
 cudaError_t launch_softmin(const double* cost, int64_t T, int K, double tau_scale, double* loss, float* weights,
                            cudaStream_t st);

@@ -1459,33 +1459,59 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
 }
 
 // Prefix table of b^2 for k_jitter, P[(m+1) x (n+1)] (exact u64), in two
-// passes: k_sq_prefix_rows (one thread per row, row 0 all zero), then
-// k_sq_prefix_cols (one thread per column).
-static __global__ void k_sq_prefix_rows(const uint16_t* __restrict__ tmpl, int m, int n, u64* __restrict__ P) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// passes. k_sq_prefix_rows: one warp per row, 32-wide warp scans with a
+// carry (row 0 and column 0 zero). k_sq_prefix_cols: one CTA of 32 warps per
+// 32 columns; warp w owns a slice of rows: the slice's column sums, an
+// exclusive sum over the earlier slices, then the slice rewritten as running
+// sums (two passes over P, each coalesced along the columns).
+static __global__ void __launch_bounds__(256) k_sq_prefix_rows(const uint16_t* __restrict__ tmpl, int m, int n,
+                                                               u64* __restrict__ P) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t ld = n + 1;
-    if (i == 0)
-        for (int j = 0; j <= n; ++j) P[j] = 0;
+    if (blockIdx.x == 0)
+        for (int j = threadIdx.x; j <= n; j += blockDim.x) P[j] = 0;
     if (i >= m) return;
-    u64 run = 0;
     u64* row = P + (int64_t)(i + 1) * ld;
-    row[0] = 0;
-    for (int j = 0; j < n; ++j) {
-        const u64 v = tmpl[(int64_t)i * n + j];
-        run += v * v;
-        row[j + 1] = run;
+    if (lane == 0) row[0] = 0;
+    u64 carry = 0;
+    for (int j0 = 0; j0 < n; j0 += 32) {
+        const int j = j0 + lane;
+        u64 v = 0;
+        if (j < n) {
+            const u64 b = tmpl[(int64_t)i * n + j];
+            v = b * b;
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u64 u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        v += carry;
+        if (j < n) row[j + 1] = v;
+        carry = __shfl_sync(0xffffffffu, v, 31);
     }
 }
 
-static __global__ void k_sq_prefix_cols(int m, int n, u64* __restrict__ P) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j > n) return;
+static __global__ void __launch_bounds__(1024) k_sq_prefix_cols(int m, int n, u64* __restrict__ P) {
+    __shared__ u64 part[32][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + lane;  // column of P
     const int64_t ld = n + 1;
-    u64 run = 0;  // in a register: the loads down the column do not wait on the stores
-    for (int i = 1; i <= m; ++i) {
-        run += P[i * ld + j];
-        P[i * ld + j] = run;
-    }
+    const int slice = (m + 31) / 32;
+    const int r0 = 1 + w * slice, r1 = min(m + 1, r0 + slice);  // rows [r0, r1) of P
+    u64 s = 0;
+    if (j <= n)
+        for (int r = r0; r < r1; ++r) s += P[(int64_t)r * ld + j];
+    part[w][lane] = s;
+    __syncthreads();
+    u64 run = 0;
+    for (int k = 0; k < w; ++k) run += part[k][lane];
+    if (j <= n)
+        for (int r = r0; r < r1; ++r) {
+            run += P[(int64_t)r * ld + j];
+            P[(int64_t)r * ld + j] = run;
+        }
 }
 
 // For searches without a level: the searched optimum is the answer.
@@ -1498,42 +1524,59 @@ static __global__ void k_copy_shifts(const int32_t* __restrict__ coarse, int32_t
 
 // ---------------------------------------------------------------------------
 // Template offset c = round(mean of the searched-grid template), integer.
-// One CTA. U16: exact integer sum of the (box-summed) template; F32: FP64.
+// U16: exact integer sum of the (box-summed) template; F32: FP64 sum of FP32
+// partial sums (the rounding of the mean only needs it near). Two kernels:
+// k_offset_partial, CTA b summing a slice of rows into part[b] (bits of a u64
+// or a double), then k_offset_final adding the parts in order.
 template <bool F32>
-__global__ void __launch_bounds__(1024)
-k_template_offset(const void* __restrict__ tmpl, int m, int n, int levels, int32_t* __restrict__ coff_i,
-                  float* __restrict__ coff_f) {
-    __shared__ double redd[32];
-    __shared__ u64 redu[32];
-    const int tid = threadIdx.x, nthr = blockDim.x;
+__global__ void __launch_bounds__(256)
+k_offset_partial(const void* __restrict__ tmpl, int m, int n, int levels, u64* __restrict__ part) {
+    __shared__ u64 redu[8];
+    __shared__ double redd[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int mc = m >> levels, nc = n >> levels;
     const int rows = mc << levels, cols = nc << levels;  // the pixels the searched grid covers
+    const int i0 = (int)((int64_t)blockIdx.x * rows / gridDim.x), i1 = (int)((int64_t)(blockIdx.x + 1) * rows / gridDim.x);
     u64 su = 0;
     double sd = 0.0;
-    // one warp per row at a time (coalesced; no per-element division)
-    for (int i = tid >> 5; i < rows; i += nthr >> 5)
-        for (int j = tid & 31; j < cols; j += 32) {
-            if (F32) sd += (double)static_cast<const float*>(tmpl)[(int64_t)i * n + j];
+    for (int i = i0 + warp; i < i1; i += 8) {
+        float rf = 0.f;
+        for (int j = lane; j < cols; j += 32) {
+            if (F32) rf += static_cast<const float*>(tmpl)[(int64_t)i * n + j];
             else su += static_cast<const uint16_t*>(tmpl)[(int64_t)i * n + j];
         }
+        sd += (double)rf;
+    }
     su = warp_sum(su);
     sd = warp_sum(sd);
-    if ((tid & 31) == 0) { redu[tid >> 5] = su; redd[tid >> 5] = sd; }
+    if (lane == 0) { redu[warp] = su; redd[warp] = sd; }
     __syncthreads();
     if (tid == 0) {
         u64 tu = 0;
         double td = 0.0;
-        for (int i = 0; i < (nthr + 31) / 32; ++i) { tu += redu[i]; td += redd[i]; }
-        const u64 cnt = (u64)mc * (u64)nc;
-        if (F32) {
-            const double c = rint(td / (double)cnt);
-            *coff_i = (int32_t)c;
-            *coff_f = (float)c;
-        } else {
-            const u64 c = (2 * tu + cnt) / (2 * cnt);  // round half up of the mean
-            *coff_i = (int32_t)c;
-            *coff_f = (float)c;
-        }
+        for (int k = 0; k < 8; ++k) { tu += redu[k]; td += redd[k]; }
+        part[blockIdx.x] = F32 ? (u64)__double_as_longlong(td) : tu;
+    }
+}
+
+template <bool F32>
+__global__ void k_offset_final(const u64* __restrict__ part, int nparts, int m, int n, int levels,
+                               int32_t* __restrict__ coff_i, float* __restrict__ coff_f) {
+    const u64 cnt = (u64)(m >> levels) * (u64)(n >> levels);
+    u64 tu = 0;
+    double td = 0.0;
+    for (int k = 0; k < nparts; ++k) {
+        if (F32) td += __longlong_as_double((long long)part[k]);
+        else tu += part[k];
+    }
+    if (F32) {
+        const double c = rint(td / (double)cnt);
+        *coff_i = (int32_t)c;
+        *coff_f = (float)c;
+    } else {
+        const u64 c = (2 * tu + cnt) / (2 * cnt);  // round half up of the mean
+        *coff_i = (int32_t)c;
+        *coff_f = (float)c;
     }
 }
 

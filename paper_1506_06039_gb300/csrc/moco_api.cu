@@ -266,7 +266,9 @@ moco_status prepare_template(ShapePlan& sp, const void* tmpl_dev, cudaStream_t s
     const size_t bytes = (size_t)sp.desc.m * sp.desc.n * (sp.f32 ? 4 : 2);
     cudaError_t e = cudaMemcpyAsync(sp.tmpl, tmpl_dev, bytes, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "template copy");
-    e = launch_template_offset(sp.f32, sp.tmpl, sp.desc.m, sp.desc.n, sp.levels, sp.coff_i, sp.coff_f, st);
+    // (the per-frame totals' scratch, free here, holds the slice sums)
+    e = launch_template_offset(sp.f32, sp.tmpl, sp.desc.m, sp.desc.n, sp.levels, sp.coff_i, sp.coff_f, sp.tot,
+                               sp.group, st);
     if (e != cudaSuccess) return cuda_fail(e, "template offset");
     if (sp.has_fft)
         e = launch_frame_rows(sp.Nc, sp.f32, sp.tmpl, 0, 1, sp.desc.m, sp.desc.n, sp.levels, sp.mc, sp.nc,

@@ -1,4 +1,5 @@
 // Energies, jitter, template offset, and small host helpers.
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -115,9 +116,8 @@ cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg,
 }
 
 cudaError_t launch_sq_prefix(const uint16_t* tmpl, int m, int n, u64* P, cudaStream_t st) {
-    const int threads = 128;
-    k_sq_prefix_rows<<<(m + threads - 1) / threads, threads, 0, st>>>(tmpl, m, n, P);
-    k_sq_prefix_cols<<<(n + 1 + threads - 1) / threads, threads, 0, st>>>(m, n, P);
+    k_sq_prefix_rows<<<(m + 7) / 8, 256, 0, st>>>(tmpl, m, n, P);
+    k_sq_prefix_cols<<<(n + 1 + 31) / 32, 1024, 0, st>>>(m, n, P);
     return cudaGetLastError();
 }
 
@@ -131,9 +131,15 @@ cudaError_t launch_copy_shifts(const int32_t* coarse, int32_t* shifts, const dou
 }
 
 cudaError_t launch_template_offset(bool f32, const void* tmpl, int m, int n, int levels, int32_t* coff_i,
-                                   float* coff_f, cudaStream_t st) {
-    if (f32) k_template_offset<true><<<1, 1024, 0, st>>>(tmpl, m, n, levels, coff_i, coff_f);
-    else k_template_offset<false><<<1, 1024, 0, st>>>(tmpl, m, n, levels, coff_i, coff_f);
+                                   float* coff_f, u64* part, int64_t nparts, cudaStream_t st) {
+    const int rows = (m >> levels) << levels;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>({nparts, 64, (int64_t)std::max(1, rows)}));
+    if (f32) k_offset_partial<true><<<blocks, 256, 0, st>>>(tmpl, m, n, levels, part);
+    else k_offset_partial<false><<<blocks, 256, 0, st>>>(tmpl, m, n, levels, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (f32) k_offset_final<true><<<1, 1, 0, st>>>(part, blocks, m, n, levels, coff_i, coff_f);
+    else k_offset_final<false><<<1, 1, 0, st>>>(part, blocks, m, n, levels, coff_i, coff_f);
     return cudaGetLastError();
 }
 
