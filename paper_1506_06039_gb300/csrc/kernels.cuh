@@ -1359,7 +1359,7 @@ __device__ __forceinline__ int ratio_lt(u64 S1, u64 A1, u64 S2, u64 A2, int* eq)
 
 // bsq: the prefix table of b^2 (TABLE) or nullptr (sum b^2 in the loop).
 template <bool TABLE>
-__global__ void __launch_bounds__(kJitterThreads, TABLE ? 2 : 1)
+__global__ void __launch_bounds__(kJitterThreads, TABLE ? 3 : 1)
 k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* __restrict__ tmpl, int m, int n,
          const u64* __restrict__ bsq, const int32_t* __restrict__ coarse, int32_t* __restrict__ shifts,
          double* __restrict__ ffinal, u64* __restrict__ acc_g, unsigned int* __restrict__ ticket, int band_rows) {
