@@ -50,7 +50,9 @@ cudaError_t ensure_smem(const void* func, size_t bytes) {
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(mu);
     size_t& cur = limit[std::make_pair(func, dev)];
-    if (bytes <= cur || bytes <= 48 * 1024) return cudaSuccess;
+    // (also below 48 KiB: the default limit counts the kernel's static shared
+    // memory too, so dynamic + static may exceed it)
+    if (bytes == 0 || bytes <= cur) return cudaSuccess;
     e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     cur = bytes;
