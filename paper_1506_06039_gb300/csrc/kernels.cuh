@@ -839,7 +839,9 @@ __device__ __forceinline__ float combine_f32(float2 sa, float2 sb, float h, floa
 
 // k_rows_inv: one CTA per frame. Inverse real DFTs along the image columns
 // (length Nc) of Y's 2w-1 rows, two rows per complex transform, keeping the
-// 2w-1 columns t in [-(w-1), w-1] -> h[s][t]. Then
+// 2w-1 columns t in [-(w-1), w-1] -> h[s][t]. Then the frame's exact
+// energies Sa_st (energy_frame, from the frame pass's edge sums and corner
+// blocks, in the shared memory the transforms no longer need) and
 //     f_st = (Sa_st + Sb_st - 2 h_st) / Area_st * unit   (combine_f32)
 // and the argmin over the window with the tie-break: smallest f, then
 // smallest |s|+|t|, then smallest s, then smallest t. Also the second-best
@@ -1018,8 +1020,9 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 // wholly outside the frame, so every thread runs the same code: a word
 // outside is a predicated-off load that leaves zero. A row outside the frame
 // is the same for the whole warp (one band, one frame).
-// The next frame and template rows are prefetched one row ahead, and the
-// loop is unrolled three times so that the window rotates without copies.
+// Frame and template rows arrive through a ring of asynchronous copies
+// kJitRing rows ahead (below), and the loop is unrolled three times so that
+// the window rotates without copies.
 //
 // sum a^2: the frame rows that all three u share accumulate once per row;
 // the two rows at each end of the band's frame range are added at the end.
