@@ -16,8 +16,10 @@
 // bytes, core matrices 128 bytes apart along K and 1024 bytes apart along
 // M/N), so a K step copies them with one bulk copy each. A tiles (128
 // frames x 64 pixels, BF16 hi and lo planes written by the frame pass) come
-// in with 16-byte asynchronous copies. Three stages: the copies for steps
-// k+1 and k+2 run while the MMAs of step k do. One thread issues the MMAs; every
+// in as one TMA tensor load per plane (box 64 pixels x 1 row x 128 frames,
+// 128-byte swizzle: the MMA's swizzled K-major layout; frames past the batch
+// read as zeros). One thread issues all copies of a K step. Three stages:
+// the copies for steps k+1 and k+2 run while the MMAs of step k do. One thread issues the MMAs; every
 // mbarrier wait is bounded (about a second) and sets an error flag instead
 // of hanging.
 //
@@ -28,6 +30,7 @@
 // before the hi*hi ones, and every thread adds the finished accumulator of
 // its frame into round-to-nearest FP32 registers.
 #pragma once
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -97,6 +100,22 @@ __device__ __forceinline__ uint64_t smem_desc(const void* p) {
     const uint64_t a = smem_u32(p);
     return ((a >> 4) & 0x3FFFull) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46);
 }
+// K-major with 128-byte swizzle (as a TMA load with that swizzle writes a
+// box whose rows are 128 bytes): 8-row groups 1024 bytes apart; the start
+// address advances by 32 bytes per 16-element K slice within the row.
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
+    const uint64_t a = smem_u32(p);
+    return ((a >> 4) & 0x3FFFull) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+// 3-D tiled TMA load of the box at (x, y, z) into shared memory, completing
+// on the mbarrier's transaction count.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
 // kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major.
 __host__ __device__ constexpr uint32_t direct_idesc(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -144,8 +163,10 @@ __device__ __forceinline__ void drain_acc(uint32_t addr, int N, float (&hsum)[kD
 // Grid (N tiles, M tiles). N tile j covers shift rows s = -(w-1) + j*NS ..
 // (NS = 256 / Wp of them, Wp = W rounded up to 16); M tile covers frames
 // f0 .. f0 + 127. Output h[f][(s+w-1)*W + (t+w-1)] (FP32).
+// tmap_hi / tmap_lo: the frame planes [T][mc][ncp] BF16 as 3-D tensors
+// (x = column, y = row, z = frame), box 64 x 1 x 128, 128-byte swizzle.
 static __global__ void __launch_bounds__(kDirThreads, 1)
-k_direct(const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict__ a_lo, int64_t T, int mc,
+k_direct(const __grid_constant__ CUtensorMap tmap_hi, const __grid_constant__ CUtensorMap tmap_lo, int64_t T, int mc,
          int ncp, int nqc, int wm1, const uint8_t* __restrict__ tiles, float* __restrict__ h,
          unsigned int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char dsm_raw[];
@@ -186,25 +207,10 @@ k_direct(const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict
         return dsm + st * stage + 2 * (size_t)kDirM * kDirK * 2 + (size_t)plane * NS * tb;
     };
 
-    // Copies of K step k into stage st: A rows by cp.async, B tiles by bulk copies.
+    // Copies of K step k into stage st: A tiles by TMA, B tiles by bulk copies
+    // (one thread), out-of-window B tiles zeroed by all threads.
     auto issue = [&](int k, int st) {
         const int p = k / nqc, qc = k - p * nqc;
-        {
-            const int m = tid;  // one frame row per thread
-            const int64_t f = f0 + m;
-            for (int plane = 0; plane < 2; ++plane) {
-                unsigned char* dst = sA(st, plane);
-                if (f < T) {
-                    const __nv_bfloat16* src = (plane ? a_lo : a_hi) + ((f * mc + p) * (int64_t)ncp + (int64_t)qc * kDirQ);
-#pragma unroll
-                    for (int kg = 0; kg < 8; ++kg) cp16(dst + core_off(m, kg * 8), src + kg * 8);
-                } else {
-#pragma unroll
-                    for (int kg = 0; kg < 8; ++kg) *reinterpret_cast<uint4*>(dst + core_off(m, kg * 8)) = make_uint4(0, 0, 0, 0);
-                }
-            }
-        }
-        cp_commit();
         // Tiles of shift rows that fall outside the window or the template: zeros.
         for (int sl = 0; sl < NS; ++sl) {
             const int s = s_first + sl, r = p - s;
@@ -215,12 +221,14 @@ k_direct(const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict
             }
         }
         if (tid == 0) {
-            uint32_t bytes = 0;
+            uint32_t bytes = 2u * kDirM * kDirK * 2u;  // both A planes: the whole box, zeros past the batch included
             for (int sl = 0; sl < NS; ++sl) {
                 const int s = s_first + sl, r = p - s;
                 if (s <= wm1 && r >= 0 && r < mc) bytes += 2 * (uint32_t)tb;
             }
             mbar_expect_tx(&load_bar[st], bytes);
+            tma_load_3d(sA(st, 0), &tmap_hi, qc * kDirQ, p, (int)f0, &load_bar[st]);
+            tma_load_3d(sA(st, 1), &tmap_lo, qc * kDirQ, p, (int)f0, &load_bar[st]);
             for (int sl = 0; sl < NS; ++sl) {
                 const int s = s_first + sl, r = p - s;
                 if (!(s <= wm1 && r >= 0 && r < mc)) continue;
@@ -255,11 +263,6 @@ k_direct(const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict
         if (k + 2 < ksteps) {
             issue(k + 2, (k + 2) % kDirStages);
             issued = k + 3;
-            cp_wait<2>();
-        } else if (k + 1 < ksteps) {
-            cp_wait<1>();
-        } else {
-            cp_wait<0>();
         }
         if (!mbar_wait(&load_bar[st], (k / kDirStages) & 1, err)) s_abort = 1;
         fence_async_smem();
@@ -274,17 +277,15 @@ k_direct(const __nv_bfloat16* __restrict__ a_hi, const __nv_bfloat16* __restrict
             const unsigned char* B1 = sB(st, 1);
             const uint32_t d = tmem + (uint32_t)(ab * kDirNmax);
             // small terms first, then hi*hi: a fresh accumulator every K step
+            // per K16 slice: A 32 bytes along its swizzled row, B two core matrices (256 bytes)
 #pragma unroll
             for (int kk = 0; kk < kDirK / 16; ++kk) {
-                const uint32_t off = kk * 256;  // two core matrices along K per K16
-                mma_bf16(d, smem_desc(A0 + off), smem_desc(B1 + off), idesc, kk > 0 ? 1u : 0u);
-                mma_bf16(d, smem_desc(A1 + off), smem_desc(B0 + off), idesc, 1u);
+                mma_bf16(d, smem_desc_sw128(A0 + kk * 32), smem_desc(B1 + kk * 256), idesc, kk > 0 ? 1u : 0u);
+                mma_bf16(d, smem_desc_sw128(A1 + kk * 32), smem_desc(B0 + kk * 256), idesc, 1u);
             }
 #pragma unroll
-            for (int kk = 0; kk < kDirK / 16; ++kk) {
-                const uint32_t off = kk * 256;
-                mma_bf16(d, smem_desc(A0 + off), smem_desc(B0 + off), idesc, 1u);
-            }
+            for (int kk = 0; kk < kDirK / 16; ++kk)
+                mma_bf16(d, smem_desc_sw128(A0 + kk * 32), smem_desc(B0 + kk * 256), idesc, 1u);
             mma_commit(&mma_bar[ab]);
         }
     }

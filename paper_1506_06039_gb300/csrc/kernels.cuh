@@ -1271,12 +1271,12 @@ __device__ __forceinline__ void jit_band(const JitBand& B, uint4* ring, uint32_t
     for (int k = 0; k < 12; ++k) cm[k] = TABLE ? 0u : col_mask(mask, k / 4, k % 4);
     const int first = B.first, L = B.i_e - B.i_b;
     JitSlot<O> S[3];
-#pragma unroll
     JitCursor cur;
     cur.ar = B.first;
     cur.foff = (uint32_t)B.first * (uint32_t)B.n + (uint32_t)B.c0;
     cur.toff = (uint32_t)B.i_b * (uint32_t)B.n + (uint32_t)B.j0;
     cur.left = B.i_e - B.i_b + 2;  // rows first .. first + L + 1
+#pragma unroll
     for (int q = 0; q < kJitRing; ++q) jit_issue<O>(B, ring, q, cur);
     cp_wait<kJitRing - 1>();
     jit_take(ring, 0, S[0], nullptr);

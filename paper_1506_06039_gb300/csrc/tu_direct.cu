@@ -1,9 +1,44 @@
 // Launchers of the direct (tensor-core) form of the cross term.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "internal.h"
 #include "kernels.cuh"
 #include "direct.cuh"
 
 namespace moco {
+
+// The driver's tensor-map encoder, looked up once through the runtime.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// Frame planes [T][mc][ncp] BF16 as a 3-D tensor (column, row, frame) with
+// boxes of 64 columns x 1 row x kDirM frames and 128-byte swizzle.
+static cudaError_t plane_map(CUtensorMap* map, const void* planes, int64_t T, int mc, int ncp) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return cudaErrorNotSupported;
+    const cuuint64_t dims[3] = {(cuuint64_t)ncp, (cuuint64_t)mc, (cuuint64_t)T};
+    const cuuint64_t strides[2] = {(cuuint64_t)ncp * 2, (cuuint64_t)mc * ncp * 2};  // bytes, dims 1 and 2
+    const cuuint32_t box[3] = {(cuuint32_t)kDirK, 1, (cuuint32_t)kDirM};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(planes), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 
 size_t direct_tiles_bytes(int mc, int nqc, int W) { return 2 * (size_t)mc * nqc * direct_tile_bytes(W); }
 size_t direct_smem(int W) { return direct_smem_bytes(W); }
@@ -53,10 +88,12 @@ cudaError_t launch_direct(const void* a_hi, const void* a_lo, int64_t T, int mc,
     if (e != cudaSuccess) return e;
     const int ntiles = (W + direct_ns(W) - 1) / direct_ns(W);
     const int64_t mtiles = (T + kDirM - 1) / kDirM;
+    CUtensorMap map_hi, map_lo;
+    if ((e = plane_map(&map_hi, a_hi, T, mc, ncp)) != cudaSuccess) return e;
+    if ((e = plane_map(&map_lo, a_lo, T, mc, ncp)) != cudaSuccess) return e;
     dim3 grid((unsigned)ntiles, (unsigned)mtiles);
-    k_direct<<<grid, kDirThreads, smem, st>>>(static_cast<const __nv_bfloat16*>(a_hi),
-                                              static_cast<const __nv_bfloat16*>(a_lo), T, mc, ncp, nqc, wm1,
-                                              static_cast<const uint8_t*>(tiles), h, err);
+    k_direct<<<grid, kDirThreads, smem, st>>>(map_hi, map_lo, T, mc, ncp, nqc, wm1, static_cast<const uint8_t*>(tiles),
+                                              h, err);
     return cudaGetLastError();
 }
 
