@@ -25,10 +25,10 @@
 //
 // Accumulation: the tensor core's FP32 accumulator loses low bits on each
 // accumulation, which over the 12 MMAs x (mc * nc / 64) K steps of a frame
-// would bias h. So each K step accumulates into a fresh TMEM accumulator
-// (two of them, alternating), issuing the small hi*lo and lo*hi products
-// before the hi*hi ones, and every thread adds the finished accumulator of
-// its frame into round-to-nearest FP32 registers.
+// would bias h. So each group of kDirGroup K steps accumulates into a fresh
+// TMEM accumulator (two of them, alternating), issuing the small hi*lo and
+// lo*hi products before the hi*hi ones, and every thread adds the finished
+// accumulator of its frame into round-to-nearest FP32 registers.
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -50,6 +50,7 @@ __host__ __device__ inline size_t direct_stage_bytes(int W) {
     return 2 * (size_t)kDirM * kDirK * 2 + 2 * (size_t)direct_ns(W) * direct_tile_bytes(W);
 }
 constexpr int kDirStages = 3;  // copies run two K steps ahead of the MMAs
+constexpr int kDirGroup = 2;   // K steps summed in one TMEM accumulator before it is drained
 __host__ __device__ inline size_t direct_smem_bytes(int W) { return 1024 + kDirStages * direct_stage_bytes(W) + 64; }
 
 // Byte offset of element (row, k) in a K-major core-matrix tile with 64 K.
@@ -250,15 +251,17 @@ k_direct(const __grid_constant__ CUtensorMap tmap_hi, const __grid_constant__ CU
     if (ksteps > 1) issue(1, 1);
     issued = ksteps > 1 ? 2 : 1;
     for (int k = 0; k < ksteps; ++k) {
-        const int st = k % kDirStages;  // copy stage of step k
-        const int ab = k & 1;           // accumulator of step k
+        const int st = k % kDirStages;       // copy stage of step k
+        const int ab = k & 1;                // commit barrier of step k
+        const int acc = (k / kDirGroup) & 1;  // accumulator of step k's group
         if (k >= 1) {
-            // Step k-1's MMAs (its stage and accumulator ab^1) are done: drain
-            // them, then reuse that stage for step k+2.
+            // Step k-1's MMAs are done: its stage is free for step k+2, and
+            // when k-1 closed a group its accumulator is drained.
             if (!mbar_wait(&mma_bar[ab ^ 1], ((k - 1) >> 1) & 1, err)) s_abort = 1;
             __syncthreads();
             if (s_abort) break;
-            drain_acc(lane_addr + (uint32_t)((ab ^ 1) * kDirNmax), N, hsum);
+            if ((k - 1) % kDirGroup == kDirGroup - 1)
+                drain_acc(lane_addr + (uint32_t)((((k - 1) / kDirGroup) & 1) * kDirNmax), N, hsum);
         }
         if (k + 2 < ksteps) {
             issue(k + 2, (k + 2) % kDirStages);
@@ -275,12 +278,14 @@ k_direct(const __grid_constant__ CUtensorMap tmap_hi, const __grid_constant__ CU
             const unsigned char* A1 = sA(st, 1);
             const unsigned char* B0 = sB(st, 0);
             const unsigned char* B1 = sB(st, 1);
-            const uint32_t d = tmem + (uint32_t)(ab * kDirNmax);
-            // small terms first, then hi*hi: a fresh accumulator every K step
+            const uint32_t d = tmem + (uint32_t)(acc * kDirNmax);
+            // small terms first, then hi*hi; a fresh accumulator at each group's first step
             // per K16 slice: A 32 bytes along its swizzled row, B two core matrices (256 bytes)
+            const uint32_t first = (k % kDirGroup == 0) ? 1u : 0u;
 #pragma unroll
             for (int kk = 0; kk < kDirK / 16; ++kk) {
-                mma_bf16(d, smem_desc_sw128(A0 + kk * 32), smem_desc(B1 + kk * 256), idesc, kk > 0 ? 1u : 0u);
+                mma_bf16(d, smem_desc_sw128(A0 + kk * 32), smem_desc(B1 + kk * 256), idesc,
+                         (kk > 0 || !first) ? 1u : 0u);
                 mma_bf16(d, smem_desc_sw128(A1 + kk * 32), smem_desc(B0 + kk * 256), idesc, 1u);
             }
 #pragma unroll
@@ -294,7 +299,8 @@ k_direct(const __grid_constant__ CUtensorMap tmap_hi, const __grid_constant__ CU
         if (!mbar_wait(&mma_bar[(ksteps - 1) & 1], ((ksteps - 1) >> 1) & 1, err)) s_abort = 1;
     }
     __syncthreads();
-    if (!s_abort && ksteps > 0) drain_acc(lane_addr + (uint32_t)(((ksteps - 1) & 1) * kDirNmax), N, hsum);
+    if (!s_abort && ksteps > 0)
+        drain_acc(lane_addr + (uint32_t)((((ksteps - 1) / kDirGroup) & 1) * kDirNmax), N, hsum);
     if (s_abort) {
         // Leave no copy in flight into this CTA's shared memory.
         cp_wait<0>();
