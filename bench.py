@@ -364,9 +364,25 @@ def main():
         for _ in range(args.e2e_steps):
             plan.align_host(host, shifts_host=out_h)
         el = max_over_ranks(time.perf_counter() - t0, pg, "cuda")
+        h2d = int(wl.T * wl.m * wl.n * 2)
+        # The host link's own rate: one plain pinned copy of the same bytes,
+        # timed with CUDA events (the e2e ceiling when compute is hidden).
+        dev = torch.empty_like(host, device="cuda")
+        link_ms = []
+        for _ in range(3):
+            l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0.record()
+            dev.copy_(host, non_blocking=True)
+            l1.record()
+            torch.cuda.synchronize()
+            link_ms.append(l0.elapsed_time(l1))
+        del dev
+        link_gbs = h2d / (min(link_ms) / 1e3) / 1e9
+        e2e_gbs = h2d * args.e2e_steps / el / 1e9
         e2e = {"value": job_value(world, wl.T, args.e2e_steps, el), "unit": UNIT,
-               "h2d_bytes_per_step": int(wl.T * wl.m * wl.n * 2), "d2h_bytes_per_step": int(wl.T * 8),
-               "steps": args.e2e_steps, "api": "moco_align_host (pinned host buffers)"}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(wl.T * 8),
+               "steps": args.e2e_steps, "api": "moco_align_host (pinned host buffers)",
+               "h2d_link_gbs": link_gbs, "link_frac": e2e_gbs / link_gbs}
 
     correction = None
     if not args.no_correction:
