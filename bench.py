@@ -170,12 +170,14 @@ def kernel_work(info, wl, frames):
 
 
 # DRAM bytes (read + write) per frame of the current kernels, from one ncu
-# capture of 512 frames of the std512 workload (dram__bytes_read.sum +
-# dram__bytes_write.sum), scaled to a launch by its frame count.
-TRAFFIC_PER_FRAME = {"k_frame_rows": (269.646336e6 + 124.932352e6) / 512,
-                     "k_cols": (152.487936e6 + 19.695360e6) / 512,
-                     "k_rows_inv": (45.919744e6 + 0.0) / 512,
-                     "k_jitter": (261.832448e6 + 4.060416e6) / 512}
+# capture of 512 frames of the std512 workload in the FFT form
+# (dram__bytes_read.sum + dram__bytes_write.sum), scaled to a launch by its
+# frame count; other workloads and forms report no traffic.
+TRAFFIC_WORKLOAD = ("std512", "fft_fp32")
+TRAFFIC_PER_FRAME = {"k_frame_rows": (269.635840e6 + 124.160768e6) / 512,
+                     "k_cols": (152.450560e6 + 19.388416e6) / 512,
+                     "k_rows_inv": (45.925632e6 + 0.00128e6) / 512,
+                     "k_jitter": (262.634496e6 + 4.665344e6) / 512}
 
 
 def roofline(profile, info, wl, frames_per_step, steps, peaks, clocks):
@@ -211,7 +213,9 @@ def roofline(profile, info, wl, frames_per_step, steps, peaks, clocks):
         rf = {"bound": "hbm", "achieved": byts / dur_s / 1e9, "peak": hbm, "unit": "GB/s", "frac": fracs["hbm"],
               "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
     per_launch_frames = frames_per_step * steps / launches
-    traffic = TRAFFIC_PER_FRAME.get(name)
+    from paper_1506_06039_gb300 import XCORR_DIRECT_BF16X3, XCORR_FFT_FP32
+    form = {XCORR_FFT_FP32: "fft_fp32", XCORR_DIRECT_BF16X3: "direct_bf16x3"}.get(info.get("xcorr"))
+    traffic = TRAFFIC_PER_FRAME.get(name) if (wl.name, form) == TRAFFIC_WORKLOAD else None
     rf.update({"kernel": name, "launches": launches, "avg_launch_ms": ms / launches,
                "share": ms / total,
                "traffic": traffic * per_launch_frames if traffic else None,
