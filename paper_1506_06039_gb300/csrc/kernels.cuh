@@ -882,17 +882,6 @@ template <int N>
 __host__ __device__ constexpr size_t rows_inv_smem(int wm1) {
     return rows_inv_region<N>(wm1) + sizeof(float2) * N + sizeof(float) * (2 * wm1 + 1) * (2 * wm1 + 1);
 }
-// Its block size (kInvPC rows of the wider four-step stage, whole warps)
-// and the half-spectrum values each thread loads per round: enough that one
-// round of loads, all in flight together, fills a chunk's kInvPC row pairs.
-template <int N>
-__host__ __device__ constexpr int rows_inv_threads() {
-    return (kInvPC * (Four<N>::N1 > Four<N>::N2 ? Four<N>::N1 : Four<N>::N2) + 31) / 32 * 32;
-}
-template <int N>
-__host__ __device__ constexpr int rows_inv_loads() {
-    return (kInvPC * (N / 2 + 1) + rows_inv_threads<N>() - 1) / rows_inv_threads<N>();
-}
 
 template <int N>
 __global__ void __launch_bounds__(576)
@@ -919,14 +908,13 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
         __syncthreads();
         // Two real rows ra, rb = ra + 1 as one complex row: Z[k] = A[k] + i B[k]
         // from the half spectra (k <= N/2; A[N-k] = conj A[k]). Each stored
-        // value is read once; all QL of a thread's tasks' loads are issued
-        // before any store (one round covers the chunk).
-        constexpr int NK = NH + 1, QL = rows_inv_loads<N>();
+        // value is read once; four tasks' loads are issued before any store.
+        constexpr int NK = NH + 1;
         const int ntask = np * NK;
-        for (int t0 = tid; t0 < ntask; t0 += QL * nthr) {
-            float2 A[QL], B[QL];
+        for (int t0 = tid; t0 < ntask; t0 += 4 * nthr) {
+            float2 A[4], B[4];
 #pragma unroll
-            for (int q = 0; q < QL; ++q) {
+            for (int q = 0; q < 4; ++q) {
                 const int task = t0 + q * nthr;
                 A[q] = make_float2(0.f, 0.f);
                 B[q] = make_float2(0.f, 0.f);
@@ -938,7 +926,7 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
                 }
             }
 #pragma unroll
-            for (int q = 0; q < QL; ++q) {
+            for (int q = 0; q < 4; ++q) {
                 const int task = t0 + q * nthr;
                 if (task < ntask) {
                     const int pi = task / NK, kk = task - pi * NK;
