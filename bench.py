@@ -174,10 +174,10 @@ def kernel_work(info, wl, frames):
 # (dram__bytes_read.sum + dram__bytes_write.sum), scaled to a launch by its
 # frame count; other workloads and forms report no traffic.
 TRAFFIC_WORKLOAD = ("std512", "fft_fp32")
-TRAFFIC_PER_FRAME = {"k_frame_rows": (269.635840e6 + 124.160768e6) / 512,
-                     "k_cols": (152.450560e6 + 19.388416e6) / 512,
-                     "k_rows_inv": (45.925632e6 + 0.00128e6) / 512,
-                     "k_jitter": (262.634496e6 + 4.665344e6) / 512}
+TRAFFIC_PER_FRAME = {"k_frame_rows": (269.635584e6 + 124.114432e6) / 512,
+                     "k_cols": (152.445696e6 + 19.473920e6) / 512,
+                     "k_rows_inv": (45.919744e6 + 0.0) / 512,
+                     "k_jitter": (262.623744e6 + 4.628480e6) / 512}
 
 
 def roofline(profile, info, wl, frames_per_step, steps, peaks, clocks):
