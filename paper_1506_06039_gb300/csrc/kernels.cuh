@@ -647,11 +647,11 @@ k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* 
          const uint32_t* __restrict__ corners, int mc, int nc, int wm1, void* __restrict__ out,
          int flip) {
     typedef typename AccT<F32>::type Acc;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char esm_raw[];
     const int W = 2 * wm1 + 1;
     const int64_t f = blockIdx.x;
     energy_frame<F32>(rowE + f * mc, colE + f * nc, tot[f], corners + f * 4 * (size_t)wm1 * wm1, mc, nc, wm1,
-                      smem_raw, [&](int s, int t, Acc val) {
+                      esm_raw, [&](int s, int t, Acc val) {
                           const int so = flip ? -s : s, to = flip ? -t : t;
                           const int64_t k = f * (int64_t)W * W + (int64_t)(so + wm1) * W + (to + wm1);
                           if (OUT_DOUBLE) {
@@ -685,9 +685,9 @@ __global__ void __launch_bounds__(cols_threads<N>(), cols_min_blocks<N>())
 k_cols(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv,
        const float2* __restrict__ tw_g, const float2* __restrict__ bspec, float2* __restrict__ Y,
        int64_t y_fstride, int wm1, float scale) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char csm_raw[];
     constexpr int LD = fft_ld<N>();                      // skewed, padded row
-    float2* buf = reinterpret_cast<float2*>(smem_raw);  // kColsVC x LD
+    float2* buf = reinterpret_cast<float2*>(csm_raw);  // kColsVC x LD
     float2* tw = buf + kColsVC * LD;                     // 2N: forward, then inverse table
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int v0 = blockIdx.y * kColsVC, nv = min(kColsVC, ncv - v0);
@@ -890,10 +890,10 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
            const u64* __restrict__ tot, const uint32_t* __restrict__ corners, int mc, int nc,
            const float2* __restrict__ Sb2, const float* __restrict__ ia32, double* __restrict__ cost,
            int32_t* __restrict__ coarse, double* __restrict__ fbest, float* __restrict__ margin) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char ism_raw[];
     constexpr int LD = fft_ld<N>();                      // skewed, padded row
-    float2* buf = reinterpret_cast<float2*>(smem_raw);  // kInvPC x LD
-    float2* tw = reinterpret_cast<float2*>(smem_raw + rows_inv_region<N>(wm1));  // N: inverse table
+    float2* buf = reinterpret_cast<float2*>(ism_raw);  // kInvPC x LD
+    float2* tw = reinterpret_cast<float2*>(ism_raw + rows_inv_region<N>(wm1));  // N: inverse table
     const int W = 2 * wm1 + 1, WW = W * W;
     float* hbuf = reinterpret_cast<float*>(tw + N);     // W x W
     __shared__ Best red[32];
@@ -957,7 +957,7 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
     // The frame's energies Sa (exact) straight into the combine; their tables
     // take the transform buffer's place.
     energy_frame<false>(rowE + f * mc, colE + f * nc, tot[f], corners + f * 4 * (size_t)wm1 * wm1, mc, nc, wm1,
-                        smem_raw, [&](int s, int t, u64 sa) {
+                        ism_raw, [&](int s, int t, u64 sa) {
                             const int k = (s + wm1) * W + (t + wm1);
                             const float fv = combine_f32(energy_pair(sa), Sb2[k], hbuf[k], ia32[k]);
                             if (cost) cost[f * WW + k] = (double)fv;

@@ -23,7 +23,8 @@ static cudaError_t frame_rows_n(const void* src, int64_t src_fstride, int64_t ni
     const int split = (nimg == 1 && chunks > 1 && chunks <= capacity) ? 1 : 0;
     const unsigned grid = split ? (unsigned)chunks : (unsigned)nimg;
     cudaError_t e;
-    if (!F32 && n % 8 == 0 && levels <= 1 && smem_staged <= kStagedSmemMax) {
+    // (the staged loader gives each searched column its own thread)
+    if (!F32 && n % 8 == 0 && levels <= 1 && nc <= kRowsThreads && smem_staged <= kStagedSmemMax) {
         const void* fn = (const void*)k_frame_rows<N, false, false, true>;
         if ((e = ensure_smem(fn, smem_staged)) != cudaSuccess) return e;
         k_frame_rows<N, false, false, true><<<grid, kRowsThreads, smem_staged, st>>>(
