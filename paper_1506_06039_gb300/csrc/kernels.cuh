@@ -1024,8 +1024,13 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 // kJitRing rows ahead (below), and the loop is unrolled three times so that
 // the window rotates without copies.
 //
-// sum a^2: the frame rows that all three u share accumulate once per row;
-// the two rows at each end of the band's frame range are added at the end.
+// sum a^2: each window row is summed over its v = 0 columns only; the
+// frame rows that all three u share accumulate once per row, the two rows at
+// each end of the band's frame range are added at the end. The groups tile
+// the template row, so across a row the v = 1 and v = 2 windows differ from
+// v = 0 by one or two frame columns at the two ends of the row only: the
+// threads of the first and last groups subtract and add those columns'
+// squares (jit_edge_columns, a warp at a time).
 // In-loop sum b^2: template rows whose partner rows are valid for all three
 // u accumulate once; the at most four rows valid for only some u are added
 // at the end.
@@ -1101,25 +1106,11 @@ __device__ __forceinline__ void dot_acc(uint32_t x, uint32_t yp, Acc2& acc) {
 
 __device__ __forceinline__ u64 acc_value(const Acc2& a) { return (u64)a.lo + ((u64)a.hi << 8); }
 
-// Sum of squares of one window row over the columns of each v:
-// v = 0: columns 0..7, v = 1: 1..8, v = 2: 2..9 (of lead ..).
+// Sum of squares of one window row over its v = 0 columns 0..7 (of lead ..).
 template <int O>
-__device__ __forceinline__ void row_energy(const JitSlot<O>& x, Acc2 (&e)[3]) {
-    uint32_t pl[5];
+__device__ __forceinline__ void row_energy(const JitSlot<O>& x, Acc2& e) {
 #pragma unroll
-    for (int p = 0; p < 5; ++p) pl[p] = byte_planes(x.pw[p]);
-    Acc2 core = {0u, 0u};  // columns 2..7
-#pragma unroll
-    for (int p = 1; p < 4; ++p) dot_acc(x.pw[p], pl[p], core);
-#pragma unroll
-    for (int v = 0; v < 3; ++v) {
-        e[v].lo += core.lo;
-        e[v].hi += core.hi;
-    }
-    dot_acc(x.pw[0], pl[0], e[0]);                // columns 0, 1
-    dot_acc(x.pw[4], pl[4], e[2]);                // columns 8, 9
-    dot_acc(x.pw[0], pl[0] & 0xff00ff00u, e[1]);  // column 1
-    dot_acc(x.pw[4], pl[4] & 0x00ff00ffu, e[1]);  // column 8
+    for (int p = 0; p < 4; ++p) dot_acc(x.pw[p], byte_planes(x.pw[p]), e);
 }
 
 // Byte masks of template pair p for shift v: the template columns whose
@@ -1205,7 +1196,7 @@ __device__ __forceinline__ void jit_take(const uint4* ring, int q, JitSlot<O>& x
 template <bool TABLE, int O, int K>
 __device__ __forceinline__ void jit_step(const JitBand& B, int i, uint4* ring, JitCursor& cur, JitSlot<O> (&S)[3],
                                          Acc2 (&C)[9],
-                                         Acc2 (&M)[3], Acc2 (&QB)[3], const uint32_t (&cm)[12]) {
+                                         Acc2& M, Acc2 (&QB)[3], const uint32_t (&cm)[12]) {
     const int j = i - B.i_b;
     JitSlot<O>& w0 = S[K];
     JitSlot<O>& w1 = S[(K + 1) % 3];
@@ -1235,22 +1226,63 @@ __device__ __forceinline__ void jit_step(const JitBand& B, int i, uint4* ring, J
     jit_issue<O>(B, ring, j + 2 + kJitRing, cur);  // the stage just read (its data is consumed)
 }
 
-// X[u*3+v] += energy e of frame row r for each u whose range
-// first + u .. first + u + L - 1 holds r.
-__device__ __forceinline__ void jit_add_row(int r, int first, int L, const Acc2 (&e)[3], u64 (&X)[9]) {
+// X[u*3+v] += energy e of frame row r (its v = 0 window, every v) for each
+// u whose range first + u .. first + u + L - 1 holds r.
+__device__ __forceinline__ void jit_add_row(int r, int first, int L, const Acc2& e, u64 (&X)[9]) {
+    const u64 ev = acc_value(e);
 #pragma unroll
     for (int u = 0; u < 3; ++u)
         if (r >= first + u && r <= first + u + L - 1)
 #pragma unroll
-            for (int v = 0; v < 3; ++v) X[u * 3 + v] += acc_value(e[v]);
+            for (int v = 0; v < 3; ++v) X[u * 3 + v] += ev;
+}
+
+// The v = 1, 2 windows of a band's frame rows against v = 0: at the left end
+// of the template row (group 0, bit 0 of need) they lack frame columns
+// c = t0 - 1 (v = 1, 2) and c + 1 (v = 2), at the right end (group G - 1,
+// bit 1) they add columns c + n and c + n + 1; each row counts for every u
+// whose range first + u .. first + u + L - 1 holds it. The whole warp takes
+// the bands of its lanes that hold an end group one at a time, a frame row
+// per lane, so the loads of a band are in flight together. Sums mod 2^64
+// (the totals are exact); values outside the frame are zero.
+__device__ __forceinline__ void jit_edge_columns(const uint16_t* __restrict__ a, int m, int n, int t0, int first,
+                                                 int L, uint32_t need, u64 (&X)[9]) {
+    const int lane = threadIdx.x & 31;
+    uint32_t todo = __ballot_sync(0xffffffffu, need != 0u);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int bf = __shfl_sync(0xffffffffu, first, src);
+        const int bL = __shfl_sync(0xffffffffu, L, src);
+        const uint32_t bn = __shfl_sync(0xffffffffu, need, src);
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            if (!((bn >> side) & 1u)) continue;
+            const int c = t0 - 1 + (side ? n : 0);
+            for (int r = bf + lane; r <= bf + bL + 1; r += 32) {
+                if (r < 0 || r >= m) continue;
+                const uint16_t* row = a + (int64_t)r * n;
+                const u64 a0 = (c >= 0 && c < n) ? (u64)__ldg(row + c) : 0ull;
+                const u64 a1 = (c + 1 >= 0 && c + 1 < n) ? (u64)__ldg(row + c + 1) : 0ull;
+                const u64 q1 = a0 * a0, q2 = q1 + a1 * a1;
+                const u64 d1 = side ? q1 : 0ull - q1, d2 = side ? q2 : 0ull - q2;
+#pragma unroll
+                for (int u = 0; u < 3; ++u)
+                    if (r >= bf + u && r <= bf + u + bL - 1) {
+                        X[u * 3 + 1] += d1;
+                        X[u * 3 + 2] += d2;
+                    }
+            }
+        }
+    }
 }
 
 template <int O, int A, int B2>
 __device__ __forceinline__ void jit_last_rows(const JitSlot<O> (&S)[3], int first, int L, u64 (&X)[9]) {
-    Acc2 e[3] = {{0u, 0u}, {0u, 0u}, {0u, 0u}};
+    Acc2 e = {0u, 0u};
     row_energy(S[A], e);
     jit_add_row(first + L, first, L, e, X);
-    Acc2 f[3] = {{0u, 0u}, {0u, 0u}, {0u, 0u}};
+    Acc2 f = {0u, 0u};
     row_energy(S[B2], f);
     jit_add_row(first + L + 1, first, L, f, X);
 }
@@ -1258,14 +1290,11 @@ __device__ __forceinline__ void jit_last_rows(const JitSlot<O> (&S)[3], int firs
 // The nine partial sums of one thread's band, X[u*3+v] (mod 2^64).
 template <bool TABLE, int O>
 __device__ __forceinline__ void jit_band(const JitBand& B, uint4* ring, uint32_t mask, u64 (&X)[9]) {
-    Acc2 C[9], M[3], QB[3];
+    Acc2 C[9], M = {0u, 0u}, QB[3];
 #pragma unroll
     for (int k = 0; k < 9; ++k) C[k] = Acc2{0u, 0u};
 #pragma unroll
-    for (int v = 0; v < 3; ++v) {
-        M[v] = Acc2{0u, 0u};
-        QB[v] = Acc2{0u, 0u};
-    }
+    for (int v = 0; v < 3; ++v) QB[v] = Acc2{0u, 0u};
     uint32_t cm[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) cm[k] = TABLE ? 0u : col_mask(mask, k / 4, k % 4);
@@ -1297,7 +1326,7 @@ __device__ __forceinline__ void jit_band(const JitBand& B, uint4* ring, uint32_t
     for (int u = 0; u < 3; ++u)
 #pragma unroll
         for (int v = 0; v < 3; ++v)
-            X[u * 3 + v] = acc_value(M[v]) + acc_value(QB[v]) - 2ull * acc_value(C[u * 3 + v]);
+            X[u * 3 + v] = acc_value(M) + acc_value(QB[v]) - 2ull * acc_value(C[u * 3 + v]);
 
     // Frame rows at the ends of the band's range first .. first + L + 1.
     // The last two are still in slots L and L + 1 (mod 3).
@@ -1311,13 +1340,13 @@ __device__ __forceinline__ void jit_band(const JitBand& B, uint4* ring, uint32_t
     if (L >= 2) jit_fetch(B, first + 1, S[1]);
     jit_unpack(S[0]);
     {
-        Acc2 e[3] = {{0u, 0u}, {0u, 0u}, {0u, 0u}};
+        Acc2 e = {0u, 0u};
         row_energy(S[0], e);
         jit_add_row(first, first, L, e, X);
     }
     if (L >= 2) {
         jit_unpack(S[1]);
-        Acc2 e[3] = {{0u, 0u}, {0u, 0u}, {0u, 0u}};
+        Acc2 e = {0u, 0u};
         row_energy(S[1], e);
         jit_add_row(first + 1, first, L, e, X);
     }
@@ -1379,6 +1408,8 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     const int G = n / 8;
     const int nb = (m + band_rows - 1) / band_rows;  // band_rows <= kJitRows
     const int task = blockIdx.x * kJitterThreads + tid;
+    int e_first = 0, e_L = 0;  // this thread's band, for the end-column terms
+    uint32_t e_need = 0;
     if (task < G * nb) {
         const int g = task % G, band = task / G;
         JitBand B;
@@ -1415,7 +1446,11 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
             case 2: jit_band<TABLE, 2>(B, ring, mask, X); break;
             default: jit_band<TABLE, 3>(B, ring, mask, X); break;
         }
+        e_need = (g == 0 ? 1u : 0u) | (g == G - 1 ? 2u : 0u);
+        e_first = B.first;
+        e_L = B.i_e - B.i_b;
     }
+    jit_edge_columns(frames + f * fstride, m, n, t0, e_first, e_L, e_need, X);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         u64 v = X[k];
