@@ -175,10 +175,10 @@ def kernel_work(info, wl, frames):
 # (dram__bytes_read.sum + dram__bytes_write.sum), scaled to a launch by its
 # frame count; other workloads and forms report no traffic.
 TRAFFIC_WORKLOAD = ("std512", "fft_fp32")
-TRAFFIC_PER_FRAME = {"k_frame_rows": (269.635584e6 + 124.114432e6) / 512,
-                     "k_cols": (152.445696e6 + 19.473920e6) / 512,
-                     "k_rows_inv": (45.919744e6 + 0.0) / 512,
-                     "k_jitter": (262.623744e6 + 4.628480e6) / 512}
+TRAFFIC_PER_FRAME = {"k_frame_rows": (269.635584e6 + 123.821312e6) / 512,
+                     "k_cols": (152.448256e6 + 19.347200e6) / 512,
+                     "k_rows_inv": (45.920000e6 + 0.0) / 512,
+                     "k_jitter": (261.724160e6 + 3.844608e6) / 512}
 
 
 def roofline(profile, info, wl, frames_per_step, steps, peaks, clocks):
