@@ -179,6 +179,14 @@ moco_status moco_align_host(moco_plan_t plan, int32_t shape_idx, const uint16_t*
  * flag then cleared); MOCO_OK otherwise. */
 moco_status moco_plan_status(moco_plan_t plan);
 
+/* Check of the timeout path: launches on `stream` one CTA whose bounded
+ * mbarrier wait (the same wait the staged kernels use) is never satisfied; it
+ * gives up after about a second, records the timeout in shape shape_idx's
+ * device status word and returns, with no copy in flight. The next
+ * moco_plan_status then reports MOCO_ERR_TIMEOUT and clears the word; the
+ * plan and the CUDA context stay usable. Asynchronous; no allocation. */
+moco_status moco_selftest_wait(moco_plan_t plan, int32_t shape_idx, void* stream);
+
 /* The correction step: applies each frame's shift (Section 2: the found
  * shifts "motion correct" the video; the paper gives no formula, this is the
  * library's definition). For frames_dev [T][m][n] uint16 (shape shape_idx,

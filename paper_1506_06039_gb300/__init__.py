@@ -10,5 +10,5 @@ from .binding import (  # noqa: F401
     EXPORTS, FrameStream, MocoError, Plan, TEMPLATE_F32, TEMPLATE_U16, XCORR_AUTO, XCORR_DIRECT_BF16X3,
     XCORR_FFT_FP32, moco_align_host, moco_align_stack, moco_apply_shifts, moco_cost_backward, moco_cost_surface,
     moco_plan, moco_plan_destroy, moco_plan_query, moco_plan_status, moco_profile_enable, moco_profile_read,
-    moco_set_template, moco_softmin, moco_softmin_grad, moco_status_string,
+    moco_selftest_wait, moco_set_template, moco_softmin, moco_softmin_grad, moco_status_string,
 )

@@ -33,7 +33,7 @@ EXPORTS = (
     "moco_cost_backward", "moco_align_host", "moco_plan_query", "moco_plan_destroy",
     "moco_status_string", "moco_last_error", "moco_profile_enable", "moco_profile_read", "moco_plan_status",
     "moco_jitter_noalloc", "moco_apply_shifts", "moco_stream_create", "moco_stream_align", "moco_stream_destroy",
-    "moco_softmin_grad",
+    "moco_softmin_grad", "moco_selftest_wait",
 )
 
 
@@ -99,6 +99,7 @@ def lib():
             L.moco_last_error.restype = ctypes.c_char_p
             L.moco_profile_enable.argtypes = [P, i32]
             L.moco_plan_status.argtypes = [P]
+            L.moco_selftest_wait.argtypes = [P, i32, P]
             L.moco_jitter_noalloc.argtypes = [P, i64, i32, i32, P, P, P, P]
             L.moco_apply_shifts.argtypes = [P, i32, P, i64, P, ctypes.c_uint16, P, P, P]
             L.moco_stream_create.argtypes = [P, i32, P, P, ctypes.POINTER(P)]
@@ -322,6 +323,10 @@ def moco_plan_status(plan):
     _check(lib().moco_plan_status(plan))
 
 
+def moco_selftest_wait(plan, shape_idx: int = 0, stream=None):
+    _check(lib().moco_selftest_wait(plan, shape_idx, _stream(stream)))
+
+
 def moco_profile_enable(plan, max_launches: int):
     _check(lib().moco_profile_enable(plan, int(max_launches)))
 
@@ -445,6 +450,11 @@ class Plan:
     def status(self):
         """Raises MocoError (MOCO_ERR_TIMEOUT) if a device-side wait gave up."""
         moco_plan_status(self.handle)
+
+    def selftest_wait(self, shape_idx: int = 0, stream=None):
+        """Launches the timeout path's check (a bounded wait that gives up
+        after about a second); the next status() raises MOCO_ERR_TIMEOUT."""
+        moco_selftest_wait(self.handle, shape_idx, stream)
 
     def profile(self, max_launches: int):
         moco_profile_enable(self.handle, max_launches)

@@ -120,4 +120,8 @@ cudaError_t launch_pair_from_double(const double* x, float2* out, int64_t count,
 // Sets the dynamic shared-memory limit of `func` on the current device once.
 cudaError_t ensure_smem(const void* func, size_t bytes);
 
+// One CTA whose bounded mbarrier wait is never satisfied: sets *err after
+// about a second and returns (the timeout path's check).
+cudaError_t launch_wait_selftest(unsigned int* err, cudaStream_t st);
+
 }  // namespace moco

@@ -741,6 +741,15 @@ moco_status moco_softmin_grad(moco_plan_t plan, int32_t shape_idx, const uint16_
     return MOCO_OK;
 }
 
+moco_status moco_selftest_wait(moco_plan_t plan, int32_t shape_idx, void* stream) {
+    if (!plan) return fail(MOCO_ERR_INVALID_ARG, "null plan");
+    if (shape_idx < 0 || shape_idx >= (int)plan->shapes.size()) return fail(MOCO_ERR_INVALID_ARG, "bad shape_idx");
+    DeviceGuard guard(plan->device);
+    cudaError_t e = launch_wait_selftest(plan->shapes[shape_idx].dev_err, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "moco_selftest_wait");
+    return MOCO_OK;
+}
+
 moco_status moco_plan_status(moco_plan_t plan) {
     if (!plan) return fail(MOCO_ERR_INVALID_ARG, "null plan");
     DeviceGuard guard(plan->device);
@@ -753,7 +762,7 @@ moco_status moco_plan_status(moco_plan_t plan) {
         if (e != cudaSuccess) return cuda_fail(e, "status read-back");
         if (flag) {
             cudaMemset(sp.dev_err, 0, 4);
-            r = fail(MOCO_ERR_TIMEOUT, "a device-side wait gave up (tensor-core pipeline)");
+            r = fail(MOCO_ERR_TIMEOUT, "a bounded device-side wait gave up");
         }
     }
     return r;

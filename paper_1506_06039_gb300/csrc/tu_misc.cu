@@ -145,4 +145,21 @@ cudaError_t launch_template_offset(bool f32, const void* tmpl, int m, int n, int
     return cudaGetLastError();
 }
 
+// The timeout path's check: an mbarrier that expects one arrival nobody
+// makes, waited on by the staged kernels' bounded wait (about a second by
+// clock64), which then sets *err and returns. No asynchronous copy is issued,
+// so nothing is in flight when the CTA exits.
+__global__ void k_wait_selftest(unsigned int* __restrict__ err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_wait(&bar, 0u, err);
+    }
+}
+
+cudaError_t launch_wait_selftest(unsigned int* err, cudaStream_t st) {
+    k_wait_selftest<<<1, 32, 0, st>>>(err);
+    return cudaGetLastError();
+}
+
 }  // namespace moco
