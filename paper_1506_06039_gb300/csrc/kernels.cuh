@@ -212,6 +212,9 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
                     const int hw = n >> 1;
                     const uint32_t* s32 = reinterpret_cast<const uint32_t*>(stage);
                     const int bias = 0x4B400000 - ci_off;  // float bits of 2^23 + 2^22 + d
+                    // Only chunks that hold an edge row (r < w-1 or r >= mc-(w-1))
+                    // have per-row energies or corner values to record.
+                    const bool edge_chunk = r0 < wm1 || r0 + rows > mc - wm1;
                     for (int pr = p0; pr < nfft; pr += PPI) {
                         const int rl = 2 * pr;
                         const bool has1 = rl + 1 < rows;  // the same for the whole warp
@@ -233,6 +236,7 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
                             add_sq(colreg[0], d0);
                             add_sq(colreg[0], d1);
                         }
+                        if (edge_chunk)
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             if (h == 1 && !has1) break;
