@@ -187,6 +187,23 @@ moco_status moco_plan_status(moco_plan_t plan);
  * plan and the CUDA context stay usable. Asynchronous; no allocation. */
 moco_status moco_selftest_wait(moco_plan_t plan, int32_t shape_idx, void* stream);
 
+/* Measured arithmetic peaks (instrumentation; the paper has no counterpart):
+ * the rate at which this device issues the operation the search's
+ * compute-bound kernels are limited by, for roofline fractions against a
+ * measured rather than a nominal number.
+ *   MOCO_PEAK_FP32_FMA: FP32 fused multiply-adds; *ops_per_s in flop/s
+ *     (2 per instruction). Bounds the FFT form's transforms.
+ *   MOCO_PEAK_DP2A: 32-bit integer dot products (dp2a: two 16-bit values
+ *     times two bytes plus an accumulator); *ops_per_s in instructions/s.
+ *     Bounds the exact full-resolution sums of the upsampling step.
+ * One resident wave of CTAs on every SM runs 16 independent chains per
+ * thread for about 20 ms (best of three launches, CUDA events on `stream`,
+ * after one warm-up launch). sink_dev: 4 bytes of caller-owned device
+ * memory the kernels may write (the results never reach it in practice).
+ * Synchronises `stream`; allocates nothing on the device. */
+typedef enum { MOCO_PEAK_FP32_FMA = 0, MOCO_PEAK_DP2A = 1 } moco_peak_kind;
+moco_status moco_alu_peak(int32_t kind, uint32_t* sink_dev, double* ops_per_s, void* stream);
+
 /* The correction step: applies each frame's shift (Section 2: the found
  * shifts "motion correct" the video; the paper gives no formula, this is the
  * library's definition). For frames_dev [T][m][n] uint16 (shape shape_idx,
@@ -233,13 +250,17 @@ moco_status moco_stream_destroy(moco_stream_t handle);
  * memory, or a real-time loop that must never block in the allocator).
  * frames_dev [T][m][n] and template_dev [m][n] are uint16, 16-byte aligned,
  * n % 8 == 0; coarse_dev [T][2] holds each frame's optimum (s_c, t_c) on the
- * 2x2-box grid (|2 s_c| + 1 < m, |2 t_c| + 1 < n); shifts_dev [T][2]
- * receives the best of (2 s_c + u, 2 t_c + v), u, v in {-1, 0, 1}, by exact
- * integer sums and the same tie-break as moco_align_stack.
+ * 2x2-box grid; shifts_dev [T][2] receives the best of (2 s_c + u, 2 t_c + v),
+ * u, v in {-1, 0, 1}, by exact integer sums and the same tie-break as
+ * moco_align_stack. Every candidate needs a non-empty overlap with the
+ * frame, |2 s_c| + 1 < m and |2 t_c| + 1 < n (a searched-grid optimum always
+ * has it); a frame whose coarse shift breaks that gets (INT32_MIN, INT32_MIN)
+ * in shifts_dev (checked on the device: the call itself still returns MOCO_OK).
  * Its scratch is one static device array sized for at most 8192 frames per
- * call (640 KiB, held by every GPU that loads this library until the process
- * exits); larger T returns MOCO_ERR_INVALID_ARG. The first call on a device
- * looks the array's address up (cudaGetSymbolAddress) and should come before
+ * call (608 KiB, held by every GPU that loads this library until the process
+ * exits); larger T returns MOCO_ERR_INVALID_ARG. Every call looks the array's
+ * address up in the current context (cudaGetSymbolAddress); the first call on
+ * a device also loads the library's device code there and should come before
  * any stream capture. Every call shares the array and clears the part it
  * uses first, on `stream`; calls that overlap on the GPU (different streams,
  * or different host threads on one device) race on it. */

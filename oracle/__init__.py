@@ -69,6 +69,8 @@ def lib():
             L.oracle_median.argtypes = [P, i32]
             L.oracle_softmin_loss.restype = dbl
             L.oracle_softmin_loss.argtypes = [P, i64, P, i32, i32, i32, P, P, P, P, i32]
+            L.oracle_refine.restype = i32
+            L.oracle_refine.argtypes = [P, i64, P, i32, i32, P, P, P, i32]
             L.oracle_apply_shifts.restype = None
             L.oracle_apply_shifts.argtypes = [P, i64, i32, i32, P, ctypes.c_uint16, P, P]
             _lib = L
@@ -128,6 +130,24 @@ def align(frames, template, w, levels=-1, nthreads=0):
     if rc != 0:
         raise ValueError("oracle_align rejected the arguments (rc=%d)" % rc)
     return out
+
+
+def refine(frames, template, coarse, nthreads=0):
+    """The upsampling step alone: the best of the nine full-resolution shifts
+    around 2 * coarse per frame. Returns (shifts (T,2), ffinal (T,)); a frame
+    whose coarse shift leaves a candidate without overlap gets INT32_MIN."""
+    frames = _c(frames, np.uint16)
+    template = _c(template, np.uint16)
+    if frames.ndim == 2:
+        frames = frames[None]
+    T, m, n = frames.shape
+    coarse = _c(coarse, np.int32).reshape(T, 2)
+    shifts = np.empty((T, 2), np.int32)
+    ffinal = np.empty(T)
+    rc = lib().oracle_refine(_p(frames), T, _p(template), m, n, _p(coarse), _p(shifts), _p(ffinal), nthreads)
+    if rc != 0:
+        raise MemoryError("oracle_refine failed (rc=%d)" % rc)
+    return shifts, ffinal
 
 
 def cost_surface(frames, template, w, levels=-1, with_sums=False, nthreads=0):

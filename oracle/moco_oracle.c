@@ -258,6 +258,60 @@ int oracle_align(const uint16_t *frames, int64_t T, const uint16_t *tmpl, int m,
     return failed ? -2 : 0;
 }
 
+/* The upsampling step of Section 2 on its own, at full resolution: for each
+ * frame and its given optimum (sc, tc) on the 2x2-box grid, the best of the
+ * nine shifts (2 sc + u, 2 tc + v), u, v in {-1, 0, 1}, by exact sums over D
+ * and the same tie-break as the search. Every candidate needs a non-empty D
+ * (|2 sc| + 1 < m and |2 tc| + 1 < n); a frame whose coarse shift breaks that
+ * gets (INT32_MIN, INT32_MIN) and ffinal NaN (the library's contract for
+ * caller-given coarse shifts). Returns 0, or -2 when out of memory. */
+int oracle_refine(const uint16_t *frames, int64_t T, const uint16_t *tmpl, int m, int n, const int32_t *coarse,
+                  int32_t *shifts, double *ffinal, int nthreads) {
+    int32_t *b = (int32_t *)malloc(sizeof(int32_t) * (size_t)m * n);
+    if (!b) return -2;
+    widen(tmpl, (int64_t)m * n, b);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    int failed = 0;
+#pragma omp parallel
+    {
+        int32_t *a = (int32_t *)malloc(sizeof(int32_t) * (size_t)m * n);
+        if (!a) {
+#pragma omp atomic write
+            failed = 1;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t f = 0; f < T; ++f) {
+                const int64_t sc = coarse[2 * f], tc = coarse[2 * f + 1];
+                const int64_t as = sc < 0 ? -sc : sc, at = tc < 0 ? -tc : tc;
+                if (2 * as + 1 >= m || 2 * at + 1 >= n) {
+                    shifts[2 * f] = INT32_MIN; shifts[2 * f + 1] = INT32_MIN;
+                    if (ffinal) ffinal[f] = NAN;
+                    continue;
+                }
+                widen(frames + f * (int64_t)m * n, (int64_t)m * n, a);
+                int bs = 0, bt = 0, first = 1;
+                int64_t bS = 0, bA = 1;
+                for (int u = -1; u <= 1; ++u)
+                    for (int v = -1; v <= 1; ++v) {
+                        const int s = (int)(2 * sc + u), t = (int)(2 * tc + v);
+                        const int64_t S = oracle_ssd_one(a, b, m, n, s, t);
+                        const int64_t Ar = oracle_area(m, n, s, t);
+                        if (first || better(S, Ar, s, t, bS, bA, bs, bt)) {
+                            bS = S; bA = Ar; bs = s; bt = t; first = 0;
+                        }
+                    }
+                shifts[2 * f] = bs; shifts[2 * f + 1] = bt;
+                if (ffinal) ffinal[f] = (double)bS / (double)bA;
+            }
+        }
+        free(a);
+    }
+    free(b);
+    return failed ? -2 : 0;
+}
+
 /* The searched-grid cost surface of T frames in FP64, box-mean units:
  * cost[f][(s+w-1)*(2w-1) + (t+w-1)] = f_{s,t}. Optional exact sums S (int64). */
 int oracle_cost_surface(const uint16_t *frames, int64_t T, const uint16_t *tmpl, int m, int n,

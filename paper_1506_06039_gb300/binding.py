@@ -33,8 +33,11 @@ EXPORTS = (
     "moco_cost_backward", "moco_align_host", "moco_plan_query", "moco_plan_destroy",
     "moco_status_string", "moco_last_error", "moco_profile_enable", "moco_profile_read", "moco_plan_status",
     "moco_jitter_noalloc", "moco_apply_shifts", "moco_stream_create", "moco_stream_align", "moco_stream_destroy",
-    "moco_softmin_grad", "moco_selftest_wait",
+    "moco_softmin_grad", "moco_selftest_wait", "moco_alu_peak",
 )
+
+PEAK_FP32_FMA = 0
+PEAK_DP2A = 1
 
 
 class MocoShape(ctypes.Structure):
@@ -101,6 +104,7 @@ def lib():
             L.moco_plan_status.argtypes = [P]
             L.moco_selftest_wait.argtypes = [P, i32, P]
             L.moco_jitter_noalloc.argtypes = [P, i64, i32, i32, P, P, P, P]
+            L.moco_alu_peak.argtypes = [i32, P, ctypes.POINTER(dbl), P]
             L.moco_apply_shifts.argtypes = [P, i32, P, i64, P, ctypes.c_uint16, P, P, P]
             L.moco_stream_create.argtypes = [P, i32, P, P, ctypes.POINTER(P)]
             L.moco_stream_align.argtypes = [P, P]
@@ -308,15 +312,38 @@ def moco_plan_destroy(plan):
 
 
 def moco_jitter_noalloc(frames, template, coarse, shifts, stream=None):
-    """3x3 full-resolution refinement of given 2x2-grid optima; allocates nothing."""
+    """3x3 full-resolution refinement of given 2x2-grid optima; allocates nothing.
+    frames (T, m, n) uint16, template (m, n) uint16, coarse and shifts (T, 2)
+    int32, all on one CUDA device; runs on that device."""
     import torch
     _need(frames, torch.uint16, "frames")
     _need(template, torch.uint16, "template")
     _need(coarse, torch.int32, "coarse")
     _need(shifts, torch.int32, "shifts")
+    if frames.dim() != 3:
+        raise ValueError("frames must be (T, m, n)")
     T, m, n = frames.shape
-    _check(lib().moco_jitter_noalloc(_ptr(frames), T, m, n, _ptr(template), _ptr(coarse), _ptr(shifts),
-                                     _stream(stream)))
+    if tuple(template.shape) != (m, n):
+        raise ValueError("template must be (%d, %d), got %s" % (m, n, tuple(template.shape)))
+    if tuple(coarse.shape) != (T, 2) or tuple(shifts.shape) != (T, 2):
+        raise ValueError("coarse and shifts must be (%d, 2)" % T)
+    if len({t.device for t in (frames, template, coarse, shifts)}) != 1:
+        raise ValueError("frames, template, coarse and shifts must be on one device")
+    with torch.cuda.device(frames.device):
+        _check(lib().moco_jitter_noalloc(_ptr(frames), T, m, n, _ptr(template), _ptr(coarse), _ptr(shifts),
+                                         _stream(stream)))
+
+
+def moco_alu_peak(kind: int, device=None) -> float:
+    """Measured FP32 FMA (flop/s) or dp2a (instructions/s) rate of the current
+    (or given) CUDA device; synchronises."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        sink = torch.zeros(1, dtype=torch.int32, device=dev)
+        rate = ctypes.c_double(0.0)
+        _check(lib().moco_alu_peak(int(kind), _ptr(sink), ctypes.byref(rate), _stream(None)))
+    return float(rate.value)
 
 
 def moco_plan_status(plan):

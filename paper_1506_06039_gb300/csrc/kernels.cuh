@@ -1405,7 +1405,13 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     uint4* ring = reinterpret_cast<uint4*>(jit_smem) + threadIdx.x;  // kJitRingBytes
     const int tid = threadIdx.x;
     const int64_t f = blockIdx.y;
-    const int s0 = 2 * coarse[2 * f], t0 = 2 * coarse[2 * f + 1];
+    // Every candidate needs a non-empty overlap: |2 sc| + 1 < m, |2 tc| + 1 < n
+    // (always so for a searched-grid optimum; checked for caller-given ones).
+    // A frame outside that range is computed at (0, 0), so every index stays
+    // in range, and reported as (INT32_MIN, INT32_MIN).
+    const int sc = coarse[2 * f], tc = coarse[2 * f + 1];
+    const bool valid = sc >= -((m - 2) >> 1) && sc <= ((m - 2) >> 1) && tc >= -((n - 2) >> 1) && tc <= ((n - 2) >> 1);
+    const int s0 = valid ? 2 * sc : 0, t0 = valid ? 2 * tc : 0;
     u64 X[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) X[k] = 0;
@@ -1495,9 +1501,9 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
             }
             if (take) { bk = u * 3 + v; bS = Sk; bA = A; bs = s; bt = t; }
         }
-    shifts[2 * f] = bs;
-    shifts[2 * f + 1] = bt;
-    if (ffinal) ffinal[f] = (double)bS / (double)bA;
+    shifts[2 * f] = valid ? bs : INT32_MIN;
+    shifts[2 * f + 1] = valid ? bt : INT32_MIN;
+    if (ffinal) ffinal[f] = valid ? (double)bS / (double)bA : __longlong_as_double(0x7ff8000000000000ll);
 }
 
 // Prefix table of b^2 for k_jitter, P[(m+1) x (n+1)] (exact u64), in two

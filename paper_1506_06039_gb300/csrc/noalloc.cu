@@ -7,7 +7,6 @@
 // keeps until the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "internal.h"
@@ -22,29 +21,21 @@ moco_status cuda_fail(cudaError_t e, const char* what);
 namespace {
 
 constexpr int64_t kNoallocMaxFrames = 8192;
-// Per frame: 9 u64 sums, then (after all sums) one 32-bit ticket; 640 KiB.
+// Per frame: 9 u64 sums, then (after all sums) one 32-bit ticket:
+// 8192 * (9 * 8 + 4) bytes = 608 KiB.
 constexpr int64_t kNoallocWords = kNoallocMaxFrames * 9 + kNoallocMaxFrames / 2;
+static_assert(kNoallocWords * 8 == 608 * 1024, "the size stated in include/moco.h");
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoallocWords];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device (looked up once
-// per device, with that device current).
+// Device address of the scratch array in the current context. Looked up on
+// every call (a host-side table lookup once the module is loaded): a cached
+// address would go stale if the caller reset the device or tore down its
+// primary context, after which the module loads again, possibly elsewhere.
 cudaError_t scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    *out = p;
     return cudaSuccess;
 }
 

@@ -2,7 +2,10 @@
 
 Tolerances, derived from the arithmetic: the cross term is FP32 (FFT) or
 BF16 hi+lo with FP32 accumulation; energies are exact int64; the combine is
-FP64. An FP32 FFT correlation has an absolute error of order
+FP32 from the exact energies carried as FP32 pairs (an error-free sum of the
+two energies, then one rounding in the difference with 2h and one in the
+division by the area: about 1.2e-7 relative to f itself, whatever the
+cancellation). An FP32 FFT correlation has an absolute error of order
 u * log2(N) * ||a|| * ||b|| (u = 2^-24), so the error of f is of order
 1e-6 * max f whatever f itself is. The cost surface must therefore agree
 with the oracle's FP64 value within 1e-4 relative wherever f >= 1e-2 * max f
@@ -53,3 +56,37 @@ def check_align(frames, template, w, levels, shifts_gpu, best_gpu=None, ref=None
                                                                              COST_FLOOR * fmax)
             assert err2.max() <= COST_RTOL, "best cost rel err %g (frames %s)" % (err2.max(), over[:8])
     return ref, int((~decided).sum())
+
+
+def fbest_rel_err(best_gpu, ref):
+    """Un-floored relative error of the optimum's cost, |f_gpu - f_ref| / f_ref
+    (frames whose oracle optimum is exactly 0 are left out): the number the
+    floored bar does not show."""
+    best_gpu = np.asarray(best_gpu, np.float64)
+    f = np.asarray(ref["fbest"], np.float64)
+    keep = f > 0
+    if not keep.any():
+        return 0.0
+    return float((np.abs(best_gpu[keep] - f[keep]) / f[keep]).max())
+
+
+def check_margin(margin_gpu, best_gpu, ref, fmax):
+    """The CUDA margin (f2 - f1) / f1 against the oracle's. Each of f1, f2 may
+    be off by COST_RTOL * max(f, COST_FLOOR * fmax) (the cost bar), so with
+    d_k that bound over f_k the margin may differ by (1 + margin) (d1 + d2) /
+    (1 - d1). Frames with f1 = 0 compare only as 'infinite or not'."""
+    mg = np.asarray(margin_gpu, np.float64)
+    mr = np.asarray(ref["margin"], np.float64)
+    f1 = np.asarray(ref["fbest"], np.float64)
+    fmax = np.asarray(fmax, np.float64)
+    f2 = f1 * (1.0 + mr)
+    floor = COST_FLOOR * fmax
+    with np.errstate(divide="ignore", invalid="ignore"):
+        d1 = COST_RTOL * np.maximum(f1, floor) / f1
+        d2 = COST_RTOL * np.maximum(f2, floor) / f2
+        bound = (1.0 + mr) * (d1 + d2) / np.maximum(1.0 - d1, 1e-12)
+    finite = np.isfinite(mr) & (f1 > 0) & (d1 < 0.5)
+    bad = np.nonzero(finite & ~(np.abs(mg - mr) <= bound))[0]
+    assert bad.size == 0, "margin: frames %s gpu %s oracle %s bound %s" % (
+        bad[:8], mg[bad[:8]], mr[bad[:8]], bound[bad[:8]])
+    return float(np.max(np.abs(mg - mr)[finite] / np.maximum(mr[finite], 1e-30))) if finite.any() else 0.0

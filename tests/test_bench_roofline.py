@@ -1,8 +1,10 @@
 """The benchmark's roofline arithmetic on the host: the dominant kernel is the
-one with the largest share of device time, `achieved` is its algorithmic work
-per second over the live duration, `frac` divides by the stated peak, and the
-DRAM traffic constants are reported only for the workload and form they were
-captured on."""
+one with the largest share of device time, its bound is the one the method's
+roofline gives it (HBM for the frame pass and the upsampling step, FP32 for
+the transforms, tensor cores for the direct form), `achieved` is its
+algorithmic work per second over the live duration, `frac` divides by that
+bound's peak with the other fractions beside it, and the DRAM traffic
+constants are reported only for the workload and form they were captured on."""
 import math
 
 import pytest
@@ -12,27 +14,32 @@ from paper_1506_06039_gb300 import XCORR_DIRECT_BF16X3, XCORR_FFT_FP32, synth
 
 PEAKS = {"hbm_gbs": 6787.2, "bf16_tflops": 1942.7, "bf16_tflops_sustained": 1714.2}
 INFO_288 = {"mc": 256, "nc": 256, "fft_rows": 288, "fft_cols": 288, "xcorr": XCORR_FFT_FP32}
+# measured ALU peaks as moco_alu_peak would report them (T ops/s, source)
+ALU = {"fp32": (71.5, "measured"), "int": (19.0, "measured")}
 
 
 def _rf(profile, info, name="std512", frames=2000, steps=300):
-    return bench.roofline(profile, info, synth.WORKLOADS[name], frames, steps, PEAKS, None)
+    return bench.roofline(profile, info, synth.WORKLOADS[name], frames, steps, PEAKS, ALU)
 
 
-def test_jitter_dominant_is_reported_against_the_integer_pipe():
+def test_jitter_dominant_is_hbm_bound_with_the_integer_pipe_beside_it():
     # ms summed over 300 launches, as the library's profile returns them
     prof = {"k_frame_rows": (300, 137.0), "k_cols": (300, 125.0), "k_rows_inv": (300, 52.0),
             "k_jitter": (300, 144.0)}
     rf = _rf(prof, INFO_288)
-    assert rf["kernel"] == "k_jitter" and rf["bound"] == "alu"
+    assert rf["kernel"] == "k_jitter" and rf["bound"] == "hbm" and rf["unit"] == "GB/s"
     assert rf["avg_launch_ms"] == pytest.approx(144.0 / 300)
-    # nine exact products per full-resolution pixel of 2000 frames of 512 x 512
+    # every full-resolution pixel of 2000 frames of 512 x 512 read once
+    byts = 2.0 * 512 * 512 * 2000
+    assert rf["algorithmic_per_launch"]["bytes"] == pytest.approx(byts)
+    achieved = byts / (144.0 / 300 / 1e3) / 1e9
+    assert rf["achieved"] == pytest.approx(achieved)
+    assert rf["peak"] == PEAKS["hbm_gbs"]
+    assert rf["frac"] == pytest.approx(achieved / PEAKS["hbm_gbs"])
+    # nine exact products per pixel, against the measured dp2a rate, beside it
     mads = 9.0 * 512 * 512 * 2000
     assert rf["algorithmic_per_launch"]["int_mads"] == pytest.approx(mads)
-    achieved = mads / (144.0 / 300 / 1e3) / 1e12
-    assert rf["achieved"] == pytest.approx(achieved)
-    peak = 152 * 64 * 2070e6 / 1e12
-    assert rf["peak"] == pytest.approx(peak)
-    assert rf["frac"] == pytest.approx(achieved / peak)
+    assert rf["fractions"]["int"] == pytest.approx(mads / (144.0 / 300 / 1e3) / 1e12 / ALU["int"][0])
     assert rf["share"] == pytest.approx(144.0 / (137.0 + 125.0 + 52.0 + 144.0))
     # the captured traffic, scaled from 512 frames to a 2000-frame launch
     assert rf["traffic"] == pytest.approx(bench.TRAFFIC_PER_FRAME["k_jitter"] * 2000)
@@ -68,3 +75,14 @@ def test_direct_form_kernel_takes_the_sustained_bf16_peak():
     assert rf["achieved"] == pytest.approx(flops / (112.0 / 20 / 1e3) / 1e12)
     assert rf["peak"] == PEAKS["bf16_tflops_sustained"]
     assert math.isclose(rf["frac"], rf["achieved"] / rf["peak"])
+
+
+def test_transform_kernel_is_reported_against_the_measured_fp32_peak():
+    prof = {"k_cols": (10, 4.0), "k_jitter": (10, 1.0)}
+    rf = _rf(prof, INFO_288, frames=2000, steps=10)
+    assert rf["kernel"] == "k_cols" and rf["bound"] == "alu" and rf["unit"] == "TFLOP/s"
+    N = 288
+    flops = (N // 2 + 1) * (2 * 5.0 * N * math.log2(N) + 6 * N) * 2000
+    assert rf["achieved"] == pytest.approx(flops / 0.4e-3 / 1e12)
+    assert rf["peak"] == ALU["fp32"][0]
+    assert rf["frac"] == pytest.approx(rf["achieved"] / ALU["fp32"][0])

@@ -230,25 +230,6 @@ def test_several_shapes_and_stacks_in_one_call():
     check_align(sb.frames, sb.template, 5, -1, outb.cpu().numpy())
 
 
-def test_std512_full_workload_sampled():
-    # The standard workload at full size (2000 frames, template = mean of the
-    # first 100 frames), in the launch configuration the benchmark times; the
-    # oracle checks a seeded sample of frames one by one. The mean of frames
-    # shifted by up to 40 px is a blurred template, so planted shifts are not
-    # expected here; parity with the oracle is.
-    wl = synth.WORKLOADS["std512"]
-    st = synth.make_stack_torch(wl.m, wl.n, wl.T, wl.nblobs, wl.shift_max, wl.seed, template=wl.template)
-    with Plan(dict(m=wl.m, n=wl.n, w=wl.w), st.template) as plan:
-        shifts, best, margin = plan.align(st.frames, best_cost=True, margin=True)
-        torch.cuda.synchronize()
-        info = plan.info()
-    assert info["levels"] == 1 and info["mc"] == 256
-    shifts = shifts.cpu().numpy()
-    sample = np.random.default_rng(0).choice(wl.T, 12, replace=False)
-    fr = st.frames.cpu().numpy()[sample]
-    check_align(fr, st.template.cpu().numpy(), wl.w, -1, shifts[sample], best.cpu().numpy()[sample])
-
-
 def test_std512_clean_template_recovers_planted_shifts():
     # Same frame recipe with the clean (unshifted, noise-free) template: the
     # planted shifts are the answer on (almost) every frame.

@@ -60,22 +60,6 @@ def test_direct_more_than_one_m_tile():
     check_align(st.frames, st.template, 6, 0, shifts)
 
 
-@pytest.mark.parametrize("name,frames", [("std512", 2000), ("large512", 1000)])
-def test_direct_full_workloads_sampled(name, frames):
-    wl = synth.WORKLOADS[name]
-    st = synth.make_stack_torch(wl.m, wl.n, frames, wl.nblobs, wl.shift_max, wl.seed, template=wl.template)
-    with direct_plan(wl.m, wl.n, wl.w, st.template) as plan:
-        shifts, best, _ = plan.align(st.frames, best_cost=True)
-        sample = np.random.default_rng(2).choice(frames, 6, replace=False)
-        fr = st.frames.cpu().numpy()[sample]
-        cost = plan.cost_surface(torch.from_numpy(fr).cuda()).cpu().numpy()
-        torch.cuda.synchronize()
-        plan.status()
-    tm = st.template.cpu().numpy()
-    assert cost_rel_err(cost, oracle.cost_surface(fr, tm, wl.w)) <= COST_RTOL
-    check_align(fr, tm, wl.w, -1, shifts.cpu().numpy()[sample], best.cpu().numpy()[sample])
-
-
 def test_auto_form_agrees_with_both():
     st = synth.make_stack_np(128, 128, 12, 30, 6, seed=5, template="clean")
     res = {}

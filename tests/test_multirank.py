@@ -113,3 +113,68 @@ def test_two_rank_refinement_equals_one_process_over_all_frames():
     np.testing.assert_allclose(res[0][1], t1.numpy(), rtol=0, atol=1e-4)
     np.testing.assert_allclose(res[0][2], l1, rtol=1e-8)  # float32 gradients summed in another order
     assert not np.array_equal(t1.numpy(), tmpl)  # the template moved
+
+
+# ---- one stack sharded over ranks: contiguous frame ranges, gathered shifts --
+
+def test_frame_ranges_tile_the_stack():
+    from paper_1506_06039_gb300.shard import frame_range
+    for T in (0, 1, 7, 2000, 2001):
+        for world in (1, 2, 3, 8):
+            ranges = [frame_range(T, world, r) for r in range(world)]
+            assert ranges[0][0] == 0 and ranges[-1][1] == T
+            assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
+            sizes = [hi - lo for lo, hi in ranges]
+            assert max(sizes) - min(sizes) <= 1
+
+
+def _shard_problem():
+    from paper_1506_06039_gb300 import synth
+    # 11 frames over two ranks (6 + 5): a ragged split; one 2x2 level and the jitter
+    return synth.make_stack_np(272, 264, 11, 40, 10, seed=606, template="clean"), 6
+
+
+def _shard_worker(rank, world, port, q):
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1506_06039_gb300.shard import align_sharded, broadcast_template
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        st, w = _shard_problem()
+        # only rank 0 holds the template at first; the broadcast gives it to the other
+        tmpl = torch.from_numpy(st.template.astype(np.int32)) if rank == 0 else torch.zeros(st.template.shape,
+                                                                                              dtype=torch.int32)
+        broadcast_template(tmpl)
+        seen = []
+
+        def align_fn(fr):
+            seen.append(fr.shape[0])
+            r = oracle.align(fr, tmpl.numpy().astype(np.uint16), w)
+            return torch.from_numpy(r["shifts"])
+
+        shifts = align_sharded(st.frames, align_fn)
+        q.put((rank, shifts.numpy(), seen))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_sharded_stack_equals_one_process():
+    import numpy as np
+    import oracle
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_shard_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    res = sorted((q.get(timeout=5) for _ in range(world)), key=lambda r: r[0])
+    st, w = _shard_problem()
+    ref = oracle.align(st.frames, st.template, w)
+    assert res[0][2] == [6] and res[1][2] == [5]  # each rank searched its own range only
+    for r in res:
+        assert np.array_equal(r[1], ref["shifts"])

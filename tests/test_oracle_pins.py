@@ -64,6 +64,66 @@ def test_constant_images_closed_form():
     assert r["margin"][0] == 0.0
 
 
+# ---- The margin (f2 - f1) / f1, f2 the smallest f over every other shift ----
+# Hand-worked cases with every f written out as a fraction: a wrong
+# denominator (f2 instead of f1), f2 taken among the optimum's own ties, or
+# the level's unit applied to one of the two values only changes the number.
+
+def test_margin_hand_worked_delta():
+    # 3 x 4, w = 2, b = 0, a = 3 at (1, 1): that pixel is inside the a-side of
+    # every D_{s,t}, so S = 9 for all nine shifts and f = 9 / Area with
+    # Area = (3 - |s|)(4 - |t|): f(0,0) = 9/12, f(0,+-1) = 9/9, f(+-1,0) = 9/8,
+    # f(+-1,+-1) = 9/6. Best (0, 0) = 3/4, next 1: margin (1 - 3/4)/(3/4) = 1/3.
+    a = np.zeros((3, 4), np.uint16); a[1, 1] = 3
+    b = np.zeros((3, 4), np.uint16)
+    cost = oracle.cost_surface(a, b, 2, levels=0)[0]
+    assert np.array_equal(cost, np.array([[9 / 6, 9 / 8, 9 / 6], [9 / 9, 9 / 12, 9 / 9], [9 / 6, 9 / 8, 9 / 6]]))
+    r = oracle.align(a, b, 2, levels=0)
+    assert tuple(r["shifts"][0]) == (0, 0) and r["fbest"][0] == 0.75
+    assert r["margin"][0] == pytest.approx(1 / 3, rel=1e-15)
+
+
+def test_margin_hand_worked_template_bump():
+    # 3 x 3, w = 2, a = 1 everywhere, b = 3 at (1, 1) and 0 elsewhere: the
+    # template pixel (1, 1) is in every D, so S = (Area - 1) * 1 + (1 - 3)^2
+    # = Area + 3 and f = 1 + 3 / Area: f(0,0) = 4/3, f at one-axis shifts 3/2,
+    # at diagonal shifts 7/4. Margin (3/2 - 4/3) / (4/3) = 1/8.
+    a = np.ones((3, 3), np.uint16)
+    b = np.zeros((3, 3), np.uint16); b[1, 1] = 3
+    r = oracle.align(a, b, 2, levels=0)
+    assert tuple(r["shifts"][0]) == (0, 0) and r["fbest"][0] == pytest.approx(4 / 3, rel=1e-15)
+    assert r["margin"][0] == pytest.approx(1 / 8, rel=1e-15)
+
+
+def test_margin_hand_worked_one_level():
+    # The delta case at twice the size with one 2x2 level: a 2x2 block of 3s
+    # at rows 2-3, columns 2-3 of a 6 x 8 frame sums to 12 at coarse (1, 1),
+    # so the searched-grid costs are 144 / Area / 16 in box-mean units, the
+    # same fractions as the delta case: fbest 3/4, margin 1/3.
+    a = np.zeros((6, 8), np.uint16); a[2:4, 2:4] = 3
+    b = np.zeros((6, 8), np.uint16)
+    r = oracle.align(a, b, 2, levels=1)
+    assert tuple(r["coarse"][0]) == (0, 0) and r["fbest"][0] == 0.75
+    assert r["margin"][0] == pytest.approx(1 / 3, rel=1e-15)
+
+
+def test_margin_best_away_from_centre():
+    # b[i][j] = 10 j + 3 i^2 and a the same image moved right by one column
+    # (a[i][j] = b[i][j-1], first column 0): f(0, 1) = 0 exactly is the optimum
+    # and every other shift has f > 0 (b varies along both axes), so
+    # the margin is infinite; with the frame's first column raised from 0 to 5
+    # the optimum stays at (0, 1) with S = 0 still (that column is outside
+    # D_{0,1}'s a-side), so the margin stays infinite: the margin is taken over
+    # the other shifts only, never over the optimum itself.
+    m, n = 5, 6
+    b = (10 * np.arange(n)[None, :] + 3 * np.arange(m)[:, None] ** 2).astype(np.uint16)
+    a = np.zeros((m, n), np.uint16); a[:, 1:] = b[:, :-1]
+    for first in (0, 5):
+        a[:, 0] = first
+        r = oracle.align(a, b, 2, levels=0)
+        assert tuple(r["shifts"][0]) == (0, 1) and r["fbest"][0] == 0 and r["margin"][0] == np.inf
+
+
 # ---- Invariants ---------------------------------------------------------------
 
 def test_identity_gives_zero_shift():
