@@ -298,7 +298,7 @@ def accuracy_sample(plan, frames_dev, template_host, w, shifts_dev, sample=16, s
     del cost
     torch.cuda.synchronize()
     deterministic = bool(torch.equal(shifts2, shifts_dev))
-    fr = frames_dev[sel].cpu().numpy()
+    fr = frames_dev.view(torch.int16)[sel].view(torch.uint16).cpu().numpy()  # (no uint16 gather kernel)
     shifts = shifts_dev[sel].cpu().numpy()
     best, margin = best[sel].cpu().numpy(), margin[sel].cpu().numpy()
     ref_cost = oracle.cost_surface(fr, template_host, w)

@@ -64,7 +64,7 @@ def test_full_workload_cost_surface_pointwise(stacks, name, form):
         idx = torch.from_numpy(sample).cuda()
         cost_s = cost[idx].cpu().numpy()
         del cost
-    fr = st.frames[idx].cpu().numpy()
+    fr = st.frames.view(torch.int16)[idx].view(torch.uint16).cpu().numpy()  # (no uint16 gather kernel)
     tm = st.template.cpu().numpy()
     ref_cost = oracle.cost_surface(fr, tm, wl.w)
     err = cost_rel_err(cost_s, ref_cost)
