@@ -550,6 +550,15 @@ def run_mixed(args, world, rank, local):
     items = [dict(shape_idx=k, frames=st.frames, shifts=outs[k]) for k, (st, _) in enumerate(stacks)]
     moco_align_stack(plan.handle, items)
     torch.cuda.synchronize()
+    # Per-kernel device times from profiled eager calls (untimed), summed over
+    # the stacks; the timed steps are replays of one captured call.
+    prof_steps = max(1, min(3, args.steps))
+    plan.profile(max_launches=prof_steps * 1024)
+    for _ in range(prof_steps):
+        moco_align_stack(plan.handle, items)
+    torch.cuda.synchronize()
+    profile = plan.profile_read(reset=True)
+    plan.profile(0)
     g = torch.cuda.CUDAGraph()
     cs = torch.cuda.Stream()
     cs.wait_stream(torch.cuda.current_stream())
@@ -573,6 +582,7 @@ def run_mixed(args, world, rank, local):
     ms = ev0.elapsed_time(ev1)
     frames = sum(st.frames.shape[0] for st, _ in stacks)
     forms = [plan.info(k)["xcorr"] for k in range(len(specs))]
+    rf, kernels = mixed_roofline(profile, plan, specs, stacks, prof_steps, load_peaks(), measured_alu_peaks())
     if rank == 0:
         out = {"metric": METRIC + " [batching form: 32 uneven stacks]", "value": world * frames * args.steps / (ms / 1e3),
                "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
@@ -582,9 +592,46 @@ def run_mixed(args, world, rank, local):
                           "frames": frames, "bytes": int(sum(st.frames.numel() * 2 for st, _ in stacks)),
                           "forms": {"fft_fp32": forms.count(1), "direct_bf16x3": forms.count(2)},
                           "graph": "one captured moco_align_stack call"},
-               "clocks": clocks}
+               "clocks": clocks, "roofline": rf, "kernels": kernels,
+               "gpu_launches": sum(l for l, _ in profile.values()) // prof_steps}
         print(json.dumps(out), flush=True)
     plan.close()
+
+
+def mixed_roofline(profile, plan, specs, stacks, steps, peaks, alu):
+    """Per-kernel algorithmic work summed over the stacks (each with its own
+    shape, window and FFT lengths) against the profiled device time; the
+    dominant kernel against its bound."""
+    import types
+    tot = {}
+    for k, (s_, (st, _)) in enumerate(zip(specs, stacks)):
+        wl = types.SimpleNamespace(m=s_["m"], n=s_["n"], w=s_["w"], name="mixed")
+        for name, (b, f, i) in kernel_work(plan.info(k), wl, st.frames.shape[0] * steps).items():
+            acc = tot.setdefault(name, [0.0, 0.0, 0.0])
+            acc[0] += b
+            acc[1] += f
+            acc[2] += i
+    total_ms = sum(ms for _, ms in profile.values()) or 1.0
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    kernels = {}
+    for name, (launches, ms) in profile.items():
+        b, f, i = tot.get(name, (0.0, 0.0, 0.0))
+        sec = ms / 1e3
+        kernels[name] = {"launches_per_step": launches / steps, "ms_per_step": ms / steps, "share": ms / total_ms,
+                         "hbm_frac": b / sec / 1e9 / hbm if b else None,
+                         "fp32_frac": f / sec / 1e12 / alu["fp32"][0] if f and name != "k_direct" else None,
+                         "tensor_frac": (f / sec / 1e12 / peaks.get("bf16_tflops_sustained", 1700.0)
+                                         if f and name == "k_direct" else None),
+                         "int_frac": i / sec / 1e12 / alu["int"][0] if i else None}
+    name = max(profile, key=lambda k: profile[k][1])
+    bound = KERNEL_BOUND.get(name, "hbm")
+    key = {"hbm": "hbm_frac", "fp32": "fp32_frac", "tensor": "tensor_frac"}[bound]
+    rf = {"kernel": name, "bound": "alu" if bound == "fp32" else bound, "frac": kernels[name][key],
+          "share": kernels[name]["share"], "traffic": None,
+          "peak": {"hbm": hbm, "fp32": alu["fp32"][0], "tensor": peaks.get("bf16_tflops_sustained")}[bound],
+          "unit": {"hbm": "GB/s", "fp32": "TFLOP/s", "tensor": "TFLOP/s"}[bound],
+          "note": "work summed over the 32 stacks' shapes; kernel times from profiled eager calls"}
+    return rf, kernels
 
 
 def run_grad(args, world, rank, local):

@@ -367,7 +367,7 @@ k_combine_h(const float* __restrict__ hh, int wm1, const float2* __restrict__ Sa
     for (int k = tid; k < WW; k += nthr) {
         const int s = k / W - wm1, t = k % W - wm1;
         const float fv = combine_f32(Sa2[f * WW + k], Sb2[k], hh[f * WW + k], ia32[k]);
-        if (cost) cost[f * WW + k] = (double)fv;
+        if (cost) cost[f * WW + k] = f32_to_f64(fv);
         best_push(b, fv, (abs(s) + abs(t)) * WW + k);
     }
 #pragma unroll

@@ -287,6 +287,56 @@ __device__ void fft4_fwd(float2* buf, int ld, int rows, const float2* twf, int t
     fft4_fwd_stage2<N>(buf, ld, rows, tid, nthr);
 }
 
+// The middle of a forward transform, a pointwise product and the inverse, in
+// one pass over registers: after the forward transform's first stage (and a
+// barrier), each task's contiguous N2-block is the same block that the
+// forward second stage writes, the product reads (the spectrum's forward
+// output layout keeps block k1 together) and the inverse first stage reads.
+// So task (r, k1) runs the forward N2-point codelet, multiplies by
+// spec[r * spec_ld + N2 * k1 + k2], runs the inverse N2-point codelet and
+// its twiddles, and writes the block back once. Ends with a barrier; the
+// inverse's second stage (fft4_inv_stage2) completes the inverse.
+template <int N>
+__device__ void fft4_fwd2_mul_inv1(float2* buf, int ld, int rows, const float2* spec, int spec_ld,
+                                   const float2* twi, int tid, int nthr) {
+    constexpr int N1 = Four<N>::N1, N2 = Four<N>::N2, B = N2 + Skew<N>::S;
+    for (int task = tid; task < rows * N1; task += nthr) {
+        int r = task / N1, k1 = task - r * N1;
+        float2* p = buf + r * ld + B * k1;
+        const float2* q = spec + r * spec_ld + N2 * k1;
+        float2 x[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) x[n2] = p[n2];
+        Dft<N2, false>::run(x);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) x[k2] = cmul(x[k2], q[k2]);
+        Dft<N2, true>::run(x);
+#pragma unroll
+        for (int n2 = 1; n2 < N2; ++n2) x[n2] = cmulc(x[n2], twi[n2 * N1 + k1]);
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) p[n2] = x[n2];
+    }
+    __syncthreads();
+}
+
+// Second stage of the inverse transform (after its first stage and a
+// barrier): N2 tasks per row, one N1-point codelet each; ends with a barrier.
+template <int N>
+__device__ void fft4_inv_stage2(float2* buf, int ld, int rows, int tid, int nthr) {
+    constexpr int N1 = Four<N>::N1, N2 = Four<N>::N2, B = N2 + Skew<N>::S;
+    for (int task = tid; task < rows * N2; task += nthr) {
+        int r = task / N2, n2 = task - r * N2;
+        float2* p = buf + r * ld + n2;
+        float2 x[N1];
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) x[k1] = p[B * k1];
+        Dft<N1, true>::run(x);
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) p[B * n1] = x[n1];
+    }
+    __syncthreads();
+}
+
 // Inverse (unnormalised, omega^+) transform: input in the forward output
 // layout, output in natural order.
 template <int N>

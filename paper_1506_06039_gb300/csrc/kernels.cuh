@@ -638,11 +638,186 @@ __device__ __forceinline__ void energy_frame(const u64* __restrict__ rE, const u
     }
 }
 
-// The exact energy e as the FP32 pair (nearest float, rounded remainder).
+// x as a float, exact for x < 2^23, without a conversion instruction (the
+// bits of 2^23 + x, minus 2^23).
+__device__ __forceinline__ float small_u32_to_float(uint32_t x) {
+    return __uint_as_float(0x4B000000u | x) - 8388608.0f;
+}
+
+// The exact energy e (< 2^53) as an FP32 pair hi + lo. e splits into three
+// limbs exact in FP32, e = H 2^32 + M 2^16 + L0 (H < 2^21, M, L0 < 2^16);
+// hi + r = H 2^32 + M 2^16 by an error-free sum (TwoSum) and lo = r + L0
+// rounds once at |lo| <= 2^-24 |hi| + 2^16: hi + lo is e to within
+// 2^-24 |lo|, far below FP32's own resolution of e. 64-bit integer
+// conversions run on this part's narrow FP64 pipe; this takes only integer
+// logic and FP32 additions.
 __device__ __forceinline__ float2 energy_pair(u64 e) {
-    const float hi = __ull2float_rn(e);
-    const long long r = (long long)(e - __float2ull_rn(hi));  // |r| <= ulp(hi) / 2
-    return make_float2(hi, __ll2float_rn(r));
+    const uint32_t H = (uint32_t)(e >> 32), L = (uint32_t)e;
+    const float e2 = small_u32_to_float(H) * 4294967296.0f;
+    const float e1 = small_u32_to_float(L >> 16) * 65536.0f;
+    const float e0 = small_u32_to_float(L & 0xffffu);
+    const float hi = e2 + e1;
+    const float bb = hi - e2;
+    const float r = (e2 - (hi - bb)) + (e1 - bb);
+    return make_float2(hi, r + e0);
+}
+
+// (double)x for a float, by moving the bits (the same value: every float is a
+// double); zero, subnormal, infinite and NaN inputs take the conversion
+// instruction, which runs on the narrow FP64 pipe.
+__device__ __forceinline__ double f32_to_f64(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t ex = (u >> 23) & 0xffu;
+    if (ex == 0u || ex == 0xffu) return (double)x;
+    const u64 bits = ((u64)(u & 0x80000000u) << 32) | ((u64)(ex + 896u) << 52) | ((u64)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+// The same energies as energy_frame (integer frames), by warp sweeps instead
+// of corner tables in shared memory. For corner quadrant q the table
+//     P_q[a][b] = sum over the a rows and b columns nearest q's corner of a'^2
+// (a, b < w) is a 2-D prefix sum of the squared corner block. Each lane owns
+// K consecutive columns b = K lane + k; the rows [1, w) of a quadrant are
+// split into G contiguous segments, one warp each. A warp first sums its
+// segment's rows per column and turns that into a prefix along the columns
+// (the segment's share of every P_q[a][b] below it), which the warps of
+// later segments add as their starting carry; then it walks its rows: each
+// row's squares, their prefix along the columns (lane-local, then one warp
+// scan of the lane totals), added to the carry, give P_q[a][b] for the row,
+// and emit(s, t, Sa) is called for each of its shifts. Every thread of the
+// block must call it (it synchronises once); shared memory:
+// energy_sweep_smem(wm1, warps). Needs w <= 32 K and at least four warps.
+__host__ __device__ constexpr int sweep_groups(int warps) { return warps >= 8 ? warps / 4 : 1; }
+__host__ __device__ constexpr size_t energy_sweep_smem(int wm1, int warps) {
+    return sizeof(u64) * (2 * (2 * (size_t)wm1 + 1) + 4 * (size_t)sweep_groups(warps) * (wm1 + 1));
+}
+
+template <int K, typename Emit>
+__device__ __forceinline__ void energy_sweep(const u64* __restrict__ rE, const u64* __restrict__ cE, u64 T,
+                                             const uint32_t* __restrict__ corners_f, int mc, int nc, int wm1,
+                                             unsigned char* smem, Emit emit) {
+    const int W = 2 * wm1 + 1, w = wm1 + 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int G = sweep_groups(nwarps);
+    u64* exR = reinterpret_cast<u64*>(smem);  // W
+    u64* exC = exR + W;                       // W
+    u64* seg = exC + W;                       // 4 x G x w
+    // Edge strips (as energy_frame): exR[wm1 + k] = energy of the first k
+    // rows, exR[wm1 - k] of the last k rows; the same for columns. Warps 0-3.
+    if (warp < 4) {
+        const u64* src = warp < 2 ? rE : cE;
+        const int len = warp < 2 ? mc : nc;
+        u64* dst = warp < 2 ? exR : exC;
+        const bool from_end = warp & 1;
+        u64 carry = 0;
+        if (lane == 0) dst[wm1] = 0;
+        for (int k0 = 0; k0 < wm1; k0 += 32) {
+            const int k = k0 + lane;
+            u64 v = k < wm1 ? src[from_end ? len - 1 - k : k] : 0ull;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const u64 u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            v += carry;
+            if (k < wm1) dst[from_end ? wm1 - 1 - k : wm1 + 1 + k] = v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    const int q = warp / G, g = warp - q * G;
+    const bool active = q < 4;
+    const bool bottom = q >= 2, right = q & 1;
+    const int L = (wm1 + G - 1) / G;
+    const int a0 = 1 + g * L, a1 = min(w, 1 + (g + 1) * L);
+    const size_t wm1sq = (size_t)wm1 * wm1;
+    const uint32_t* blk = corners_f + (size_t)(q & 3) * wm1sq;
+    // Squares of table row a at this lane's columns (0 at b = 0 and b >= w).
+    auto row_sq = [&](int a, u64 (&v)[K]) {
+        const uint32_t* row = blk + (size_t)(bottom ? wm1 - a : a - 1) * wm1;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int b = K * lane + k;
+            v[k] = 0ull;
+            if (b >= 1 && b < w) {
+                const long long c = (int32_t)row[right ? wm1 - b : b - 1];
+                v[k] = (u64)(c * c);
+            }
+        }
+    };
+    // Inclusive prefix of v along the columns (lane-local, then across lanes).
+    auto col_prefix = [&](u64 (&v)[K]) {
+#pragma unroll
+        for (int k = 1; k < K; ++k) v[k] += v[k - 1];
+        const u64 tot = v[K - 1];
+        u64 x = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u64 y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const u64 excl = x - tot;
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] += excl;
+    };
+    if (active) {
+        u64 cs[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) cs[k] = 0ull;
+        for (int a = a0; a < a1; ++a) {
+            u64 v[K];
+            row_sq(a, v);
+#pragma unroll
+            for (int k = 0; k < K; ++k) cs[k] += v[k];
+        }
+        col_prefix(cs);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int b = K * lane + k;
+            if (b < w) seg[((size_t)q * G + g) * w + b] = cs[k];
+        }
+    }
+    __syncthreads();
+    if (!active) return;
+    u64 carry[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int b = K * lane + k;
+        carry[k] = 0ull;
+        if (b < w)
+            for (int g2 = 0; g2 < g; ++g2) carry[k] += seg[((size_t)q * G + g2) * w + b];
+    }
+    auto emit_row = [&](int a) {
+        const int s = bottom ? -a : a;
+        const u64 base = T - exR[s + wm1];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int b = K * lane + k;
+            if (b < w && !(right && b == 0)) {
+                const int t = right ? -b : b;
+                emit(s, t, base - exC[t + wm1] + carry[k]);
+            }
+        }
+    };
+    if (g == 0 && !bottom) emit_row(0);  // a = 0: no corner rows (s = 0 belongs to the top quadrants)
+    for (int a = a0; a < a1; ++a) {
+        u64 v[K];
+        row_sq(a, v);
+        col_prefix(v);
+#pragma unroll
+        for (int k = 0; k < K; ++k) carry[k] += v[k];
+        emit_row(a);
+    }
+}
+
+// energy_sweep with K = ceil(w / 32) columns per lane (w <= 128).
+template <typename Emit>
+__device__ __forceinline__ void energy_sweep_any(const u64* __restrict__ rE, const u64* __restrict__ cE, u64 T,
+                                                 const uint32_t* __restrict__ corners_f, int mc, int nc, int wm1,
+                                                 unsigned char* smem, Emit emit) {
+    if (wm1 < 32) energy_sweep<1>(rE, cE, T, corners_f, mc, nc, wm1, smem, emit);
+    else if (wm1 < 64) energy_sweep<2>(rE, cE, T, corners_f, mc, nc, wm1, smem, emit);
+    else if (wm1 < 96) energy_sweep<3>(rE, cE, T, corners_f, mc, nc, wm1, smem, emit);
+    else energy_sweep<4>(rE, cE, T, corners_f, mc, nc, wm1, smem, emit);
 }
 
 template <bool F32, bool OUT_DOUBLE>
@@ -654,6 +829,16 @@ k_energy(const u64* __restrict__ rowE, const u64* __restrict__ colE, const u64* 
     extern __shared__ __align__(16) unsigned char esm_raw[];
     const int W = 2 * wm1 + 1;
     const int64_t f = blockIdx.x;
+    if constexpr (!F32 && !OUT_DOUBLE) {
+        // integer frames' energies as FP32 pairs (the direct form's combine): the warp sweep
+        auto emit = [&](int s, int t, u64 val) {
+            const int so = flip ? -s : s, to = flip ? -t : t;
+            static_cast<float2*>(out)[f * (int64_t)W * W + (int64_t)(so + wm1) * W + (to + wm1)] = energy_pair(val);
+        };
+        energy_sweep_any(rowE + f * mc, colE + f * nc, tot[f], corners + f * 4 * (size_t)wm1 * wm1, mc, nc, wm1,
+                         esm_raw, emit);
+        return;
+    }
     energy_frame<F32>(rowE + f * mc, colE + f * nc, tot[f], corners + f * 4 * (size_t)wm1 * wm1, mc, nc, wm1,
                       esm_raw, [&](int s, int t, Acc val) {
                           const int so = flip ? -s : s, to = flip ? -t : t;
@@ -714,8 +899,8 @@ k_cols(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv
         }
     }
     __syncthreads();
-    fft4_fwd<N>(buf, LD, nv, tw, tid, nthr);
     if (SPECTRUM) {
+        fft4_fwd<N>(buf, LD, nv, tw, tid, nthr);
         for (int p = tid; p < N; p += nthr) {
             const int skp = sk<N>(p);
 #pragma unroll
@@ -724,21 +909,12 @@ k_cols(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv
         }
         return;
     }
-    for (int p = tid; p < N; p += nthr) {
-        const int skp = sk<N>(p);
-#pragma unroll
-        for (int v8 = 0; v8 < kColsVC; v8 += 8) {
-            float2 b[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                b[u] = v8 + u < nv ? bspec[(int64_t)(v0 + v8 + u) * N + p] : make_float2(0.f, 0.f);
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (v8 + u < nv) buf[(v8 + u) * LD + skp] = cmul(buf[(v8 + u) * LD + skp], b[u]);
-        }
-    }
+    // forward first stage in place (each task reads its comb before writing it)
+    fft4_fwd_stage1_gen<N>([&](int r, int n) { return buf[r * LD + sk<N>(n)]; }, buf, LD, nv, tw, tid, nthr);
     __syncthreads();
-    fft4_inv<N>(buf, LD, nv, tw + N, tid, nthr);
+    // forward second stage, template product and inverse first stage in one pass
+    fft4_fwd2_mul_inv1<N>(buf, LD, nv, bspec + (int64_t)v0 * N, N, tw + N, tid, nthr);
+    fft4_inv_stage2<N>(buf, LD, nv, tid, nthr);
     const int W = 2 * wm1 + 1;
     float2* ys = Y + f * y_fstride + v0;
     for (int task = tid; task < W * kColsVC; task += nthr) {
@@ -809,15 +985,9 @@ k_cols_stream(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, 
             mbar_expect_tx(&bar, bytes);
             bulk_g2s(stg, X + (f + gridDim.y) * x_fstride + (int64_t)v0 * ldx, bytes, &bar);
         }
-        fft4_fwd_stage2<N>(buf, LD, nv, tid, nthr);
-        for (int p = tid; p < N; p += nthr) {
-            const int skp = sk<N>(p);
-#pragma unroll
-            for (int vi = 0; vi < kColsVC; ++vi)
-                if (vi < nv) buf[vi * LD + skp] = cmul(buf[vi * LD + skp], bs[vi * N + p]);
-        }
-        __syncthreads();
-        fft4_inv<N>(buf, LD, nv, tw + N, tid, nthr);
+        // forward second stage, template product and inverse first stage in one pass
+        fft4_fwd2_mul_inv1<N>(buf, LD, nv, bs, N, tw + N, tid, nthr);
+        fft4_inv_stage2<N>(buf, LD, nv, tid, nthr);
         float2* ys = Y + f * y_fstride + v0;
         for (int task = tid; task < W * kColsVC; task += nthr) {
             const int si = task / kColsVC, vi = task % kColsVC;
@@ -877,10 +1047,14 @@ __device__ __forceinline__ void best_merge(Best& a, const Best& o) {
 // Shared memory of k_rows_inv: the transform buffer (later the energies'
 // tables), the inverse roots, h.
 template <int N>
+__host__ __device__ constexpr int rows_inv_threads() {
+    return (kInvPC * (Four<N>::N1 > Four<N>::N2 ? Four<N>::N1 : Four<N>::N2) + 31) / 32 * 32;
+}
+template <int N>
 __host__ __device__ constexpr size_t rows_inv_region(int wm1) {
-    return (sizeof(float2) * kInvPC * fft_ld<N>() > energy_smem(wm1, 8, energy_qp(wm1, 8))
+    return (sizeof(float2) * kInvPC * fft_ld<N>() > energy_sweep_smem(wm1, rows_inv_threads<N>() / 32)
                 ? sizeof(float2) * kInvPC * fft_ld<N>()
-                : (energy_smem(wm1, 8, energy_qp(wm1, 8)) + 15) / 16 * 16);
+                : (energy_sweep_smem(wm1, rows_inv_threads<N>() / 32) + 15) / 16 * 16);
 }
 template <int N>
 __host__ __device__ constexpr size_t rows_inv_smem(int wm1) {
@@ -958,15 +1132,16 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
     b.f1 = INFINITY;
     b.r1 = 0x7fffffff;
     b.f2 = INFINITY;
-    // The frame's energies Sa (exact) straight into the combine; their tables
-    // take the transform buffer's place.
-    energy_frame<false>(rowE + f * mc, colE + f * nc, tot[f], corners + f * 4 * (size_t)wm1 * wm1, mc, nc, wm1,
-                        ism_raw, [&](int s, int t, u64 sa) {
-                            const int k = (s + wm1) * W + (t + wm1);
-                            const float fv = combine_f32(energy_pair(sa), Sb2[k], hbuf[k], ia32[k]);
-                            if (cost) cost[f * WW + k] = (double)fv;
-                            best_push(b, fv, (abs(s) + abs(t)) * WW + k);
-                        });
+    // The frame's energies Sa (exact) straight into the combine; the sweep's
+    // scratch takes the transform buffer's place.
+    auto emit = [&](int s, int t, u64 sa) {
+        const int k = (s + wm1) * W + (t + wm1);
+        const float fv = combine_f32(energy_pair(sa), Sb2[k], hbuf[k], ia32[k]);
+        if (cost) cost[f * WW + k] = f32_to_f64(fv);
+        best_push(b, fv, (abs(s) + abs(t)) * WW + k);
+    };
+    energy_sweep_any(rowE + f * mc, colE + f * nc, tot[f], corners + f * 4 * (size_t)wm1 * wm1, mc, nc, wm1, ism_raw,
+                     emit);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         Best o2;

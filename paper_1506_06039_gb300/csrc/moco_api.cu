@@ -119,7 +119,8 @@ moco_status resolve_shape(const moco_shape& d, ShapePlan& sp) {
     sp.Nr = fft_size_for(sp.mc + d.w - 1);
     sp.Nc = fft_size_for(sp.nc + d.w - 1);
     // (k_rows_inv keeps h, W x W floats, next to a transform buffer)
-    const bool fft_ok = sp.Nr && sp.Nc && rows_inv_smem_bytes(sp.Nc, sp.wm1) <= 227 * 1024;
+    // (and its energy sweep holds at most four columns per lane: w <= 128)
+    const bool fft_ok = sp.Nr && sp.Nc && rows_inv_smem_bytes(sp.Nc, sp.wm1) <= 227 * 1024 && d.w <= 128;
     // (the direct form reads 2x2 sums: at most one level)
     const bool direct_ok = direct_smem(sp.W) <= 227 * 1024 && sp.W <= 256 && sp.levels <= 1;
     sp.nqc = (sp.nc + 63) / 64;

@@ -63,7 +63,8 @@ cudaError_t launch_energy(bool f32, bool out_double, const u64* rowE, const u64*
                           const uint32_t* corners, int64_t nimg, int mc, int nc, int wm1, void* out, int flip,
                           cudaStream_t st) {
     if (nimg <= 0) return cudaSuccess;
-    const size_t smem = energy_smem(wm1, 8, energy_qp(wm1, 8));  // exR, exC, the corner tables (8-byte Acc)
+    // exR, exC and the corner tables (8-byte Acc), or the warp sweep's carries
+    const size_t smem = std::max(energy_smem(wm1, 8, energy_qp(wm1, 8)), energy_sweep_smem(wm1, kEnergyThreads / 32));
     const void* fn = f32 ? (out_double ? (const void*)k_energy<true, true> : (const void*)k_energy<true, false>)
                          : (out_double ? (const void*)k_energy<false, true> : (const void*)k_energy<false, false>);
     cudaError_t e = ensure_smem(fn, smem);

@@ -74,8 +74,7 @@ static cudaError_t rows_inv_n(const float2* Y, int64_t y_fstride, int ncv, int w
     const void* fn = (const void*)k_rows_inv<N>;
     cudaError_t e = ensure_smem(fn, smem);
     if (e != cudaSuccess) return e;
-    int threads = kInvPC * (Four<N>::N1 > Four<N>::N2 ? Four<N>::N1 : Four<N>::N2);
-    threads = (threads + 31) / 32 * 32;
+    const int threads = rows_inv_threads<N>();  // at least four warps (one per corner quadrant)
     k_rows_inv<N><<<(unsigned)nimg, threads, smem, st>>>(Y, y_fstride, ncv, wm1, tw, rowE, colE, tot, corners, mc,
                                                          nc, Sb2, ia32, cost, coarse, fbest, margin);
     return cudaGetLastError();
