@@ -47,6 +47,28 @@ cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg,
                           int n, const u64* bsq, const int32_t* coarse, int32_t* shifts, double* ffinal, u64* acc,
                           unsigned int* ticket, cudaStream_t st);
 
+// One run of one stack's frames for launch_jitter_multi: T frames from
+// `frames` (stride fstride), their searched-grid optima in coarse [T][2]
+// (may equal shifts: each frame's optimum is read before its result is
+// written), results in shifts [T][2] and ffinal [T] (nullable).
+struct JitSegment {
+    const uint16_t* frames;
+    int64_t fstride, T;
+    const uint16_t* tmpl;
+    const u64* bsq;
+    const int32_t* coarse;
+    int32_t* shifts;
+    double* ffinal;
+    int m, n;
+};
+// The refinement of every segment in persistent launches, each of at most
+// kJitSegs segments holding at most `capacity` frames; acc (9 u64 per frame)
+// and ticket (one u32 per frame) are scratch for `capacity` frames, counter
+// one 64-bit word. Every segment needs a b^2 prefix table (bsq) and at most
+// `capacity` frames (cudaErrorInvalidValue otherwise).
+cudaError_t launch_jitter_multi(const JitSegment* segs, int nseg, u64* acc, unsigned int* ticket, int64_t capacity,
+                                unsigned long long* counter, int num_sms, cudaStream_t st);
+
 // More than one level: level-l images (int32 box sums of 2^l x 2^l pixels)
 // and the 3x3 refinement on level l of the doubled level-(l+1) optimum.
 size_t level_image_elems(int m, int n, int l);

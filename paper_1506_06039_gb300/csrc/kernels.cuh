@@ -1568,23 +1568,37 @@ __device__ __forceinline__ int ratio_lt(u64 S1, u64 A1, u64 S2, u64 A2, int* eq)
     return (l_hi < r_hi) || (l_hi == r_hi && l_lo < r_lo);
 }
 
-// bsq: the prefix table of b^2 (TABLE) or nullptr (sum b^2 in the loop).
+// One stack's refinement: its frames, template, b^2 table (TABLE) or nullptr,
+// searched-grid optima in, final shifts (and costs) out, and the per-frame
+// scratch (nine sums and a ticket, zero on entry).
+struct JitParams {
+    const uint16_t* frames;
+    int64_t fstride;
+    const uint16_t* tmpl;
+    const u64* bsq;
+    const int32_t* coarse;
+    int32_t* shifts;
+    double* ffinal;
+    u64* acc;
+    unsigned int* ticket;
+    int m, n, band_rows, ctas;  // ctas: CTAs (band-and-column-group slices) per frame
+};
+
+// The work of one CTA slice `chunk` (of P.ctas) of frame f: its bands' nine
+// partial sums added to the frame's scratch; the frame's last slice to finish
+// (ticket counter) takes the minimum. Every thread of the block calls it.
 template <bool TABLE>
-__global__ void __launch_bounds__(kJitterThreads, TABLE ? 3 : 1)
-k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* __restrict__ tmpl, int m, int n,
-         const u64* __restrict__ bsq, const int32_t* __restrict__ coarse, int32_t* __restrict__ shifts,
-         double* __restrict__ ffinal, u64* __restrict__ acc_g, unsigned int* __restrict__ ticket, int band_rows) {
-    __shared__ u64 red[kJitterThreads / 32][9];
-    __shared__ bool last;
-    extern __shared__ __align__(16) unsigned char jit_smem[];
-    uint4* ring = reinterpret_cast<uint4*>(jit_smem) + threadIdx.x;  // kJitRingBytes
+__device__ __forceinline__ void jitter_slice(const JitParams& P, int64_t f, int chunk, uint4* ring,
+                                             u64 (*red)[9], bool* last) {
+    const int m = P.m, n = P.n, band_rows = P.band_rows;
+    const uint16_t* __restrict__ frames = P.frames;
+    const int64_t fstride = P.fstride;
     const int tid = threadIdx.x;
-    const int64_t f = blockIdx.y;
     // Every candidate needs a non-empty overlap: |2 sc| + 1 < m, |2 tc| + 1 < n
     // (always so for a searched-grid optimum; checked for caller-given ones).
     // A frame outside that range is computed at (0, 0), so every index stays
     // in range, and reported as (INT32_MIN, INT32_MIN).
-    const int sc = coarse[2 * f], tc = coarse[2 * f + 1];
+    const int sc = P.coarse[2 * f], tc = P.coarse[2 * f + 1];
     const bool valid = sc >= -((m - 2) >> 1) && sc <= ((m - 2) >> 1) && tc >= -((n - 2) >> 1) && tc <= ((n - 2) >> 1);
     const int s0 = valid ? 2 * sc : 0, t0 = valid ? 2 * tc : 0;
     u64 X[9];
@@ -1592,14 +1606,14 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     for (int k = 0; k < 9; ++k) X[k] = 0;
     const int G = n / 8;
     const int nb = (m + band_rows - 1) / band_rows;  // band_rows <= kJitRows
-    const int task = blockIdx.x * kJitterThreads + tid;
+    const int task = chunk * kJitterThreads + tid;
     int e_first = 0, e_L = 0;  // this thread's band, for the end-column terms
     uint32_t e_need = 0;
     if (task < G * nb) {
         const int g = task % G, band = task / G;
         JitBand B;
         B.a = frames + f * fstride;
-        B.tmpl = tmpl;
+        B.tmpl = P.tmpl;
         B.m = m;
         B.n = n;
         B.s0 = s0;
@@ -1647,13 +1661,13 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
     if (tid < 9) {
         u64 sum = 0;
         for (int wi = 0; wi < kJitterThreads / 32; ++wi) sum += red[wi][tid];
-        atomicAdd(&acc_g[f * 9 + tid], sum);
+        atomicAdd(&P.acc[f * 9 + tid], sum);
     }
     __threadfence();
     __syncthreads();
-    if (tid == 0) last = (atomicAdd(&ticket[f], 1u) == gridDim.x - 1);
+    if (tid == 0) *last = (atomicAdd(&P.ticket[f], 1u) == (unsigned)P.ctas - 1);
     __syncthreads();
-    if (!last || tid != 0) return;
+    if (!*last || tid != 0) return;
     __threadfence();
     int bk = -1;
     u64 bS = 0, bA = 1;
@@ -1662,8 +1676,8 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
         for (int v = 0; v < 3; ++v) {
             const int s = s0 + u - 1, t = t0 + v - 1;
             const u64 A = (u64)(m - abs(s)) * (u64)(n - abs(t));
-            u64 Sk = atomicAdd(&acc_g[f * 9 + u * 3 + v], 0ull);
-            if (TABLE) Sk += rect_sum(bsq, n, max(0, -s), m - max(0, s), max(0, -t), n - max(0, t));
+            u64 Sk = atomicAdd(&P.acc[f * 9 + u * 3 + v], 0ull);
+            if (TABLE) Sk += rect_sum(P.bsq, n, max(0, -s), m - max(0, s), max(0, -t), n - max(0, t));
             bool take = (bk < 0);
             if (!take) {
                 int eq;
@@ -1676,9 +1690,56 @@ k_jitter(const uint16_t* __restrict__ frames, int64_t fstride, const uint16_t* _
             }
             if (take) { bk = u * 3 + v; bS = Sk; bA = A; bs = s; bt = t; }
         }
-    shifts[2 * f] = valid ? bs : INT32_MIN;
-    shifts[2 * f + 1] = valid ? bt : INT32_MIN;
-    if (ffinal) ffinal[f] = valid ? (double)bS / (double)bA : __longlong_as_double(0x7ff8000000000000ll);
+    P.shifts[2 * f] = valid ? bs : INT32_MIN;
+    P.shifts[2 * f + 1] = valid ? bt : INT32_MIN;
+    if (P.ffinal) P.ffinal[f] = valid ? (double)bS / (double)bA : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// bsq: the prefix table of b^2 (TABLE) or nullptr (sum b^2 in the loop).
+// Grid (CTAs per frame, frames).
+template <bool TABLE>
+__global__ void __launch_bounds__(kJitterThreads, TABLE ? 3 : 1) k_jitter(JitParams P) {
+    __shared__ u64 red[kJitterThreads / 32][9];
+    __shared__ bool last;
+    extern __shared__ __align__(16) unsigned char jit_smem[];
+    uint4* ring = reinterpret_cast<uint4*>(jit_smem) + threadIdx.x;  // kJitRingBytes
+    jitter_slice<TABLE>(P, blockIdx.y, blockIdx.x, ring, red, &last);
+}
+
+// The refinement of several stacks (shapes, templates) in one persistent
+// launch: resident CTAs take (stack, frame, slice) work items in order from a
+// device counter until none is left. Item i belongs to the segment k with
+// item_base[k] <= i < item_base[k + 1] (segment k covers P[k].ctas slices of
+// each of its frames). A segment is a run of one stack's frames; its P
+// pointers are already offset to the run's first frame.
+constexpr int kJitSegs = 40;  // segments per launch (the parameters stay under 4 KiB)
+struct JitBatch {
+    JitParams P[kJitSegs];
+    int64_t item_base[kJitSegs + 1];
+    int nseg;
+};
+static_assert(sizeof(JitBatch) <= 4096, "kernel parameters of k_jitter_multi");
+
+static __global__ void __launch_bounds__(kJitterThreads, 3) k_jitter_multi(const __grid_constant__ JitBatch batch,
+                                                                     unsigned long long* __restrict__ counter) {
+    __shared__ u64 red[kJitterThreads / 32][9];
+    __shared__ bool last;
+    __shared__ long long s_item;
+    extern __shared__ __align__(16) unsigned char jit_smem[];
+    uint4* ring = reinterpret_cast<uint4*>(jit_smem) + threadIdx.x;  // kJitRingBytes
+    const long long total = batch.item_base[batch.nseg];
+    while (true) {
+        __syncthreads();  // the previous item's reads of s_item are done
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long i = s_item;
+        if (i >= total) break;
+        int k = 0;
+        while (k + 1 < batch.nseg && batch.item_base[k + 1] <= i) ++k;
+        const JitParams& P = batch.P[k];
+        const long long local = i - batch.item_base[k];
+        jitter_slice<true>(P, local / P.ctas, (int)(local % P.ctas), ring, red, &last);
+    }
 }
 
 // Prefix table of b^2 for k_jitter, P[(m+1) x (n+1)] (exact u64), in two

@@ -307,10 +307,12 @@ moco_status prepare_template(ShapePlan& sp, const void* tmpl_dev, cudaStream_t s
 }
 
 // The searched-grid pass over frames [f0, f0+g) staged at `frames`:
-// energies, cross term, combine, argmin -> sp.coarse (and optional outputs).
+// energies, cross term, combine, argmin -> coarse_out, or sp.coarse when
+// null (and optional outputs).
 moco_status search_group(ShapePlan& sp, const uint16_t* frames, int64_t g, double* cost, double* fbest,
-                         float* margin, cudaStream_t st) {
+                         float* margin, cudaStream_t st, int32_t* coarse_out = nullptr) {
     const int m = sp.desc.m, n = sp.desc.n;
+    int32_t* coarse = coarse_out ? coarse_out : sp.coarse;
     Profiler& P = *sp.prof;
     if (sp.form == MOCO_XCORR_DIRECT_BF16X3) {
         P.begin(K_FRAME_ROWS, st);
@@ -329,7 +331,7 @@ moco_status search_group(ShapePlan& sp, const uint16_t* frames, int64_t g, doubl
         P.end(st);
         if (e != cudaSuccess) return cuda_fail(e, "k_direct");
         P.begin(K_ROWS_INV, st);
-        e = launch_combine_h(sp.hbuf, g, sp.wm1, reinterpret_cast<const float2*>(sp.Sa), sp.Sb2, sp.ia32, cost, sp.coarse,
+        e = launch_combine_h(sp.hbuf, g, sp.wm1, reinterpret_cast<const float2*>(sp.Sa), sp.Sb2, sp.ia32, cost, coarse,
                              fbest ? fbest : sp.fbest, margin ? margin : sp.margin, st);
         P.end(st);
         if (e != cudaSuccess) return cuda_fail(e, "k_combine_h");
@@ -348,7 +350,7 @@ moco_status search_group(ShapePlan& sp, const uint16_t* frames, int64_t g, doubl
     if (e != cudaSuccess) return cuda_fail(e, "k_cols");
     P.begin(K_ROWS_INV, st);
     e = launch_rows_inv(sp.Nc, sp.Y, sp.y_fstride, sp.ncv, sp.wm1, g, sp.twc, sp.rowE, sp.colE, sp.tot, sp.corners,
-                        sp.mc, sp.nc, sp.Sb2, sp.ia32, cost, sp.coarse, fbest ? fbest : sp.fbest,
+                        sp.mc, sp.nc, sp.Sb2, sp.ia32, cost, coarse, fbest ? fbest : sp.fbest,
                         margin ? margin : sp.margin, st);
     P.end(st);
     if (e != cudaSuccess) return cuda_fail(e, "k_rows_inv");
@@ -462,6 +464,7 @@ moco_status moco_plan_destroy(moco_plan_t plan) {
     for (auto& sp : plan->shapes)
         if (sp.base) cudaFree(sp.base);
     if (plan->scratch) cudaFree(plan->scratch);
+    if (plan->mj_base) cudaFree(plan->mj_base);
     if (plan->aux) cudaStreamDestroy(plan->aux);
     for (auto& ev : plan->prof.pool) cudaEventDestroy(ev);
     for (auto& ev : plan->ev)
@@ -501,6 +504,26 @@ moco_status moco_plan(const moco_shape* shapes, int32_t nshapes, const void* con
     }
     for (int k = 0; k < nshapes && s == MOCO_OK; ++k) s = prepare_template(plan->shapes[k], templates_dev[k], st);
     for (int k = 0; k < nshapes && s == MOCO_OK; ++k) s = autotune(plan->shapes[k], st);
+    if (s == MOCO_OK) {
+        // Scratch of the several-stack refinement (nine sums and a ticket per
+        // frame of one launch) and the SM count its persistent launch fills.
+        const size_t mj = align_up(sizeof(u64) * 9 * kMultiJitFrames, 256) +
+                          align_up(sizeof(unsigned int) * kMultiJitFrames, 256) + 256;
+        cudaError_t e = cudaMalloc(&plan->mj_base, mj);
+        if (e != cudaSuccess) {
+            plan->mj_base = nullptr;
+            cudaGetLastError();
+            s = fail(MOCO_ERR_OOM, "cudaMalloc of the refinement scratch failed");
+        } else {
+            char* b = static_cast<char*>(plan->mj_base);
+            plan->mj_acc = reinterpret_cast<u64*>(b);
+            plan->mj_ticket = reinterpret_cast<unsigned int*>(b + align_up(sizeof(u64) * 9 * kMultiJitFrames, 256));
+            plan->mj_counter = reinterpret_cast<unsigned long long*>(
+                b + align_up(sizeof(u64) * 9 * kMultiJitFrames, 256) + align_up(sizeof(unsigned int) * kMultiJitFrames, 256));
+            e = cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device);
+            if (e != cudaSuccess) s = cuda_fail(e, "device query");
+        }
+    }
     if (s == MOCO_OK) {
         cudaError_t e = cudaStreamCreateWithFlags(&plan->aux, cudaStreamNonBlocking);
         for (auto& ev : plan->ev)
@@ -558,12 +581,57 @@ moco_status moco_align_stack(moco_plan_t plan, const moco_stack* stacks, int32_t
     }
     DeviceGuard guard(plan->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Stacks searched on one 2x2 level and refined at full resolution (the
+    // paper's rule above 256x256): with two or more of them, every stack's
+    // search runs first, writing its searched-grid optima into the caller's
+    // shift buffer, then one persistent refinement launch takes (stack,
+    // frame, slice) items of all of them until none is left.
+    auto deferred = [&](const moco_stack& s) {
+        const ShapePlan& sp = plan->shapes[s.shape_idx];
+        return s.T > 0 && sp.levels == 1 && sp.bsq != nullptr;
+    };
+    int ndef = 0;
+    for (int k = 0; k < nstacks; ++k) ndef += deferred(stacks[k]) ? 1 : 0;
+    std::vector<JitSegment> segs;
     for (int k = 0; k < nstacks; ++k) {
         const moco_stack& s = stacks[k];
         if (s.T == 0) continue;
-        moco_status r = align_frames(plan->shapes[s.shape_idx], s.frames_dev, s.T, s.shifts_dev, s.best_cost_dev,
-                                     s.margin_dev, s.final_cost_dev, st);
-        if (r != MOCO_OK) return r;
+        ShapePlan& sp = plan->shapes[s.shape_idx];
+        if (ndef < 2 || !deferred(s)) {
+            moco_status r = align_frames(sp, s.frames_dev, s.T, s.shifts_dev, s.best_cost_dev, s.margin_dev,
+                                         s.final_cost_dev, st);
+            if (r != MOCO_OK) return r;
+            continue;
+        }
+        const int64_t mn = (int64_t)sp.desc.m * sp.desc.n;
+        for (int64_t f0 = 0; f0 < s.T; f0 += sp.group) {
+            const int64_t g = std::min<int64_t>(sp.group, s.T - f0);
+            moco_status r = search_group(sp, s.frames_dev + f0 * mn, g, nullptr,
+                                         s.best_cost_dev ? s.best_cost_dev + f0 : nullptr,
+                                         s.margin_dev ? s.margin_dev + f0 : nullptr, st, s.shifts_dev + 2 * f0);
+            if (r != MOCO_OK) return r;
+        }
+        for (int64_t f0 = 0; f0 < s.T; f0 += kMultiJitFrames) {
+            JitSegment g;
+            g.frames = s.frames_dev + f0 * mn;
+            g.fstride = mn;
+            g.T = std::min<int64_t>(kMultiJitFrames, s.T - f0);
+            g.tmpl = static_cast<const uint16_t*>(sp.tmpl);
+            g.bsq = sp.bsq;
+            g.coarse = s.shifts_dev + 2 * f0;  // read before each frame's result overwrites it
+            g.shifts = s.shifts_dev + 2 * f0;
+            g.ffinal = s.final_cost_dev ? s.final_cost_dev + f0 : nullptr;
+            g.m = sp.desc.m;
+            g.n = sp.desc.n;
+            segs.push_back(g);
+        }
+    }
+    if (!segs.empty()) {
+        plan->prof.begin(K_JITTER, st);
+        cudaError_t e = launch_jitter_multi(segs.data(), (int)segs.size(), plan->mj_acc, plan->mj_ticket,
+                                            kMultiJitFrames, plan->mj_counter, plan->num_sms, st);
+        plan->prof.end(st);
+        if (e != cudaSuccess) return cuda_fail(e, "k_jitter_multi");
     }
     return MOCO_OK;
 }

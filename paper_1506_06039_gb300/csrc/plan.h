@@ -99,6 +99,8 @@ struct ShapePlan {
     Profiler* prof = nullptr;  // the owning plan's profiler
 };
 
+constexpr int64_t kMultiJitFrames = 32768;  // frames per launch of the several-stack refinement
+
 struct DeviceGuard {
     explicit DeviceGuard(int dev);
     ~DeviceGuard();
@@ -118,4 +120,10 @@ struct moco_plan_s {
     moco::Profiler prof;
     void* scratch = nullptr;  // per-batch scratch shared by all shapes
     size_t scratch_bytes = 0;
+    // the several-stack refinement (moco_align_stack): kMultiJitFrames frames per launch
+    void* mj_base = nullptr;
+    moco::u64* mj_acc = nullptr;
+    unsigned int* mj_ticket = nullptr;
+    unsigned long long* mj_counter = nullptr;
+    int num_sms = 0;
 };

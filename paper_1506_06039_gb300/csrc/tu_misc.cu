@@ -92,6 +92,17 @@ cudaError_t launch_pair_from_double(const double* x, float2* out, int64_t count,
     return cudaGetLastError();
 }
 
+// Slices of kJitterThreads threads per frame, and the band height: bands of
+// kJitRows rows; a small batch (fewer CTAs than two waves of 152 SMs) takes
+// bands of 16 or 8 rows so that more CTAs share a frame.
+static void jitter_shape(int m, int n, int64_t nimg, int* band_rows, int* ctas) {
+    int br = kJitRows;
+    auto ctas_for = [&](int b) { return ((n / 8) * ((m + b - 1) / b) + kJitterThreads - 1) / kJitterThreads; };
+    while (br > 8 && (int64_t)ctas_for(br) * nimg < 2 * 152) br /= 2;
+    *band_rows = br;
+    *ctas = ctas_for(br);
+}
+
 cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg, const uint16_t* tmpl, int m,
                           int n, const u64* bsq, const int32_t* coarse, int32_t* shifts, double* ffinal, u64* acc,
                           unsigned int* ticket, cudaStream_t st) {
@@ -99,23 +110,75 @@ cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg,
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(u64) * 9 * nimg, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int) * nimg, st);
     if (e != cudaSuccess) return e;
-    // Bands of kJitRows rows; a small batch (fewer CTAs than two waves of
-    // 152 SMs) takes bands of 16 or 8 rows so that more CTAs share a frame.
-    int band_rows = kJitRows;
-    auto ctas_for = [&](int br) { return ((n / 8) * ((m + br - 1) / br) + kJitterThreads - 1) / kJitterThreads; };
-    while (band_rows > 8 && (int64_t)ctas_for(band_rows) * nimg < 2 * 152) band_rows /= 2;
-    const int ctas = ctas_for(band_rows);
-    dim3 grid((unsigned)ctas, (unsigned)nimg);
+    JitParams P;
+    P.frames = frames;
+    P.fstride = fstride;
+    P.tmpl = tmpl;
+    P.bsq = bsq;
+    P.coarse = coarse;
+    P.shifts = shifts;
+    P.ffinal = ffinal;
+    P.acc = acc;
+    P.ticket = ticket;
+    P.m = m;
+    P.n = n;
+    jitter_shape(m, n, nimg, &P.band_rows, &P.ctas);
+    dim3 grid((unsigned)P.ctas, (unsigned)nimg);
     const void* fn = bsq ? reinterpret_cast<const void*>(k_jitter<true>) : reinterpret_cast<const void*>(k_jitter<false>);
     e = ensure_smem(fn, kJitRingBytes);
     if (e != cudaSuccess) return e;
-    if (bsq)
-        k_jitter<true><<<grid, kJitterThreads, kJitRingBytes, st>>>(frames, fstride, tmpl, m, n, bsq, coarse, shifts,
-                                                                    ffinal, acc, ticket, band_rows);
-    else
-        k_jitter<false><<<grid, kJitterThreads, kJitRingBytes, st>>>(frames, fstride, tmpl, m, n, nullptr, coarse,
-                                                                     shifts, ffinal, acc, ticket, band_rows);
+    if (bsq) k_jitter<true><<<grid, kJitterThreads, kJitRingBytes, st>>>(P);
+    else k_jitter<false><<<grid, kJitterThreads, kJitRingBytes, st>>>(P);
     return cudaGetLastError();
+}
+
+cudaError_t launch_jitter_multi(const JitSegment* segs, int nseg, u64* acc, unsigned int* ticket, int64_t capacity,
+                                unsigned long long* counter, int num_sms, cudaStream_t st) {
+    int k0 = 0;
+    while (k0 < nseg) {
+        // The next launch: up to kJitSegs segments whose frames fit the scratch.
+        JitBatch batch;
+        int ns = 0;
+        int64_t frames = 0, items = 0;
+        while (k0 + ns < nseg && ns < kJitSegs) {
+            const JitSegment& g = segs[k0 + ns];
+            if (g.T > capacity) return cudaErrorInvalidValue;
+            if (frames + g.T > capacity) break;
+            JitParams& P = batch.P[ns];
+            P.frames = g.frames;
+            P.fstride = g.fstride;
+            P.tmpl = g.tmpl;
+            P.bsq = g.bsq;
+            P.coarse = g.coarse;
+            P.shifts = g.shifts;
+            P.ffinal = g.ffinal;
+            P.acc = acc + 9 * frames;
+            P.ticket = ticket + frames;
+            P.m = g.m;
+            P.n = g.n;
+            // bands sized for a launch that spreads over every SM
+            jitter_shape(g.m, g.n, 1 << 20, &P.band_rows, &P.ctas);
+            batch.item_base[ns] = items;
+            items += g.T * P.ctas;
+            frames += g.T;
+            ++ns;
+        }
+        batch.nseg = ns;
+        batch.item_base[ns] = items;
+        k0 += ns;
+        if (items == 0) continue;
+        cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(u64) * 9 * frames, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int) * frames, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) e = ensure_smem(reinterpret_cast<const void*>(k_jitter_multi), kJitRingBytes);
+        if (e != cudaSuccess) return e;
+        const int64_t resident = (int64_t)num_sms * 3;  // three CTAs per SM (__launch_bounds__)
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(resident, items));
+        k_jitter_multi<<<grid, kJitterThreads, kJitRingBytes, st>>>(batch, counter);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_sq_prefix(const uint16_t* tmpl, int m, int n, u64* P, cudaStream_t st) {

@@ -75,3 +75,55 @@ def test_mixed_batch_from_captured_graph(batch):
         torch.cuda.synchronize()
         for k in range(len(stacks)):
             assert np.array_equal(outs[k].cpu().numpy(), eager[k]), k
+
+
+def all_outputs(plan, items):
+    """One moco_align_stack call over `items` [(shape_idx, frames)] with every
+    output requested; returns numpy (shifts, best, margin, final) per item."""
+    outs = []
+    for k, fr in items:
+        T = fr.shape[0]
+        outs.append(dict(shape_idx=k, frames=fr, shifts=torch.empty((T, 2), dtype=torch.int32, device="cuda"),
+                         best_cost=torch.empty(T, dtype=torch.float64, device="cuda"),
+                         margin=torch.empty(T, dtype=torch.float32, device="cuda"),
+                         final_cost=torch.empty(T, dtype=torch.float64, device="cuda")))
+    moco_align_stack(plan.handle, outs)
+    torch.cuda.synchronize()
+    return [tuple(o[key].cpu().numpy() for key in ("shifts", "best_cost", "margin", "final_cost")) for o in outs]
+
+
+def test_several_stacks_equal_one_stack_at_a_time(batch):
+    # Several stacks with a level take the persistent several-stack refinement
+    # (their optima parked in the shift buffers); alone, each takes the
+    # one-stack path. Every output must be identical.
+    plan, stacks = batch
+    together = all_outputs(plan, [(k, st.frames) for k, (st, _) in enumerate(stacks)])
+    for k, (st, _) in enumerate(stacks):
+        alone = all_outputs(plan, [(k, st.frames)])[0]
+        for a, b in zip(together[k], alone):
+            assert np.array_equal(a, b), k
+
+
+def test_several_stacks_beyond_one_refinement_launch():
+    # 33000 frames of 16 x 16 with one level (more than the 32768 frames one
+    # refinement launch holds) next to a 272 x 264 stack: the refinement is
+    # split over launches; results equal the one-stack path and the oracle.
+    build.build()
+    big = synth.make_stack_np(16, 16, 33000, 2, 2, seed=91, template="clean")
+    small = synth.make_stack_np(272, 264, 9, 40, 6, seed=92, template="clean")
+    plan = Plan([dict(m=16, n=16, w=2, levels=1), dict(m=272, n=264, w=5)],
+                [torch.from_numpy(big.template).cuda(), torch.from_numpy(small.template).cuda()])
+    try:
+        fb, fs = torch.from_numpy(big.frames).cuda(), torch.from_numpy(small.frames).cuda()
+        together = all_outputs(plan, [(0, fb), (1, fs)])
+        alone = [all_outputs(plan, [(0, fb)])[0], all_outputs(plan, [(1, fs)])[0]]
+        plan.status()
+    finally:
+        plan.close()
+    for t, a in zip(together, alone):
+        for x, y in zip(t, a):
+            assert np.array_equal(x, y)
+    pick = np.random.default_rng(3).choice(33000, 64, replace=False)
+    pick = np.concatenate([pick, [32767, 32768, 32999]])  # around the launch boundary
+    check_align(big.frames[pick], big.template, 2, 1, together[0][0][pick])
+    check_align(small.frames, small.template, 5, -1, together[1][0])
