@@ -161,9 +161,13 @@ __device__ __forceinline__ void drain_acc(uint32_t addr, int N, float (&hsum)[kD
 
 // ---- the GEMM ----------------------------------------------------------------
 //
-// Grid (N tiles, M tiles). N tile j covers shift rows s = -(w-1) + j*NS ..
-// (NS = 256 / Wp of them, Wp = W rounded up to 16); M tile covers frames
-// f0 .. f0 + 127. Output h[f][(s+w-1)*W + (t+w-1)] (FP32).
+// Grid (N tiles, M tiles, K splits). N tile j covers shift rows s = -(w-1) +
+// j*NS .. (NS = 128 / Wp of them, Wp = W rounded up to 16); M tile covers
+// frames f0 .. f0 + 127; K split z covers K steps [z K / Z, (z+1) K / Z)
+// (K = mc * nqc, Z = gridDim.z) and writes its partial sum to
+// h[z][f][(s+w-1)*W + (t+w-1)] (FP32, z-th slab of T * W * W), which the
+// combine adds up in order of z. Splitting K keeps every SM busy when the
+// window is small (few N tiles) or the batch short (few M tiles).
 // tmap_hi / tmap_lo: the frame planes [T][mc][ncp] BF16 as 3-D tensors
 // (x = column, y = row, z = frame), box 64 x 1 x 128, 128-byte swizzle.
 static __global__ void __launch_bounds__(kDirThreads, 1)
@@ -181,7 +185,10 @@ k_direct(const __grid_constant__ CUtensorMap tmap_hi, const __grid_constant__ CU
     const int tid = threadIdx.x, warp = tid >> 5;
     const int s_first = -wm1 + (int)blockIdx.x * NS;
     const int64_t f0 = (int64_t)blockIdx.y * kDirM;
-    const int ksteps = mc * nqc;
+    const int kall = mc * nqc;
+    const int kb = (int)((int64_t)blockIdx.z * kall / gridDim.z);
+    const int ksteps = (int)((int64_t)(blockIdx.z + 1) * kall / gridDim.z) - kb;  // this split's K steps
+    h += (int64_t)blockIdx.z * T * W * W;
     const uint32_t idesc = direct_idesc(kDirM, N);
     const size_t plane_tiles = (size_t)mc * nqc * tb;
     constexpr uint32_t kTmemCols = 2 * kDirNmax;  // two accumulators
@@ -211,7 +218,7 @@ k_direct(const __grid_constant__ CUtensorMap tmap_hi, const __grid_constant__ CU
     // Copies of K step k into stage st: A tiles by TMA, B tiles by bulk copies
     // (one thread), out-of-window B tiles zeroed by all threads.
     auto issue = [&](int k, int st) {
-        const int p = k / nqc, qc = k - p * nqc;
+        const int p = (kb + k) / nqc, qc = (kb + k) - p * nqc;
         // Tiles of shift rows that fall outside the window or the template: zeros.
         for (int sl = 0; sl < NS; ++sl) {
             const int s = s_first + sl, r = p - s;
@@ -352,10 +359,11 @@ __global__ void k_coarse_image(const void* __restrict__ src, int m, int n, int l
 
 // f = (Sa + Sb - 2 h) / Area * unit with the argmin and margin, from an h
 // computed by the direct form. One CTA per frame.
+// h is the sum, in order, of nsplit partial slabs of slab elements each.
 static __global__ void __launch_bounds__(256)
-k_combine_h(const float* __restrict__ hh, int wm1, const float2* __restrict__ Sa2, const float2* __restrict__ Sb2,
-            const float* __restrict__ ia32, double* __restrict__ cost, int32_t* __restrict__ coarse,
-            double* __restrict__ fbest, float* __restrict__ margin) {
+k_combine_h(const float* __restrict__ hh, int nsplit, int64_t slab, int wm1, const float2* __restrict__ Sa2,
+            const float2* __restrict__ Sb2, const float* __restrict__ ia32, double* __restrict__ cost,
+            int32_t* __restrict__ coarse, double* __restrict__ fbest, float* __restrict__ margin) {
     __shared__ Best red[8];
     const int W = 2 * wm1 + 1, WW = W * W;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -366,7 +374,9 @@ k_combine_h(const float* __restrict__ hh, int wm1, const float2* __restrict__ Sa
     b.f2 = INFINITY;
     for (int k = tid; k < WW; k += nthr) {
         const int s = k / W - wm1, t = k % W - wm1;
-        const float fv = combine_f32(Sa2[f * WW + k], Sb2[k], hh[f * WW + k], ia32[k]);
+        float hv = hh[f * WW + k];
+        for (int z = 1; z < nsplit; ++z) hv += hh[z * slab + f * WW + k];
+        const float fv = combine_f32(Sa2[f * WW + k], Sb2[k], hv, ia32[k]);
         if (cost) cost[f * WW + k] = f32_to_f64(fv);
         best_push(b, fv, (abs(s) + abs(t)) * WW + k);
     }

@@ -190,9 +190,20 @@ MOCO_FOUR(576, 16, 36)
 // Shared-memory slot of logical position p in a row: with an even N2 one
 // spare slot follows every N2 positions, so that the second stage's
 // contiguous N2-blocks (one per thread) start on different banks.
+// Row stride ROW: the first forward and second inverse stages run N2 tasks
+// per row along the row, so a half-warp (16 complex values, 128 bytes)
+// straddles two rows; a stride congruent to N2 modulo 16 complex values
+// makes consecutive tasks land on consecutive bank pairs across the row
+// boundary (N1 = 16 sizes whose N2 is not a multiple of 16). Otherwise one
+// more than the skewed length (odd: row-strided reads stay conflict-free).
 template <int N>
 struct Skew {
-    enum { S = (Four<N>::N2 % 2 == 0) ? 1 : 0, ROW = N + S * Four<N>::N1 + 1 };
+    enum {
+        S = (Four<N>::N2 % 2 == 0) ? 1 : 0,
+        BASE = N + S * Four<N>::N1,
+        ROW = (Four<N>::N1 == 16 && Four<N>::N2 % 16 != 0) ? BASE + ((Four<N>::N2 - BASE) % 16 + 16) % 16
+                                                           : BASE + 1
+    };
 };
 template <int N>
 __device__ __forceinline__ int sk(int p) {

@@ -130,9 +130,13 @@ cudaError_t launch_frame_planes(bool f32, const void* src, int64_t src_fstride, 
                                 int ldp, cudaStream_t st);
 cudaError_t launch_toeplitz(bool f32, const void* tmpl, int m, int n, int levels, int mc, int nc, int nqc, int wm1,
                             const int32_t* coff_i, const float* coff_f, float* bprime, void* tiles, cudaStream_t st);
+// K splits of one direct-form launch (1 .. kDirSplitMax): each writes a
+// partial h slab of T * W * W floats, which launch_combine_h adds in order.
+constexpr int kDirSplits = 8;
+int direct_ksplit(int W, int64_t T, int mc, int nqc, int num_sms);
 cudaError_t launch_direct(const void* a_hi, const void* a_lo, int64_t T, int mc, int ncp, int nqc, int wm1,
-                          const void* tiles, float* h, unsigned int* err, cudaStream_t st);
-cudaError_t launch_combine_h(const float* h, int64_t nimg, int wm1, const float2* Sa2, const float2* Sb2,
+                          const void* tiles, float* h, int ksplit, unsigned int* err, cudaStream_t st);
+cudaError_t launch_combine_h(const float* h, int ksplit, int64_t nimg, int wm1, const float2* Sa2, const float2* Sb2,
                              const float* ia32, double* cost, int32_t* coarse, double* fbest, float* margin,
                              cudaStream_t st);
 

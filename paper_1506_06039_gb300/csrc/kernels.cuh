@@ -934,20 +934,32 @@ k_cols(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv
 // as soon as the previous frame's first transform stage has read the buffer,
 // so the copy runs under the rest of that frame's transforms. The bounded
 // wait on the copy sets *err and ends the CTA (after the copy in flight).
+// Row stride of the staging buffer (complex values): ldx, padded so that it
+// is congruent to N2 modulo 16 (the first stage reads N2 tasks per row along
+// the row, see Skew) when the padding keeps every row 16-byte aligned.
+template <int N>
+__host__ __device__ constexpr int cols_stage_ld(int ldx) {
+    const int pad = ((Four<N>::N2 - ldx) % 16 + 16) % 16;
+    return ldx + (pad % 2 == 0 ? pad : 0);
+}
 template <int N>
 __host__ __device__ constexpr size_t cols_stream_smem(int ldx) {
-    return sizeof(float2) * ((size_t)kColsVC * ldx + (size_t)kColsVC * fft_ld<N>() + (size_t)kColsVC * N + 2 * N);
+    return sizeof(float2) *
+           ((size_t)kColsVC * cols_stage_ld<N>(ldx) + (size_t)kColsVC * fft_ld<N>() + (size_t)kColsVC * N + 2 * N);
 }
 
+// (two CTAs per SM for the transforms of up to 320 points; one beyond, where
+// shared memory holds one anyway, so the codelets keep their registers)
 template <int N>
-__global__ void __launch_bounds__(cols_threads<N>(), 2)
+__global__ void __launch_bounds__(cols_threads<N>(), cols_threads<N>() <= 320 ? 2 : 1)
 k_cols_stream(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, int ncv, int64_t T,
               const float2* __restrict__ tw_g, const float2* __restrict__ bspec, float2* __restrict__ Y,
               int64_t y_fstride, int wm1, unsigned int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int LD = fft_ld<N>();
-    float2* stg = reinterpret_cast<float2*>(smem_raw);  // kColsVC x ldx: the frame's block (ldx even)
-    float2* buf = stg + kColsVC * ldx;                   // kColsVC x LD
+    const int SL = cols_stage_ld<N>(ldx);              // staging row stride (even: rows 16-byte aligned)
+    float2* stg = reinterpret_cast<float2*>(smem_raw);  // kColsVC x SL: the frame's block, one row per column
+    float2* buf = stg + kColsVC * SL;                    // kColsVC x LD
     float2* bs = buf + kColsVC * LD;                     // kColsVC x N: template spectrum, forward output layout
     float2* tw = bs + kColsVC * N;                       // 2N: forward, then inverse table
     __shared__ __align__(8) uint64_t bar;
@@ -955,16 +967,22 @@ k_cols_stream(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, 
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int v0 = (int)((int64_t)blockIdx.x * ncv / gridDim.x);
     const int nv = (int)((int64_t)(blockIdx.x + 1) * ncv / gridDim.x) - v0;  // <= kColsVC (host)
-    const uint32_t bytes = (uint32_t)(sizeof(float2) * nv * ldx);
+    const uint32_t row_bytes = (uint32_t)(sizeof(float2) * ldx);
     const int W = 2 * wm1 + 1;
+    // The frame's rows v0 .. v0 + nv - 1 of X (contiguous in global memory)
+    // into the staging rows, one bulk copy per row (one thread).
+    auto issue = [&](int64_t fr) {
+        mbar_expect_tx(&bar, row_bytes * (uint32_t)nv);
+        const float2* g = X + fr * x_fstride + (int64_t)v0 * ldx;
+        for (int vi = 0; vi < nv; ++vi) bulk_g2s(stg + vi * SL, g + (int64_t)vi * ldx, row_bytes, &bar);
+    };
     int64_t f = blockIdx.y;
     if (f >= T) return;  // the same for the whole CTA
     if (tid == 0) {
         mbar_init(&bar, 1);
         s_abort = 0;
         fence_async_smem();
-        mbar_expect_tx(&bar, bytes);
-        bulk_g2s(stg, X + f * x_fstride + (int64_t)v0 * ldx, bytes, &bar);
+        issue(f);
     }
     for (int i = tid; i < 2 * N; i += nthr) tw[i] = tw_g[i];
     for (int i = tid; i < nv * N; i += nthr) bs[i] = bspec[(int64_t)v0 * N + i];
@@ -978,12 +996,11 @@ k_cols_stream(const float2* __restrict__ X, int64_t x_fstride, int ldx, int mc, 
             return;
         }
         phase ^= 1u;
-        fft4_fwd_stage1_from<N>(stg, ldx, mc, buf, LD, nv, tw, tid, nthr);
+        fft4_fwd_stage1_from<N>(stg, SL, mc, buf, LD, nv, tw, tid, nthr);
         __syncthreads();
         if (tid == 0 && f + gridDim.y < T) {
             fence_async_smem();  // this frame's reads of the staging buffer come before the next copy
-            mbar_expect_tx(&bar, bytes);
-            bulk_g2s(stg, X + (f + gridDim.y) * x_fstride + (int64_t)v0 * ldx, bytes, &bar);
+            issue(f + gridDim.y);
         }
         // forward second stage, template product and inverse first stage in one pass
         fft4_fwd2_mul_inv1<N>(buf, LD, nv, bs, N, tw + N, tid, nthr);

@@ -82,7 +82,7 @@ int64_t per_frame_scratch_bytes(const ShapePlan& sp) {
     int64_t b = 0;
     // The two forms' cross-term scratch is never live at once: one region.
     const int64_t fft = sp.has_fft ? (int64_t)sp.ncv * sp.ldx * 8 + W * sp.ncv * 8 : 0;  // X, Y
-    const int64_t dir = sp.has_direct ? (int64_t)sp.mc * sp.ncp * 4 + W * W * 4 : 0;     // planes, h
+    const int64_t dir = sp.has_direct ? (int64_t)sp.mc * sp.ncp * 4 + W * W * 4 * kDirSplits : 0;  // planes, h slabs
     b += std::max(fft, dir);
     b += ((int64_t)sp.mc + sp.nc + 1) * 8;     // rowE, colE, tot
     b += 4 * wm1 * wm1 * 4;                    // corners
@@ -104,6 +104,14 @@ moco_status resolve_shape(const moco_shape& d, ShapePlan& sp) {
         return fail(MOCO_ERR_INVALID_ARG, "bad xcorr");
     if (d.group_frames < 0) return fail(MOCO_ERR_INVALID_ARG, "group_frames must be >= 0");
     sp.desc = d;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sp.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MOCO_ERR_CUDA, "device query");
+        }
+    }
     sp.levels = d.levels < 0 ? ((d.m > 256 || d.n > 256) ? 1 : 0) : d.levels;
     sp.f32 = d.template_dtype == MOCO_TEMPLATE_F32;
     if (sp.f32 && sp.levels != 0)
@@ -227,7 +235,7 @@ size_t bind_scratch(ShapePlan& sp, void* base) {
     const size_t fft_x = sp.has_fft ? (size_t)(G * sp.x_fstride * 8) : 0;
     const size_t fft_y = sp.has_fft ? (size_t)(G * sp.y_fstride * 8) : 0;
     const size_t dir_p = sp.has_direct ? (size_t)(G * sp.mc * sp.ncp * 2) : 0;
-    const size_t dir_h = sp.has_direct ? (size_t)(G * W * W * 4) : 0;
+    const size_t dir_h = sp.has_direct ? (size_t)(G * W * W * 4 * kDirSplits) : 0;  // one h slab per K split
     const size_t fft_total = align_up(fft_x, 256) + fft_y;
     const size_t dir_total = 2 * align_up(dir_p, 256) + dir_h;
     void* xregion = nullptr;
@@ -326,12 +334,13 @@ moco_status search_group(ShapePlan& sp, const uint16_t* frames, int64_t g, doubl
         P.end(st);
         if (e != cudaSuccess) return cuda_fail(e, "k_energy");
         P.begin(K_DIRECT, st);
-        e = launch_direct(sp.planes_hi, sp.planes_lo, g, sp.mc, sp.ncp, sp.nqc, sp.wm1, sp.dtiles, sp.hbuf, sp.dev_err,
+        const int ksplit = direct_ksplit(sp.W, g, sp.mc, sp.nqc, sp.num_sms);
+        e = launch_direct(sp.planes_hi, sp.planes_lo, g, sp.mc, sp.ncp, sp.nqc, sp.wm1, sp.dtiles, sp.hbuf, ksplit, sp.dev_err,
                           st);
         P.end(st);
         if (e != cudaSuccess) return cuda_fail(e, "k_direct");
         P.begin(K_ROWS_INV, st);
-        e = launch_combine_h(sp.hbuf, g, sp.wm1, reinterpret_cast<const float2*>(sp.Sa), sp.Sb2, sp.ia32, cost, coarse,
+        e = launch_combine_h(sp.hbuf, ksplit, g, sp.wm1, reinterpret_cast<const float2*>(sp.Sa), sp.Sb2, sp.ia32, cost, coarse,
                              fbest ? fbest : sp.fbest, margin ? margin : sp.margin, st);
         P.end(st);
         if (e != cudaSuccess) return cuda_fail(e, "k_combine_h");
@@ -396,16 +405,32 @@ moco_status align_frames(ShapePlan& sp, const uint16_t* frames, int64_t T, int32
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-// MOCO_XCORR_AUTO: time both forms on one batch (zero frames in the staging
-// buffer: the work does not depend on the values) and keep the faster.
+// MOCO_XCORR_AUTO: time both forms on one batch of zero frames (the work
+// does not depend on the values) and keep the faster. The batch is as long
+// as the plan's internal batch, up to 512 MiB of frames (a short one would
+// time both forms far from their steady state: too few frame tiles for the
+// direct form, too few frames per column CTA for the FFT form), in a
+// buffer freed before returning; if that allocation fails, the host staging
+// buffer's frames.
 moco_status autotune(ShapePlan& sp, cudaStream_t st) {
     if (!(sp.has_fft && sp.has_direct)) {
         sp.tuned = true;
         return MOCO_OK;
     }
-    const int64_t g = std::min<int64_t>(sp.stage_frames, sp.group);
-    cudaError_t e = cudaMemsetAsync(sp.stage[0], 0, (size_t)(g * sp.desc.m * sp.desc.n * 2), st);
-    if (e != cudaSuccess) return cuda_fail(e, "autotune clear");
+    const int64_t fbytes = (int64_t)sp.desc.m * sp.desc.n * 2;
+    int64_t g = std::min<int64_t>(sp.group, std::max<int64_t>(sp.stage_frames, (512ll << 20) / fbytes));
+    void* tune = nullptr;
+    if (cudaMalloc(&tune, (size_t)(g * fbytes)) != cudaSuccess) {
+        cudaGetLastError();
+        tune = nullptr;
+        g = std::min<int64_t>(sp.stage_frames, sp.group);
+    }
+    const uint16_t* frames = tune ? static_cast<const uint16_t*>(tune) : sp.stage[0];
+    cudaError_t e = cudaMemsetAsync(const_cast<uint16_t*>(frames), 0, (size_t)(g * fbytes), st);
+    if (e != cudaSuccess) {
+        if (tune) cudaFree(tune);
+        return cuda_fail(e, "autotune clear");
+    }
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
@@ -416,11 +441,18 @@ moco_status autotune(ShapePlan& sp, cudaStream_t st) {
     float best = 0.f;
     int best_form = MOCO_XCORR_FFT_FP32;
     for (int form : {MOCO_XCORR_FFT_FP32, MOCO_XCORR_DIRECT_BF16X3}) {
+        if (form == MOCO_XCORR_DIRECT_BF16X3) {
+            // Skip timing the direct form when even the tensor cores' nominal
+            // dense BF16 rate (2.25 PFLOP/s) could not beat the FFT form: its
+            // three products of the (2w-1)^2-shift contraction alone take longer.
+            const double flops = 3.0 * 2.0 * (double)sp.W * sp.W * sp.mc * sp.nc * (double)g;
+            if (flops / 2.25e15 * 1e3 >= (double)sp.tuned_ms[MOCO_XCORR_FFT_FP32]) break;
+        }
         sp.form = form;
-        r = search_group(sp, sp.stage[0], g, nullptr, nullptr, nullptr, st);  // warm-up
+        r = search_group(sp, frames, g, nullptr, nullptr, nullptr, st);  // warm-up
         if (r != MOCO_OK) break;
         cudaEventRecord(a, st);
-        for (int it = 0; it < 3 && r == MOCO_OK; ++it) r = search_group(sp, sp.stage[0], g, nullptr, nullptr, nullptr, st);
+        for (int it = 0; it < 3 && r == MOCO_OK; ++it) r = search_group(sp, frames, g, nullptr, nullptr, nullptr, st);
         cudaEventRecord(b, st);
         e = cudaEventSynchronize(b);
         if (e != cudaSuccess) { r = cuda_fail(e, "autotune"); break; }
@@ -432,6 +464,10 @@ moco_status autotune(ShapePlan& sp, cudaStream_t st) {
     sp.prof = keep;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    if (tune) {
+        cudaStreamSynchronize(st);
+        cudaFree(tune);
+    }
     sp.form = best_form;
     sp.tuned = true;
     return r;

@@ -49,6 +49,7 @@ struct ShapePlan {
     bool tuned = false;                       // form fixed: template changes prepare only its tables
     int group = 1;
     int stage_frames = 1;  // frames per host staging buffer
+    int num_sms = 0;       // of the plan's device
     bool f32 = false;
     double unit = 1.0;
     int64_t x_fstride = 0, y_fstride = 0;

@@ -8,8 +8,10 @@
 
 namespace moco {
 
-// The streaming form when two of its CTAs fit on an SM.
-constexpr size_t kColsStreamSmemMax = 113 * 1024 + 512;
+// The streaming form whenever one of its CTAs fits on an SM (two fit up to
+// N = 288 at 256 searched rows; longer transforms run one per SM, still
+// hiding each frame's copy under the previous frame's transforms).
+constexpr size_t kColsStreamSmemMax = 227 * 1024;
 
 // Frame slices of one resident wave of the streaming form (0 when it does
 // not apply): every CTA then walks about T / slices frames.

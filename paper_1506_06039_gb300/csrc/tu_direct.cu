@@ -79,8 +79,17 @@ cudaError_t launch_toeplitz(bool f32, const void* tmpl, int m, int n, int levels
     return cudaGetLastError();
 }
 
+int direct_ksplit(int W, int64_t T, int mc, int nqc, int num_sms) {
+    // Enough K splits for two CTAs per SM (one resident per SM), each split
+    // keeping at least 16 K steps; at most kDirSplits.
+    const int64_t tiles = (int64_t)((W + direct_ns(W) - 1) / direct_ns(W)) * ((T + kDirM - 1) / kDirM);
+    int z = 1;
+    while (z < kDirSplits && tiles * z < 2 * (int64_t)num_sms && (int64_t)mc * nqc / (2 * z) >= 16) z *= 2;
+    return z;
+}
+
 cudaError_t launch_direct(const void* a_hi, const void* a_lo, int64_t T, int mc, int ncp, int nqc, int wm1,
-                          const void* tiles, float* h, unsigned int* err, cudaStream_t st) {
+                          const void* tiles, float* h, int ksplit, unsigned int* err, cudaStream_t st) {
     if (T <= 0) return cudaSuccess;
     const int W = 2 * wm1 + 1;
     const size_t smem = direct_smem_bytes(W);
@@ -91,17 +100,18 @@ cudaError_t launch_direct(const void* a_hi, const void* a_lo, int64_t T, int mc,
     CUtensorMap map_hi, map_lo;
     if ((e = plane_map(&map_hi, a_hi, T, mc, ncp)) != cudaSuccess) return e;
     if ((e = plane_map(&map_lo, a_lo, T, mc, ncp)) != cudaSuccess) return e;
-    dim3 grid((unsigned)ntiles, (unsigned)mtiles);
+    dim3 grid((unsigned)ntiles, (unsigned)mtiles, (unsigned)ksplit);
     k_direct<<<grid, kDirThreads, smem, st>>>(map_hi, map_lo, T, mc, ncp, nqc, wm1, static_cast<const uint8_t*>(tiles),
                                               h, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_combine_h(const float* h, int64_t nimg, int wm1, const float2* Sa2, const float2* Sb2,
+cudaError_t launch_combine_h(const float* h, int ksplit, int64_t nimg, int wm1, const float2* Sa2, const float2* Sb2,
                              const float* ia32, double* cost, int32_t* coarse, double* fbest, float* margin,
                              cudaStream_t st) {
     if (nimg <= 0) return cudaSuccess;
-    k_combine_h<<<(unsigned)nimg, 256, 0, st>>>(h, wm1, Sa2, Sb2, ia32, cost, coarse, fbest, margin);
+    const int64_t slab = nimg * (int64_t)(2 * wm1 + 1) * (2 * wm1 + 1);
+    k_combine_h<<<(unsigned)nimg, 256, 0, st>>>(h, ksplit, slab, wm1, Sa2, Sb2, ia32, cost, coarse, fbest, margin);
     return cudaGetLastError();
 }
 

@@ -5,9 +5,11 @@
 
 namespace moco {
 
-// Staging the chunk's frame rows in shared memory pays when two CTAs still
-// fit on an SM (228 KiB, 1 KiB reserved per CTA).
-constexpr size_t kStagedSmemMax = 112 * 1024;
+// Staging the chunk's frame rows in shared memory: two CTAs per SM up to
+// 112 KiB each (228 KiB, 1 KiB reserved per CTA); wider frames (1024
+// columns: 128 KiB of staged rows per chunk) run one staged CTA per SM,
+// which still hides the copies that the unstaged loader waits for.
+constexpr size_t kStagedSmemMax = 227 * 1024;
 
 template <int N, bool F32>
 static cudaError_t frame_rows_n(const void* src, int64_t src_fstride, int64_t nimg, int m, int n, int levels,
