@@ -173,13 +173,14 @@ def kernel_work(info, wl, frames):
 
 # DRAM bytes (read + write) per frame of the current kernels, from one ncu
 # capture of 512 frames of the std512 workload in the FFT form
-# (dram__bytes_read.sum + dram__bytes_write.sum), scaled to a launch by its
-# frame count; other workloads and forms report no traffic, nor does a kernel
-# changed since that capture (k_frame_rows).
+# (dram__bytes_read.sum + dram__bytes_write.sum of the first timed step's
+# launches), scaled to a launch by its frame count; other workloads and
+# forms report no traffic.
 TRAFFIC_WORKLOAD = ("std512", "fft_fp32")
-TRAFFIC_PER_FRAME = {"k_cols": (152.448256e6 + 19.347200e6) / 512,
-                     "k_rows_inv": (45.920000e6 + 0.0) / 512,
-                     "k_jitter": (261.724160e6 + 3.844608e6) / 512}
+TRAFFIC_PER_FRAME = {"k_frame_rows": (269.645824e6 + 124.245504e6) / 512,
+                     "k_cols": (152.446976e6 + 19.978240e6) / 512,
+                     "k_rows_inv": (45.940480e6 + 0.002048e6) / 512,
+                     "k_jitter": (261.728000e6 + 3.831808e6) / 512}
 
 
 # The bound of each kernel in the method's roofline (the frame pass and the
@@ -591,6 +592,9 @@ def run_mixed(args, world, rank, local):
                "config": {"workload": "mixed: 32 stacks, sizes {256,512,1024}^2, 100-3000 frames, w in {8,16,32,64}",
                           "frames": frames, "bytes": int(sum(st.frames.numel() * 2 for st, _ in stacks)),
                           "forms": {"fft_fp32": forms.count(1), "direct_bf16x3": forms.count(2)},
+                          "form_by_stack": ["%dx%d w=%d: %s" % (s_["m"], s_["n"], s_["w"],
+                                                                 "direct" if f_ == 2 else "fft")
+                                            for s_, f_ in zip(specs, forms)],
                           "graph": "one captured moco_align_stack call"},
                "clocks": clocks, "roofline": rf, "kernels": kernels,
                "gpu_launches": sum(l for l, _ in profile.values()) // prof_steps}
