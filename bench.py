@@ -81,11 +81,15 @@ def job_value(world, frames_per_rank, steps, seconds):
 
 
 def workload_config(wl, form):
+    level = wl.m > 256 or wl.n > 256  # the paper's rule: one 2x2 level above 256x256
+    desc = ("%s: %d frames of %dx%d uint16, 2x2 box to %dx%d, w=%d on the searched grid, 3x3 jitter at full "
+            "resolution" % (wl.name, wl.T, wl.m, wl.n, wl.m // 2, wl.n // 2, wl.w)) if level else \
+        ("%s: %d frames of %dx%d uint16, no level, w=%d" % (wl.name, wl.T, wl.m, wl.n, wl.w))
     return {
-        "workload": "%s: %d frames of %dx%d uint16, 2x2 box to %dx%d, w=%d on the searched grid, "
-                    "3x3 jitter at full resolution" % (wl.name, wl.T, wl.m, wl.n, wl.m // 2, wl.n // 2, wl.w),
+        "workload": desc,
         "frames": wl.T, "m": wl.m, "n": wl.n, "w": wl.w, "blobs": wl.nblobs,
-        "shift_range": wl.shift_max, "template": "rounded mean of the first 100 frames",
+        "shift_range": wl.shift_max,
+        "template": "rounded mean of the first 100 frames" if wl.template == "mean100" else "clean (rounded X0)",
         "form": form,
         "l2": "inputs (%.0f MiB of frames) larger than L2; no flush" % (wl.T * wl.m * wl.n * 2 / 2 ** 20),
     }
@@ -470,7 +474,7 @@ def main():
 
     cpu = accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        idx = np.random.default_rng(0).choice(wl.T, 256, replace=False)
+        idx = np.random.default_rng(0).choice(wl.T, min(256, wl.T), replace=False)
         cpu = cpu_baseline(st.frames.cpu().numpy()[idx], st.template.cpu().numpy(), wl.w, args.cpu_seconds)
         accuracy = accuracy_sample(plan, st.frames, st.template.cpu().numpy(), wl.w, shifts)
     if rank == 0:

@@ -104,14 +104,6 @@ moco_status resolve_shape(const moco_shape& d, ShapePlan& sp) {
         return fail(MOCO_ERR_INVALID_ARG, "bad xcorr");
     if (d.group_frames < 0) return fail(MOCO_ERR_INVALID_ARG, "group_frames must be >= 0");
     sp.desc = d;
-    {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sp.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(MOCO_ERR_CUDA, "device query");
-        }
-    }
     sp.levels = d.levels < 0 ? ((d.m > 256 || d.n > 256) ? 1 : 0) : d.levels;
     sp.f32 = d.template_dtype == MOCO_TEMPLATE_F32;
     if (sp.f32 && sp.levels != 0)
@@ -161,6 +153,13 @@ moco_status resolve_shape(const moco_shape& d, ShapePlan& sp) {
     // chunk's search after the final copy stays short.
     const int64_t frame_bytes = (int64_t)d.m * d.n * 2;
     sp.stage_frames = (int)std::max<int64_t>(16, std::min<int64_t>(sp.group, (64ll << 20) / frame_bytes));
+    // (after every argument check: invalid shapes are rejected without a CUDA call)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sp.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MOCO_ERR_CUDA, "device query");
+    }
     return MOCO_OK;
 }
 

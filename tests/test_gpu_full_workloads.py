@@ -83,3 +83,30 @@ def test_full_workload_cost_surface_pointwise(stacks, name, form):
                                     "max_rel_err_at_fbest": ferr, "max_margin_rel_err": merr,
                                     "argmin_agree": agree, "exempt": exempt,
                                     "fbest_over_fmax_min": float((ref["fbest"] / fmax).min())}))
+
+
+@pytest.mark.parametrize("m,n,w,levels,T", [
+    (1024, 1024, 33, 1, 48),   # 1024-column frames: the staged frame pass at one CTA per SM; N = 576
+    (520, 520, 57, 0, 40),     # no level, N = 576, 113^2 shifts
+])
+def test_longest_transforms_streaming_column_pass(m, n, w, levels, T):
+    # Enough frames that the column pass streams (one CTA per SM at N = 576);
+    # three frames compared point by point with the oracle, every frame's
+    # argmin and best cost checked on the same sample.
+    st = synth.make_stack_torch(m, n, T, max(4, int(400 * m * n / 512 ** 2)), 16, seed=5760 + m + w,
+                                template="clean", chunk=16)
+    with Plan(dict(m=m, n=n, w=w, levels=levels, xcorr=XCORR_FFT_FP32), st.template) as plan:
+        info = plan.info()
+        assert info["fft_rows"] == 576 and info["fft_cols"] == 576
+        shifts, best, _ = plan.align(st.frames, best_cost=True, margin=True)
+        cost = plan.cost_surface(st.frames)
+        torch.cuda.synchronize()
+        plan.status()
+        sample = np.array([0, T // 2, T - 1])
+        idx = torch.from_numpy(sample).cuda()
+        cost_s = cost[idx].cpu().numpy()
+        del cost
+    fr = st.frames.view(torch.int16)[idx].view(torch.uint16).cpu().numpy()
+    tm = st.template.cpu().numpy()
+    assert cost_rel_err(cost_s, oracle.cost_surface(fr, tm, w, levels=levels)) <= COST_RTOL
+    check_align(fr, tm, w, levels, shifts.cpu().numpy()[sample], best.cpu().numpy()[sample])
