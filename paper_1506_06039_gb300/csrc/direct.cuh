@@ -10,18 +10,19 @@
 // hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory.
 //
 // For one K step (image row p, 64 columns from q0) and one shift row s, the
-// B block is the 64 x Wp Toeplitz matrix of template row r = p - s; those
-// blocks are precomputed per template (k_toeplitz) directly in the MMA's
+// B block is the 64 x Wp Toeplitz matrix of template row r = p - s. Builder
+// warps write these blocks into shared memory each step, in the MMA's
 // canonical K-major layout without swizzle (8 x 8 core matrices of 128
-// bytes, core matrices 128 bytes apart along K and 1024 bytes apart along
-// M/N), so a K step copies them with one bulk copy each. A tiles (128
-// frames x 64 pixels, BF16 hi and lo planes written by the frame pass) come
-// in as one TMA tensor load per plane (box 64 pixels x 1 row x 128 frames,
-// 128-byte swizzle: the MMA's swizzled K-major layout; frames past the batch
-// read as zeros). One thread issues all copies of a K step. Three stages:
-// the copies for steps k+1 and k+2 run while the MMAs of step k do. One thread issues the MMAs; every
-// mbarrier wait is bounded (about a second) and sets an error flag instead
-// of hanging.
+// bytes, 128 bytes apart along K and 1024 bytes apart along N), from a
+// per-template table of the rows in 8 phase-shifted copies
+// (k_toeplitz_rows), so that each 16-byte chunk is one aligned load. A
+// tiles (128 frames x 64 pixels, BF16 hi and lo planes written by the frame
+// pass) come in as one TMA tensor load per plane (box 64 pixels x 1 row x
+// 128 frames, 128-byte swizzle: the MMA's swizzled K-major layout; frames
+// past the batch read as zeros). The kernel is warp-specialised: a TMA warp,
+// an MMA-issuing thread, builder warps and drain warps, three stages deep,
+// meeting only on mbarriers (k_direct below); every wait is bounded (about a
+// second) and sets an error flag instead of hanging.
 //
 // Accumulation: the tensor core's FP32 accumulator loses low bits on each
 // accumulation, which over the 12 MMAs x (mc * nc / 64) K steps of a frame
@@ -37,7 +38,12 @@
 
 namespace moco {
 
-constexpr int kDirThreads = 128;
+// Warp roles of k_direct (ten warps): warp 0 issues the A tiles' TMA loads,
+// warp 1 the MMAs (one thread each), warps 2-5 drain the accumulators (warp
+// w reads TMEM lanes 32 (w % 4) .. + 31, so the four cover the 128 frames),
+// warps 6-9 build the B tiles in shared memory (thread t owns B row t).
+constexpr int kDirThreads = 320;
+constexpr int kDirWarpTma = 0, kDirWarpMma = 1, kDirWarpDrain = 2, kDirWarpBuild = 6;
 constexpr int kDirM = 128;      // frames per tile (MMA M)
 constexpr int kDirK = 64;       // pixels per K step
 constexpr int kDirQ = kDirK;    // columns per K step
@@ -46,12 +52,13 @@ constexpr int kDirNmax = 128;   // MMA N (shifts per tile)
 __host__ __device__ inline int direct_wp(int W) { return (W + 15) / 16 * 16; }
 __host__ __device__ inline int direct_ns(int W) { return kDirNmax / direct_wp(W); }
 __host__ __device__ inline size_t direct_tile_bytes(int W) { return (size_t)direct_wp(W) * kDirK * 2; }
-__host__ __device__ inline size_t direct_stage_bytes(int W) {
-    return 2 * (size_t)kDirM * kDirK * 2 + 2 * (size_t)direct_ns(W) * direct_tile_bytes(W);
-}
-constexpr int kDirStages = 3;  // copies run two K steps ahead of the MMAs
+constexpr size_t kDirAStage = 2 * (size_t)kDirM * kDirK * 2;    // A tiles of a step, both planes
+constexpr size_t kDirBStage = 2 * (size_t)kDirNmax * kDirK * 2; // B tiles of a step, both planes
+constexpr int kDirStages = 3;  // operands are prepared up to three K steps ahead of the MMAs
 constexpr int kDirGroup = 2;   // K steps summed in one TMEM accumulator before it is drained
-__host__ __device__ inline size_t direct_smem_bytes(int W) { return 1024 + kDirStages * direct_stage_bytes(W) + 64; }
+__host__ __device__ inline size_t direct_smem_bytes(int /*W*/) {
+    return 1024 + kDirStages * (kDirAStage + kDirBStage) + 64;
+}
 
 // Byte offset of element (row, k) in a K-major core-matrix tile with 64 K.
 __device__ __forceinline__ uint32_t core_off(int row, int k) {
@@ -63,30 +70,37 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-// Toeplitz tiles of the template: tiles[plane][r][qc] is the Wp x 64 block
-// B[(r row), q = qc*64 + k][t] = b'[r][qc*64 + k - t], t = ti - (w-1),
-// zero for ti >= W or a column outside [0, nc). plane 0 = hi, 1 = lo.
-static __global__ void k_toeplitz(const float* __restrict__ bprime, int mc, int nc, int nqc, int wm1,
-                                  uint8_t* __restrict__ tiles) {
-    const int W = 2 * wm1 + 1, Wp = direct_wp(W);
-    const size_t tb = direct_tile_bytes(W);
-    const int64_t per_plane = (int64_t)mc * nqc * Wp * kDirK;
+// The template rows the B (Toeplitz) tiles are built from. For template row
+// r, column chunk qc and shift column ti (t = ti - (w-1)), a tile holds
+// B[k][ti] = b'[r][qc*64 + k - ti + (w-1)] (zero outside [0, nc) and for
+// ti >= W). A 16-byte chunk of it (8 consecutive k at one ti) is 8
+// consecutive template values: the table keeps each row of b' (hi and lo
+// BF16 planes) zero-padded by Wp on the left, in 8 copies shifted by one
+// value each, so that every chunk is one aligned 16-byte load (which hits
+// L1: a K step's tiles need NS rows of the table):
+//   rows[plane][r][ph][x] = b'[r][x + ph - Wp]   (x < Lq, zero outside).
+__host__ __device__ inline int direct_row_len(int W, int ncp) {
+    return (direct_wp(W) + ncp + (W - 1) / 2 + 16 + 7) / 8 * 8;
+}
+__host__ __device__ inline size_t direct_rows_bytes(int mc, int ncp, int W) {
+    return 2 * (size_t)mc * 8 * direct_row_len(W, ncp) * 2;
+}
+
+static __global__ void k_toeplitz_rows(const float* __restrict__ bprime, int mc, int nc, int ncp, int wm1,
+                                       __nv_bfloat16* __restrict__ rows) {
+    const int W = 2 * wm1 + 1, Wp = direct_wp(W), Lq = direct_row_len(W, ncp);
+    const int64_t per_plane = (int64_t)mc * 8 * Lq;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per_plane;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(e % kDirK);
-        int64_t rest = e / kDirK;
-        const int ti = (int)(rest % Wp);
-        rest /= Wp;
-        const int qc = (int)(rest % nqc);
-        const int r = (int)(rest / nqc);
-        const int col = qc * kDirQ + k - (ti - wm1);
-        float v = 0.f;
-        if (ti < W && col >= 0 && col < nc) v = bprime[(int64_t)r * nc + col];
+        const int x = (int)(e % Lq);
+        const int ph = (int)((e / Lq) % 8);
+        const int r = (int)(e / ((int64_t)Lq * 8));
+        const int col = x + ph - Wp;
+        const float v = (col >= 0 && col < nc) ? bprime[(int64_t)r * nc + col] : 0.f;
         __nv_bfloat16 hi, lo;
         split_bf16(v, hi, lo);
-        const size_t base = ((size_t)r * nqc + qc) * tb + core_off(ti, k);
-        *reinterpret_cast<__nv_bfloat16*>(tiles + base) = hi;
-        *reinterpret_cast<__nv_bfloat16*>(tiles + (size_t)mc * nqc * tb + base) = lo;
+        rows[e] = hi;
+        rows[per_plane + e] = lo;
     }
 }
 
@@ -168,36 +182,58 @@ __device__ __forceinline__ void drain_acc(uint32_t addr, int N, float (&hsum)[kD
 // h[z][f][(s+w-1)*W + (t+w-1)] (FP32, z-th slab of T * W * W), which the
 // combine adds up in order of z. Splitting K keeps every SM busy when the
 // window is small (few N tiles) or the batch short (few M tiles).
-// tmap_hi / tmap_lo: the frame planes [T][mc][ncp] BF16 as 3-D tensors
-// (x = column, y = row, z = frame), box 64 x 1 x 128, 128-byte swizzle.
+//
+// The warps meet only on mbarriers (every wait bounded: about a second, then
+// the error flag and an orderly exit):
+//   full_a[st]  the TMA warp's loads of step k's A tiles landed (transaction
+//               count), stage st = k % kDirStages;
+//   full_b[st]  the 128 builder threads stored step k's B tiles (and fenced
+//               them for the tensor core's asynchronous reads);
+//   empty[st]   step k's MMAs completed (tcgen05.commit): the stage is free;
+//   acc_full[a] a group's MMAs into accumulator a completed (commit);
+//   acc_empty[a] the 128 drain threads have read accumulator a.
+// The MMA thread issues step k's 12 MMAs as soon as its operands are ready
+// and, at a group's first step, the accumulator it reuses has been drained;
+// loads and builds run up to three steps ahead, drains one group behind.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 static __global__ void __launch_bounds__(kDirThreads, 1)
 k_direct(const __grid_constant__ CUtensorMap tmap_hi, const __grid_constant__ CUtensorMap tmap_lo, int64_t T, int mc,
-         int ncp, int nqc, int wm1, const uint8_t* __restrict__ tiles, float* __restrict__ h,
+         int ncp, int nqc, int wm1, const __nv_bfloat16* __restrict__ rows, float* __restrict__ h,
          unsigned int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char dsm_raw[];
     unsigned char* dsm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t load_bar[kDirStages];
-    __shared__ __align__(8) uint64_t mma_bar[2];
+    __shared__ __align__(8) uint64_t full_a[kDirStages], full_b[kDirStages], empty[kDirStages];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_abort;
+    __shared__ volatile int s_abort;
+    __shared__ int s_consumed;  // K steps whose A tiles the MMA thread has seen land
     const int W = 2 * wm1 + 1, Wp = direct_wp(W), NS = direct_ns(W), N = NS * Wp;
-    const size_t tb = direct_tile_bytes(W), stage = direct_stage_bytes(W);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int s_first = -wm1 + (int)blockIdx.x * NS;
     const int64_t f0 = (int64_t)blockIdx.y * kDirM;
     const int kall = mc * nqc;
     const int kb = (int)((int64_t)blockIdx.z * kall / gridDim.z);
     const int ksteps = (int)((int64_t)(blockIdx.z + 1) * kall / gridDim.z) - kb;  // this split's K steps
+    const int ngroups = (ksteps + kDirGroup - 1) / kDirGroup;
     h += (int64_t)blockIdx.z * T * W * W;
-    const uint32_t idesc = direct_idesc(kDirM, N);
-    const size_t plane_tiles = (size_t)mc * nqc * tb;
     constexpr uint32_t kTmemCols = 2 * kDirNmax;  // two accumulators
 
     if (tid == 0) {
-        for (int i = 0; i < kDirStages; ++i) mbar_init(&load_bar[i], 1);
-        mbar_init(&mma_bar[0], 1);
-        mbar_init(&mma_bar[1], 1);
+        for (int i = 0; i < kDirStages; ++i) {
+            mbar_init(&full_a[i], 1);
+            mbar_init(&full_b[i], 128);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 128);
+        }
         s_abort = 0;
+        s_consumed = 0;
+        fence_async_smem();
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -209,119 +245,141 @@ k_direct(const __grid_constant__ CUtensorMap tmap_hi, const __grid_constant__ CU
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-
-    auto sA = [&](int st, int plane) { return dsm + st * stage + (size_t)plane * kDirM * kDirK * 2; };
+    auto sA = [&](int st, int plane) { return dsm + st * kDirAStage + (size_t)plane * kDirM * kDirK * 2; };
     auto sB = [&](int st, int plane) {
-        return dsm + st * stage + 2 * (size_t)kDirM * kDirK * 2 + (size_t)plane * NS * tb;
+        return dsm + kDirStages * kDirAStage + st * kDirBStage + (size_t)plane * (kDirBStage / 2);
+    };
+    // A bounded wait that also gives up at once when another role already has.
+    auto wait = [&](uint64_t* bar, uint32_t parity) {
+        if (s_abort) return false;
+        if (mbar_wait(bar, parity, err)) return true;
+        s_abort = 1;
+        return false;
     };
 
-    // Copies of K step k into stage st: A tiles by TMA, B tiles by bulk copies
-    // (one thread), out-of-window B tiles zeroed by all threads.
-    auto issue = [&](int k, int st) {
-        const int p = (kb + k) / nqc, qc = (kb + k) - p * nqc;
-        // Tiles of shift rows that fall outside the window or the template: zeros.
-        for (int sl = 0; sl < NS; ++sl) {
-            const int s = s_first + sl, r = p - s;
-            if (s <= wm1 && r >= 0 && r < mc) continue;
-            for (int plane = 0; plane < 2; ++plane) {
-                uint4* z = reinterpret_cast<uint4*>(sB(st, plane) + sl * tb);
-                for (size_t i = tid; i < tb / 16; i += kDirThreads) z[i] = make_uint4(0, 0, 0, 0);
+    if (warp == kDirWarpTma) {
+        // A tiles: one TMA tensor load per plane and step (frames past the batch read as zeros).
+        if (lane == 0) {
+            int issued = 0;
+            for (int k = 0; k < ksteps; ++k) {
+                const int st = k % kDirStages;
+                if (k >= kDirStages && !wait(&empty[st], ((k / kDirStages) - 1) & 1)) break;
+                const int kk = kb + k, p = kk / nqc, qc = kk - p * nqc;
+                mbar_expect_tx(&full_a[st], (uint32_t)kDirAStage);
+                tma_load_3d(sA(st, 0), &tmap_hi, qc * kDirQ, p, (int)f0, &full_a[st]);
+                tma_load_3d(sA(st, 1), &tmap_lo, qc * kDirQ, p, (int)f0, &full_a[st]);
+                issued = k + 1;
+            }
+            if (s_abort) {
+                // Leave no copy in flight into shared memory: wait (bounded) for the
+                // loads of the last stages that the MMA thread has not seen land.
+                for (int k = max(s_consumed, issued - kDirStages); k < issued; ++k)
+                    mbar_wait(&full_a[k % kDirStages], (k / kDirStages) & 1, err);
             }
         }
-        if (tid == 0) {
-            uint32_t bytes = 2u * kDirM * kDirK * 2u;  // both A planes: the whole box, zeros past the batch included
-            for (int sl = 0; sl < NS; ++sl) {
-                const int s = s_first + sl, r = p - s;
-                if (s <= wm1 && r >= 0 && r < mc) bytes += 2 * (uint32_t)tb;
-            }
-            mbar_expect_tx(&load_bar[st], bytes);
-            tma_load_3d(sA(st, 0), &tmap_hi, qc * kDirQ, p, (int)f0, &load_bar[st]);
-            tma_load_3d(sA(st, 1), &tmap_lo, qc * kDirQ, p, (int)f0, &load_bar[st]);
-            for (int sl = 0; sl < NS; ++sl) {
-                const int s = s_first + sl, r = p - s;
-                if (!(s <= wm1 && r >= 0 && r < mc)) continue;
-                const uint8_t* src = tiles + ((size_t)r * nqc + qc) * tb;
-                bulk_g2s(sB(st, 0) + sl * tb, src, (uint32_t)tb, &load_bar[st]);
-                bulk_g2s(sB(st, 1) + sl * tb, src + plane_tiles, (uint32_t)tb, &load_bar[st]);
-            }
-        }
-    };
-
-    // FP32 sum of this thread's frame row over the K steps (columns < N).
-    float hsum[kDirNmax];
+    } else if (warp == kDirWarpMma) {
+        if (lane == 0) {
+            const uint32_t idesc = direct_idesc(kDirM, N);
+            int committed = -1;  // last step whose MMAs were committed
+            for (int k = 0; k < ksteps; ++k) {
+                const int st = k % kDirStages, par = (k / kDirStages) & 1;
+                const int g = k / kDirGroup, acc = g & 1;
+                if (!wait(&full_a[st], (uint32_t)par)) break;
+                s_consumed = k + 1;
+                if (!wait(&full_b[st], (uint32_t)par)) break;
+                // a group's first step reuses the accumulator of group g - 2: drained?
+                if (k % kDirGroup == 0 && g >= 2 && !wait(&acc_empty[acc], ((g - 2) >> 1) & 1)) break;
+                tc_fence_after();
+                const unsigned char* A0 = sA(st, 0);
+                const unsigned char* A1 = sA(st, 1);
+                const unsigned char* B0 = sB(st, 0);
+                const unsigned char* B1 = sB(st, 1);
+                const uint32_t d = tmem + (uint32_t)(acc * kDirNmax);
+                // small terms first, then hi*hi; a fresh accumulator at each group's first step
+                // per K16 slice: A 32 bytes along its swizzled row, B two core matrices (256 bytes)
+                const uint32_t first = (k % kDirGroup == 0) ? 1u : 0u;
 #pragma unroll
-    for (int c = 0; c < kDirNmax; ++c) hsum[c] = 0.f;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-
-    int issued = 0, loaded = 0;  // K steps whose copies were issued / have landed
-    issue(0, 0);
-    if (ksteps > 1) issue(1, 1);
-    issued = ksteps > 1 ? 2 : 1;
-    for (int k = 0; k < ksteps; ++k) {
-        const int st = k % kDirStages;       // copy stage of step k
-        const int ab = k & 1;                // commit barrier of step k
-        const int acc = (k / kDirGroup) & 1;  // accumulator of step k's group
-        if (k >= 1) {
-            // Step k-1's MMAs are done: its stage is free for step k+2, and
-            // when k-1 closed a group its accumulator is drained.
-            if (!mbar_wait(&mma_bar[ab ^ 1], ((k - 1) >> 1) & 1, err)) s_abort = 1;
-            __syncthreads();
-            if (s_abort) break;
-            if ((k - 1) % kDirGroup == kDirGroup - 1)
-                drain_acc(lane_addr + (uint32_t)((((k - 1) / kDirGroup) & 1) * kDirNmax), N, hsum);
-        }
-        if (k + 2 < ksteps) {
-            issue(k + 2, (k + 2) % kDirStages);
-            issued = k + 3;
-        }
-        if (!mbar_wait(&load_bar[st], (k / kDirStages) & 1, err)) s_abort = 1;
-        fence_async_smem();
-        __syncthreads();
-        if (s_abort) break;
-        loaded = k + 1;
-        if (tid == 0) {
-            tc_fence_after();
-            const unsigned char* A0 = sA(st, 0);
-            const unsigned char* A1 = sA(st, 1);
-            const unsigned char* B0 = sB(st, 0);
-            const unsigned char* B1 = sB(st, 1);
-            const uint32_t d = tmem + (uint32_t)(acc * kDirNmax);
-            // small terms first, then hi*hi; a fresh accumulator at each group's first step
-            // per K16 slice: A 32 bytes along its swizzled row, B two core matrices (256 bytes)
-            const uint32_t first = (k % kDirGroup == 0) ? 1u : 0u;
+                for (int kk = 0; kk < kDirK / 16; ++kk) {
+                    mma_bf16(d, smem_desc_sw128(A0 + kk * 32), smem_desc(B1 + kk * 256), idesc,
+                             (kk > 0 || !first) ? 1u : 0u);
+                    mma_bf16(d, smem_desc_sw128(A1 + kk * 32), smem_desc(B0 + kk * 256), idesc, 1u);
+                }
 #pragma unroll
-            for (int kk = 0; kk < kDirK / 16; ++kk) {
-                mma_bf16(d, smem_desc_sw128(A0 + kk * 32), smem_desc(B1 + kk * 256), idesc,
-                         (kk > 0 || !first) ? 1u : 0u);
-                mma_bf16(d, smem_desc_sw128(A1 + kk * 32), smem_desc(B0 + kk * 256), idesc, 1u);
+                for (int kk = 0; kk < kDirK / 16; ++kk)
+                    mma_bf16(d, smem_desc_sw128(A0 + kk * 32), smem_desc(B0 + kk * 256), idesc, 1u);
+                mma_commit(&empty[st]);
+                if (k % kDirGroup == kDirGroup - 1 || k == ksteps - 1) mma_commit(&acc_full[acc]);
+                committed = k;
             }
+            // On an abort, the MMAs in flight finish (bounded wait) before the tensor
+            // memory is released and the CTA's shared memory goes away.
+            if (s_abort && committed >= 0)
+                mbar_wait(&empty[committed % kDirStages], (committed / kDirStages) & 1, err);
+        }
+    } else if (warp >= kDirWarpBuild) {
+        // B tiles: thread n owns B row n (shift column ti of tile sl): 64 consecutive
+        // template values of one row of the table at a phase and offset fixed for
+        // the thread, eight aligned 16-byte loads and stores per plane and step.
+        const int n = tid - kDirWarpBuild * 32;
+        const int sl = n / Wp, ti = n - sl * Wp;
+        const bool col = n < N && ti < W && s_first + sl <= wm1;
+        const int php = (Wp - ti + wm1) & 7;
+        const int x0 = Wp - ti + wm1 - php;  // a multiple of 8: aligned chunks
+        const uint32_t soff = (uint32_t)((n >> 3) * 1024 + (n & 7) * 16);
+        const int Lq = direct_row_len(W, ncp);
+        const size_t plane_rows = (size_t)mc * 8 * Lq;
+        for (int k = 0; k < ksteps; ++k) {
+            const int st = k % kDirStages;
+            if (k >= kDirStages && !wait(&empty[st], ((k / kDirStages) - 1) & 1)) break;
+            if (n < N) {
+                const int kk = kb + k, p = kk / nqc, qc = kk - p * nqc;
+                const int r = p - (s_first + sl);
+                const bool live = col && r >= 0 && r < mc;
 #pragma unroll
-            for (int kk = 0; kk < kDirK / 16; ++kk)
-                mma_bf16(d, smem_desc_sw128(A0 + kk * 32), smem_desc(B0 + kk * 256), idesc, 1u);
-            mma_commit(&mma_bar[ab]);
+                for (int plane = 0; plane < 2; ++plane) {
+                    unsigned char* dst = sB(st, plane) + soff;
+                    uint4 v[8];
+                    if (live) {
+                        const uint4* src = reinterpret_cast<const uint4*>(
+                            rows + plane * plane_rows + ((size_t)r * 8 + php) * Lq + qc * kDirQ + x0);
+#pragma unroll
+                        for (int kc = 0; kc < 8; ++kc) v[kc] = __ldg(src + kc);
+                    } else {
+#pragma unroll
+                        for (int kc = 0; kc < 8; ++kc) v[kc] = make_uint4(0u, 0u, 0u, 0u);
+                    }
+#pragma unroll
+                    for (int kc = 0; kc < 8; ++kc) *reinterpret_cast<uint4*>(dst + kc * 128) = v[kc];
+                }
+                fence_async_smem();  // the stores, visible to the tensor core's reads
+            }
+            mbar_arrive(&full_b[st]);
         }
     }
-    // Drain the last step (its commit covers every earlier MMA).
-    if (!s_abort && ksteps > 0) {
-        if (!mbar_wait(&mma_bar[(ksteps - 1) & 1], ((ksteps - 1) >> 1) & 1, err)) s_abort = 1;
+    // Drain warps: FP32 sum of this thread's frame row over the groups (round to
+    // nearest, in group order), then the row's h values.
+    float hsum[kDirNmax];
+    const bool drainer = warp >= kDirWarpDrain && warp < kDirWarpBuild;
+    if (drainer) {
+#pragma unroll
+        for (int c = 0; c < kDirNmax; ++c) hsum[c] = 0.f;
+        const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        for (int g = 0; g < ngroups; ++g) {
+            const int acc = g & 1;
+            if (!wait(&acc_full[acc], (g >> 1) & 1)) break;
+            drain_acc(lane_addr + (uint32_t)(acc * kDirNmax), N, hsum);
+            mbar_arrive(&acc_empty[acc]);
+        }
     }
     __syncthreads();
-    if (!s_abort && ksteps > 0)
-        drain_acc(lane_addr + (uint32_t)((((ksteps - 1) / kDirGroup) & 1) * kDirNmax), N, hsum);
-    if (s_abort) {
-        // Leave no copy in flight into this CTA's shared memory.
-        cp_wait<0>();
-        if (tid == 0)
-            for (int j = loaded; j < issued; ++j) mbar_wait(&load_bar[j % kDirStages], (j / kDirStages) & 1, err);
-    }
-    if (!s_abort) {
-        const int64_t f = f0 + warp * 32 + (tid & 31);
+    if (drainer && !s_abort) {
+        const int64_t f = f0 + (warp & 3) * 32 + lane;
         if (f < T) {
 #pragma unroll
             for (int c = 0; c < kDirNmax; ++c) {
-                const int sl = c / Wp, ti = c - sl * Wp;
-                const int s = s_first + sl;
-                if (c < N && ti < W && s <= wm1) h[f * (int64_t)W * W + (int64_t)(s + wm1) * W + ti] = hsum[c];
+                const int slc = c / Wp, tc = c - slc * Wp;
+                const int s = s_first + slc;
+                if (c < N && tc < W && s <= wm1) h[f * (int64_t)W * W + (int64_t)(s + wm1) * W + tc] = hsum[c];
             }
         }
     }

@@ -122,13 +122,13 @@ cudaError_t launch_adj_inverse(int Nr, int Nc, const float2* Acc, int ncv, int m
                                const float2* twc, float2* Yt, float* out, cudaStream_t st);
 
 // ---- the direct (tensor-core) form -----------------------------------------
-size_t direct_tiles_bytes(int mc, int nqc, int W);  // hi + lo Toeplitz tiles
+size_t direct_tiles_bytes(int mc, int ncp, int W);  // the template-row table the Toeplitz tiles are built from
 size_t direct_smem(int W);
 cudaError_t launch_frame_planes(bool f32, const void* src, int64_t src_fstride, int64_t nimg, int m, int n, int levels,
                                 int mc, int nc, const int32_t* coff_i, const float* coff_f, const float2* tw,
                                 u64* rowE, u64* colE, u64* tot, uint32_t* corners, int wm1, void* p_hi, void* p_lo,
                                 int ldp, cudaStream_t st);
-cudaError_t launch_toeplitz(bool f32, const void* tmpl, int m, int n, int levels, int mc, int nc, int nqc, int wm1,
+cudaError_t launch_toeplitz(bool f32, const void* tmpl, int m, int n, int levels, int mc, int nc, int ncp, int wm1,
                             const int32_t* coff_i, const float* coff_f, float* bprime, void* tiles, cudaStream_t st);
 // K splits of one direct-form launch (1 .. kDirSplitMax): each writes a
 // partial h slab of T * W * W floats, which launch_combine_h adds in order.

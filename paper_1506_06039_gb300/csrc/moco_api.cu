@@ -176,7 +176,7 @@ moco_status allocate_shape(ShapePlan& sp) {
     c.add(&sp.dev_err, 4);
     if (sp.has_direct) {
         c.add(&sp.bprime, (size_t)sp.mc * sp.nc * 4);
-        c.add(&sp.dtiles, direct_tiles_bytes(sp.mc, sp.nqc, sp.W));
+        c.add(&sp.dtiles, direct_tiles_bytes(sp.mc, sp.ncp, sp.W));
     }
     c.add(&sp.Sb, (size_t)W * W * 8);
     c.add(&sp.inv_area, (size_t)W * W * 8);
@@ -298,7 +298,7 @@ moco_status prepare_template(ShapePlan& sp, const void* tmpl_dev, cudaStream_t s
         if (e != cudaSuccess) return cuda_fail(e, "template spectrum");
     }
     if (sp.has_direct && (!sp.tuned || sp.form == MOCO_XCORR_DIRECT_BF16X3)) {
-        e = launch_toeplitz(sp.f32, sp.tmpl, sp.desc.m, sp.desc.n, sp.levels, sp.mc, sp.nc, sp.nqc, sp.wm1, sp.coff_i,
+        e = launch_toeplitz(sp.f32, sp.tmpl, sp.desc.m, sp.desc.n, sp.levels, sp.mc, sp.nc, sp.ncp, sp.wm1, sp.coff_i,
                             sp.coff_f, sp.bprime, sp.dtiles, st);
         if (e != cudaSuccess) return cuda_fail(e, "template Toeplitz tiles");
     }

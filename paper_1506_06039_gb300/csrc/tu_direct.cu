@@ -40,7 +40,7 @@ static cudaError_t plane_map(CUtensorMap* map, const void* planes, int64_t T, in
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-size_t direct_tiles_bytes(int mc, int nqc, int W) { return 2 * (size_t)mc * nqc * direct_tile_bytes(W); }
+size_t direct_tiles_bytes(int mc, int ncp, int W) { return direct_rows_bytes(mc, ncp, W); }
 size_t direct_smem(int W) { return direct_smem_bytes(W); }
 
 cudaError_t launch_frame_planes(bool f32, const void* src, int64_t src_fstride, int64_t nimg, int m, int n, int levels,
@@ -66,7 +66,7 @@ cudaError_t launch_frame_planes(bool f32, const void* src, int64_t src_fstride, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_toeplitz(bool f32, const void* tmpl, int m, int n, int levels, int mc, int nc, int nqc, int wm1,
+cudaError_t launch_toeplitz(bool f32, const void* tmpl, int m, int n, int levels, int mc, int nc, int ncp, int wm1,
                             const int32_t* coff_i, const float* coff_f, float* bprime, void* tiles,
                             cudaStream_t st) {
     if (f32)
@@ -75,7 +75,7 @@ cudaError_t launch_toeplitz(bool f32, const void* tmpl, int m, int n, int levels
         k_coarse_image<false><<<256, 256, 0, st>>>(tmpl, m, n, levels, mc, nc, coff_i, coff_f, bprime);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_toeplitz<<<1024, 256, 0, st>>>(bprime, mc, nc, nqc, wm1, static_cast<uint8_t*>(tiles));
+    k_toeplitz_rows<<<1024, 256, 0, st>>>(bprime, mc, nc, ncp, wm1, static_cast<__nv_bfloat16*>(tiles));
     return cudaGetLastError();
 }
 
@@ -101,7 +101,8 @@ cudaError_t launch_direct(const void* a_hi, const void* a_lo, int64_t T, int mc,
     if ((e = plane_map(&map_hi, a_hi, T, mc, ncp)) != cudaSuccess) return e;
     if ((e = plane_map(&map_lo, a_lo, T, mc, ncp)) != cudaSuccess) return e;
     dim3 grid((unsigned)ntiles, (unsigned)mtiles, (unsigned)ksplit);
-    k_direct<<<grid, kDirThreads, smem, st>>>(map_hi, map_lo, T, mc, ncp, nqc, wm1, static_cast<const uint8_t*>(tiles),
+    k_direct<<<grid, kDirThreads, smem, st>>>(map_hi, map_lo, T, mc, ncp, nqc, wm1,
+                                              static_cast<const __nv_bfloat16*>(tiles),
                                               h, err);
     return cudaGetLastError();
 }
