@@ -412,13 +412,24 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
                         }
                     __nv_bfloat16* ph = p_hi + (f * mc + r) * (int64_t)ldp + g * CW;
                     __nv_bfloat16* pl = p_lo + (f * mc + r) * (int64_t)ldp + g * CW;
+                    // CW (4 or 8) consecutive values per plane: one 8- or 16-byte store each
+                    // (ldp and g * CW are multiples of CW, the planes 256-byte aligned)
+                    uint32_t hw[4], lw[4];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k)
-                        if (k < CW) {
-                            const __nv_bfloat16 hi = __float2bfloat16_rn(val[k]);
-                            ph[k] = hi;
-                            pl[k] = __float2bfloat16_rn(val[k] - __bfloat162float(hi));
-                        }
+                    for (int k = 0; k < 8; k += 2) {
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(val[k]), h1 = __float2bfloat16_rn(val[k + 1]);
+                        const __nv_bfloat16 l0 = __float2bfloat16_rn(val[k] - __bfloat162float(h0));
+                        const __nv_bfloat16 l1 = __float2bfloat16_rn(val[k + 1] - __bfloat162float(h1));
+                        hw[k / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                        lw[k / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                    }
+                    if (CW == 4) {
+                        *reinterpret_cast<uint2*>(ph) = make_uint2(hw[0], hw[1]);
+                        *reinterpret_cast<uint2*>(pl) = make_uint2(lw[0], lw[1]);
+                    } else {
+                        *reinterpret_cast<uint4*>(ph) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4*>(pl) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
                 } else {
                     float* dst = reinterpret_cast<float*>(buf + (rl >> 1) * LD) + (rl & 1);
 #pragma unroll
