@@ -96,6 +96,15 @@ def test_null_arguments(lib):
     assert lib.moco_align_host(None, 0, None, 1, None, None) == binding.MOCO_ERR_INVALID_ARG
 
 
+def test_alu_peak_rejects_bad_arguments(lib):
+    rate = ctypes.c_double(0.0)
+    assert lib.moco_alu_peak(7, ctypes.c_void_p(16), ctypes.byref(rate), None) == binding.MOCO_ERR_INVALID_ARG
+    assert lib.moco_alu_peak(binding.PEAK_DP2A, None, ctypes.byref(rate), None) == binding.MOCO_ERR_INVALID_ARG
+    assert lib.moco_alu_peak(binding.PEAK_FP32_FMA, ctypes.c_void_p(16), None, None) == binding.MOCO_ERR_INVALID_ARG
+    assert lib.moco_alu_peak(binding.PEAK_FP32_FMA, ctypes.c_void_p(18), ctypes.byref(rate), None) == \
+        binding.MOCO_ERR_INVALID_ARG  # sink not 4-byte aligned
+
+
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(binding, "_lib", None)
     monkeypatch.setattr(binding._build, "LIB", str(tmp_path / "missing.so"))
