@@ -742,18 +742,19 @@ __device__ __forceinline__ void energy_sweep(const u64* __restrict__ rE, const u
     const int a0 = 1 + g * L, a1 = min(w, 1 + (g + 1) * L);
     const size_t wm1sq = (size_t)wm1 * wm1;
     const uint32_t* blk = corners_f + (size_t)(q & 3) * wm1sq;
-    // Squares of table row a at this lane's columns (0 at b = 0 and b >= w).
-    auto row_sq = [&](int a, u64 (&v)[K]) {
+    // Corner values of table row a at this lane's columns (0 at b = 0 and
+    // b >= w), and their squares.
+    auto row_raw = [&](int a, int32_t (&c)[K]) {
         const uint32_t* row = blk + (size_t)(bottom ? wm1 - a : a - 1) * wm1;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int b = K * lane + k;
-            v[k] = 0ull;
-            if (b >= 1 && b < w) {
-                const long long c = (int32_t)row[right ? wm1 - b : b - 1];
-                v[k] = (u64)(c * c);
-            }
+            c[k] = (b >= 1 && b < w) ? (int32_t)row[right ? wm1 - b : b - 1] : 0;
         }
+    };
+    auto squares = [&](const int32_t (&c)[K], u64 (&v)[K]) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = (u64)((long long)c[k] * c[k]);
     };
     // Inclusive prefix of v along the columns (lane-local, then across lanes).
     auto col_prefix = [&](u64 (&v)[K]) {
@@ -775,8 +776,10 @@ __device__ __forceinline__ void energy_sweep(const u64* __restrict__ rE, const u
 #pragma unroll
         for (int k = 0; k < K; ++k) cs[k] = 0ull;
         for (int a = a0; a < a1; ++a) {
+            int32_t c[K];
             u64 v[K];
-            row_sq(a, v);
+            row_raw(a, c);
+            squares(c, v);
 #pragma unroll
             for (int k = 0; k < K; ++k) cs[k] += v[k];
         }
@@ -810,9 +813,15 @@ __device__ __forceinline__ void energy_sweep(const u64* __restrict__ rE, const u
         }
     };
     if (g == 0 && !bottom) emit_row(0);  // a = 0: no corner rows (s = 0 belongs to the top quadrants)
+    int32_t nxt[K];  // the next row's corner values, loaded one row ahead
+    if (a0 < a1) row_raw(a0, nxt);
     for (int a = a0; a < a1; ++a) {
+        int32_t c[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) c[k] = nxt[k];
+        if (a + 1 < a1) row_raw(a + 1, nxt);
         u64 v[K];
-        row_sq(a, v);
+        squares(c, v);
         col_prefix(v);
 #pragma unroll
         for (int k = 0; k < K; ++k) carry[k] += v[k];
@@ -1090,7 +1099,7 @@ __host__ __device__ constexpr size_t rows_inv_smem(int wm1) {
 }
 
 template <int N>
-__global__ void __launch_bounds__(576)
+__global__ void __launch_bounds__(rows_inv_threads<N>() <= 288 ? 288 : 576, rows_inv_threads<N>() <= 288 ? 3 : 1)
 k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
            const float2* __restrict__ tw_g, const u64* __restrict__ rowE, const u64* __restrict__ colE,
            const u64* __restrict__ tot, const uint32_t* __restrict__ corners, int mc, int nc,

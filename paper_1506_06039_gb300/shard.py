@@ -24,9 +24,13 @@ def frame_range(T: int, world: int, rank: int) -> tuple[int, int]:
 
 
 def broadcast_template(template, group=None, src: int = 0):
-    """Every rank's `template` (same shape and dtype) becomes rank src's, in place."""
+    """Every rank's `template` (same shape and dtype) becomes rank src's, in place.
+    A 16-bit template travels as its bytes (a uint8 view): NCCL has no unsigned
+    16-bit type and gloo no 16-bit integer type at all."""
+    import torch
     import torch.distributed as dist
-    dist.broadcast(template, src=src, group=group)
+    wire = template.view(torch.uint8) if template.dtype in (torch.uint16, torch.int16) else template
+    dist.broadcast(wire, src=src, group=group)
     return template
 
 

@@ -144,14 +144,19 @@ def _shard_worker(rank, world, port, q):
     try:
         st, w = _shard_problem()
         # only rank 0 holds the template at first; the broadcast gives it to the other
-        tmpl = torch.from_numpy(st.template.astype(np.int32)) if rank == 0 else torch.zeros(st.template.shape,
-                                                                                              dtype=torch.int32)
+        tmpl = torch.from_numpy(st.template.astype(np.uint16)) if rank == 0 else torch.zeros(st.template.shape,
+                                                                                               dtype=torch.uint16)
         broadcast_template(tmpl)
+        # counts above 32767 keep their bytes through the byte view
+        high = torch.tensor([40000, 65535, 1, 32768], dtype=torch.uint16) if rank == 0 else \
+            torch.zeros(4, dtype=torch.uint16)
+        broadcast_template(high)
+        assert high.to(torch.int32).tolist() == [40000, 65535, 1, 32768]
         seen = []
 
         def align_fn(fr):
             seen.append(fr.shape[0])
-            r = oracle.align(fr, tmpl.numpy().astype(np.uint16), w)
+            r = oracle.align(fr, tmpl.numpy(), w)
             return torch.from_numpy(r["shifts"])
 
         shifts = align_sharded(st.frames, align_fn)
