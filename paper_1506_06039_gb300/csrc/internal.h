@@ -63,11 +63,11 @@ struct JitSegment {
 };
 // The refinement of every segment in persistent launches, each of at most
 // kJitSegs segments holding at most `capacity` frames; acc (9 u64 per frame)
-// and ticket (one u32 per frame) are scratch for `capacity` frames, counter
-// one 64-bit word. Every segment needs a b^2 prefix table (bsq) and at most
-// `capacity` frames (cudaErrorInvalidValue otherwise).
+// and ticket (one u32 per frame) are scratch for `capacity` frames. Every
+// segment needs a b^2 prefix table (bsq) and at most `capacity` frames
+// (cudaErrorInvalidValue otherwise).
 cudaError_t launch_jitter_multi(const JitSegment* segs, int nseg, u64* acc, unsigned int* ticket, int64_t capacity,
-                                unsigned long long* counter, int num_sms, cudaStream_t st);
+                                int num_sms, cudaStream_t st);
 
 // More than one level: level-l images (int32 box sums of 2^l x 2^l pixels)
 // and the 3x3 refinement on level l of the doubled level-(l+1) optimum.

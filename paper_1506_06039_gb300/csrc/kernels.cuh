@@ -1618,19 +1618,67 @@ struct JitParams {
     double* ffinal;
     u64* acc;
     unsigned int* ticket;
-    int m, n, band_rows, ctas;  // ctas: CTAs (band-and-column-group slices) per frame
+    int m, n, band_rows, witems;  // witems: warp items (32 band-and-column-group tasks) per frame
 };
 
-// The work of one CTA slice `chunk` (of P.ctas) of frame f: its bands' nine
-// partial sums added to the frame's scratch; the frame's last slice to finish
-// (ticket counter) takes the minimum. Every thread of the block calls it.
+__device__ __forceinline__ u64 ld_relaxed_u64(const u64* p) {
+    u64 v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Frame f's final shift from its nine complete sums (every item's additions
+// visible): lane k < 9 forms candidate (u, v) = (k / 3, k % 3), its S (the
+// table's b^2 added) and overlap A; every lane then takes the nine in order,
+// smallest S/A first, ties to the smaller |s| + |t|, then s, then t, with
+// exact 128-bit cross products. Lane 0 writes the result.
 template <bool TABLE>
-__device__ __forceinline__ void jitter_slice(const JitParams& P, int64_t f, int chunk, uint4* ring,
-                                             u64 (*red)[9], bool* last) {
+__device__ __forceinline__ void jitter_choose(const JitParams& P, int64_t f, int s0, int t0, bool valid) {
+    const int lane = threadIdx.x & 31, m = P.m, n = P.n;
+    u64 S = 0, A = 1;
+    int s = 0, t = 0;
+    if (lane < 9) {
+        s = s0 + lane / 3 - 1;
+        t = t0 + lane % 3 - 1;
+        A = (u64)(m - abs(s)) * (u64)(n - abs(t));
+        S = ld_relaxed_u64(P.acc + f * 9 + lane);
+        if (TABLE) S += rect_sum(P.bsq, n, max(0, -s), m - max(0, s), max(0, -t), n - max(0, t));
+    }
+    u64 bS = 0, bA = 1;
+    int bs = 0, bt = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const u64 Sk = __shfl_sync(0xffffffffu, S, k), Ak = __shfl_sync(0xffffffffu, A, k);
+        const int sk = __shfl_sync(0xffffffffu, s, k), tk = __shfl_sync(0xffffffffu, t, k);
+        bool take = (k == 0);
+        if (!take) {
+            int eq;
+            const int lt = ratio_lt(Sk, Ak, bS, bA, &eq);
+            if (lt) take = true;
+            else if (eq) {
+                const int k1 = abs(sk) + abs(tk), k2 = abs(bs) + abs(bt);
+                take = (k1 < k2) || (k1 == k2 && (sk < bs || (sk == bs && tk < bt)));
+            }
+        }
+        if (take) { bS = Sk; bA = Ak; bs = sk; bt = tk; }
+    }
+    if (lane != 0) return;
+    P.shifts[2 * f] = valid ? bs : INT32_MIN;
+    P.shifts[2 * f + 1] = valid ? bt : INT32_MIN;
+    if (P.ffinal) P.ffinal[f] = valid ? (double)bS / (double)bA : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// The work of warp item `item` (of P.witems) of frame f: tasks item * 32 +
+// lane, task = band * G + g (G = n / 8 column groups), each lane its band's
+// nine partial sums; the warp adds their totals to the frame's scratch, and
+// the frame's last item to finish (ticket counter) takes the minimum. Every
+// lane of the warp calls it; no other warp is waited for.
+template <bool TABLE>
+__device__ __forceinline__ void jitter_item(const JitParams& P, int64_t f, int item, uint4* ring) {
     const int m = P.m, n = P.n, band_rows = P.band_rows;
     const uint16_t* __restrict__ frames = P.frames;
     const int64_t fstride = P.fstride;
-    const int tid = threadIdx.x;
+    const int lane = threadIdx.x & 31;
     // Every candidate needs a non-empty overlap: |2 sc| + 1 < m, |2 tc| + 1 < n
     // (always so for a searched-grid optimum; checked for caller-given ones).
     // A frame outside that range is computed at (0, 0), so every index stays
@@ -1643,8 +1691,8 @@ __device__ __forceinline__ void jitter_slice(const JitParams& P, int64_t f, int 
     for (int k = 0; k < 9; ++k) X[k] = 0;
     const int G = n / 8;
     const int nb = (m + band_rows - 1) / band_rows;  // band_rows <= kJitRows
-    const int task = chunk * kJitterThreads + tid;
-    int e_first = 0, e_L = 0;  // this thread's band, for the end-column terms
+    const int task = item * 32 + lane;
+    int e_first = 0, e_L = 0;  // this lane's band, for the end-column terms
     uint32_t e_need = 0;
     if (task < G * nb) {
         const int g = task % G, band = task / G;
@@ -1687,68 +1735,43 @@ __device__ __forceinline__ void jitter_slice(const JitParams& P, int64_t f, int 
         e_L = B.i_e - B.i_b;
     }
     jit_edge_columns(frames + f * fstride, m, n, t0, e_first, e_L, e_need, X);
+    u64 mine = 0;  // lane k < 9: the warp's total of sum k
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         u64 v = X[k];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if ((tid & 31) == 0) red[tid >> 5][k] = v;
+        if (lane == k) mine = v;
     }
-    __syncthreads();
-    if (tid < 9) {
-        u64 sum = 0;
-        for (int wi = 0; wi < kJitterThreads / 32; ++wi) sum += red[wi][tid];
-        atomicAdd(&P.acc[f * 9 + tid], sum);
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) *last = (atomicAdd(&P.ticket[f], 1u) == (unsigned)P.ctas - 1);
-    __syncthreads();
-    if (!*last || tid != 0) return;
-    __threadfence();
-    int bk = -1;
-    u64 bS = 0, bA = 1;
-    int bs = 0, bt = 0;
-    for (int u = 0; u < 3; ++u)
-        for (int v = 0; v < 3; ++v) {
-            const int s = s0 + u - 1, t = t0 + v - 1;
-            const u64 A = (u64)(m - abs(s)) * (u64)(n - abs(t));
-            u64 Sk = atomicAdd(&P.acc[f * 9 + u * 3 + v], 0ull);
-            if (TABLE) Sk += rect_sum(P.bsq, n, max(0, -s), m - max(0, s), max(0, -t), n - max(0, t));
-            bool take = (bk < 0);
-            if (!take) {
-                int eq;
-                const int lt = ratio_lt(Sk, A, bS, bA, &eq);
-                if (lt) take = true;
-                else if (eq) {
-                    const int k1 = abs(s) + abs(t), k2 = abs(bs) + abs(bt);
-                    take = (k1 < k2) || (k1 == k2 && (s < bs || (s == bs && t < bt)));
-                }
-            }
-            if (take) { bk = u * 3 + v; bS = Sk; bA = A; bs = s; bt = t; }
-        }
-    P.shifts[2 * f] = valid ? bs : INT32_MIN;
-    P.shifts[2 * f + 1] = valid ? bt : INT32_MIN;
-    if (P.ffinal) P.ffinal[f] = valid ? (double)bS / (double)bA : __longlong_as_double(0x7ff8000000000000ll);
+    if (lane < 9) atomicAdd(&P.acc[f * 9 + lane], mine);
+    __threadfence();  // the sums before the ticket
+    __syncwarp();
+    unsigned int t = 0;
+    if (lane == 0) t = atomicAdd(&P.ticket[f], 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t != (unsigned int)P.witems - 1) return;
+    __threadfence();  // the other items' sums, seen through their tickets
+    jitter_choose<TABLE>(P, f, s0, t0, valid);
 }
 
-// bsq: the prefix table of b^2 (TABLE) or nullptr (sum b^2 in the loop).
-// Grid (CTAs per frame, frames).
+// Grid (ceil(witems / 8), frames): warp w of CTA x takes item 8 x + w.
 template <bool TABLE>
 __global__ void __launch_bounds__(kJitterThreads, TABLE ? 3 : 1) k_jitter(JitParams P) {
-    __shared__ u64 red[kJitterThreads / 32][9];
-    __shared__ bool last;
     extern __shared__ __align__(16) unsigned char jit_smem[];
     uint4* ring = reinterpret_cast<uint4*>(jit_smem) + threadIdx.x;  // kJitRingBytes
-    jitter_slice<TABLE>(P, blockIdx.y, blockIdx.x, ring, red, &last);
+    const int item = blockIdx.x * (kJitterThreads / 32) + (threadIdx.x >> 5);
+    if (item >= P.witems) return;  // the whole warp
+    jitter_item<TABLE>(P, blockIdx.y, item, ring);
 }
 
-// The refinement of several stacks (shapes, templates) in one persistent
-// launch: resident CTAs take (stack, frame, slice) work items in order from a
-// device counter until none is left. Item i belongs to the segment k with
-// item_base[k] <= i < item_base[k + 1] (segment k covers P[k].ctas slices of
-// each of its frames). A segment is a run of one stack's frames; its P
-// pointers are already offset to the run's first frame.
+// The refinement of one or several stacks (shapes, templates) in one launch:
+// a grid over the (stack, frame, warp item) work items of every segment,
+// warp w of CTA x taking item i = 8 x + w. Item i belongs to the segment k
+// with item_base[k] <= i < item_base[k + 1] (segment k covers P[k].witems
+// items of each of its frames). A segment is a run of one stack's frames; its
+// P pointers are already offset to the run's first frame. (A persistent form,
+// resident warps striding over the items, ran slower here, and one fetching
+// items from a shared counter slower still: every fetch hit one address.)
 constexpr int kJitSegs = 40;  // segments per launch (the parameters stay under 4 KiB)
 struct JitBatch {
     JitParams P[kJitSegs];
@@ -1757,26 +1780,16 @@ struct JitBatch {
 };
 static_assert(sizeof(JitBatch) <= 4096, "kernel parameters of k_jitter_multi");
 
-static __global__ void __launch_bounds__(kJitterThreads, 3) k_jitter_multi(const __grid_constant__ JitBatch batch,
-                                                                     unsigned long long* __restrict__ counter) {
-    __shared__ u64 red[kJitterThreads / 32][9];
-    __shared__ bool last;
-    __shared__ long long s_item;
+static __global__ void __launch_bounds__(kJitterThreads, 3) k_jitter_multi(const __grid_constant__ JitBatch batch) {
     extern __shared__ __align__(16) unsigned char jit_smem[];
     uint4* ring = reinterpret_cast<uint4*>(jit_smem) + threadIdx.x;  // kJitRingBytes
-    const long long total = batch.item_base[batch.nseg];
-    while (true) {
-        __syncthreads();  // the previous item's reads of s_item are done
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
-        __syncthreads();
-        const long long i = s_item;
-        if (i >= total) break;
-        int k = 0;
-        while (k + 1 < batch.nseg && batch.item_base[k + 1] <= i) ++k;
-        const JitParams& P = batch.P[k];
-        const long long local = i - batch.item_base[k];
-        jitter_slice<true>(P, local / P.ctas, (int)(local % P.ctas), ring, red, &last);
-    }
+    const long long i = (long long)blockIdx.x * (kJitterThreads / 32) + (threadIdx.x >> 5);
+    if (i >= batch.item_base[batch.nseg]) return;  // the whole warp
+    int k = 0;
+    while (k + 1 < batch.nseg && batch.item_base[k + 1] <= i) ++k;
+    const JitParams& P = batch.P[k];
+    const long long local = i - batch.item_base[k];
+    jitter_item<true>(P, local / P.witems, (int)(local % P.witems), ring);
 }
 
 // Prefix table of b^2 for k_jitter, P[(m+1) x (n+1)] (exact u64), in two

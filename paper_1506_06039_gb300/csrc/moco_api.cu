@@ -389,7 +389,20 @@ moco_status align_frames(ShapePlan& sp, const uint16_t* frames, int64_t T, int32
             cin = cout;
         }
         sp.prof->begin(sp.levels ? K_JITTER : K_COPY_SHIFTS, st);
-        if (sp.levels)
+        if (sp.levels && sp.bsq) {
+            JitSegment seg;
+            seg.frames = frames + f0 * mn;
+            seg.fstride = mn;
+            seg.T = g;
+            seg.tmpl = static_cast<const uint16_t*>(sp.tmpl);
+            seg.bsq = sp.bsq;
+            seg.coarse = cin;
+            seg.shifts = shifts + 2 * f0;
+            seg.ffinal = final_cost ? final_cost + f0 : nullptr;
+            seg.m = sp.desc.m;
+            seg.n = sp.desc.n;
+            e = launch_jitter_multi(&seg, 1, sp.jit_acc, sp.jit_ticket, g, sp.num_sms, st);
+        } else if (sp.levels)
             e = launch_jitter(frames + f0 * mn, mn, g, static_cast<const uint16_t*>(sp.tmpl), sp.desc.m,
                               sp.desc.n, sp.bsq, cin, shifts + 2 * f0, final_cost ? final_cost + f0 : nullptr,
                               sp.jit_acc, sp.jit_ticket, st);
@@ -543,7 +556,7 @@ moco_status moco_plan(const moco_shape* shapes, int32_t nshapes, const void* con
         // Scratch of the several-stack refinement (nine sums and a ticket per
         // frame of one launch) and the SM count its persistent launch fills.
         const size_t mj = align_up(sizeof(u64) * 9 * kMultiJitFrames, 256) +
-                          align_up(sizeof(unsigned int) * kMultiJitFrames, 256) + 256;
+                          align_up(sizeof(unsigned int) * kMultiJitFrames, 256);
         cudaError_t e = cudaMalloc(&plan->mj_base, mj);
         if (e != cudaSuccess) {
             plan->mj_base = nullptr;
@@ -553,8 +566,6 @@ moco_status moco_plan(const moco_shape* shapes, int32_t nshapes, const void* con
             char* b = static_cast<char*>(plan->mj_base);
             plan->mj_acc = reinterpret_cast<u64*>(b);
             plan->mj_ticket = reinterpret_cast<unsigned int*>(b + align_up(sizeof(u64) * 9 * kMultiJitFrames, 256));
-            plan->mj_counter = reinterpret_cast<unsigned long long*>(
-                b + align_up(sizeof(u64) * 9 * kMultiJitFrames, 256) + align_up(sizeof(unsigned int) * kMultiJitFrames, 256));
             e = cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device);
             if (e != cudaSuccess) s = cuda_fail(e, "device query");
         }
@@ -664,7 +675,7 @@ moco_status moco_align_stack(moco_plan_t plan, const moco_stack* stacks, int32_t
     if (!segs.empty()) {
         plan->prof.begin(K_JITTER, st);
         cudaError_t e = launch_jitter_multi(segs.data(), (int)segs.size(), plan->mj_acc, plan->mj_ticket,
-                                            kMultiJitFrames, plan->mj_counter, plan->num_sms, st);
+                                            kMultiJitFrames, plan->num_sms, st);
         plan->prof.end(st);
         if (e != cudaSuccess) return cuda_fail(e, "k_jitter_multi");
     }

@@ -125,6 +125,5 @@ struct moco_plan_s {
     void* mj_base = nullptr;
     moco::u64* mj_acc = nullptr;
     unsigned int* mj_ticket = nullptr;
-    unsigned long long* mj_counter = nullptr;
     int num_sms = 0;
 };

@@ -92,15 +92,15 @@ cudaError_t launch_pair_from_double(const double* x, float2* out, int64_t count,
     return cudaGetLastError();
 }
 
-// Slices of kJitterThreads threads per frame, and the band height: bands of
-// kJitRows rows; a small batch (fewer CTAs than two waves of 152 SMs) takes
-// bands of 16 or 8 rows so that more CTAs share a frame.
-static void jitter_shape(int m, int n, int64_t nimg, int* band_rows, int* ctas) {
+// Warp items per frame (32 band-and-column-group tasks each) and the band
+// height: bands of kJitRows rows; a small batch (fewer warps than two waves of
+// eight per SM) takes bands of 16 or 8 rows so that more warps share a frame.
+static void jitter_shape(int m, int n, int64_t nimg, int num_sms, int* band_rows, int* witems) {
     int br = kJitRows;
-    auto ctas_for = [&](int b) { return ((n / 8) * ((m + b - 1) / b) + kJitterThreads - 1) / kJitterThreads; };
-    while (br > 8 && (int64_t)ctas_for(br) * nimg < 2 * 152) br /= 2;
+    auto items_for = [&](int b) { return ((n / 8) * ((m + b - 1) / b) + 31) / 32; };
+    while (br > 8 && (int64_t)items_for(br) * nimg < 2 * (int64_t)num_sms * (kJitterThreads / 32)) br /= 2;
     *band_rows = br;
-    *ctas = ctas_for(br);
+    *witems = items_for(br);
 }
 
 cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg, const uint16_t* tmpl, int m,
@@ -122,8 +122,9 @@ cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg,
     P.ticket = ticket;
     P.m = m;
     P.n = n;
-    jitter_shape(m, n, nimg, &P.band_rows, &P.ctas);
-    dim3 grid((unsigned)P.ctas, (unsigned)nimg);
+    jitter_shape(m, n, nimg, 152, &P.band_rows, &P.witems);
+    constexpr int wpc = kJitterThreads / 32;  // warps (items) per CTA
+    dim3 grid((unsigned)((P.witems + wpc - 1) / wpc), (unsigned)nimg);
     const void* fn = bsq ? reinterpret_cast<const void*>(k_jitter<true>) : reinterpret_cast<const void*>(k_jitter<false>);
     e = ensure_smem(fn, kJitRingBytes);
     if (e != cudaSuccess) return e;
@@ -133,18 +134,24 @@ cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg,
 }
 
 cudaError_t launch_jitter_multi(const JitSegment* segs, int nseg, u64* acc, unsigned int* ticket, int64_t capacity,
-                                unsigned long long* counter, int num_sms, cudaStream_t st) {
+                                int num_sms, cudaStream_t st) {
     int k0 = 0;
     while (k0 < nseg) {
         // The next launch: up to kJitSegs segments whose frames fit the scratch.
-        JitBatch batch;
         int ns = 0;
-        int64_t frames = 0, items = 0;
+        int64_t frames = 0;
         while (k0 + ns < nseg && ns < kJitSegs) {
             const JitSegment& g = segs[k0 + ns];
-            if (g.T > capacity) return cudaErrorInvalidValue;
+            if (g.T > capacity || !g.bsq) return cudaErrorInvalidValue;
             if (frames + g.T > capacity) break;
-            JitParams& P = batch.P[ns];
+            frames += g.T;
+            ++ns;
+        }
+        JitBatch batch;
+        int64_t items = 0, f = 0;
+        for (int k = 0; k < ns; ++k) {
+            const JitSegment& g = segs[k0 + k];
+            JitParams& P = batch.P[k];
             P.frames = g.frames;
             P.fstride = g.fstride;
             P.tmpl = g.tmpl;
@@ -152,16 +159,15 @@ cudaError_t launch_jitter_multi(const JitSegment* segs, int nseg, u64* acc, unsi
             P.coarse = g.coarse;
             P.shifts = g.shifts;
             P.ffinal = g.ffinal;
-            P.acc = acc + 9 * frames;
-            P.ticket = ticket + frames;
+            P.acc = acc + 9 * f;
+            P.ticket = ticket + f;
             P.m = g.m;
             P.n = g.n;
-            // bands sized for a launch that spreads over every SM
-            jitter_shape(g.m, g.n, 1 << 20, &P.band_rows, &P.ctas);
-            batch.item_base[ns] = items;
-            items += g.T * P.ctas;
-            frames += g.T;
-            ++ns;
+            // bands sized by the whole launch's frames
+            jitter_shape(g.m, g.n, frames, num_sms, &P.band_rows, &P.witems);
+            batch.item_base[k] = items;
+            items += g.T * P.witems;
+            f += g.T;
         }
         batch.nseg = ns;
         batch.item_base[ns] = items;
@@ -169,12 +175,10 @@ cudaError_t launch_jitter_multi(const JitSegment* segs, int nseg, u64* acc, unsi
         if (items == 0) continue;
         cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(u64) * 9 * frames, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int) * frames, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
         if (e == cudaSuccess) e = ensure_smem(reinterpret_cast<const void*>(k_jitter_multi), kJitRingBytes);
         if (e != cudaSuccess) return e;
-        const int64_t resident = (int64_t)num_sms * 3;  // three CTAs per SM (__launch_bounds__)
-        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(resident, items));
-        k_jitter_multi<<<grid, kJitterThreads, kJitRingBytes, st>>>(batch, counter);
+        constexpr int wpc = kJitterThreads / 32;  // warps (items) per CTA
+        k_jitter_multi<<<(unsigned)((items + wpc - 1) / wpc), kJitterThreads, kJitRingBytes, st>>>(batch);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
