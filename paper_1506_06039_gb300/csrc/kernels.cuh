@@ -1349,12 +1349,14 @@ __device__ __forceinline__ uint4 jit_tmpl_row(const JitBand& B, int i) {
     return __ldg(reinterpret_cast<const uint4*>(B.tmpl + (int64_t)i * B.n + B.j0));
 }
 
-// Shared-memory ring of rows in flight: stage q % kJitRing holds, per thread,
-// the raw chunks of frame row first + q and (q >= 2) template row
-// i_b + q - 2, as ring[((stage * 4) + c) * kJitterThreads + tid], c = 0, 1, 2
-// frame chunks, 3 template; each thread copies and reads only its own column
-// (cp.async, one commit group per row), so no barrier is needed.
-constexpr int kJitRing = 4;
+// Shared-memory ring of rows in flight: stage q % 3 holds, per thread, the
+// raw chunks of frame row first + q and (q >= 2) template row i_b + q - 2, as
+// ring[((stage * 4) + c) * kJitterThreads + tid], c = 0, 1, 2 frame chunks,
+// 3 template; each thread copies and reads only its own column (cp.async,
+// one commit group per row), so no barrier is needed. Three stages, as many
+// as the window's slots, so that the loop unrolled three times names every
+// stage at compile time.
+constexpr int kJitRing = 3;
 constexpr size_t kJitRingBytes = (size_t)kJitRing * 4 * kJitterThreads * 16;
 
 // The next row to copy: its frame row ar, the 32-bit element offsets of its
@@ -1366,9 +1368,9 @@ struct JitCursor {
     int ar, left;
 };
 
-template <int O>
-__device__ __forceinline__ void jit_issue(const JitBand& B, uint4* ring, int q, JitCursor& cur) {
-    uint4* st = ring + (q & (kJitRing - 1)) * 4 * kJitterThreads;
+template <int O, int STAGE>
+__device__ __forceinline__ void jit_issue(const JitBand& B, uint4* ring, bool with_tmpl, JitCursor& cur) {
+    uint4* st = ring + STAGE * 4 * kJitterThreads;
     if (cur.left > 0) {
         const bool rok = (unsigned)cur.ar < (unsigned)B.m;  // the same for the whole warp
 #pragma unroll
@@ -1376,7 +1378,7 @@ __device__ __forceinline__ void jit_issue(const JitBand& B, uint4* ring, int q, 
             const bool ok = rok && ((B.cvalid >> c) & 1u);
             cp16z(st + c * kJitterThreads, B.a + (ok ? cur.foff + 8u * c : 0u), ok ? 16u : 0u);
         }
-        if (q >= 2) {
+        if (with_tmpl) {
             cp16z(st + 3 * kJitterThreads, B.tmpl + cur.toff, 16u);
             cur.toff += (uint32_t)B.n;
         }
@@ -1387,11 +1389,11 @@ __device__ __forceinline__ void jit_issue(const JitBand& B, uint4* ring, int q, 
     cp_commit();
 }
 
-// Row q from the ring (its copy group complete) into slot x; its template row
-// into *tr when asked.
-template <int O>
-__device__ __forceinline__ void jit_take(const uint4* ring, int q, JitSlot<O>& x, uint4* tr) {
-    const uint4* st = ring + (q & (kJitRing - 1)) * 4 * kJitterThreads;
+// The row in ring stage STAGE (its copy group complete) into slot x; its
+// template row into *tr when asked.
+template <int O, int STAGE>
+__device__ __forceinline__ void jit_take(const uint4* ring, JitSlot<O>& x, uint4* tr) {
+    const uint4* st = ring + STAGE * 4 * kJitterThreads;
     const uint4 c0 = st[0], c1 = st[kJitterThreads];
     x.raw[0] = c0.x;
     x.raw[1] = c0.y;
@@ -1407,19 +1409,19 @@ __device__ __forceinline__ void jit_take(const uint4* ring, int q, JitSlot<O>& x
 }
 
 // Step j of a band (K = j mod 3), template row i = i_b + j: slots K, K+1
-// hold frame rows i+s0-1, i+s0; slot K+2 receives row i+s0+1 (ring row j+2)
-// with template row i, and ring row j+2+kJitRing is issued into its stage.
+// hold frame rows i+s0-1, i+s0; slot K+2 receives row i+s0+1 (ring row j+2,
+// stage (K + 2) mod 3) with template row i, and ring row j+5 is issued into
+// the same stage.
 template <bool TABLE, int O, int K>
 __device__ __forceinline__ void jit_step(const JitBand& B, int i, uint4* ring, JitCursor& cur, JitSlot<O> (&S)[3],
                                          Acc2 (&C)[9],
                                          Acc2& M, Acc2 (&QB)[3], const uint32_t (&cm)[12]) {
-    const int j = i - B.i_b;
     JitSlot<O>& w0 = S[K];
     JitSlot<O>& w1 = S[(K + 1) % 3];
     JitSlot<O>& w2 = S[(K + 2) % 3];
     uint4 tr;
     cp_wait<kJitRing - 1>();
-    jit_take(ring, j + 2, w2, &tr);
+    jit_take<O, (K + 2) % 3>(ring, w2, &tr);
     const uint32_t bw[4] = {tr.x, tr.y, tr.z, tr.w};
     uint32_t bp[4];
 #pragma unroll
@@ -1439,7 +1441,7 @@ __device__ __forceinline__ void jit_step(const JitBand& B, int i, uint4* ring, J
     if (i <= B.i_e - 3) row_energy(w2, M);  // frame row shared by all three u
     if (!TABLE)
         if (i + B.s0 - 1 >= 0 && i + B.s0 + 1 <= B.m - 1) tmpl_energy(bw, bp, cm, QB);
-    jit_issue<O>(B, ring, j + 2 + kJitRing, cur);  // the stage just read (its data is consumed)
+    jit_issue<O, (K + 2) % 3>(B, ring, true, cur);  // the stage just read (its data is consumed)
 }
 
 // X[u*3+v] += energy e of frame row r (its v = 0 window, every v) for each
@@ -1521,14 +1523,15 @@ __device__ __forceinline__ void jit_band(const JitBand& B, uint4* ring, uint32_t
     cur.foff = (uint32_t)B.first * (uint32_t)B.n + (uint32_t)B.c0;
     cur.toff = (uint32_t)B.i_b * (uint32_t)B.n + (uint32_t)B.j0;
     cur.left = B.i_e - B.i_b + 2;  // rows first .. first + L + 1
-#pragma unroll
-    for (int q = 0; q < kJitRing; ++q) jit_issue<O>(B, ring, q, cur);
+    jit_issue<O, 0>(B, ring, false, cur);
+    jit_issue<O, 1>(B, ring, false, cur);
+    jit_issue<O, 2>(B, ring, true, cur);
     cp_wait<kJitRing - 1>();
-    jit_take(ring, 0, S[0], nullptr);
-    jit_issue<O>(B, ring, kJitRing, cur);
+    jit_take<O, 0>(ring, S[0], nullptr);
+    jit_issue<O, 0>(B, ring, true, cur);
     cp_wait<kJitRing - 1>();
-    jit_take(ring, 1, S[1], nullptr);
-    jit_issue<O>(B, ring, kJitRing + 1, cur);
+    jit_take<O, 1>(ring, S[1], nullptr);
+    jit_issue<O, 1>(B, ring, true, cur);
     for (int i = B.i_b;;) {
         jit_step<TABLE, O, 0>(B, i, ring, cur, S, C, M, QB, cm);
         if (++i >= B.i_e) break;
