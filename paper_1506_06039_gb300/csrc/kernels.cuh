@@ -1355,16 +1355,19 @@ __device__ __forceinline__ uint4 jit_tmpl_row(const JitBand& B, int i) {
 // 3 template; each thread copies and reads only its own column (cp.async,
 // one commit group per row), so no barrier is needed. Three stages, as many
 // as the window's slots, so that the loop unrolled three times names every
-// stage at compile time.
+// stage at compile time. Only chunks inside the frame are copied: a chunk
+// outside it (the same columns for every row of a band) is zeroed in every
+// stage once, when the band starts, and a row outside the frame is zeroed
+// when it is taken.
 constexpr int kJitRing = 3;
 constexpr size_t kJitRingBytes = (size_t)kJitRing * 4 * kJitterThreads * 16;
 
-// The next row to copy: its frame row ar, the 32-bit element offsets of its
-// first raw chunk in the frame and of its template row, rows left to issue.
-// The offsets advance by n per row (modular: exact whenever a chunk is inside
-// the frame, m n < 2^31).
+// The next row to copy: its frame row ar, the addresses of its first raw
+// chunk (columns c0 .. c0 + 7 of row ar; read only where inside the frame)
+// and of its template row's chunk, rows left to issue.
 struct JitCursor {
-    uint32_t foff, toff;
+    const uint16_t* fp;
+    const uint16_t* tp;
     int ar, left;
 };
 
@@ -1372,27 +1375,26 @@ template <int O, int STAGE>
 __device__ __forceinline__ void jit_issue(const JitBand& B, uint4* ring, bool with_tmpl, JitCursor& cur) {
     uint4* st = ring + STAGE * 4 * kJitterThreads;
     if (cur.left > 0) {
-        const bool rok = (unsigned)cur.ar < (unsigned)B.m;  // the same for the whole warp
+        const bool rok = (unsigned)cur.ar < (unsigned)B.m;
 #pragma unroll
-        for (int c = 0; c < (O == 3 ? 3 : 2); ++c) {
-            const bool ok = rok && ((B.cvalid >> c) & 1u);
-            cp16z(st + c * kJitterThreads, B.a + (ok ? cur.foff + 8u * c : 0u), ok ? 16u : 0u);
-        }
+        for (int c = 0; c < (O == 3 ? 3 : 2); ++c)
+            cp16_if(rok && ((B.cvalid >> c) & 1u), st + c * kJitterThreads, cur.fp + 8 * c);
         if (with_tmpl) {
-            cp16z(st + 3 * kJitterThreads, B.tmpl + cur.toff, 16u);
-            cur.toff += (uint32_t)B.n;
+            cp16(st + 3 * kJitterThreads, cur.tp);
+            cur.tp += B.n;
         }
-        cur.foff += (uint32_t)B.n;
+        cur.fp += B.n;
         ++cur.ar;
         --cur.left;
     }
     cp_commit();
 }
 
-// The row in ring stage STAGE (its copy group complete) into slot x; its
-// template row into *tr when asked.
+// The row in ring stage STAGE (its copy group complete) into slot x, zeros
+// when the row lies outside the frame (rok false); its template row into *tr
+// when asked.
 template <int O, int STAGE>
-__device__ __forceinline__ void jit_take(const uint4* ring, JitSlot<O>& x, uint4* tr) {
+__device__ __forceinline__ void jit_take(const uint4* ring, bool rok, JitSlot<O>& x, uint4* tr) {
     const uint4* st = ring + STAGE * 4 * kJitterThreads;
     const uint4 c0 = st[0], c1 = st[kJitterThreads];
     x.raw[0] = c0.x;
@@ -1404,6 +1406,9 @@ __device__ __forceinline__ void jit_take(const uint4* ring, JitSlot<O>& x, uint4
     x.raw[6] = c1.z;
     x.raw[7] = c1.w;
     if (O == 3) x.raw[(O == 3) ? 8 : 0] = st[2 * kJitterThreads].x;
+    if (!rok)
+#pragma unroll
+        for (int k = 0; k < (O == 3 ? 9 : 8); ++k) x.raw[k] = 0u;
     if (tr) *tr = st[3 * kJitterThreads];
     jit_unpack(x);
 }
@@ -1421,7 +1426,7 @@ __device__ __forceinline__ void jit_step(const JitBand& B, int i, uint4* ring, J
     JitSlot<O>& w2 = S[(K + 2) % 3];
     uint4 tr;
     cp_wait<kJitRing - 1>();
-    jit_take<O, (K + 2) % 3>(ring, w2, &tr);
+    jit_take<O, (K + 2) % 3>(ring, (unsigned)(i + B.s0 + 1) < (unsigned)B.m, w2, &tr);
     const uint32_t bw[4] = {tr.x, tr.y, tr.z, tr.w};
     uint32_t bp[4];
 #pragma unroll
@@ -1520,17 +1525,22 @@ __device__ __forceinline__ void jit_band(const JitBand& B, uint4* ring, uint32_t
     JitSlot<O> S[3];
     JitCursor cur;
     cur.ar = B.first;
-    cur.foff = (uint32_t)B.first * (uint32_t)B.n + (uint32_t)B.c0;
-    cur.toff = (uint32_t)B.i_b * (uint32_t)B.n + (uint32_t)B.j0;
+    cur.fp = B.a + ((int64_t)B.first * B.n + B.c0);
+    cur.tp = B.tmpl + ((int64_t)B.i_b * B.n + B.j0);
     cur.left = B.i_e - B.i_b + 2;  // rows first .. first + L + 1
+#pragma unroll
+    for (int c = 0; c < (O == 3 ? 3 : 2); ++c)
+        if (!((B.cvalid >> c) & 1u))
+#pragma unroll
+            for (int q = 0; q < kJitRing; ++q) ring[(q * 4 + c) * kJitterThreads] = make_uint4(0u, 0u, 0u, 0u);
     jit_issue<O, 0>(B, ring, false, cur);
     jit_issue<O, 1>(B, ring, false, cur);
     jit_issue<O, 2>(B, ring, true, cur);
     cp_wait<kJitRing - 1>();
-    jit_take<O, 0>(ring, S[0], nullptr);
+    jit_take<O, 0>(ring, (unsigned)first < (unsigned)B.m, S[0], nullptr);
     jit_issue<O, 0>(B, ring, true, cur);
     cp_wait<kJitRing - 1>();
-    jit_take<O, 1>(ring, S[1], nullptr);
+    jit_take<O, 1>(ring, (unsigned)(first + 1) < (unsigned)B.m, S[1], nullptr);
     jit_issue<O, 1>(B, ring, true, cur);
     for (int i = B.i_b;;) {
         jit_step<TABLE, O, 0>(B, i, ring, cur, S, C, M, QB, cm);

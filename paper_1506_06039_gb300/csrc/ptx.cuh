@@ -47,6 +47,15 @@ __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 16-byte asynchronous copy issued only when p: a predicated-off copy reads
+// and writes nothing.
+__device__ __forceinline__ void cp16_if(bool p, void* smem, const void* gmem) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q cp.async.cg.shared.global [%0], [%1], 16;\n\t}" ::"r"(
+            smem_u32(smem)),
+        "l"(gmem), "r"((uint32_t)p)
+        : "memory");
+}
 // 16-byte asynchronous copy that reads src_bytes (0 or 16) and fills the
 // rest of the 16 bytes with zeros (src is not read when src_bytes is 0).
 __device__ __forceinline__ void cp16z(void* smem, const void* gmem, uint32_t src_bytes) {
