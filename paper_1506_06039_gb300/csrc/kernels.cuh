@@ -215,6 +215,28 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
                     // Only chunks that hold an edge row (r < w-1 or r >= mc-(w-1))
                     // have per-row energies or corner values to record.
                     const bool edge_chunk = r0 < wm1 || r0 + rows > mc - wm1;
+                    if (levels && !edge_chunk && rows == kRC) {
+                        // A full chunk without edge rows (most of them): box sums,
+                        // values and the energies of the total and the edge
+                        // columns only, by pointers that step a row pair at a time.
+                        const uint32_t* q = s32 + (size_t)(4 * p0) * hw + c;
+                        float2* bq = buf + p0 * LD + skc;
+                        const int qstep = 4 * PPI * hw, bstep = PPI * LD;
+#pragma unroll 4
+                        for (int pr = p0; pr < nfft; pr += PPI, q += qstep, bq += bstep) {
+                            const int s0 = (int)add_halves(q[0], add_halves(q[hw], 0u));
+                            const int s1 = (int)add_halves(q[2 * hw], add_halves(q[3 * hw], 0u));
+                            *bq = make_float2(__int_as_float(s0 + bias) - 12582912.0f,
+                                              __int_as_float(s1 + bias) - 12582912.0f);
+                            const int d0 = s0 - ci_off, d1 = s1 - ci_off;
+                            add_sq(tacc, d0);
+                            add_sq(tacc, d1);
+                            if (ecol) {
+                                add_sq(colreg[0], d0);
+                                add_sq(colreg[0], d1);
+                            }
+                        }
+                    } else
                     for (int pr = p0; pr < nfft; pr += PPI) {
                         const int rl = 2 * pr;
                         const bool has1 = rl + 1 < rows;  // the same for the whole warp
