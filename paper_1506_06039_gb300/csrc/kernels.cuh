@@ -1242,11 +1242,11 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 //
 // Frame values outside the frame are read as zero, so sum a b and sum a^2
 // need no mask. sum_D b^2 depends on the template and (s, t) only: with a
-// 2-D prefix table of b^2 (TABLE) the frame's last CTA reads it at four
+// 2-D prefix table of b^2 (TABLE) the frame's last warp item reads it at four
 // corners per shift; without one it is summed in the loop, a template
 // position counting only when its partner lies inside the frame.
 //
-// Grid (CTAs per frame, frames). Each thread owns the template columns
+// Work comes in warp items (below). Each thread owns the template columns
 // j0 .. j0+7 of a band of band_rows (<= kJitRows) rows and walks down it keeping the three
 // frame rows r = i + 2 sc - 1 + u (u = 0, 1, 2) as 16-bit pairs, columns
 // counted from lead = j0 + 2 tc - 1 (odd):
@@ -1256,8 +1256,8 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 // rw are the aligned 32-bit words themselves; pw take one byte permute each.
 // An aligned word (even column c, c + 1; n even) lies wholly inside or
 // wholly outside the frame, so every thread runs the same code: a word
-// outside is a predicated-off load that leaves zero. A row outside the frame
-// is the same for the whole warp (one band, one frame).
+// outside is a predicated-off load that leaves zero; so is a row outside the
+// frame.
 // Frame and template rows arrive through a ring of asynchronous copies
 // kJitRing rows ahead (below), and the loop is unrolled three times so that
 // the window rotates without copies.
@@ -1272,9 +1272,9 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
 // In-loop sum b^2: template rows whose partner rows are valid for all three
 // u accumulate once; the at most four rows valid for only some u are added
 // at the end.
-// Per-CTA partial sums go to acc[f][9] by 64-bit atomics (two's complement
-// wrap-around: the total is exact); the last CTA of a frame (ticket counter)
-// adds sum_D b^2 (TABLE) and takes the minimum of S / Area with the
+// Per-warp partial sums go to acc[f][9] by 64-bit atomics (two's complement
+// wrap-around: the total is exact); the last warp item of a frame (ticket
+// counter) adds sum_D b^2 (TABLE) and takes the minimum of S / Area with the
 // tie-break, compared as exact rationals. acc and ticket are zero on entry.
 constexpr int kJitRows = 32;  // band height (at most: the launcher may pick shorter bands)
 static_assert(kJitRows <= 32, "32-bit dot-product sums are exact for at most 32 rows of 8 columns");
