@@ -236,6 +236,43 @@ k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, in
                                 add_sq(colreg[0], d1);
                             }
                         }
+                    } else if (levels && rows == kRC && warp_rows) {
+                        // A full chunk with edge rows: the same, plus each edge row's
+                        // energy (a warp holds one row pair: two 32-bit warp sums of
+                        // the 18-bit halves of d^2, added by lane 0) and, in the edge
+                        // columns, its corner values.
+                        const uint32_t* q = s32 + (size_t)(4 * p0) * hw + c;
+                        float2* bq = buf + p0 * LD + skc;
+                        const int qstep = 4 * PPI * hw, bstep = PPI * LD;
+                        const int cj = c >= nc - wm1 ? c - (nc - wm1) : c, qc = c >= nc - wm1 ? 1 : 0;
+                        for (int pr = p0; pr < nfft; pr += PPI, q += qstep, bq += bstep) {
+                            const int s0 = (int)add_halves(q[0], add_halves(q[hw], 0u));
+                            const int s1 = (int)add_halves(q[2 * hw], add_halves(q[3 * hw], 0u));
+                            *bq = make_float2(__int_as_float(s0 + bias) - 12582912.0f,
+                                              __int_as_float(s1 + bias) - 12582912.0f);
+                            const int d0 = s0 - ci_off, d1 = s1 - ci_off;
+                            add_sq(tacc, d0);
+                            add_sq(tacc, d1);
+                            if (ecol) {
+                                add_sq(colreg[0], d0);
+                                add_sq(colreg[0], d1);
+                            }
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int rr = r0 + 2 * pr + h;  // the same for the whole warp
+                                const bool top = rr < wm1, bot = rr >= mc - wm1;
+                                if (!(top || bot)) continue;
+                                const int dh = h ? d1 : d0;
+                                const u64 eh = (u64)((long long)dh * dh);
+                                const uint32_t lo = __reduce_add_sync(0xffffffffu, (uint32_t)(eh & 0x3ffffu));
+                                const uint32_t hi = __reduce_add_sync(0xffffffffu, (uint32_t)(eh >> 18));
+                                if ((tid & 31) == 0) atomicAdd(&rowacc[2 * pr + h], ((u64)hi << 18) + lo);
+                                if (ecol) {
+                                    const int ri = top ? rr : rr - (mc - wm1);
+                                    corners[(f * 4 + (bot ? 2 : 0) + qc) * wm1sq + (size_t)ri * wm1 + cj] = (uint32_t)dh;
+                                }
+                            }
+                        }
                     } else
                     for (int pr = p0; pr < nfft; pr += PPI) {
                         const int rl = 2 * pr;
