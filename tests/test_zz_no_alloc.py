@@ -59,7 +59,9 @@ def two_calls(frames, tmpl, coarse):
 
 def test_noalloc_jitter_matches_align_stack_and_oracle_twice():
     build.build()
-    m, n, w, T = 320, 272, 10, 200  # 2 CTAs per frame x 200 frames: full 32-row bands
+    # 11 warp items per frame (34 column groups x 10 bands of 32 rows) x 240 frames = 2640
+    # warps, at least two waves of eight per SM of 152: the launcher keeps full 32-row bands
+    m, n, w, T = 320, 272, 10, 240
     st = synth.make_stack_np(m, n, T, 60, 12, seed=2718, template="clean")
     frames = torch.from_numpy(st.frames).cuda()
     tmpl = torch.from_numpy(st.template).cuda()
