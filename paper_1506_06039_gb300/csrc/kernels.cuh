@@ -107,8 +107,14 @@ __host__ __device__ constexpr size_t frame_rows_stage_bytes(int n, int levels) {
 }
 constexpr uint32_t kStageCopyBytes = 16384;  // bulk copies of at most 16 KiB each
 
+// Staged passes at N >= 512 hold more than half of an SM's shared memory
+// (n > 2 (N_prev - 127) columns of staged rows beside the transform buffer):
+// one CTA per SM, so the registers are not capped for two.
+template <int N, bool STAGED>
+__host__ __device__ constexpr int frame_rows_min_blocks() { return STAGED && N >= 512 ? 1 : 2; }
+
 template <int N, bool F32IN, bool PLANES = false, bool STAGED = false>
-__global__ void __launch_bounds__(kRowsThreads, 2)
+__global__ void __launch_bounds__(kRowsThreads, frame_rows_min_blocks<N, STAGED>())
 k_frame_rows(const void* __restrict__ src, int64_t src_fstride, int m, int n, int levels, int mc,
              int nc, const int32_t* __restrict__ coff_i, const float* __restrict__ coff_f,
              const float2* __restrict__ tw_g, float2* __restrict__ X, int64_t x_fstride, int ldx,

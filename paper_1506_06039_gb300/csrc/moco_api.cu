@@ -630,8 +630,8 @@ moco_status moco_align_stack(moco_plan_t plan, const moco_stack* stacks, int32_t
     // Stacks searched on one 2x2 level and refined at full resolution (the
     // paper's rule above 256x256): with two or more of them, every stack's
     // search runs first, writing its searched-grid optima into the caller's
-    // shift buffer, then one persistent refinement launch takes (stack,
-    // frame, slice) items of all of them until none is left.
+    // shift buffer, then one refinement launch runs a grid over the (stack,
+    // frame, warp item) work items of all of them.
     auto deferred = [&](const moco_stack& s) {
         const ShapePlan& sp = plan->shapes[s.shape_idx];
         return s.T > 0 && sp.levels == 1 && sp.bsq != nullptr;
