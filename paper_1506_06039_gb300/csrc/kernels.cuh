@@ -760,18 +760,33 @@ __device__ __forceinline__ double f32_to_f64(float x) {
 // later segments add as their starting carry; then it walks its rows: each
 // row's squares, their prefix along the columns (lane-local, then one warp
 // scan of the lane totals), added to the carry, give P_q[a][b] for the row,
-// and emit(s, t, Sa) is called for each of its shifts. Every thread of the
-// block must call it (it synchronises once); shared memory:
-// energy_sweep_smem(wm1, warps). Needs w <= 32 K and at least four warps.
+// and emit(s, t, Sa) is called for each of its shifts. With a fetch functor,
+// fetch(s, t) is called for every shift of the lane's next row while the
+// current row is scanned (loads in flight a row ahead), and its value comes
+// back as emit(s, t, Sa, value). Every thread of the block must call it (it
+// synchronises once); shared memory: energy_sweep_smem(wm1, warps). Needs
+// w <= 32 K and at least four warps.
 __host__ __device__ constexpr int sweep_groups(int warps) { return warps >= 8 ? warps / 4 : 1; }
 __host__ __device__ constexpr size_t energy_sweep_smem(int wm1, int warps) {
     return sizeof(u64) * (2 * (2 * (size_t)wm1 + 1) + 4 * (size_t)sweep_groups(warps) * (wm1 + 1));
 }
 
-template <int K, typename Emit>
-__device__ __forceinline__ void energy_sweep(const u64* __restrict__ rE, const u64* __restrict__ cE, u64 T,
-                                             const uint32_t* __restrict__ corners_f, int mc, int nc, int wm1,
-                                             unsigned char* smem, Emit emit) {
+// No per-shift values to fetch: emit(s, t, Sa).
+struct SweepNoFetch {
+    struct V {};
+    __device__ __forceinline__ V operator()(int, int) const { return V{}; }
+};
+template <typename Emit>
+struct SweepEmit3 {
+    Emit& e;
+    __device__ __forceinline__ void operator()(int s, int t, u64 sa, SweepNoFetch::V) const { e(s, t, sa); }
+};
+
+template <int K, typename Emit, typename Fetch>
+__device__ __forceinline__ void energy_sweep_f(const u64* __restrict__ rE, const u64* __restrict__ cE, u64 T,
+                                               const uint32_t* __restrict__ corners_f, int mc, int nc, int wm1,
+                                               unsigned char* smem, Emit emit, Fetch fetch) {
+    using V = decltype(fetch(0, 0));
     const int W = 2 * wm1 + 1, w = wm1 + 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int G = sweep_groups(nwarps);
@@ -865,7 +880,16 @@ __device__ __forceinline__ void energy_sweep(const u64* __restrict__ rE, const u
         if (b < w)
             for (int g2 = 0; g2 < g; ++g2) carry[k] += seg[((size_t)q * G + g2) * w + b];
     }
-    auto emit_row = [&](int a) {
+    // The shifts of table row a at this lane's columns: whether each exists.
+    auto row_fetch = [&](int a, V (&val)[K]) {
+        const int s = bottom ? -a : a;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int b = K * lane + k;
+            if (b < w && !(right && b == 0)) val[k] = fetch(s, right ? -b : b);
+        }
+    };
+    auto emit_row = [&](int a, const V (&val)[K]) {
         const int s = bottom ? -a : a;
         const u64 base = T - exR[s + wm1];
 #pragma unroll
@@ -873,25 +897,47 @@ __device__ __forceinline__ void energy_sweep(const u64* __restrict__ rE, const u
             const int b = K * lane + k;
             if (b < w && !(right && b == 0)) {
                 const int t = right ? -b : b;
-                emit(s, t, base - exC[t + wm1] + carry[k]);
+                emit(s, t, base - exC[t + wm1] + carry[k], val[k]);
             }
         }
     };
-    if (g == 0 && !bottom) emit_row(0);  // a = 0: no corner rows (s = 0 belongs to the top quadrants)
+    V vnext[K];  // the next row's fetched values, loaded one row ahead
+    if (g == 0 && !bottom) {  // a = 0: no corner rows (s = 0 belongs to the top quadrants)
+        V v0[K];
+        row_fetch(0, v0);
+        emit_row(0, v0);
+    }
     int32_t nxt[K];  // the next row's corner values, loaded one row ahead
-    if (a0 < a1) row_raw(a0, nxt);
+    if (a0 < a1) {
+        row_raw(a0, nxt);
+        row_fetch(a0, vnext);
+    }
     for (int a = a0; a < a1; ++a) {
         int32_t c[K];
+        V vcur[K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) c[k] = nxt[k];
-        if (a + 1 < a1) row_raw(a + 1, nxt);
+        for (int k = 0; k < K; ++k) {
+            c[k] = nxt[k];
+            vcur[k] = vnext[k];
+        }
+        if (a + 1 < a1) {
+            row_raw(a + 1, nxt);
+            row_fetch(a + 1, vnext);
+        }
         u64 v[K];
         squares(c, v);
         col_prefix(v);
 #pragma unroll
         for (int k = 0; k < K; ++k) carry[k] += v[k];
-        emit_row(a);
+        emit_row(a, vcur);
     }
+}
+
+template <int K, typename Emit>
+__device__ __forceinline__ void energy_sweep(const u64* __restrict__ rE, const u64* __restrict__ cE, u64 T,
+                                             const uint32_t* __restrict__ corners_f, int mc, int nc, int wm1,
+                                             unsigned char* smem, Emit emit) {
+    energy_sweep_f<K>(rE, cE, T, corners_f, mc, nc, wm1, smem, SweepEmit3<Emit>{emit}, SweepNoFetch{});
 }
 
 // energy_sweep with K = ceil(w / 32) columns per lane (w <= 128).
@@ -904,6 +950,21 @@ __device__ __forceinline__ void energy_sweep_any(const u64* __restrict__ rE, con
     else if (wm1 < 96) energy_sweep<3>(rE, cE, T, corners_f, mc, nc, wm1, smem, emit);
     else energy_sweep<4>(rE, cE, T, corners_f, mc, nc, wm1, smem, emit);
 }
+template <typename Emit, typename Fetch>
+__device__ __forceinline__ void energy_sweep_any_f(const u64* __restrict__ rE, const u64* __restrict__ cE, u64 T,
+                                                   const uint32_t* __restrict__ corners_f, int mc, int nc, int wm1,
+                                                   unsigned char* smem, Emit emit, Fetch fetch) {
+    if (wm1 < 32) energy_sweep_f<1>(rE, cE, T, corners_f, mc, nc, wm1, smem, emit, fetch);
+    else if (wm1 < 64) energy_sweep_f<2>(rE, cE, T, corners_f, mc, nc, wm1, smem, emit, fetch);
+    else if (wm1 < 96) energy_sweep_f<3>(rE, cE, T, corners_f, mc, nc, wm1, smem, emit, fetch);
+    else energy_sweep_f<4>(rE, cE, T, corners_f, mc, nc, wm1, smem, emit, fetch);
+}
+
+// The template-side operands of one shift's combine.
+struct CombineOps {
+    float2 sb;  // Sb as an FP32 pair
+    float ia;   // 1 / Area (times the unit)
+};
 
 template <bool F32, bool OUT_DOUBLE>
 __global__ void __launch_bounds__(kEnergyThreads)
@@ -1235,15 +1296,20 @@ k_rows_inv(const float2* __restrict__ Y, int64_t y_fstride, int ncv, int wm1,
     b.r1 = 0x7fffffff;
     b.f2 = INFINITY;
     // The frame's energies Sa (exact) straight into the combine; the sweep's
-    // scratch takes the transform buffer's place.
-    auto emit = [&](int s, int t, u64 sa) {
+    // scratch takes the transform buffer's place. The template's Sb and
+    // 1/Area of a row's shifts are loaded a row ahead.
+    auto fetch = [&](int s, int t) {
         const int k = (s + wm1) * W + (t + wm1);
-        const float fv = combine_f32(energy_pair(sa), Sb2[k], hbuf[k], ia32[k]);
+        return CombineOps{__ldg(Sb2 + k), __ldg(ia32 + k)};
+    };
+    auto emit = [&](int s, int t, u64 sa, const CombineOps& o) {
+        const int k = (s + wm1) * W + (t + wm1);
+        const float fv = combine_f32(energy_pair(sa), o.sb, hbuf[k], o.ia);
         if (cost) cost[f * WW + k] = f32_to_f64(fv);
         best_push(b, fv, (abs(s) + abs(t)) * WW + k);
     };
-    energy_sweep_any(rowE + f * mc, colE + f * nc, tot[f], corners + f * 4 * (size_t)wm1 * wm1, mc, nc, wm1, ism_raw,
-                     emit);
+    energy_sweep_any_f(rowE + f * mc, colE + f * nc, tot[f], corners + f * 4 * (size_t)wm1 * wm1, mc, nc, wm1,
+                       ism_raw, emit, fetch);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         Best o2;
