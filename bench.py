@@ -181,10 +181,10 @@ def kernel_work(info, wl, frames):
 # launches), scaled to a launch by its frame count; other workloads and
 # forms report no traffic.
 TRAFFIC_WORKLOAD = ("std512", "fft_fp32")
-TRAFFIC_PER_FRAME = {"k_frame_rows": (270.701568e6 + 127.209728e6) / 512,
-                     "k_cols": (152.453376e6 + 19.932928e6) / 512,
-                     "k_rows_inv": (45.940480e6 + 0.003584e6) / 512,
-                     "k_jitter": (261.737216e6 + 4.383744e6) / 512}
+TRAFFIC_PER_FRAME = {"k_frame_rows": (270.745600e6 + 126.752256e6) / 512,
+                     "k_cols": (152.447488e6 + 20.004864e6) / 512,
+                     "k_rows_inv": (45.940224e6 + 0.0e6) / 512,
+                     "k_jitter": (261.718528e6 + 3.864832e6) / 512}
 
 
 # The bound of each kernel in the method's roofline (the frame pass and the
