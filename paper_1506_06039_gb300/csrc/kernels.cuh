@@ -1414,26 +1414,6 @@ struct JitBand {
     uint32_t cvalid;       // bit c: raw chunk c (columns c0 + 8c .. + 7) inside the frame
 };
 
-// Frame row ar into slot x (zeros where outside the frame).
-template <int O>
-__device__ __forceinline__ void jit_fetch(const JitBand& B, int ar, JitSlot<O>& x) {
-#pragma unroll
-    for (int k = 0; k < (O == 3 ? 9 : 8); ++k) x.raw[k] = 0u;
-    if (ar < 0 || ar >= B.m) return;  // the same for the whole warp
-    const uint16_t* row = B.a + (int64_t)ar * B.n;
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-        if ((B.cvalid >> c) & 1u) {
-            const uint4 q = __ldg(reinterpret_cast<const uint4*>(row + B.c0 + 8 * c));
-            x.raw[4 * c] = q.x;
-            x.raw[4 * c + 1] = q.y;
-            x.raw[4 * c + 2] = q.z;
-            x.raw[4 * c + 3] = q.w;
-        }
-    if (O == 3)
-        if ((B.cvalid >> 2) & 1u) x.raw[(O == 3) ? 8 : 0] = __ldg(reinterpret_cast<const uint32_t*>(row + B.c0 + 16));
-}
-
 template <int O>
 __device__ __forceinline__ void jit_unpack(JitSlot<O>& x) {
 #pragma unroll
@@ -1492,6 +1472,9 @@ __device__ __forceinline__ uint4 jit_tmpl_row(const JitBand& B, int i) {
 // when it is taken.
 constexpr int kJitRing = 3;
 constexpr size_t kJitRingBytes = (size_t)kJitRing * 4 * kJitterThreads * 16;
+// After the ring, one 16-byte cell per thread: the energies of its band's
+// first two frame rows (taken when they arrive, added at the band's end).
+constexpr size_t kJitSmemBytes = kJitRingBytes + (size_t)kJitterThreads * 16;
 
 // The next row to copy: its frame row ar, the addresses of its first raw
 // chunk (columns c0 .. c0 + 7 of row ar; read only where inside the frame)
@@ -1673,6 +1656,14 @@ __device__ __forceinline__ void jit_band(const JitBand& B, uint4* ring, uint32_t
     cp_wait<kJitRing - 1>();
     jit_take<O, 1>(ring, (unsigned)(first + 1) < (unsigned)B.m, S[1], nullptr);
     jit_issue<O, 1>(B, ring, true, cur);
+    {
+        // Frame rows first and first + 1 are not shared by all three u: their
+        // energies wait in the thread's cell until the band's end.
+        Acc2 e0 = {0u, 0u}, e1 = {0u, 0u};
+        row_energy(S[0], e0);
+        row_energy(S[1], e1);
+        ring[kJitRing * 4 * kJitterThreads] = make_uint4(e0.lo, e0.hi, e1.lo, e1.hi);
+    }
     for (int i = B.i_b;;) {
         jit_step<TABLE, O, 0>(B, i, ring, cur, S, C, M, QB, cm);
         if (++i >= B.i_e) break;
@@ -1695,20 +1686,11 @@ __device__ __forceinline__ void jit_band(const JitBand& B, uint4* ring, uint32_t
         case 1: jit_last_rows<O, 1, 2>(S, first, L, X); break;
         default: jit_last_rows<O, 2, 0>(S, first, L, X); break;
     }
-    // The first two are loaded again (row first + 1 is row first + L when L = 1).
-    jit_fetch(B, first, S[0]);
-    if (L >= 2) jit_fetch(B, first + 1, S[1]);
-    jit_unpack(S[0]);
+    // The first two, from the cell (row first + 1 is row first + L when L = 1).
     {
-        Acc2 e = {0u, 0u};
-        row_energy(S[0], e);
-        jit_add_row(first, first, L, e, X);
-    }
-    if (L >= 2) {
-        jit_unpack(S[1]);
-        Acc2 e = {0u, 0u};
-        row_energy(S[1], e);
-        jit_add_row(first + 1, first, L, e, X);
+        const uint4 q = ring[kJitRing * 4 * kJitterThreads];
+        jit_add_row(first, first, L, Acc2{q.x, q.y}, X);
+        if (L >= 2) jit_add_row(first + 1, first, L, Acc2{q.z, q.w}, X);
     }
     if (TABLE) return;
     // In-loop sum b^2: template rows whose partner row is valid for some but
@@ -1902,7 +1884,7 @@ __device__ __forceinline__ void jitter_item(const JitParams& P, int64_t f, int i
 template <bool TABLE>
 __global__ void __launch_bounds__(kJitterThreads, TABLE ? 3 : 1) k_jitter(JitParams P) {
     extern __shared__ __align__(16) unsigned char jit_smem[];
-    uint4* ring = reinterpret_cast<uint4*>(jit_smem) + threadIdx.x;  // kJitRingBytes
+    uint4* ring = reinterpret_cast<uint4*>(jit_smem) + threadIdx.x;  // kJitSmemBytes
     const int item = blockIdx.x * (kJitterThreads / 32) + (threadIdx.x >> 5);
     if (item >= P.witems) return;  // the whole warp
     jitter_item<TABLE>(P, blockIdx.y, item, ring);
@@ -1926,7 +1908,7 @@ static_assert(sizeof(JitBatch) <= 4096, "kernel parameters of k_jitter_multi");
 
 static __global__ void __launch_bounds__(kJitterThreads, 3) k_jitter_multi(const __grid_constant__ JitBatch batch) {
     extern __shared__ __align__(16) unsigned char jit_smem[];
-    uint4* ring = reinterpret_cast<uint4*>(jit_smem) + threadIdx.x;  // kJitRingBytes
+    uint4* ring = reinterpret_cast<uint4*>(jit_smem) + threadIdx.x;  // kJitSmemBytes
     const long long i = (long long)blockIdx.x * (kJitterThreads / 32) + (threadIdx.x >> 5);
     if (i >= batch.item_base[batch.nseg]) return;  // the whole warp
     int k = 0;

@@ -126,10 +126,10 @@ cudaError_t launch_jitter(const uint16_t* frames, int64_t fstride, int64_t nimg,
     constexpr int wpc = kJitterThreads / 32;  // warps (items) per CTA
     dim3 grid((unsigned)((P.witems + wpc - 1) / wpc), (unsigned)nimg);
     const void* fn = bsq ? reinterpret_cast<const void*>(k_jitter<true>) : reinterpret_cast<const void*>(k_jitter<false>);
-    e = ensure_smem(fn, kJitRingBytes);
+    e = ensure_smem(fn, kJitSmemBytes);
     if (e != cudaSuccess) return e;
-    if (bsq) k_jitter<true><<<grid, kJitterThreads, kJitRingBytes, st>>>(P);
-    else k_jitter<false><<<grid, kJitterThreads, kJitRingBytes, st>>>(P);
+    if (bsq) k_jitter<true><<<grid, kJitterThreads, kJitSmemBytes, st>>>(P);
+    else k_jitter<false><<<grid, kJitterThreads, kJitSmemBytes, st>>>(P);
     return cudaGetLastError();
 }
 
@@ -175,10 +175,10 @@ cudaError_t launch_jitter_multi(const JitSegment* segs, int nseg, u64* acc, unsi
         if (items == 0) continue;
         cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(u64) * 9 * frames, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(ticket, 0, sizeof(unsigned int) * frames, st);
-        if (e == cudaSuccess) e = ensure_smem(reinterpret_cast<const void*>(k_jitter_multi), kJitRingBytes);
+        if (e == cudaSuccess) e = ensure_smem(reinterpret_cast<const void*>(k_jitter_multi), kJitSmemBytes);
         if (e != cudaSuccess) return e;
         constexpr int wpc = kJitterThreads / 32;  // warps (items) per CTA
-        k_jitter_multi<<<(unsigned)((items + wpc - 1) / wpc), kJitterThreads, kJitRingBytes, st>>>(batch);
+        k_jitter_multi<<<(unsigned)((items + wpc - 1) / wpc), kJitterThreads, kJitSmemBytes, st>>>(batch);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
