@@ -184,7 +184,7 @@ TRAFFIC_WORKLOAD = ("std512", "fft_fp32")
 TRAFFIC_PER_FRAME = {"k_frame_rows": (270.745600e6 + 126.752256e6) / 512,
                      "k_cols": (152.447488e6 + 20.004864e6) / 512,
                      "k_rows_inv": (45.940224e6 + 0.0e6) / 512,
-                     "k_jitter": (261.718528e6 + 3.864832e6) / 512}
+                     "k_jitter": (261.729792e6 + 3.866624e6) / 512}
 
 
 # The bound of each kernel in the method's roofline (the frame pass and the
