@@ -1753,6 +1753,28 @@ __device__ __forceinline__ u64 ld_relaxed_u64(const u64* p) {
     return v;
 }
 
+// The best of nine candidates held by lanes 0-8 of the warp (S / A with the
+// tie-break: smallest ratio, then |s| + |t|, then s, then t; exact 128-bit
+// cross products), taken in order by every lane from shuffles.
+__device__ __forceinline__ void choose_nine(u64 S, u64 A, int s, int t, u64& bS, u64& bA, int& bs, int& bt) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const u64 Sk = __shfl_sync(0xffffffffu, S, k), Ak = __shfl_sync(0xffffffffu, A, k);
+        const int sk = __shfl_sync(0xffffffffu, s, k), tk = __shfl_sync(0xffffffffu, t, k);
+        bool take = (k == 0);
+        if (!take) {
+            int eq;
+            const int lt = ratio_lt(Sk, Ak, bS, bA, &eq);
+            if (lt) take = true;
+            else if (eq) {
+                const int k1 = abs(sk) + abs(tk), k2 = abs(bs) + abs(bt);
+                take = (k1 < k2) || (k1 == k2 && (sk < bs || (sk == bs && tk < bt)));
+            }
+        }
+        if (take) { bS = Sk; bA = Ak; bs = sk; bt = tk; }
+    }
+}
+
 // Frame f's final shift from its nine complete sums (every item's additions
 // visible): lane k < 9 forms candidate (u, v) = (k / 3, k % 3), its S (the
 // table's b^2 added) and overlap A; every lane then takes the nine in order,
@@ -1772,22 +1794,7 @@ __device__ __forceinline__ void jitter_choose(const JitParams& P, int64_t f, int
     }
     u64 bS = 0, bA = 1;
     int bs = 0, bt = 0;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const u64 Sk = __shfl_sync(0xffffffffu, S, k), Ak = __shfl_sync(0xffffffffu, A, k);
-        const int sk = __shfl_sync(0xffffffffu, s, k), tk = __shfl_sync(0xffffffffu, t, k);
-        bool take = (k == 0);
-        if (!take) {
-            int eq;
-            const int lt = ratio_lt(Sk, Ak, bS, bA, &eq);
-            if (lt) take = true;
-            else if (eq) {
-                const int k1 = abs(sk) + abs(tk), k2 = abs(bs) + abs(bt);
-                take = (k1 < k2) || (k1 == k2 && (sk < bs || (sk == bs && tk < bt)));
-            }
-        }
-        if (take) { bS = Sk; bA = Ak; bs = sk; bt = tk; }
-    }
+    choose_nine(S, A, s, t, bS, bA, bs, bt);
     if (lane != 0) return;
     P.shifts[2 * f] = valid ? bs : INT32_MIN;
     P.shifts[2 * f + 1] = valid ? bt : INT32_MIN;

@@ -24,24 +24,56 @@ static __global__ void k_box_level(const uint16_t* __restrict__ img, int m, int 
     out[p] = (int32_t)box_sum_l(img, n, i, j, l);
 }
 
-// The nine candidates (2 sc + u - 1, 2 tc + v - 1) of level l: exact int64
-// S = sum over D of (a_l[i+s][j+t] - b_l[i][j])^2 on level l's (ml x nl)
+// Level-LV pixel (r, c) of a uint16 image: the sum of its 2^LV x 2^LV
+// full-resolution pixels, each of their rows read by one aligned 4-, 8- or
+// 16-byte load (two at LV = 4; n % 8 == 0, the image 16-byte aligned).
+template <int LV>
+__device__ __forceinline__ uint32_t box_sum_vec(const uint16_t* __restrict__ img, int n, int r, int c) {
+    constexpr int B = 1 << LV;
+    const uint16_t* p0 = img + ((int64_t)r << LV) * n + ((int64_t)c << LV);
+    uint32_t s = 0;
+#pragma unroll
+    for (int dr = 0; dr < B; ++dr) {
+        const uint16_t* p = p0 + (int64_t)dr * n;
+        if constexpr (B == 2) {
+            s = add_halves(__ldg(reinterpret_cast<const uint32_t*>(p)), s);
+        } else if constexpr (B == 4) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+            s = add_halves(q.x, add_halves(q.y, s));
+        } else {
+#pragma unroll
+            for (int h = 0; h < B / 8; ++h) {
+                const uint4 q = __ldg(reinterpret_cast<const uint4*>(p) + h);
+                s = add_halves(q.x, add_halves(q.y, add_halves(q.z, add_halves(q.w, s))));
+            }
+        }
+    }
+    return s;
+}
+
+// The nine candidates (2 sc + u - 1, 2 tc + v - 1) of level LV: exact int64
+// S = sum over D of (a_l[i+s][j+t] - b_l[i][j])^2 on level LV's (ml x nl)
 // images. Grid (bands of kLevelRows level rows, frames): a CTA forms the
 // frame's level rows its band needs (kLevelRows + 2) from the full-
-// resolution frame in shared memory, sums its band, and adds the nine sums to
-// the frame's accumulators; the frame's last CTA (ticket) takes the minimum
-// of S / Area with the tie-break, compared as exact rationals. acc and ticket
-// are zero on entry. b_l is the plan's level image.
+// resolution frame in shared memory, sums its band (a candidate whose frame
+// pixel lies outside the frame contributes zero, by a select), and adds the
+// nine sums to the frame's accumulators; on the frame's last CTA (ticket)
+// the lanes of one warp take the minimum of S / Area with the tie-break,
+// compared as exact rationals. acc and ticket are zero on entry. b_l is the
+// plan's level image.
+// Band height in level rows (taller bands, 64 rows at 512^2, were slower:
+// fewer CTAs per frame to hide the latency of the box sums' loads).
 constexpr int kLevelRows = 16;
 
+template <int LV>
 static __global__ void __launch_bounds__(kLevelThreads)
-k_jitter_level(const uint16_t* __restrict__ frames, int64_t fstride, int m, int n, int l,
+k_jitter_level(const uint16_t* __restrict__ frames, int64_t fstride, int m, int n,
                const int32_t* __restrict__ bl, const int32_t* __restrict__ cin, int32_t* __restrict__ cout,
                u64* __restrict__ acc_g, unsigned int* __restrict__ ticket) {
     extern __shared__ __align__(16) int32_t arows[];  // (kLevelRows + 2) x nl
-    __shared__ long long red[kLevelThreads / 32][9];
+    __shared__ u64 red[kLevelThreads / 32][9];
     __shared__ bool last;
-    const int ml = m >> l, nl = n >> l;
+    const int ml = m >> LV, nl = n >> LV;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t f = blockIdx.y;
     const uint16_t* a = frames + f * fstride;
@@ -51,69 +83,71 @@ k_jitter_level(const uint16_t* __restrict__ frames, int64_t fstride, int m, int 
     for (int rr = warp; rr < rows + 2; rr += kLevelThreads / 32) {
         const int ar = i0 + s0 - 1 + rr;
         const bool in = ar >= 0 && ar < ml;  // the same for the whole warp
-        for (int j = lane; j < nl; j += 32) arows[rr * nl + j] = in ? (int32_t)box_sum_l(a, n, ar, j, l) : 0;
+        for (int j = lane; j < nl; j += 32) arows[rr * nl + j] = in ? (int32_t)box_sum_vec<LV>(a, n, ar, j) : 0;
     }
     __syncthreads();
-    long long acc[9];
+    u64 acc[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = 0;
     for (int ri = warp; ri < rows; ri += kLevelThreads / 32) {
         const int i = i0 + ri;
         for (int j = lane; j < nl; j += 32) {
-            const int32_t b = bl[(int64_t)i * nl + j];
+            const int32_t b = __ldg(bl + (int64_t)i * nl + j);
+            int cj[3];
+            bool cin_v[3];
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                const int ac = j + t0 - 1 + v;
+                cin_v[v] = (unsigned)ac < (unsigned)nl;
+                cj[v] = min(max(ac, 0), nl - 1);
+            }
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
                 const int ar = i + s0 - 1 + u;
-                if (ar < 0 || ar >= ml) continue;
+                if (ar < 0 || ar >= ml) continue;  // the same for the whole warp
+                const int32_t* ap = arows + (ri + u) * nl;
 #pragma unroll
                 for (int v = 0; v < 3; ++v) {
-                    const int ac = j + t0 - 1 + v;
-                    if (ac < 0 || ac >= nl) continue;
-                    const long long d = (long long)(arows[(ri + u) * nl + ac] - b);
-                    acc[u * 3 + v] += d * d;
+                    const int32_t d = cin_v[v] ? ap[cj[v]] - b : 0;
+                    add_sq(acc[u * 3 + v], d);
                 }
             }
         }
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        long long v = acc[k];
+        u64 v = acc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red[warp][k] = v;
     }
     __syncthreads();
     if (tid < 9) {
-        long long sum = 0;
+        u64 sum = 0;
         for (int wi = 0; wi < kLevelThreads / 32; ++wi) sum += red[wi][tid];
-        atomicAdd(&acc_g[f * 9 + tid], (u64)sum);
+        atomicAdd(&acc_g[f * 9 + tid], sum);
     }
     __threadfence();
     __syncthreads();
     if (tid == 0) last = (atomicAdd(&ticket[f], 1u) == gridDim.x - 1);
     __syncthreads();
-    if (!last || tid != 0) return;
+    if (!last || warp != 0) return;
     __threadfence();
-    int bk = -1, bs = 0, bt = 0;
+    u64 S = 0, A = 1;
+    int s = 0, t = 0;
+    if (lane < 9) {
+        s = s0 + lane / 3 - 1;
+        t = t0 + lane % 3 - 1;
+        A = (u64)(ml - abs(s)) * (u64)(nl - abs(t));
+        S = ld_relaxed_u64(acc_g + f * 9 + lane);
+    }
     u64 bS = 0, bA = 1;
-    for (int u = 0; u < 3; ++u)
-        for (int v = 0; v < 3; ++v) {
-            const int s = s0 + u - 1, t = t0 + v - 1;
-            const u64 S = atomicAdd(&acc_g[f * 9 + u * 3 + v], 0ull);
-            const u64 A = (u64)(ml - abs(s)) * (u64)(nl - abs(t));
-            bool take = bk < 0;
-            if (!take) {
-                int eq;
-                if (ratio_lt(S, A, bS, bA, &eq)) take = true;
-                else if (eq) {
-                    const int k1 = abs(s) + abs(t), k2 = abs(bs) + abs(bt);
-                    take = (k1 < k2) || (k1 == k2 && (s < bs || (s == bs && t < bt)));
-                }
-            }
-            if (take) { bk = u * 3 + v; bS = S; bA = A; bs = s; bt = t; }
-        }
-    cout[2 * f] = bs;
-    cout[2 * f + 1] = bt;
+    int bs = 0, bt = 0;
+    choose_nine(S, A, s, t, bS, bA, bs, bt);
+    if (lane == 0) {
+        cout[2 * f] = bs;
+        cout[2 * f + 1] = bt;
+    }
 }
 
 size_t level_image_elems(int m, int n, int l) { return (size_t)(m >> l) * (size_t)(n >> l); }
@@ -134,10 +168,20 @@ cudaError_t launch_jitter_level(const uint16_t* frames, int64_t fstride, int64_t
     if (e != cudaSuccess) return e;
     const int ml = m >> l, nl = n >> l;
     const size_t smem = sizeof(int32_t) * (size_t)(kLevelRows + 2) * nl;  // <= 18 x 2048 x 4 bytes
-    e = ensure_smem(reinterpret_cast<const void*>(k_jitter_level), smem);
-    if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((ml + kLevelRows - 1) / kLevelRows), (unsigned)nimg);
-    k_jitter_level<<<grid, kLevelThreads, smem, st>>>(frames, fstride, m, n, l, bl, cin, cout, acc, ticket);
+    auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t r = ensure_smem(reinterpret_cast<const void*>(kern), smem);
+        if (r != cudaSuccess) return r;
+        kern<<<grid, kLevelThreads, smem, st>>>(frames, fstride, m, n, bl, cin, cout, acc, ticket);
+        return cudaSuccess;
+    };
+    switch (l) {  // refinement levels 1 .. 3 (at most four levels in all)
+        case 1: e = run(k_jitter_level<1>); break;
+        case 2: e = run(k_jitter_level<2>); break;
+        case 3: e = run(k_jitter_level<3>); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
