@@ -55,8 +55,9 @@ __device__ __forceinline__ uint32_t box_sum_vec(const uint16_t* __restrict__ img
 // S = sum over D of (a_l[i+s][j+t] - b_l[i][j])^2 on level LV's (ml x nl)
 // images. Grid (bands of kLevelRows level rows, frames): a CTA forms the
 // frame's level rows its band needs (kLevelRows + 2) from the full-
-// resolution frame in shared memory, sums its band (a candidate whose frame
-// pixel lies outside the frame contributes zero, by a select), and adds the
+// resolution frame in shared memory, sums its band (four neighbouring level
+// pixels per lane at a time; a candidate whose frame pixel lies outside the
+// frame contributes zero, by a select), and adds the
 // nine sums to the frame's accumulators; on the frame's last CTA (ticket)
 // the lanes of one warp take the minimum of S / Area with the tie-break,
 // compared as exact rationals. acc and ticket are zero on entry. b_l is the
@@ -89,28 +90,44 @@ k_jitter_level(const uint16_t* __restrict__ frames, int64_t fstride, int m, int 
     u64 acc[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) acc[k] = 0;
+    // Each lane takes four neighbouring level pixels of a row at a time: their
+    // windows span six frame columns per window row, loaded (and clamped and
+    // checked) once for all twelve of the row's candidates.
     for (int ri = warp; ri < rows; ri += kLevelThreads / 32) {
         const int i = i0 + ri;
-        for (int j = lane; j < nl; j += 32) {
-            const int32_t b = __ldg(bl + (int64_t)i * nl + j);
-            int cj[3];
-            bool cin_v[3];
+        const int32_t* brow = bl + (int64_t)i * nl;
+        for (int j0 = 4 * lane; j0 < nl; j0 += 128) {
+            int32_t b[4];
+            bool pv[4];
 #pragma unroll
-            for (int v = 0; v < 3; ++v) {
-                const int ac = j + t0 - 1 + v;
-                cin_v[v] = (unsigned)ac < (unsigned)nl;
-                cj[v] = min(max(ac, 0), nl - 1);
+            for (int p = 0; p < 4; ++p) {
+                pv[p] = j0 + p < nl;
+                b[p] = 0;
+                if (pv[p]) b[p] = __ldg(brow + j0 + p);
+            }
+            int cj[6];
+            bool cv[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const int ac = j0 + t0 - 1 + c;
+                cv[c] = (unsigned)ac < (unsigned)nl;
+                cj[c] = min(max(ac, 0), nl - 1);
             }
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
                 const int ar = i + s0 - 1 + u;
                 if (ar < 0 || ar >= ml) continue;  // the same for the whole warp
                 const int32_t* ap = arows + (ri + u) * nl;
+                int32_t av[6];
 #pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                    const int32_t d = cin_v[v] ? ap[cj[v]] - b : 0;
-                    add_sq(acc[u * 3 + v], d);
-                }
+                for (int c = 0; c < 6; ++c) av[c] = ap[cj[c]];
+#pragma unroll
+                for (int v = 0; v < 3; ++v)
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const int32_t d = (cv[p + v] && pv[p]) ? av[p + v] - b[p] : 0;
+                        add_sq(acc[u * 3 + v], d);
+                    }
             }
         }
     }
