@@ -59,15 +59,41 @@ __device__ __forceinline__ uint32_t add_halves(uint32_t w, uint32_t acc) {
     asm("dp2a.lo.u32.u32 %0, %1, %2, %0;" : "+r"(acc) : "r"(w), "r"(0x0101u));
     return acc;
 }
-// Sum of the 2^L x 2^L full-resolution pixels behind level-L pixel (r, c)
-// (L >= 1; below 2^32 for L <= 4).
-__device__ __forceinline__ uint32_t box_sum_l(const uint16_t* __restrict__ img, int n, int r, int c, int L) {
-    const int B = 1 << L;
-    const uint32_t* p = reinterpret_cast<const uint32_t*>(img + ((int64_t)r << L) * n + ((int64_t)c << L));
+// Sum of the 2^LV x 2^LV full-resolution pixels behind level-LV pixel (r, c)
+// (LV >= 1; below 2^32 for LV <= 4): each of the block's 2^LV rows read by one
+// aligned 4-, 8- or 16-byte load (two at LV = 4; n % 8 == 0, the image
+// 16-byte aligned).
+template <int LV>
+__device__ __forceinline__ uint32_t box_sum_vec(const uint16_t* __restrict__ img, int n, int r, int c) {
+    constexpr int B = 1 << LV;
+    const uint16_t* p0 = img + ((int64_t)r << LV) * n + ((int64_t)c << LV);
     uint32_t s = 0;
-    for (int dr = 0; dr < B; ++dr)
-        for (int k = 0; k < B / 2; ++k) s = add_halves(__ldg(p + (int64_t)dr * (n / 2) + k), s);
+#pragma unroll
+    for (int dr = 0; dr < B; ++dr) {
+        const uint16_t* p = p0 + (int64_t)dr * n;
+        if constexpr (B == 2) {
+            s = add_halves(__ldg(reinterpret_cast<const uint32_t*>(p)), s);
+        } else if constexpr (B == 4) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+            s = add_halves(q.x, add_halves(q.y, s));
+        } else {
+#pragma unroll
+            for (int h = 0; h < B / 8; ++h) {
+                const uint4 q = __ldg(reinterpret_cast<const uint4*>(p) + h);
+                s = add_halves(q.x, add_halves(q.y, add_halves(q.z, add_halves(q.w, s))));
+            }
+        }
+    }
     return s;
+}
+// The same at a level known at run time (1 <= L <= 4).
+__device__ __forceinline__ uint32_t box_sum_l(const uint16_t* __restrict__ img, int n, int r, int c, int L) {
+    switch (L) {  // the same for every thread of a launch
+        case 1: return box_sum_vec<1>(img, n, r, c);
+        case 2: return box_sum_vec<2>(img, n, r, c);
+        case 3: return box_sum_vec<3>(img, n, r, c);
+        default: return box_sum_vec<4>(img, n, r, c);
+    }
 }
 // acc += d * d exactly (|d| < 2^31), one 32 x 32 -> 64-bit multiply-add.
 __device__ __forceinline__ void add_sq(u64& acc, int32_t d) {

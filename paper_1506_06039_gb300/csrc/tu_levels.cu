@@ -24,33 +24,6 @@ static __global__ void k_box_level(const uint16_t* __restrict__ img, int m, int 
     out[p] = (int32_t)box_sum_l(img, n, i, j, l);
 }
 
-// Level-LV pixel (r, c) of a uint16 image: the sum of its 2^LV x 2^LV
-// full-resolution pixels, each of their rows read by one aligned 4-, 8- or
-// 16-byte load (two at LV = 4; n % 8 == 0, the image 16-byte aligned).
-template <int LV>
-__device__ __forceinline__ uint32_t box_sum_vec(const uint16_t* __restrict__ img, int n, int r, int c) {
-    constexpr int B = 1 << LV;
-    const uint16_t* p0 = img + ((int64_t)r << LV) * n + ((int64_t)c << LV);
-    uint32_t s = 0;
-#pragma unroll
-    for (int dr = 0; dr < B; ++dr) {
-        const uint16_t* p = p0 + (int64_t)dr * n;
-        if constexpr (B == 2) {
-            s = add_halves(__ldg(reinterpret_cast<const uint32_t*>(p)), s);
-        } else if constexpr (B == 4) {
-            const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
-            s = add_halves(q.x, add_halves(q.y, s));
-        } else {
-#pragma unroll
-            for (int h = 0; h < B / 8; ++h) {
-                const uint4 q = __ldg(reinterpret_cast<const uint4*>(p) + h);
-                s = add_halves(q.x, add_halves(q.y, add_halves(q.z, add_halves(q.w, s))));
-            }
-        }
-    }
-    return s;
-}
-
 // The nine candidates (2 sc + u - 1, 2 tc + v - 1) of level LV: exact int64
 // S = sum over D of (a_l[i+s][j+t] - b_l[i][j])^2 on level LV's (ml x nl)
 // images. Grid (bands of kLevelRows level rows, frames): a CTA forms the
