@@ -57,7 +57,12 @@ k_jitter_level(const uint16_t* __restrict__ frames, int64_t fstride, int m, int 
     for (int rr = warp; rr < rows + 2; rr += kLevelThreads / 32) {
         const int ar = i0 + s0 - 1 + rr;
         const bool in = ar >= 0 && ar < ml;  // the same for the whole warp
-        for (int j = lane; j < nl; j += 32) arows[rr * nl + j] = in ? (int32_t)box_sum_vec<LV>(a, n, ar, j) : 0;
+        if (!in) {
+            for (int j = lane; j < nl; j += 32) arows[rr * nl + j] = 0;
+            continue;
+        }
+#pragma unroll 4
+        for (int j = lane; j < nl; j += 32) arows[rr * nl + j] = (int32_t)box_sum_vec<LV>(a, n, ar, j);  // loads of four in flight
     }
     __syncthreads();
     u64 acc[9];
